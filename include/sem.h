@@ -1,0 +1,212 @@
+/*
+ * sem.h -- C ABI of the GB300 spectral-element hot path.
+ *
+ * The paper (Sec. 2.2, "NekRS") discretises each scalar field on N_e
+ * hexahedral elements of order p = N with a tensor-product nodal basis on
+ * Gauss-Lobatto-Legendre (GLL) points; operators are applied matrix-free as
+ * dense (N+1)x(N+1) tensor contractions, carried to deformed elements by the
+ * chain rule, and the stiffest substep -- the pressure Poisson solve -- is a
+ * preconditioned Krylov solve. This library implements that path on one GPU:
+ * mesh and GLL set-up, the local operator Ax, direct-stiffness summation
+ * (gather-scatter, Q Q^T), the Jacobi preconditioner and the preconditioned
+ * conjugate-gradient (PCG) solve.
+ *
+ * Conventions shared by every entry point
+ *  - All functions return an int status: SEM_OK (0) or a negative SEM_ERR_*.
+ *    sem_last_error() returns a description of the last failure on the
+ *    calling thread. No C++ exception crosses this boundary.
+ *  - "device" pointers are CUDA device (or managed) memory owned by the
+ *    caller; "host" pointers are ordinary host memory owned by the caller.
+ *    The library owns only what a handle owns (a mesh's geometry and maps)
+ *    and frees it in the matching destroy call.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream. Work is enqueued on it; functions that report results
+ *    to the host (sem_pcg_solve statistics, set-up) synchronise it.
+ *  - Layouts. An E-vector holds one value per local node, element-major:
+ *    index l = e (N+1)^3 + i + (N+1) j + (N+1)^2 k for node (i,j,k) of element
+ *    e, elements numbered e = ex + nelx (ey + nely ez). A U-vector holds one
+ *    value per unique (global) node g, numbered lexicographically in the
+ *    lattice indices (I,J,K) = (ex N + i, ey N + j, ez N + k):
+ *    g = I + nx (J + ny K), nx = nelx N + 1 (nelx N if x is periodic, with I
+ *    taken mod nelx N), likewise ny.
+ *  - Floating-point values are IEEE binary64 unless stated otherwise.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SEM_OK = 0,
+  SEM_ERR_INVALID_ARG = -1,   /* bad pointer, size or option; nothing was done */
+  SEM_ERR_CUDA = -2,          /* a CUDA runtime call failed (message has the CUDA error) */
+  SEM_ERR_NOT_CONVERGED = -3, /* PCG hit maxit; x holds the last iterate */
+  SEM_ERR_BREAKDOWN = -4,     /* PCG met p.Ap <= 0 or a non-finite scalar */
+  SEM_ERR_TIMEOUT = -5,       /* PCG exceeded opts.timeout_s; x holds the last iterate */
+  SEM_ERR_IO = -6,
+  SEM_ERR_NOMEM = -7          /* device allocation failed */
+};
+
+/* Arithmetic used by the operator and solver kernels. */
+enum {
+  SEM_PREC_FP64 = 0, /* native binary64 FMA */
+  SEM_PREC_DF64 = 1  /* binary64-accurate double-float: each value carried as an
+                        unevaluated sum of two binary32 (hi + lo) and combined
+                        with error-free transformations (Dekker 1971; Knuth's
+                        TwoSum; Joldes, Muller & Popescu 2017). About 2^-44
+                        relative accuracy per operator application; values
+                        must stay within |x| in [2^-100, 2^100]. */
+};
+
+typedef struct sem_mesh sem_mesh; /* opaque */
+
+/* A structured box of nelx x nely x nelz hexahedra of order N (1 <= N <= 10,
+ * the range of polynomial orders NekRS supports, Sec. 4.1).
+ * Element interfaces are uniform along x and y; along z they are uniform when
+ * z_stretch == 0, else follow the tanh map
+ *   z_k = Lz/2 [1 + tanh(s (2k/nelz - 1)) / tanh(s)],  s = z_stretch,
+ * (the paper's tangent-hyperbolic vertical stretching, Sec. 4.2). Every GLL
+ * node is then displaced (deform_amp != 0) by
+ *   d_c = deform_amp h_c sin(pi xh) sin(pi yh) sin(pi zh) cos(2 pi kappa_c.xh + phi_c),
+ * xh = (x/Lx, y/Ly, z/Lz), h_c = L_c / nel_c, kappa_c = kappa[3c..3c+2].
+ * dirichlet[] flags the faces x=0, x=Lx, y=0, y=Ly, z=0, z=Lz that carry
+ * homogeneous Dirichlet conditions (ignored in periodic directions). */
+typedef struct {
+  int nelx, nely, nelz;
+  int N;
+  double Lx, Ly, Lz;
+  int periodic[3];
+  int dirichlet[6];
+  double z_stretch;
+  double deform_amp;
+  double kappa[9];
+  double phi[3];
+} sem_box_desc;
+
+/* Read-only views into a mesh. Device pointers stay valid until
+ * sem_mesh_destroy. G is stored element-major and factor-major within an
+ * element: factor f (0..5 = rr, rs, rt, ss, st, tt) of local node p of element
+ * e is G[(6 e + f) (N+1)^3 + p]. */
+typedef struct {
+  int64_t E, n_local, n_unique;
+  int N;
+  double detJ_min;
+  const double *X, *Y, *Z; /* device E-vectors: node coordinates */
+  const double *G;         /* device: geometric factors (6 per local node)     */
+  const double *B;         /* device E-vector: rho_i rho_j rho_k |J|            */
+  const int32_t *l2g;      /* device E-vector: unique id of each local node     */
+  const uint8_t *mask;     /* device U-vector: 1 free, 0 Dirichlet              */
+  const double *mult;      /* device U-vector: number of local copies (Q^T 1)  */
+} sem_mesh_info;
+
+typedef struct {
+  double tol;      /* stop at the first iteration k with ||r_k||_2 <= tol ||b||_2 */
+  int maxit;       /* > 0 */
+  int precision;   /* SEM_PREC_* */
+  double timeout_s;/* <= 0: no limit */
+} sem_solver_opts;
+
+typedef struct {
+  int iterations;       /* operator applications performed */
+  double rel_residual;  /* ||r||_2 / ||b||_2 at exit (Euclidean, unique nodes) */
+  double solve_ms;      /* wall time of the solve on the host clock */
+  int status;           /* same as the return value */
+} sem_solve_stats;
+
+/* Last error text of the calling thread ("" if none). Never NULL. */
+const char *sem_last_error(void);
+
+/* Library version string. */
+const char *sem_version(void);
+
+/* GLL nodes xi[N+1] (ascending, xi_0 = -1, xi_N = 1), weights
+ * rho_i = 2 / (N (N+1) P_N(xi_i)^2) and derivative matrix D[(N+1)^2],
+ * row-major, D[i (N+1) + j] = l_j'(xi_i), the (p+1)x(p+1) operator matrix of
+ * Sec. 2.2. Host arrays, caller-owned. SEM_ERR_INVALID_ARG for N outside
+ * [1, 10] or NULL pointers. */
+int sem_gll(int N, double *xi, double *rho, double *D);
+
+/* Build a box mesh on the current CUDA device: node coordinates, geometric
+ * factors G (chain rule, Sec. 2.2), mass B, the local-to-unique map l2g
+ * (lattice formula in the header comment), the Dirichlet mask, the
+ * gather-scatter tables and multiplicities. All set-up runs in kernels on
+ * `stream`; the call synchronises it. SEM_ERR_INVALID_ARG if a size is out of
+ * range, the local node count exceeds 2^31 - 1, or det J <= 0 anywhere;
+ * SEM_ERR_NOMEM if device memory runs out. On success *out owns all of it. */
+int sem_mesh_create_box(const sem_box_desc *desc, void *stream, sem_mesh **out);
+
+/* Free a mesh and everything it owns (NULL is accepted). */
+int sem_mesh_destroy(sem_mesh *m);
+
+/* Fill *info with sizes and device views. */
+int sem_mesh_info_get(const sem_mesh *m, sem_mesh_info *info);
+
+/* Copy l2g (n_local int32) and mask (n_unique uint8) to host arrays; either
+ * may be NULL. Synchronous. */
+int sem_mesh_copy_maps(const sem_mesh *m, int32_t *l2g_host, uint8_t *mask_host);
+
+/* Copy the gather-scatter tables to host arrays: offsets (n_unique + 1 int32)
+ * and perm (n_local int32); local nodes of unique node g are
+ * perm[offsets[g] .. offsets[g+1]-1], in ascending order. Synchronous. */
+int sem_mesh_copy_gs_tables(const sem_mesh *m, int32_t *offsets_host, int32_t *perm_host);
+
+/* Local Helmholtz operator on E-vectors (no summation, no mask):
+ *   w_L = h1 * sum_ab D_a^T G_ab D_b u_L + h2 * B u_L
+ * (Sec. 2.2 tensor-contraction form). u_L and w_L are device E-vectors of
+ * n_local values and must not overlap. precision = SEM_PREC_*. */
+int sem_ax_apply(const sem_mesh *m, double h1, double h2, const double *u_L, double *w_L,
+                 int precision, void *stream);
+
+/* In-place direct stiffness summation on a device E-vector:
+ * v_L <- Q Q^T v_L, i.e. every local copy of a unique node receives the sum
+ * of all its copies; with apply_mask != 0 Dirichlet nodes then become 0.
+ * Deterministic: copies are summed in ascending local index. */
+int sem_gs_op(const sem_mesh *m, double *v_L, int apply_mask, void *stream);
+
+/* Q^T: v_g[g] = sum of the copies of g (device E-vector -> device U-vector). */
+int sem_gather(const sem_mesh *m, const double *v_L, double *v_g, void *stream);
+
+/* Q: v_L[l] = v_g[l2g[l]] (device U-vector -> device E-vector). */
+int sem_scatter(const sem_mesh *m, const double *v_g, double *v_L, void *stream);
+
+/* Assembled operator on U-vectors in one fused pass:
+ *   w_g = M Q^T (h1 A_L + h2 B) Q M u_g,  M = Dirichlet mask,
+ * gathering u through l2g and summing element contributions into w_g (the
+ * order of the summation is not fixed, so results may differ between calls
+ * in the last bits). u_g and w_g must not overlap. */
+int sem_ax_assembled(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
+                     int precision, void *stream);
+
+/* Weak-form load vector b_g = M Q^T (B f_L): the mass-weighted, summed and
+ * masked right-hand side of -lap u = f (or of a Helmholtz problem) for a
+ * forcing f given at the local nodes (device E-vector in, U-vector out). */
+int sem_weak_rhs(const sem_mesh *m, const double *f_L, double *b_g, void *stream);
+
+/* Masked inverse of the assembled diagonal of h1 A + h2 B (the Jacobi
+ * preconditioner, including the D_ii D_jj G_rs cross terms at element
+ * boundaries): dinv_g[g] = mask[g] / (Q^T diag_L)[g]. Device U-vector out. */
+int sem_jacobi_inv(const sem_mesh *m, double h1, double h2, double *dinv_g, void *stream);
+
+/* Number of bytes of device workspace sem_pcg_solve needs for this mesh. */
+int sem_pcg_workspace_bytes(const sem_mesh *m, size_t *bytes);
+
+/* Jacobi-preconditioned CG for (h1 A + h2 B) x = b on the free unique nodes,
+ * x0 = 0, textbook Hestenes-Stiefel recurrences; stops after the first
+ * iteration k with ||r_k||_2 <= tol ||b||_2. b_g, x_g: device U-vectors
+ * (b must vanish on Dirichlet nodes; x is 0 there on exit). workspace: device
+ * memory of sem_pcg_workspace_bytes() bytes, 256-byte aligned, caller-owned.
+ * Returns SEM_OK, SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN or SEM_ERR_TIMEOUT
+ * (stats filled in every case) or an argument/CUDA error. */
+int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
+                  const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats,
+                  void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEM_H */

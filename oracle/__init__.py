@@ -64,6 +64,9 @@ def lib():
         L.or_box_coords.argtypes = [ctypes.c_int] * 4 + [_dp, ctypes.c_double, ctypes.c_double,
                                                          _dp, _dp, _dp, _dp, _dp, _dp]
         L.or_box_coords.restype = None
+        L.or_box_coords_subset.argtypes = [ctypes.c_int] * 4 + [_dp, ctypes.c_double, ctypes.c_double,
+                                                                _dp, _dp, _dp, _i64p, ctypes.c_int64, _dp, _dp, _dp]
+        L.or_box_coords_subset.restype = None
         L.or_geom.argtypes = [ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
         L.or_geom.restype = ctypes.c_double
         L.or_ax_local.argtypes = [ctypes.c_int64, ctypes.c_int, _dp, ctypes.c_void_p, ctypes.c_void_p,
@@ -180,6 +183,39 @@ def box_mesh(nel, N=7, L=(1.0, 1.0, 1.0), periodic=(0, 0, 0), dirichlet=(1, 1, 1
         G = G.reshape(6, nL)
     return Mesh(nel, N, tuple(periodic), tuple(dirichlet), xi, rho, D, X, Y, Z, G, B, l2g, mask, nU,
                 detmin, tuple(L))
+
+
+def element_subset(w, elems):
+    """Coordinates, geometric factors and mass of selected elements of a
+    workload's mesh (element-local quantities only), for spot checks of meshes
+    too large to build whole: returns (X, Y, Z, G[6, ne*n3], B, D) packed in
+    the order of ``elems``."""
+    from workloads import deformation_params
+    kappa, phi = deformation_params(w.deform_seed)
+    xi, rho, D = gll(w.N)
+    elems = np.ascontiguousarray(elems, dtype=np.int64)
+    n3 = (w.N + 1) ** 3
+    nL = len(elems) * n3
+    X, Y, Z = np.zeros(nL), np.zeros(nL), np.zeros(nL)
+    lib().or_box_coords_subset(w.nel[0], w.nel[1], w.nel[2], w.N, np.asarray(w.L, dtype=np.float64),
+                               float(w.z_stretch), float(w.deform_amp), np.ascontiguousarray(kappa.ravel()),
+                               np.ascontiguousarray(phi), xi, elems, len(elems), X, Y, Z)
+    G = np.zeros(6 * nL)
+    B = np.zeros(nL)
+    lib().or_geom(len(elems), w.N, np.ascontiguousarray(D.ravel()), rho, X, Y, Z, G, B)
+    return X, Y, Z, G.reshape(6, nL), B, D
+
+
+def ax_local_raw(N, D, G, B, u, h1=1.0, h2=0.0):
+    """Local operator on packed element data (G shaped [6, nL])."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    w = np.zeros_like(u)
+    n3 = (N + 1) ** 3
+    Gc = np.ascontiguousarray(G.ravel())
+    Bc = np.ascontiguousarray(B)
+    lib().or_ax_local(len(u) // n3, N, np.ascontiguousarray(D.ravel()), Gc.ctypes.data if h1 != 0.0 else None,
+                      Bc.ctypes.data if h2 != 0.0 else None, float(h1), float(h2), u, w)
+    return w
 
 
 def mesh_from_workload(w, geometry=True) -> Mesh:

@@ -143,42 +143,62 @@ static double interface_coord(int k, int nel, double L, double s) {
  * x = x_e (1 - xi)/2 + x_{e+1} (1 + xi)/2, then every node is displaced by
  *   d_c = amp h_c sin(pi xh) sin(pi yh) sin(pi zh) cos(2 pi kappa_c . xh + phi_c),
  * xh = x / L (normalised position), h_c = L_c / nel_c. */
-void or_box_coords(int nelx, int nely, int nelz, int N, const double *L, double z_stretch, double amp,
-                   const double *kappa, const double *phi, const double *xi, double *X, double *Y,
-                   double *Z) {
+static void box_coords_element(int nelx, int nely, int nelz, int N, const double *L, double z_stretch, double amp,
+                               const double *kappa, const double *phi, const double *xi, int64_t e, double *X,
+                               double *Y, double *Z) {
   const int n = N + 1;
   const int nel[3] = {nelx, nely, nelz};
   const double pi = 3.14159265358979323846;
-  for (int ez = 0; ez < nelz; ++ez)
-    for (int ey = 0; ey < nely; ++ey)
-      for (int ex = 0; ex < nelx; ++ex) {
-        int64_t e = ex + (int64_t)nelx * (ey + (int64_t)nely * ez);
-        int eidx[3] = {ex, ey, ez};
-        for (int k = 0; k < n; ++k)
-          for (int j = 0; j < n; ++j)
-            for (int i = 0; i < n; ++i) {
-              int node[3] = {i, j, k};
-              double x[3];
-              for (int d = 0; d < 3; ++d) {
-                double s = (d == 2) ? z_stretch : 0.0;
-                double a = interface_coord(eidx[d], nel[d], L[d], s);
-                double b = interface_coord(eidx[d] + 1, nel[d], L[d], s);
-                double t = xi[node[d]];
-                x[d] = a * (0.5 * (1.0 - t)) + b * (0.5 * (1.0 + t));
-              }
-              double xo[3] = {x[0], x[1], x[2]};
-              if (amp != 0.0) {
-                double xh[3] = {x[0] / L[0], x[1] / L[1], x[2] / L[2]};
-                double bump = sin(pi * xh[0]) * sin(pi * xh[1]) * sin(pi * xh[2]);
-                for (int c = 0; c < 3; ++c) {
-                  double arg = 2.0 * pi * (kappa[3 * c] * xh[0] + kappa[3 * c + 1] * xh[1] + kappa[3 * c + 2] * xh[2]) + phi[c];
-                  xo[c] = x[c] + amp * (L[c] / nel[c]) * bump * cos(arg);
-                }
-              }
-              int64_t l = e * n * n * n + i + n * j + n * n * k;
-              X[l] = xo[0]; Y[l] = xo[1]; Z[l] = xo[2];
-            }
+  int eidx[3] = {(int)(e % nelx), (int)((e / nelx) % nely), (int)(e / ((int64_t)nelx * nely))};
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        int node[3] = {i, j, k};
+        double x[3];
+        for (int d = 0; d < 3; ++d) {
+          double s = (d == 2) ? z_stretch : 0.0;
+          double a = interface_coord(eidx[d], nel[d], L[d], s);
+          double b = interface_coord(eidx[d] + 1, nel[d], L[d], s);
+          double t = xi[node[d]];
+          x[d] = a * (0.5 * (1.0 - t)) + b * (0.5 * (1.0 + t));
+        }
+        double xo[3] = {x[0], x[1], x[2]};
+        if (amp != 0.0) {
+          double xh[3] = {x[0] / L[0], x[1] / L[1], x[2] / L[2]};
+          double bump = sin(pi * xh[0]) * sin(pi * xh[1]) * sin(pi * xh[2]);
+          for (int c = 0; c < 3; ++c) {
+            double arg = 2.0 * pi * (kappa[3 * c] * xh[0] + kappa[3 * c + 1] * xh[1] + kappa[3 * c + 2] * xh[2]) + phi[c];
+            xo[c] = x[c] + amp * (L[c] / nel[c]) * bump * cos(arg);
+          }
+        }
+        int p = i + n * j + n * n * k;
+        X[p] = xo[0]; Y[p] = xo[1]; Z[p] = xo[2];
       }
+}
+
+/* GLL node coordinates of a box mesh, E-vector order. The reference
+ * coordinate xi maps linearly into each element,
+ * x = x_e (1 - xi)/2 + x_{e+1} (1 + xi)/2, then every node is displaced by
+ *   d_c = amp h_c sin(pi xh) sin(pi yh) sin(pi zh) cos(2 pi kappa_c . xh + phi_c),
+ * xh = x / L (normalised position), h_c = L_c / nel_c. */
+void or_box_coords(int nelx, int nely, int nelz, int N, const double *L, double z_stretch, double amp,
+                   const double *kappa, const double *phi, const double *xi, double *X, double *Y,
+                   double *Z) {
+  const int64_t n3 = (int64_t)(N + 1) * (N + 1) * (N + 1);
+  const int64_t E = (int64_t)nelx * nely * nelz;
+  for (int64_t e = 0; e < E; ++e)
+    box_coords_element(nelx, nely, nelz, N, L, z_stretch, amp, kappa, phi, xi, e, X + e * n3, Y + e * n3, Z + e * n3);
+}
+
+/* The same coordinates for a list of elements only (ne elements, output
+ * packed element after element), for spot checks of very large meshes. */
+void or_box_coords_subset(int nelx, int nely, int nelz, int N, const double *L, double z_stretch, double amp,
+                          const double *kappa, const double *phi, const double *xi, const int64_t *elems,
+                          int64_t ne, double *X, double *Y, double *Z) {
+  const int64_t n3 = (int64_t)(N + 1) * (N + 1) * (N + 1);
+  for (int64_t t = 0; t < ne; ++t)
+    box_coords_element(nelx, nely, nelz, N, L, z_stretch, amp, kappa, phi, xi, elems[t], X + t * n3, Y + t * n3,
+                       Z + t * n3);
 }
 
 /* Geometric factors. G is stored factor-major: G[a*nL + l], a = 0..5 for

@@ -1,0 +1,329 @@
+"""Thin ctypes binding of libsemgb.so (include/sem.h): the GB300 spectral-element
+hot path -- GLL set-up, box meshes, the matrix-free Helmholtz operator Ax,
+gather-scatter and the Jacobi-preconditioned CG solve (the paper's Sec. 2.2).
+
+Every function here only marshals arguments: torch tensors become device
+pointers, the current torch stream becomes the stream argument, and a
+non-zero status becomes a ``SemError``. All computation runs in the library's
+CUDA kernels. There is no CPU fallback: if libsemgb.so is missing the first
+call raises ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsemgb.so")
+
+SEM_OK = 0
+SEM_ERR_INVALID_ARG = -1
+SEM_ERR_CUDA = -2
+SEM_ERR_NOT_CONVERGED = -3
+SEM_ERR_BREAKDOWN = -4
+SEM_ERR_TIMEOUT = -5
+SEM_ERR_IO = -6
+SEM_ERR_NOMEM = -7
+SEM_PREC_FP64 = 0
+SEM_PREC_DF64 = 1
+
+# every symbol include/sem.h declares
+EXPORTS = (
+    "sem_last_error", "sem_version", "sem_gll", "sem_mesh_create_box", "sem_mesh_destroy",
+    "sem_mesh_info_get", "sem_mesh_copy_maps", "sem_mesh_copy_gs_tables", "sem_ax_apply", "sem_gs_op",
+    "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
+    "sem_pcg_solve",
+)
+
+
+class SemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class sem_box_desc(ctypes.Structure):
+    _fields_ = [("nelx", ctypes.c_int), ("nely", ctypes.c_int), ("nelz", ctypes.c_int), ("N", ctypes.c_int),
+                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+                ("periodic", ctypes.c_int * 3), ("dirichlet", ctypes.c_int * 6), ("z_stretch", ctypes.c_double),
+                ("deform_amp", ctypes.c_double), ("kappa", ctypes.c_double * 9), ("phi", ctypes.c_double * 3)]
+
+
+class sem_mesh_info(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_int64), ("n_local", ctypes.c_int64), ("n_unique", ctypes.c_int64),
+                ("N", ctypes.c_int), ("detJ_min", ctypes.c_double),
+                ("X", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("Z", ctypes.c_void_p), ("G", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("l2g", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("mult", ctypes.c_void_p)]
+
+
+class sem_solver_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
+                ("timeout_s", ctypes.c_double)]
+
+
+class sem_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsemgb.so (built by ``paper_2501_13240_gb300.build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2501_13240_gb300.build.build(); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "sem_last_error": ([], ctypes.c_char_p),
+            "sem_version": ([], ctypes.c_char_p),
+            "sem_gll": ([_i, _vp, _vp, _vp], _i),
+            "sem_mesh_create_box": ([ctypes.POINTER(sem_box_desc), _vp, ctypes.POINTER(_vp)], _i),
+            "sem_mesh_destroy": ([_vp], _i),
+            "sem_mesh_info_get": ([_vp, ctypes.POINTER(sem_mesh_info)], _i),
+            "sem_mesh_copy_maps": ([_vp, _vp, _vp], _i),
+            "sem_mesh_copy_gs_tables": ([_vp, _vp, _vp], _i),
+            "sem_ax_apply": ([_vp, _d, _d, _vp, _vp, _i, _vp], _i),
+            "sem_gs_op": ([_vp, _vp, _i, _vp], _i),
+            "sem_gather": ([_vp, _vp, _vp, _vp], _i),
+            "sem_scatter": ([_vp, _vp, _vp, _vp], _i),
+            "sem_ax_assembled": ([_vp, _d, _d, _vp, _vp, _i, _vp], _i),
+            "sem_jacobi_inv": ([_vp, _d, _d, _vp, _vp], _i),
+            "sem_weak_rhs": ([_vp, _vp, _vp, _vp], _i),
+            "sem_pcg_workspace_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], _i),
+            "sem_pcg_solve": ([_vp, _d, _d, _vp, _vp, ctypes.POINTER(sem_solver_opts), _vp,
+                               ctypes.POINTER(sem_solve_stats), _vp], _i),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int) -> int:
+    if rc != SEM_OK:
+        raise SemError(rc, lib().sem_last_error().decode())
+    return rc
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype=None, n=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def sem_version() -> str:
+    return lib().sem_version().decode()
+
+
+def sem_gll(N: int):
+    """GLL nodes, weights and derivative matrix (host numpy arrays)."""
+    xi = np.zeros(N + 1)
+    rho = np.zeros(N + 1)
+    D = np.zeros((N + 1) * (N + 1))
+    _check(lib().sem_gll(N, xi.ctypes.data, rho.ctypes.data, D.ctypes.data))
+    return xi, rho, D.reshape(N + 1, N + 1)
+
+
+class Mesh:
+    """Owns a ``sem_mesh`` handle; exposes sizes and the device views."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        info = sem_mesh_info()
+        _check(lib().sem_mesh_info_get(self._h, ctypes.byref(info)))
+        self.info = info
+        self.E = int(info.E)
+        self.N = int(info.N)
+        self.n_local = int(info.n_local)
+        self.n_unique = int(info.n_unique)
+        self.detJ_min = float(info.detJ_min)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("mesh has been destroyed")
+        return self._h
+
+    def destroy(self):
+        if self._h is not None:
+            lib().sem_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def maps(self):
+        """(l2g int32[n_local], mask uint8[n_unique]) on the host."""
+        l2g = np.zeros(self.n_local, dtype=np.int32)
+        mask = np.zeros(self.n_unique, dtype=np.uint8)
+        _check(lib().sem_mesh_copy_maps(self.handle, l2g.ctypes.data, mask.ctypes.data))
+        return l2g, mask
+
+    def gs_tables(self):
+        off = np.zeros(self.n_unique + 1, dtype=np.int32)
+        perm = np.zeros(self.n_local, dtype=np.int32)
+        _check(lib().sem_mesh_copy_gs_tables(self.handle, off.ctypes.data, perm.ctypes.data))
+        return off, perm
+
+    def field(self, name: str):
+        """Copy of a device view ('X', 'Y', 'Z', 'B', 'G', 'mult') as a torch tensor."""
+        sizes = {"X": self.n_local, "Y": self.n_local, "Z": self.n_local, "B": self.n_local,
+                 "G": 6 * self.n_local, "mult": self.n_unique}
+        return _device_copy(getattr(self.info, name), sizes[name])
+
+
+class _DeviceView:
+    """Zero-copy descriptor of library-owned device memory (CUDA array interface)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (int(ptr), True),
+                                         "version": 2, "strides": None}
+
+
+def _device_copy(ptr: int, n: int, typestr: str = "<f8"):
+    """Copy of n elements of library-owned device memory into a new torch tensor."""
+    import torch
+    torch.cuda.synchronize()
+    return torch.as_tensor(_DeviceView(ptr, n, typestr), device="cuda").clone()
+
+
+def sem_mesh_create_box(nel, N=7, L=(1.0, 1.0, 1.0), periodic=(0, 0, 0), dirichlet=(1, 1, 1, 1, 1, 1),
+                        z_stretch=0.0, deform_amp=0.0, kappa=None, phi=None, stream=None) -> Mesh:
+    d = sem_box_desc()
+    d.nelx, d.nely, d.nelz = (int(v) for v in nel)
+    d.N = int(N)
+    d.Lx, d.Ly, d.Lz = (float(v) for v in L)
+    for c in range(3):
+        d.periodic[c] = int(periodic[c])
+    for f in range(6):
+        d.dirichlet[f] = int(dirichlet[f])
+    d.z_stretch = float(z_stretch)
+    d.deform_amp = float(deform_amp)
+    kap = np.zeros(9) if kappa is None else np.asarray(kappa, dtype=np.float64).ravel()
+    ph = np.zeros(3) if phi is None else np.asarray(phi, dtype=np.float64).ravel()
+    for t in range(9):
+        d.kappa[t] = float(kap[t])
+    for t in range(3):
+        d.phi[t] = float(ph[t])
+    h = ctypes.c_void_p()
+    _check(lib().sem_mesh_create_box(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+    return Mesh(h)
+
+
+def mesh_from_workload(w, stream=None) -> Mesh:
+    """Mesh of a ``workloads.BoxWorkload`` (sizes and seeded deformation)."""
+    from workloads import deformation_params
+    kappa, phi = deformation_params(w.deform_seed)
+    return sem_mesh_create_box(w.nel, w.N, w.L, w.periodic, w.dirichlet, w.z_stretch, w.deform_amp, kappa, phi,
+                               stream)
+
+
+def sem_ax_apply(mesh: Mesh, h1: float, h2: float, u_L, w_L, precision: int = SEM_PREC_FP64, stream=None):
+    import torch
+    _check(lib().sem_ax_apply(mesh.handle, float(h1), float(h2), _ptr(u_L, torch.float64, mesh.n_local, "u_L"),
+                              _ptr(w_L, torch.float64, mesh.n_local, "w_L"), int(precision), _stream(stream)))
+    return w_L
+
+
+def sem_gs_op(mesh: Mesh, v_L, apply_mask: bool = False, stream=None):
+    import torch
+    _check(lib().sem_gs_op(mesh.handle, _ptr(v_L, torch.float64, mesh.n_local, "v_L"), int(bool(apply_mask)),
+                           _stream(stream)))
+    return v_L
+
+
+def sem_gather(mesh: Mesh, v_L, v_g, stream=None):
+    import torch
+    _check(lib().sem_gather(mesh.handle, _ptr(v_L, torch.float64, mesh.n_local, "v_L"),
+                            _ptr(v_g, torch.float64, mesh.n_unique, "v_g"), _stream(stream)))
+    return v_g
+
+
+def sem_scatter(mesh: Mesh, v_g, v_L, stream=None):
+    import torch
+    _check(lib().sem_scatter(mesh.handle, _ptr(v_g, torch.float64, mesh.n_unique, "v_g"),
+                             _ptr(v_L, torch.float64, mesh.n_local, "v_L"), _stream(stream)))
+    return v_L
+
+
+def sem_ax_assembled(mesh: Mesh, h1: float, h2: float, u_g, w_g, precision: int = SEM_PREC_FP64, stream=None):
+    import torch
+    _check(lib().sem_ax_assembled(mesh.handle, float(h1), float(h2), _ptr(u_g, torch.float64, mesh.n_unique, "u_g"),
+                                  _ptr(w_g, torch.float64, mesh.n_unique, "w_g"), int(precision), _stream(stream)))
+    return w_g
+
+
+def sem_jacobi_inv(mesh: Mesh, h1: float, h2: float, dinv_g, stream=None):
+    import torch
+    _check(lib().sem_jacobi_inv(mesh.handle, float(h1), float(h2), _ptr(dinv_g, torch.float64, mesh.n_unique, "dinv"),
+                                _stream(stream)))
+    return dinv_g
+
+
+def sem_weak_rhs(mesh: Mesh, f_L, b_g, stream=None):
+    import torch
+    _check(lib().sem_weak_rhs(mesh.handle, _ptr(f_L, torch.float64, mesh.n_local, "f_L"),
+                              _ptr(b_g, torch.float64, mesh.n_unique, "b_g"), _stream(stream)))
+    return b_g
+
+
+def sem_pcg_workspace_bytes(mesh: Mesh) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sem_pcg_workspace_bytes(mesh.handle, ctypes.byref(b)))
+    return int(b.value)
+
+
+def sem_pcg_solve(mesh: Mesh, h1: float, h2: float, b_g, x_g, tol: float = 1e-8, maxit: int = 1000,
+                  precision: int = SEM_PREC_FP64, timeout_s: float = 0.0, workspace=None, stream=None,
+                  raise_on_error: bool = True):
+    """Jacobi-PCG; returns a dict of the solve statistics. ``workspace`` is a
+    uint8 CUDA tensor of at least sem_pcg_workspace_bytes(mesh) bytes (allocated
+    here through torch when None)."""
+    import torch
+    need = sem_pcg_workspace_bytes(mesh)
+    if workspace is None:
+        workspace = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    if workspace.numel() < need:
+        raise ValueError("workspace too small")
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    if aligned + need > base + workspace.numel():
+        raise ValueError("workspace too small after 256-byte alignment (allocate 256 extra bytes)")
+    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s))
+    st = sem_solve_stats()
+    rc = lib().sem_pcg_solve(mesh.handle, float(h1), float(h2), _ptr(b_g, torch.float64, mesh.n_unique, "b_g"),
+                             _ptr(x_g, torch.float64, mesh.n_unique, "x_g"), ctypes.byref(o),
+                             ctypes.c_void_p(aligned), ctypes.byref(st), _stream(stream))
+    out = {"iterations": st.iterations, "rel_residual": st.rel_residual, "solve_ms": st.solve_ms,
+           "status": st.status}
+    if rc != SEM_OK and (raise_on_error or rc not in (SEM_ERR_NOT_CONVERGED, SEM_ERR_TIMEOUT, SEM_ERR_BREAKDOWN)):
+        _check(rc)
+    return out

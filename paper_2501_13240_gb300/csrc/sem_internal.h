@@ -1,0 +1,78 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sem.h"
+
+#define SEM_MAXN 10
+#define SEM_MAXNP (SEM_MAXN + 1)
+
+struct sem_mesh {
+  int nel[3];
+  int N;
+  int n;          // N + 1
+  int n3;         // (N + 1)^3
+  int64_t E;
+  int64_t n_local;
+  int64_t n_unique;
+  int periodic[3];
+  int dirichlet[6];
+  double L[3];
+  double detJ_min;
+  double xi[SEM_MAXNP], rho[SEM_MAXNP], D[SEM_MAXNP * SEM_MAXNP];
+  // device arrays (owned)
+  double *X = nullptr, *Y = nullptr, *Z = nullptr;
+  double *G = nullptr;      // [E][6][n3]
+  float2 *Gdf = nullptr;    // [E][6][n3] double-float split of G (hi, lo)
+  double *B = nullptr;      // [E][n3]
+  int32_t *l2g = nullptr;   // [n_local]
+  int32_t *l2gm = nullptr;  // [n_local] l2g, or -1 on Dirichlet nodes
+  uint8_t *mask = nullptr;  // [n_unique]
+  double *mult = nullptr;   // [n_unique]
+  int32_t *gs_off = nullptr;   // [n_unique + 1]
+  int32_t *gs_perm = nullptr;  // [n_local]
+  double *dD = nullptr;     // device copy of D (n*n)
+  int device = 0;
+};
+
+// thread-local error reporting
+int sem_fail(int code, const std::string &msg);
+int sem_cuda_fail(cudaError_t e, const char *what);
+#define SEM_CUDA(call)                                              \
+  do {                                                              \
+    cudaError_t _e = (call);                                        \
+    if (_e != cudaSuccess) return sem_cuda_fail(_e, #call);         \
+  } while (0)
+#define SEM_LAUNCH_CHECK(what)                                      \
+  do {                                                              \
+    cudaError_t _e = cudaGetLastError();                            \
+    if (_e != cudaSuccess) return sem_cuda_fail(_e, what);          \
+  } while (0)
+
+static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// host-side GLL (long double Newton), shared by the set-up code
+int sem_gll_host(int N, double *xi, double *rho, double *D);
+
+// kernels launched from other translation units
+int sem_launch_ax_local(const sem_mesh *m, double h1, double h2, const double *u, double *w,
+                        int precision, cudaStream_t st);
+int sem_launch_ax_assembled(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
+                            double *pw_partial, int precision, cudaStream_t st);
+int sem_ax_assembled_blocks(const sem_mesh *m);
+int sem_launch_gs(const sem_mesh *m, double *v, int apply_mask, cudaStream_t st);
+int sem_launch_gather(const sem_mesh *m, const double *vL, double *vg, cudaStream_t st);
+int sem_launch_scatter(const sem_mesh *m, const double *vg, double *vL, cudaStream_t st);
+int sem_launch_diag_local(const sem_mesh *m, double h1, double h2, double *dL, cudaStream_t st);
+
+// grid helpers
+static inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 32) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}

@@ -1,0 +1,337 @@
+// Operator entry points of the C ABI and the Jacobi-preconditioned conjugate
+// gradient solve of the assembled Helmholtz system (Sec. 2.2: the pressure
+// Poisson solve is the stiffest substep and is preconditioned).
+//
+// Vectors are U-vectors (one value per unique node). Each iteration runs
+//   w = 0; w = M Q^T A_L Q p  (fused operator, also the p.w partial sums)
+//   update1: alpha = rho / p.w;  x += alpha p;  r -= alpha w;  partial r.z, r.r
+//   update2: beta = r.z / rho;   p = z + beta p   (z = dinv * r, not stored)
+// All reductions are two-level and in a fixed order, so for a given mesh and
+// input every scalar is reproducible except through the operator's atomics.
+#include <math.h>
+
+#include <chrono>
+#include <string>
+
+#include "sem_internal.h"
+
+namespace {
+
+constexpr int kUpdThreads = 256;
+constexpr int kUpdBlocks = 152 * 4;
+
+struct PcgScalars {
+  double rho[2];  // r.z, ping-pong by iteration parity
+  double pw;      // p.w of the last iteration
+  double alpha;
+  double beta;
+  double rr;      // r.r after the last update
+  double bb;      // b.b
+  double pad;
+};
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  // fixed-order block reduction; red must hold 32 doubles; result in all threads
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    s = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// every block sums the same partial array in the same order
+__device__ __forceinline__ double sum_partials(const double *__restrict__ part, int n, double *red) {
+  double v = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) v += part[t];
+  return block_sum(v, red);
+}
+
+__global__ void __launch_bounds__(kUpdThreads)
+    k_pcg_init(int64_t nU, const double *__restrict__ b, double *__restrict__ x, double *__restrict__ r,
+               double *__restrict__ p, const double *__restrict__ dinv, double *__restrict__ part_a,
+               double *__restrict__ part_b) {
+  __shared__ double red[32];
+  double rz = 0.0, bb = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
+    const double bv = b[g];
+    const double z = dinv[g] * bv;
+    x[g] = 0.0;
+    r[g] = bv;
+    p[g] = z;
+    rz = fma(bv, z, rz);
+    bb = fma(bv, bv, bb);
+  }
+  rz = block_sum(rz, red);
+  bb = block_sum(bb, red);
+  if (threadIdx.x == 0) {
+    part_a[blockIdx.x] = rz;
+    part_b[blockIdx.x] = bb;
+  }
+}
+
+__global__ void __launch_bounds__(kUpdThreads)
+    k_pcg_init_finish(const double *__restrict__ part_a, const double *__restrict__ part_b, int n, PcgScalars *s) {
+  __shared__ double red[32];
+  const double rz = sum_partials(part_a, n, red);
+  const double bb = sum_partials(part_b, n, red);
+  if (threadIdx.x == 0) {
+    s->rho[0] = rz;
+    s->bb = bb;
+    s->rr = bb;
+  }
+}
+
+__global__ void __launch_bounds__(kUpdThreads)
+    k_pcg_update1(int64_t nU, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                  const double *__restrict__ w, const double *__restrict__ dinv, const double *__restrict__ pw_part,
+                  int n_pw, PcgScalars *s, int par, double *__restrict__ rz_part, double *__restrict__ rr_part) {
+  __shared__ double red[32];
+  const double pw = sum_partials(pw_part, n_pw, red);
+  const double alpha = s->rho[par] / pw;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    s->pw = pw;
+    s->alpha = alpha;
+  }
+  double rz = 0.0, rr = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
+    const double pv = p[g];
+    x[g] = fma(alpha, pv, x[g]);
+    const double rv = fma(-alpha, w[g], r[g]);
+    r[g] = rv;
+    const double z = dinv[g] * rv;
+    rz = fma(rv, z, rz);
+    rr = fma(rv, rv, rr);
+  }
+  rz = block_sum(rz, red);
+  rr = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    rz_part[blockIdx.x] = rz;
+    rr_part[blockIdx.x] = rr;
+  }
+}
+
+__global__ void __launch_bounds__(kUpdThreads)
+    k_pcg_update2(int64_t nU, const double *__restrict__ r, double *__restrict__ p, const double *__restrict__ dinv,
+                  const double *__restrict__ rz_part, const double *__restrict__ rr_part, int n_part, PcgScalars *s,
+                  int par) {
+  __shared__ double red[32];
+  const double rz = sum_partials(rz_part, n_part, red);
+  const double beta = rz / s->rho[par];
+  if (blockIdx.x == 0) {  // only block 0 needs r.r (block-uniform branch)
+    const double rr = sum_partials(rr_part, n_part, red);
+    if (threadIdx.x == 0) {
+      s->rr = rr;
+      s->beta = beta;
+      s->rho[par ^ 1] = rz;
+    }
+  }
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x)
+    p[g] = fma(beta, p[g], dinv[g] * r[g]);
+}
+
+// dinv[g] = mask[g] / sum over copies of the local diagonal
+__global__ void k_jacobi_inv(int n, int64_t nU, const int32_t *__restrict__ off, const int32_t *__restrict__ perm,
+                             const uint8_t *__restrict__ mask, const double *__restrict__ Dg,
+                             const double *__restrict__ G, const double *__restrict__ B, double h1, double h2,
+                             double *__restrict__ dinv) {
+  const int n3 = n * n * n;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
+    double tot = 0.0;
+    for (int32_t t = off[g]; t < off[g + 1]; ++t) {
+      const int64_t l = perm[t];
+      const int64_t e = l / n3;
+      const int q = (int)(l - e * n3);
+      const int i = q % n, j = (q / n) % n, k = q / (n * n);
+      const double *Ge = G + 6 * e * n3;
+      double s = 0.0;
+      for (int m = 0; m < n; ++m) {
+        const double a = Dg[m * n + i], b = Dg[m * n + j], c = Dg[m * n + k];
+        s += a * a * Ge[0 * n3 + m + n * (j + n * k)];
+        s += b * b * Ge[3 * n3 + i + n * (m + n * k)];
+        s += c * c * Ge[5 * n3 + i + n * (j + n * m)];
+      }
+      const double di = Dg[i * n + i], dj = Dg[j * n + j], dk = Dg[k * n + k];
+      s += 2.0 * di * dj * Ge[1 * n3 + q];
+      s += 2.0 * di * dk * Ge[2 * n3 + q];
+      s += 2.0 * dj * dk * Ge[4 * n3 + q];
+      tot += h1 * s + h2 * B[l];
+    }
+    dinv[g] = mask[g] ? 1.0 / tot : 0.0;
+  }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct PcgWork {
+  double *r, *p, *w, *dinv, *pw_part, *part_a, *part_b;
+  PcgScalars *s;
+};
+
+size_t pcg_layout(const sem_mesh *m, char *base, PcgWork *wk) {
+  const size_t vec = align256(sizeof(double) * (size_t)m->n_unique);
+  const size_t npw = align256(sizeof(double) * (size_t)sem_ax_assembled_blocks(m));
+  const size_t npart = align256(sizeof(double) * kUpdBlocks);
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    char *p = base ? base + off : nullptr;
+    off += b;
+    return p;
+  };
+  PcgWork w;
+  w.r = (double *)take(vec);
+  w.p = (double *)take(vec);
+  w.w = (double *)take(vec);
+  w.dinv = (double *)take(vec);
+  w.pw_part = (double *)take(npw);
+  w.part_a = (double *)take(npart);
+  w.part_b = (double *)take(npart);
+  w.s = (PcgScalars *)take(align256(sizeof(PcgScalars)));
+  if (wk) *wk = w;
+  return off;
+}
+
+int check_mesh(const sem_mesh *m, const char *fn) {
+  if (!m) return sem_fail(SEM_ERR_INVALID_ARG, std::string(fn) + ": NULL mesh");
+  return SEM_OK;
+}
+
+bool bad_ptr(const void *p) { return p == nullptr || ((uintptr_t)p & 7) != 0; }
+
+}  // namespace
+
+extern "C" int sem_ax_apply(const sem_mesh *m, double h1, double h2, const double *u_L, double *w_L, int precision,
+                            void *stream) {
+  if (int rc = check_mesh(m, "sem_ax_apply")) return rc;
+  if (bad_ptr(u_L) || bad_ptr(w_L)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_apply: NULL or misaligned vector");
+  if (u_L == w_L) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_apply: u_L and w_L must not overlap");
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_DF64)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_apply: unknown precision");
+  return sem_launch_ax_local(m, h1, h2, u_L, w_L, precision, as_stream(stream));
+}
+
+extern "C" int sem_gs_op(const sem_mesh *m, double *v_L, int apply_mask, void *stream) {
+  if (int rc = check_mesh(m, "sem_gs_op")) return rc;
+  if (bad_ptr(v_L)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_gs_op: NULL or misaligned vector");
+  return sem_launch_gs(m, v_L, apply_mask, as_stream(stream));
+}
+
+extern "C" int sem_gather(const sem_mesh *m, const double *v_L, double *v_g, void *stream) {
+  if (int rc = check_mesh(m, "sem_gather")) return rc;
+  if (bad_ptr(v_L) || bad_ptr(v_g)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_gather: NULL or misaligned vector");
+  return sem_launch_gather(m, v_L, v_g, as_stream(stream));
+}
+
+extern "C" int sem_scatter(const sem_mesh *m, const double *v_g, double *v_L, void *stream) {
+  if (int rc = check_mesh(m, "sem_scatter")) return rc;
+  if (bad_ptr(v_L) || bad_ptr(v_g)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_scatter: NULL or misaligned vector");
+  return sem_launch_scatter(m, v_g, v_L, as_stream(stream));
+}
+
+extern "C" int sem_ax_assembled(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g, int precision,
+                                void *stream) {
+  if (int rc = check_mesh(m, "sem_ax_assembled")) return rc;
+  if (bad_ptr(u_g) || bad_ptr(w_g)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled: NULL or misaligned vector");
+  if (u_g == w_g) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled: u_g and w_g must not overlap");
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_DF64)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled: unknown precision");
+  cudaStream_t st = as_stream(stream);
+  SEM_CUDA(cudaMemsetAsync(w_g, 0, sizeof(double) * m->n_unique, st));
+  // p.w partials are not wanted here: a small scratch is not needed because
+  // the kernel writes them only when given a buffer
+  return sem_launch_ax_assembled(m, h1, h2, u_g, w_g, nullptr, precision, st);
+}
+
+extern "C" int sem_jacobi_inv(const sem_mesh *m, double h1, double h2, double *dinv_g, void *stream) {
+  if (int rc = check_mesh(m, "sem_jacobi_inv")) return rc;
+  if (bad_ptr(dinv_g)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_jacobi_inv: NULL or misaligned vector");
+  k_jacobi_inv<<<grid_for(m->n_unique, 256), 256, 0, as_stream(stream)>>>(
+      m->n, m->n_unique, m->gs_off, m->gs_perm, m->mask, m->dD, m->G, m->B, h1, h2, dinv_g);
+  SEM_LAUNCH_CHECK("k_jacobi_inv");
+  return SEM_OK;
+}
+
+extern "C" int sem_pcg_workspace_bytes(const sem_mesh *m, size_t *bytes) {
+  if (int rc = check_mesh(m, "sem_pcg_workspace_bytes")) return rc;
+  if (!bytes) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_workspace_bytes: NULL output");
+  *bytes = pcg_layout(m, nullptr, nullptr);
+  return SEM_OK;
+}
+
+extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
+                             const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats, void *stream) {
+  if (int rc = check_mesh(m, "sem_pcg_solve")) return rc;
+  if (bad_ptr(b_g) || bad_ptr(x_g)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: NULL or misaligned vector");
+  if (!opts || !stats) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: NULL opts or stats");
+  if (!workspace || ((uintptr_t)workspace & 255))
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: workspace must be non-NULL and 256-byte aligned");
+  if (!(opts->tol >= 0.0) || opts->maxit < 1) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: bad tol or maxit");
+  if (opts->precision != SEM_PREC_FP64 && opts->precision != SEM_PREC_DF64)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: unknown precision");
+  if (!(h1 >= 0.0) || !(h2 >= 0.0) || (h1 == 0.0 && h2 == 0.0))
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: need h1 >= 0, h2 >= 0, not both zero");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = as_stream(stream);
+  PcgWork wk;
+  pcg_layout(m, (char *)workspace, &wk);
+  const int n_pw = sem_ax_assembled_blocks(m);
+  const int64_t nU = m->n_unique;
+  stats->iterations = 0;
+  stats->rel_residual = 0.0;
+  stats->solve_ms = 0.0;
+  stats->status = SEM_OK;
+
+  int rc;
+  if ((rc = sem_jacobi_inv(m, h1, h2, wk.dinv, stream)) != SEM_OK) return rc;
+  k_pcg_init<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, x_g, wk.r, wk.p, wk.dinv, wk.part_a, wk.part_b);
+  k_pcg_init_finish<<<1, kUpdThreads, 0, st>>>(wk.part_a, wk.part_b, kUpdBlocks, wk.s);
+  SEM_LAUNCH_CHECK("k_pcg_init");
+  PcgScalars hs;
+  SEM_CUDA(cudaMemcpyAsync(&hs, wk.s, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  SEM_CUDA(cudaStreamSynchronize(st));
+  const double bnorm = sqrt(hs.bb);
+  auto finish = [&](int status, int it, double rr) {
+    stats->iterations = it;
+    stats->rel_residual = (bnorm > 0.0) ? sqrt(rr) / bnorm : 0.0;
+    stats->solve_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    stats->status = status;
+    if (status == SEM_ERR_NOT_CONVERGED) sem_fail(status, "sem_pcg_solve: maxit reached");
+    if (status == SEM_ERR_BREAKDOWN) sem_fail(status, "sem_pcg_solve: breakdown (p.Ap <= 0 or non-finite)");
+    if (status == SEM_ERR_TIMEOUT) sem_fail(status, "sem_pcg_solve: timeout");
+    return status;
+  };
+  if (!(bnorm > 0.0)) {
+    if (!std::isfinite(hs.bb)) return finish(SEM_ERR_BREAKDOWN, 0, hs.bb);
+    return finish(SEM_OK, 0, 0.0);  // b = 0: x = 0 (already written)
+  }
+  const double thresh = opts->tol * bnorm;
+  for (int it = 1; it <= opts->maxit; ++it) {
+    const int par = (it - 1) & 1;
+    SEM_CUDA(cudaMemsetAsync(wk.w, 0, sizeof(double) * nU, st));
+    if ((rc = sem_launch_ax_assembled(m, h1, h2, wk.p, wk.w, wk.pw_part, opts->precision, st)) != SEM_OK) return rc;
+    k_pcg_update1<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, x_g, wk.r, wk.p, wk.w, wk.dinv, wk.pw_part, n_pw, wk.s, par,
+                                                      wk.part_a, wk.part_b);
+    k_pcg_update2<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, wk.r, wk.p, wk.dinv, wk.part_a, wk.part_b, kUpdBlocks, wk.s,
+                                                      par);
+    SEM_LAUNCH_CHECK("pcg iteration");
+    SEM_CUDA(cudaMemcpyAsync(&hs, wk.s, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    SEM_CUDA(cudaStreamSynchronize(st));
+    if (!(hs.pw > 0.0) || !std::isfinite(hs.pw) || !std::isfinite(hs.rr)) return finish(SEM_ERR_BREAKDOWN, it, hs.rr);
+    if (sqrt(hs.rr) <= thresh) return finish(SEM_OK, it, hs.rr);
+    if (opts->timeout_s > 0.0) {
+      double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > opts->timeout_s) return finish(SEM_ERR_TIMEOUT, it, hs.rr);
+    }
+  }
+  return finish(SEM_ERR_NOT_CONVERGED, opts->maxit, hs.rr);
+}

@@ -1,0 +1,49 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, it
+exports every function include/sem.h declares, and the host GLL set-up agrees
+with the oracle (Sec. 2.2: GLL nodal basis)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2501_13240_gb300 as sem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "sem.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sem_\w+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = sem.lib()
+    names = header_functions()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(sem.EXPORTS)
+
+
+def test_version_and_error_text():
+    assert "sm_103a" in sem.sem_version()
+    assert isinstance(sem.lib().sem_last_error(), bytes)
+
+
+@pytest.mark.parametrize("N", range(1, 11))
+def test_library_gll_matches_oracle(N):
+    xi, rho, D = sem.sem_gll(N)
+    xo, ro, Do = oracle.gll(N)
+    np.testing.assert_allclose(xi, xo, rtol=0, atol=2e-16)
+    np.testing.assert_allclose(rho, ro, rtol=4e-16, atol=0)
+    np.testing.assert_allclose(D, Do, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("N", [0, 11])
+def test_library_gll_rejects_bad_order(N):
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_gll(N)
+    assert ei.value.code == sem.SEM_ERR_INVALID_ARG
