@@ -41,6 +41,10 @@ METRIC = "Ax+gs GDOF/s & PCG solve time, FP64 vs mixed at 1e-8 residual; % HBM p
 FLOP_PER_POINT = 111        # 3 x 2n (D) + 15 (metric) + 3 x 2n (D^T), n = 8
 BYTES_PER_POINT_AXGS = 62.7  # G 48 + l2g 4 + (u read + w write) 16 per unique node x 0.674
 FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 rate (vector and tensor)
+DTYPES = {"df64": "f32x2 (double-float, binary64-accurate)", "fp64": "f64"}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the assembled
+# operator kernel (ncu, scaled from the 32^3-element case); None until measured
+TRAFFIC = {}
 
 
 def parse():
@@ -53,6 +57,7 @@ def parse():
     ap.add_argument("--no-pcg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
+    ap.add_argument("--precision", default="df64", choices=["df64", "fp64"])
     return ap.parse_args()
 
 
@@ -202,9 +207,22 @@ def main():
     ug_host = workloads.unique_field(mesh.n_unique)
     u = torch.from_numpy(ug_host).cuda()
     wg = torch.empty_like(u)
+    precs = {"df64": sem.SEM_PREC_DF64, "fp64": sem.SEM_PREC_FP64}
+    head = args.precision
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def step():
-        sem.sem_ax_assembled(mesh, 1.0, 0.0, u, wg)
+    def step(prec=precs[head]):
+        sem.sem_ax_assembled(mesh, 1.0, 0.0, u, wg, precision=prec)
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
 
     # --- device-resident throughput (the headline value)
     for _ in range(max(args.warmup, 3)):
@@ -212,7 +230,6 @@ def main():
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
@@ -225,38 +242,35 @@ def main():
     value = world * w.dofs / (ms * 1e-3) / 1e9
     clocks = clk.summary()
 
-    # --- kernel-only timing of the dominant kernel (the operator kernel), for the roofline
-    dom_ms = ms  # the memset is ~0.1 ms of it; time the kernel through the E-vector entry point too
+    # --- per-precision timings: assembled op, its kernel alone (accumulating
+    # entry point, no clearing of w), and the E-vector Ax + gs pair
     uL = torch.empty(mesh.n_local, dtype=torch.float64, device="cuda")
     sem.sem_scatter(mesh, u, uL)
     wL = torch.empty_like(uL)
-    for _ in range(3):
-        sem.sem_ax_apply(mesh, 1.0, 0.0, uL, wL)
-    e0.record(stream)
-    for _ in range(args.steps):
-        sem.sem_ax_apply(mesh, 1.0, 0.0, uL, wL)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ax_local_ms = e0.elapsed_time(e1) / args.steps
-    # E-vector Ax + gs pair (the unfused form)
-    e0.record(stream)
-    for _ in range(args.steps):
-        sem.sem_ax_apply(mesh, 1.0, 0.0, uL, wL)
-        sem.sem_gs_op(mesh, wL, True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    evec_ms = e0.elapsed_time(e1) / args.steps
+    nrep = max(3, min(args.steps, 10))
+    per = {}
+    for name, prec in precs.items():
+        per[name] = {
+            "assembled_ms": timed(lambda: step(prec), nrep),
+            "kernel_ms": timed(lambda: sem.sem_ax_assembled_add(mesh, 1.0, 0.0, u, wg, precision=prec), nrep),
+            "ax_local_ms": timed(lambda: sem.sem_ax_apply(mesh, 1.0, 0.0, uL, wL, precision=prec), nrep),
+            "evector_ax_gs_ms": timed(lambda: (sem.sem_ax_apply(mesh, 1.0, 0.0, uL, wL, precision=prec),
+                                               sem.sem_gs_op(mesh, wL, True)), nrep),
+        }
+        per[name]["assembled_gdofs"] = w.dofs / (per[name]["assembled_ms"] * 1e-3) / 1e9
     del uL, wL
 
-    flops = FLOP_PER_POINT * w.n_local
     hbm_gbs, hbm_src = peaks()
-    achieved_tf = flops / (ax_local_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "k_ax_fp64<8,false> (sem_ax_apply)", "peak_source": "nominal GB300 FP64 rate",
-                "hbm_achieved_gbs": BYTES_PER_POINT_AXGS * w.n_local / (dom_ms * 1e-3) / 1e9,
-                "hbm_peak_gbs": hbm_gbs, "hbm_peak_source": hbm_src}
-    roofline["hbm_frac"] = roofline["hbm_achieved_gbs"] / hbm_gbs
+    kms = per[head]["kernel_ms"]
+    algo_bytes = BYTES_PER_POINT_AXGS * w.n_local
+    achieved = algo_bytes / (kms * 1e-3) / 1e9
+    fp64_tf = FLOP_PER_POINT * w.n_local / (per["fp64"]["kernel_ms"] * 1e-3) / 1e12
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
+                "traffic": TRAFFIC.get(head), "kernel": f"k_ax_{head}<8, assembled>",
+                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": algo_bytes, "kernel_ms": kms,
+                "fp64_kernel": {"bound": "alu", "achieved_tflops": fp64_tf, "peak_tflops": FP64_PEAK_TFLOPS,
+                                "frac": fp64_tf / FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64 rate"}}
 
     # --- end to end through the C ABI with host buffers
     pin_in = torch.from_numpy(ug_host).pin_memory()
@@ -294,7 +308,7 @@ def main():
         del fL
         x = torch.zeros_like(u)
         pcg = {}
-        for name, prec in (("fp64", sem.SEM_PREC_FP64),):
+        for name, prec in (("df64", sem.SEM_PREC_DF64), ("fp64", sem.SEM_PREC_FP64)):
             torch.cuda.synchronize()
             st = sem.sem_pcg_solve(mesh, 1.0, 0.0, b, x, tol=args.pcg_tol, maxit=20000, precision=prec,
                                    raise_on_error=False)
@@ -313,15 +327,13 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
             "config": {"workload": w.name, "N": w.N, "nel": list(w.nel), "n_local": w.n_local,
                        "n_unique": w.n_unique, "dofs_per_step": w.dofs, "op": "assembled Ax+gs (Poisson, h1=1)",
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clocks,
-            "extra": {"ax_local_ms": ax_local_ms, "ax_local_gdofs": w.dofs / (ax_local_ms * 1e-3) / 1e9,
-                      "evector_ax_plus_gs_ms": evec_ms,
-                      "evector_ax_plus_gs_gdofs": w.dofs / (evec_ms * 1e-3) / 1e9, "pcg": pcg},
+            "extra": {"precision": head, "per_precision": per, "pcg": pcg},
         }
         print(json.dumps(line))
     mesh.destroy()

@@ -59,8 +59,9 @@ enum {
                         unevaluated sum of two binary32 (hi + lo) and combined
                         with error-free transformations (Dekker 1971; Knuth's
                         TwoSum; Joldes, Muller & Popescu 2017). About 2^-44
-                        relative accuracy per operator application; values
-                        must stay within |x| in [2^-100, 2^100]. */
+                        relative accuracy per operator application; inputs,
+                        outputs and intermediate values must stay within
+                        |x| in [2^-80, 2^100] (binary32 exponent range). */
 };
 
 typedef struct sem_mesh sem_mesh; /* opaque */
@@ -186,6 +187,11 @@ int sem_ax_assembled(const sem_mesh *m, double h1, double h2, const double *u_g,
  * masked right-hand side of -lap u = f (or of a Helmholtz problem) for a
  * forcing f given at the local nodes (device E-vector in, U-vector out). */
 int sem_weak_rhs(const sem_mesh *m, const double *f_L, double *b_g, void *stream);
+
+/* Same as sem_ax_assembled but accumulating: w_g += M Q^T (h1 A_L + h2 B) Q M u_g
+ * (w_g is not cleared first). */
+int sem_ax_assembled_add(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
+                         int precision, void *stream);
 
 /* Masked inverse of the assembled diagonal of h1 A + h2 B (the Jacobi
  * preconditioner, including the D_ii D_jj G_rs cross terms at element

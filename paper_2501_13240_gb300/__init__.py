@@ -33,7 +33,7 @@ SEM_PREC_DF64 = 1
 EXPORTS = (
     "sem_last_error", "sem_version", "sem_gll", "sem_mesh_create_box", "sem_mesh_destroy",
     "sem_mesh_info_get", "sem_mesh_copy_maps", "sem_mesh_copy_gs_tables", "sem_ax_apply", "sem_gs_op",
-    "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
+    "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_ax_assembled_add", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
     "sem_pcg_solve",
 )
 
@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
             "sem_gather": ([_vp, _vp, _vp, _vp], _i),
             "sem_scatter": ([_vp, _vp, _vp, _vp], _i),
             "sem_ax_assembled": ([_vp, _d, _d, _vp, _vp, _i, _vp], _i),
+            "sem_ax_assembled_add": ([_vp, _d, _d, _vp, _vp, _i, _vp], _i),
             "sem_jacobi_inv": ([_vp, _d, _d, _vp, _vp], _i),
             "sem_weak_rhs": ([_vp, _vp, _vp, _vp], _i),
             "sem_pcg_workspace_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], _i),
@@ -204,7 +205,7 @@ class _DeviceView:
     """Zero-copy descriptor of library-owned device memory (CUDA array interface)."""
 
     def __init__(self, ptr: int, n: int, typestr: str):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 2, "strides": None}
 
 
@@ -278,6 +279,14 @@ def sem_ax_assembled(mesh: Mesh, h1: float, h2: float, u_g, w_g, precision: int 
     import torch
     _check(lib().sem_ax_assembled(mesh.handle, float(h1), float(h2), _ptr(u_g, torch.float64, mesh.n_unique, "u_g"),
                                   _ptr(w_g, torch.float64, mesh.n_unique, "w_g"), int(precision), _stream(stream)))
+    return w_g
+
+
+def sem_ax_assembled_add(mesh: Mesh, h1: float, h2: float, u_g, w_g, precision: int = SEM_PREC_FP64, stream=None):
+    import torch
+    _check(lib().sem_ax_assembled_add(mesh.handle, float(h1), float(h2),
+                                      _ptr(u_g, torch.float64, mesh.n_unique, "u_g"),
+                                      _ptr(w_g, torch.float64, mesh.n_unique, "w_g"), int(precision), _stream(stream)))
     return w_g
 
 

@@ -150,7 +150,7 @@ unsigned ax_grid(const sem_mesh *m, bool assembled) {
 template <int NP>
 int dispatch_np(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
                 bool assembled, int precision, cudaStream_t st) {
-  (void)precision;
+  if (precision == SEM_PREC_DF64) return sem_launch_ax_df64(m, h1, h2, u, w, pw_partial, assembled, st);
   unsigned grid = ax_grid<NP>(m, assembled);
   if (assembled) return launch_fp64<NP, true>(m, h1, h2, u, w, pw_partial, grid, st);
   return launch_fp64<NP, false>(m, h1, h2, u, w, nullptr, grid, st);
@@ -206,7 +206,8 @@ int sem_launch_ax_assembled(const sem_mesh *m, double h1, double h2, const doubl
   return dispatch(m, h1, h2, u_g, w_g, pw_partial, true, precision, st);
 }
 
-int sem_ax_assembled_blocks(const sem_mesh *m) {
+int sem_ax_assembled_blocks(const sem_mesh *m, int precision) {
+  if (precision == SEM_PREC_DF64) return sem_df64_grid(m);
   switch (m->n) {
 #define CASE(NPV) \
   case NPV:       \

@@ -29,6 +29,7 @@ struct sem_mesh {
   double *G = nullptr;      // [E][6][n3]
   float2 *Gdf = nullptr;    // [E][6][n3] double-float split of G (hi, lo)
   double *B = nullptr;      // [E][n3]
+  float2 *Bdf = nullptr;    // [E][n3] double-float split of B
   int32_t *l2g = nullptr;   // [n_local]
   int32_t *l2gm = nullptr;  // [n_local] l2g, or -1 on Dirichlet nodes
   uint8_t *mask = nullptr;  // [n_unique]
@@ -63,7 +64,10 @@ int sem_launch_ax_local(const sem_mesh *m, double h1, double h2, const double *u
                         int precision, cudaStream_t st);
 int sem_launch_ax_assembled(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
                             double *pw_partial, int precision, cudaStream_t st);
-int sem_ax_assembled_blocks(const sem_mesh *m);
+int sem_ax_assembled_blocks(const sem_mesh *m, int precision);
+int sem_df64_grid(const sem_mesh *m);
+int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
+                       bool assembled, cudaStream_t st);
 int sem_launch_gs(const sem_mesh *m, double *v, int apply_mask, cudaStream_t st);
 int sem_launch_gather(const sem_mesh *m, const double *vL, double *vg, cudaStream_t st);
 int sem_launch_scatter(const sem_mesh *m, const double *vg, double *vL, cudaStream_t st);

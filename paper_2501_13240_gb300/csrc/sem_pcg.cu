@@ -10,6 +10,7 @@
 // input every scalar is reproducible except through the operator's atomics.
 #include <math.h>
 
+#include <algorithm>
 #include <chrono>
 #include <string>
 
@@ -179,7 +180,8 @@ struct PcgWork {
 
 size_t pcg_layout(const sem_mesh *m, char *base, PcgWork *wk) {
   const size_t vec = align256(sizeof(double) * (size_t)m->n_unique);
-  const size_t npw = align256(sizeof(double) * (size_t)sem_ax_assembled_blocks(m));
+  const size_t npw = align256(sizeof(double) * (size_t)std::max(sem_ax_assembled_blocks(m, SEM_PREC_FP64),
+                                                                 sem_ax_assembled_blocks(m, SEM_PREC_DF64)));
   const size_t npart = align256(sizeof(double) * kUpdBlocks);
   size_t off = 0;
   auto take = [&](size_t b) {
@@ -246,9 +248,17 @@ extern "C" int sem_ax_assembled(const sem_mesh *m, double h1, double h2, const d
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled: unknown precision");
   cudaStream_t st = as_stream(stream);
   SEM_CUDA(cudaMemsetAsync(w_g, 0, sizeof(double) * m->n_unique, st));
-  // p.w partials are not wanted here: a small scratch is not needed because
-  // the kernel writes them only when given a buffer
   return sem_launch_ax_assembled(m, h1, h2, u_g, w_g, nullptr, precision, st);
+}
+
+extern "C" int sem_ax_assembled_add(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
+                                    int precision, void *stream) {
+  if (int rc = check_mesh(m, "sem_ax_assembled_add")) return rc;
+  if (bad_ptr(u_g) || bad_ptr(w_g)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_add: NULL or misaligned vector");
+  if (u_g == w_g) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_add: u_g and w_g must not overlap");
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_DF64)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_add: unknown precision");
+  return sem_launch_ax_assembled(m, h1, h2, u_g, w_g, nullptr, precision, as_stream(stream));
 }
 
 extern "C" int sem_jacobi_inv(const sem_mesh *m, double h1, double h2, double *dinv_g, void *stream) {
@@ -283,7 +293,7 @@ extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const doub
   cudaStream_t st = as_stream(stream);
   PcgWork wk;
   pcg_layout(m, (char *)workspace, &wk);
-  const int n_pw = sem_ax_assembled_blocks(m);
+  const int n_pw = sem_ax_assembled_blocks(m, opts->precision);
   const int64_t nU = m->n_unique;
   stats->iterations = 0;
   stats->rel_residual = 0.0;

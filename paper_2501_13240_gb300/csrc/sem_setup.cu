@@ -160,7 +160,7 @@ __device__ __forceinline__ float2 split_df(double v) {
 __global__ void k_geom(int n, int64_t E, const double *__restrict__ Dg, const double *__restrict__ rho,
                        const double *__restrict__ X, const double *__restrict__ Y, const double *__restrict__ Z,
                        double *__restrict__ G, float2 *__restrict__ Gdf, double *__restrict__ B,
-                       double *__restrict__ detmin_e) {
+                       float2 *__restrict__ Bdf, double *__restrict__ detmin_e) {
   __shared__ double sD[SEM_MAXNP * SEM_MAXNP];
   __shared__ double red[32];
   const int n3 = n * n * n;
@@ -210,6 +210,7 @@ __global__ void k_geom(int n, int64_t E, const double *__restrict__ Dg, const do
         Gdf[(6 * e + f) * n3 + q] = split_df(g);
       }
       B[base + q] = w;
+      Bdf[base + q] = split_df(w);
     }
     // block min of det J
     for (int off = 16; off > 0; off >>= 1) dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, off));
@@ -338,7 +339,7 @@ __global__ void k_sort_segments(int64_t nU, const int32_t *off, int32_t *perm, d
 // ---------------------------------------------------------------- host
 static void free_mesh(sem_mesh *m) {
   if (!m) return;
-  void *ptrs[] = {m->X, m->Y, m->Z, m->G, m->Gdf, m->B, m->l2g, m->l2gm, m->mask, m->mult, m->gs_off, m->gs_perm, m->dD};
+  void *ptrs[] = {m->X, m->Y, m->Z, m->G, m->Gdf, m->B, m->Bdf, m->l2g, m->l2gm, m->mask, m->mult, m->gs_off, m->gs_perm, m->dD};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete m;
@@ -463,6 +464,7 @@ extern "C" int sem_mesh_create_box(const sem_box_desc *d, void *stream, sem_mesh
   if ((rc = dalloc(&m->X, nL, "cudaMalloc(X)")) || (rc = dalloc(&m->Y, nL, "cudaMalloc(Y)")) ||
       (rc = dalloc(&m->Z, nL, "cudaMalloc(Z)")) || (rc = dalloc(&m->G, 6 * nL, "cudaMalloc(G)")) ||
       (rc = dalloc(&m->Gdf, 6 * nL, "cudaMalloc(Gdf)")) || (rc = dalloc(&m->B, nL, "cudaMalloc(B)")) ||
+      (rc = dalloc(&m->Bdf, nL, "cudaMalloc(Bdf)")) ||
       (rc = dalloc(&m->l2g, nL, "cudaMalloc(l2g)")) || (rc = dalloc(&m->l2gm, nL, "cudaMalloc(l2gm)")) ||
       (rc = dalloc(&m->mask, m->n_unique, "cudaMalloc(mask)")) || (rc = dalloc(&m->dD, n * n, "cudaMalloc(D)")) ||
       (rc = dalloc(&rho_d, n, "cudaMalloc(rho)")) || (rc = dalloc(&detmin_e, E, "cudaMalloc(detmin)"))) {
@@ -475,7 +477,7 @@ extern "C" int sem_mesh_create_box(const sem_box_desc *d, void *stream, sem_mesh
   cudaMemcpyAsync(rho_d, m->rho, sizeof(double) * n, cudaMemcpyHostToDevice, st);
   k_coords<<<grid_for(nL, 256), 256, 0, st>>>(p, nL, m->X, m->Y, m->Z);
   k_geom<<<(unsigned)std::min<int64_t>(E, 152 * 16), 256, 0, st>>>(n, E, m->dD, rho_d, m->X, m->Y, m->Z, m->G,
-                                                                      m->Gdf, m->B, detmin_e);
+                                                                      m->Gdf, m->B, m->Bdf, detmin_e);
   k_l2g<<<grid_for(nL, 256), 256, 0, st>>>(p, nL, m->l2g);
   k_mask<<<grid_for(m->n_unique, 256), 256, 0, st>>>(p, m->n_unique, m->mask);
   k_l2gm<<<grid_for(nL, 256), 256, 0, st>>>(nL, m->l2g, m->mask, m->l2gm);

@@ -93,12 +93,17 @@ def test_geometry(pair):
     assert abs(gm.detJ_min - om.detJ_min) <= 1e-12 * abs(om.detJ_min)
 
 
+PRECS = [sem.SEM_PREC_FP64, sem.SEM_PREC_DF64]
+PREC_IDS = ["fp64", "df64"]
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("h1,h2", [(1.0, 0.0), (0.37, 12.5), (0.0, 2.0)])
-def test_ax_local(pair, h1, h2):
+def test_ax_local(pair, h1, h2, prec):
     om, gm = pair
     u = np.random.default_rng(11).uniform(-1, 1, om.n_local)
     w = torch.empty(om.n_local, dtype=torch.float64, device="cuda")
-    sem.sem_ax_apply(gm, h1, h2, dev(u), w)
+    sem.sem_ax_apply(gm, h1, h2, dev(u), w, precision=prec)
     assert rel_err(host(w), oracle.ax_local(om, u, h1, h2)) < RTOL
 
 
@@ -123,12 +128,13 @@ def test_gather_scatter(pair):
     np.testing.assert_array_equal(host(L), oracle.scatter(om, ug))
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("h1,h2", [(1.0, 0.0), (0.37, 12.5)])
-def test_ax_assembled(pair, h1, h2):
+def test_ax_assembled(pair, h1, h2, prec):
     om, gm = pair
     ug = np.random.default_rng(15).uniform(-1, 1, om.n_unique)
     w = torch.empty(om.n_unique, dtype=torch.float64, device="cuda")
-    sem.sem_ax_assembled(gm, h1, h2, dev(ug), w)
+    sem.sem_ax_assembled(gm, h1, h2, dev(ug), w, precision=prec)
     assert rel_err(host(w), oracle.apply_assembled(om, ug, h1, h2)) < RTOL
 
 
@@ -140,15 +146,16 @@ def test_jacobi_inv(pair, h1, h2):
     assert rel_err(host(d), oracle.jacobi_inv(om, h1, h2)) < RTOL
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
 @pytest.mark.parametrize("h1,h2", [(1.0, 0.0), (0.5, 40.0)])
-def test_pcg_solve(pair, h1, h2):
+def test_pcg_solve(pair, h1, h2, prec):
     om, gm = pair
     if om.mask.sum() == 0:
         pytest.skip("no free nodes")
     b = np.random.default_rng(16).standard_normal(om.n_unique) * om.mask
     ref = oracle.pcg(om, b, h1, h2, tol=1e-10, maxit=3000)
     x = torch.zeros(om.n_unique, dtype=torch.float64, device="cuda")
-    st = sem.sem_pcg_solve(gm, h1, h2, dev(b), x, tol=1e-10, maxit=3000)
+    st = sem.sem_pcg_solve(gm, h1, h2, dev(b), x, tol=1e-10, maxit=3000, precision=prec)
     assert st["status"] == 0 and ref.converged
     assert abs(st["iterations"] - ref.iterations) <= 1, (st, ref.iterations)
     assert st["rel_residual"] <= 1e-10
@@ -178,9 +185,24 @@ def test_large_grid_stride_assembled():
     spec = dict(nel=(24, 24, 20), N=7, deform=0.1)
     om, gm = make(spec)
     ug = np.random.default_rng(21).uniform(-1, 1, om.n_unique)
-    w = torch.empty(om.n_unique, dtype=torch.float64, device="cuda")
-    sem.sem_ax_assembled(gm, 1.0, 0.0, dev(ug), w)
-    assert rel_err(host(w), oracle.apply_assembled(om, ug)) < RTOL
+    ref = oracle.apply_assembled(om, ug)
+    for prec in PRECS:
+        w = torch.empty(om.n_unique, dtype=torch.float64, device="cuda")
+        sem.sem_ax_assembled(gm, 1.0, 0.0, dev(ug), w, precision=prec)
+        assert rel_err(host(w), ref) < RTOL, prec
+    gm.destroy()
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-20, 3.7e25, 2.0 ** -60])
+def test_df64_wide_magnitudes(scale):
+    """The double-float path keeps binary64-level accuracy for inputs far
+    from 1 in magnitude (within its documented range)."""
+    spec = dict(nel=(3, 2, 2), N=7, deform=0.05)
+    om, gm = make(spec)
+    u = np.random.default_rng(22).uniform(-1, 1, om.n_local) * scale
+    w = torch.empty(om.n_local, dtype=torch.float64, device="cuda")
+    sem.sem_ax_apply(gm, 1.0, 0.0, dev(u), w, precision=sem.SEM_PREC_DF64)
+    assert rel_err(host(w), oracle.ax_local(om, u)) < RTOL
     gm.destroy()
 
 
@@ -251,6 +273,10 @@ def test_ax_gs_64_full_size_spot_check():
     sem.sem_ax_apply(gm, 1.0, 0.0, uL, wL)
     wg = torch.empty_like(ug_d)
     sem.sem_ax_assembled(gm, 1.0, 0.0, ug_d, wg)
+    wL2 = torch.empty_like(uL)
+    sem.sem_ax_apply(gm, 1.0, 0.0, uL, wL2, precision=sem.SEM_PREC_DF64)
+    wg2 = torch.empty_like(ug_d)
+    sem.sem_ax_assembled(gm, 1.0, 0.0, ug_d, wg2, precision=sem.SEM_PREC_DF64)
     l2g, mask = gm.maps()
     n3 = 512
     rng = np.random.default_rng(5)
@@ -261,6 +287,7 @@ def test_ax_gs_64_full_size_spot_check():
     ref = oracle.ax_local_raw(w.N, D, G, B, u_sub)
     got = host(wL)[idx]
     assert rel_err(got, ref) < RTOL
+    assert rel_err(host(wL2)[idx], ref) < RTOL
     # geometry of the sampled elements
     Gg = host(gm.field("G")).reshape(w.E, 6, n3)[elems].transpose(1, 0, 2).reshape(6, -1)
     assert rel_err(Gg, G) < 1e-11
@@ -275,4 +302,7 @@ def test_ax_gs_64_full_size_spot_check():
     acc = np.zeros(w.n_unique)
     np.add.at(acc, l2g[idx2], w2)
     assert rel_err(host(wg)[gsel], acc[gsel]) < RTOL
+    assert rel_err(host(wg2)[gsel], acc[gsel]) < RTOL
+    # and the two precisions agree everywhere (norm-wise)
+    assert rel_err(host(wg2), host(wg)) < RTOL
     gm.destroy()

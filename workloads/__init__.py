@@ -83,7 +83,11 @@ PMG_48 = BoxWorkload("pmg_48", (48, 48, 48), deform_amp=0.1, deform_seed=DEFORM_
 ADJOINT_16 = BoxWorkload("adjoint_16", (16, 16, 16), periodic=(1, 1, 0),
                          dirichlet=(0, 0, 0, 0, 1, 1))
 
-WORKLOADS = {w.name: w for w in (POISSON_4, AX_GS_64, RBC_32, PMG_48, ADJOINT_16)}
+# the ax_gs_64 construction at 32^3 elements (16.8 M local points, geometry
+# 0.8 GB > L2): the small case used for detailed kernel profiles
+AX_GS_32 = AX_GS_64.with_nel((32, 32, 32), name="ax_gs_32")
+
+WORKLOADS = {w.name: w for w in (POISSON_4, AX_GS_64, RBC_32, PMG_48, ADJOINT_16, AX_GS_32)}
 
 
 def deformation_params(seed: Optional[int]):
