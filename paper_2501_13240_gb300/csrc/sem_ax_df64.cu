@@ -78,7 +78,8 @@ int ensure_tables(int device) {
   return SEM_OK;
 }
 
-// y = M x along one line (M = D, or D^T when TR), df64 in, normalised df64 out
+// y = M x along one line (M = D, or D^T when TR), df64 in, normalised df64
+// out. Compensated dot products (exact products, TwoSum accumulation).
 template <int NP, bool TR>
 __device__ __forceinline__ void line_apply(const float2 (&x)[NP], float2 (&y)[NP]) {
   constexpr int N = NP - 1;
@@ -86,25 +87,31 @@ __device__ __forceinline__ void line_apply(const float2 (&x)[NP], float2 (&y)[NP
     constexpr int H = NP / 2;
     const float2 *A = c_tab + tab_off(NP) + (TR ? 2 * H * H : 0);
     const float2 *Bq = A + H * H;
-    df::Acc xe[H], xo[H];
+    float2 xe[H], xo[H];
 #pragma unroll
     for (int m = 0; m < H; ++m) {
-      df::two_sum(x[m].x, x[N - m].x, xe[m].s, xe[m].c);
-      xe[m].c = df::add(xe[m].c, df::add(x[m].y, x[N - m].y));
-      df::two_sum(x[m].x, -x[N - m].x, xo[m].s, xo[m].c);
-      xo[m].c = df::add(xo[m].c, df::sub(x[m].y, x[N - m].y));
+      float s, e;
+      df::two_sum(x[m].x, x[N - m].x, s, e);
+      xe[m] = make_float2(s, df::add(e, df::add(x[m].y, x[N - m].y)));
+      df::two_sum(x[m].x, -x[N - m].x, s, e);
+      xo[m] = make_float2(s, df::add(e, df::sub(x[m].y, x[N - m].y)));
     }
 #pragma unroll
     for (int i = 0; i < H; ++i) {
-      df::Acc P = df::mul_first(A[i * H].x, A[i * H].y, xe[0].s, xe[0].c);
-      df::Acc Q = df::mul_first(Bq[i * H].x, Bq[i * H].y, xo[0].s, xo[0].c);
+      df::Acc P = df::mul_first(A[i * H].x, A[i * H].y, xe[0].x, xe[0].y);
+      df::Acc Q = df::mul_first(Bq[i * H].x, Bq[i * H].y, xo[0].x, xo[0].y);
 #pragma unroll
       for (int m = 1; m < H; ++m) {
-        df::mac(P, A[i * H + m].x, A[i * H + m].y, xe[m].s, xe[m].c);
-        df::mac(Q, Bq[i * H + m].x, Bq[i * H + m].y, xo[m].s, xo[m].c);
+        df::mac(P, A[i * H + m].x, A[i * H + m].y, xe[m].x, xe[m].y);
+        df::mac(Q, Bq[i * H + m].x, Bq[i * H + m].y, xo[m].x, xo[m].y);
       }
-      y[i] = df::norm(df::sum(P, Q));
-      y[N - i] = df::norm(df::diff(Q, P));
+      float s, e, h, l;
+      df::two_sum(P.s, Q.s, s, e);
+      df::fast_two_sum(s, df::add(df::add(P.c, Q.c), e), h, l);
+      y[i] = make_float2(h, l);
+      df::two_sum(Q.s, -P.s, s, e);
+      df::fast_two_sum(s, df::add(df::sub(Q.c, P.c), e), h, l);
+      y[N - i] = make_float2(h, l);
     }
   } else {
     const float2 *M = c_tab + tab_off(NP) + (TR ? NP * NP : 0);
@@ -113,9 +120,21 @@ __device__ __forceinline__ void line_apply(const float2 (&x)[NP], float2 (&y)[NP
       df::Acc a = df::mul_first(M[i * NP].x, M[i * NP].y, x[0].x, x[0].y);
 #pragma unroll
       for (int m = 1; m < NP; ++m) df::mac(a, M[i * NP + m].x, M[i * NP + m].y, x[m].x, x[m].y);
-      y[i] = df::norm(a);
+      float h, l;
+      df::fast_two_sum(a.s, a.c, h, l);
+      y[i] = make_float2(h, l);
     }
   }
+}
+
+// one output of the metric step: g0 u0 + g1 u1 + g2 u2
+__device__ __forceinline__ float2 metric_row(float2 g0, float2 g1, float2 g2, float2 u0, float2 u1, float2 u2) {
+  df::Acc a = df::mul_first(g0.x, g0.y, u0.x, u0.y);
+  df::mac(a, g1.x, g1.y, u1.x, u1.y);
+  df::mac(a, g2.x, g2.y, u2.x, u2.y);
+  float h, l;
+  df::fast_two_sum(a.s, a.c, h, l);
+  return make_float2(h, l);
 }
 
 template <int NP>
@@ -127,7 +146,7 @@ struct DfCfg {
   static constexpr int TILE = NP * PK;     // float2 per tile
   static constexpr int ELB = (N2 >= 128) ? 1 : (128 / N2 > 4 ? 4 : 128 / N2);
   static constexpr int THREADS = N2 * ELB;
-  static constexpr int SMEM = 3 * TILE * ELB * (int)sizeof(float2);
+  static constexpr int SMEM = 4 * TILE * ELB * (int)sizeof(float2);
 };
 
 template <int NP, bool ASSEMBLED, bool HELM>
@@ -141,104 +160,102 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
   const int le = tid / C::N2;
   const int t = tid - le * C::N2;
   const int a = t % NP, b = t / NP;
-  float2 *U = sm2 + le * 3 * C::TILE;
+  float2 *U = sm2 + le * 4 * C::TILE;
   float2 *R = U + C::TILE;
   float2 *S = R + C::TILE;
-  auto P = [](int i, int j, int k) { return i + C::PJ * j + C::PK * k; };
+  float2 *T = S + C::TILE;
+  const int col = a + C::PJ * b;  // padded offset of the t-column (a, b, 0)
   df::Acc pw = {0.0f, 0.0f};
+  const int64_t estride = (int64_t)gridDim.x * C::ELB;
 
-  for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += (int64_t)gridDim.x * C::ELB) {
-    const int64_t e = e0 + le;
-    const bool act = e < E;
-    // P0: gather and split
-    float2 x[NP];
+  // gather indices of this thread's column, prefetched one element ahead
+  int32_t gi[NP];
+  int64_t e = (int64_t)blockIdx.x * C::ELB + le;
+  if (ASSEMBLED) {
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-      const int p = a + NP * b + C::N2 * k;
-      double v = 0.0;
-      if (act) {
-        if (ASSEMBLED) {
-          const int32_t g = l2gm[e * C::N3 + p];
-          v = (g >= 0) ? u[g] : 0.0;
-        } else {
-          v = u[e * C::N3 + p];
-        }
+    for (int k = 0; k < NP; ++k) gi[k] = (e < E) ? l2gm[e * C::N3 + a + NP * b + C::N2 * k] : -1;
+  }
+  for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += estride) {
+    e = e0 + le;
+    const bool act = e < E;
+    // P0: gather and split the t-column
+    float2 x[NP];
+    {
+      double v[NP];
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const int p = a + NP * b + C::N2 * k;
+        if (ASSEMBLED) v[k] = (gi[k] >= 0) ? u[gi[k]] : 0.0;
+        else v[k] = act ? u[e * C::N3 + p] : 0.0;
       }
-      x[k] = df::from_f64(v);
-      U[P(a, b, k)] = x[k];
+      if (ASSEMBLED) {
+        const int64_t en = e + estride;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) gi[k] = (en < E) ? l2gm[en * C::N3 + a + NP * b + C::N2 * k] : -1;
+      }
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        x[k] = df::from_f64(v[k]);
+        U[col + C::PK * k] = x[k];
+      }
     }
     __syncthreads();
-    // P1: forward contractions
-    float2 ut[NP];
-    line_apply<NP, false>(x, ut);
-    {
+    // P1: forward contractions, r-, s- and t-lines, one loop body
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      const int base = d == 0 ? C::PJ * a + C::PK * b : (d == 1 ? a + C::PK * b : col);
+      const int str = d == 0 ? 1 : (d == 1 ? C::PJ : C::PK);
+      float2 *O = d == 0 ? R : (d == 1 ? S : T);
       float2 y[NP], z[NP];
 #pragma unroll
-      for (int m = 0; m < NP; ++m) y[m] = U[P(m, a, b)];
+      for (int m = 0; m < NP; ++m) y[m] = U[base + str * m];
       line_apply<NP, false>(y, z);
 #pragma unroll
-      for (int m = 0; m < NP; ++m) R[P(m, a, b)] = z[m];
-#pragma unroll
-      for (int m = 0; m < NP; ++m) y[m] = U[P(a, m, b)];
-      line_apply<NP, false>(y, z);
-#pragma unroll
-      for (int m = 0; m < NP; ++m) S[P(a, m, b)] = z[m];
+      for (int m = 0; m < NP; ++m) O[base + str * m] = z[m];
     }
     __syncthreads();
-    // P2: metric on the t-column (a, b, :)
-    float2 wt[NP];
-    const float2 *Ge = Gdf + (act ? e : 0) * 6 * C::N3;
+    // P2: metric on the t-column (a, b, :), in place
+    const float2 *Ge = Gdf + (act ? e : 0) * 6 * C::N3 + a + NP * b;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      const int p = a + NP * b + C::N2 * k;
-      const float2 ur = R[P(a, b, k)], us = S[P(a, b, k)], uu = ut[k];
+      const int q = col + C::PK * k;
+      const float2 ur = R[q], us = S[q], uu = T[q];
       float2 g[6];
 #pragma unroll
-      for (int f = 0; f < 6; ++f) g[f] = act ? Ge[f * C::N3 + p] : make_float2(0.0f, 0.0f);
-      df::Acc r = df::mul_first(g[0].x, g[0].y, ur.x, ur.y);
-      df::mac(r, g[1].x, g[1].y, us.x, us.y);
-      df::mac(r, g[2].x, g[2].y, uu.x, uu.y);
-      df::Acc s = df::mul_first(g[1].x, g[1].y, ur.x, ur.y);
-      df::mac(s, g[3].x, g[3].y, us.x, us.y);
-      df::mac(s, g[4].x, g[4].y, uu.x, uu.y);
-      df::Acc q = df::mul_first(g[2].x, g[2].y, ur.x, ur.y);
-      df::mac(q, g[4].x, g[4].y, us.x, us.y);
-      df::mac(q, g[5].x, g[5].y, uu.x, uu.y);
-      R[P(a, b, k)] = df::norm(r);
-      S[P(a, b, k)] = df::norm(s);
-      wt[k] = df::norm(q);
+      for (int f = 0; f < 6; ++f) g[f] = act ? Ge[f * C::N3 + C::N2 * k] : make_float2(0.0f, 0.0f);
+      R[q] = metric_row(g[0], g[1], g[2], ur, us, uu);
+      S[q] = metric_row(g[1], g[3], g[4], ur, us, uu);
+      T[q] = metric_row(g[2], g[4], g[5], ur, us, uu);
     }
     __syncthreads();
-    // P3: transposed contractions (r- and s-lines in place)
-    float2 zt[NP];
-    line_apply<NP, true>(wt, zt);
-    {
+    // P3: transposed contractions in place (lines of one direction are disjoint)
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      const int base = d == 0 ? C::PJ * a + C::PK * b : (d == 1 ? a + C::PK * b : col);
+      const int str = d == 0 ? 1 : (d == 1 ? C::PJ : C::PK);
+      float2 *O = d == 0 ? R : (d == 1 ? S : T);
       float2 y[NP], z[NP];
 #pragma unroll
-      for (int m = 0; m < NP; ++m) y[m] = R[P(m, a, b)];
+      for (int m = 0; m < NP; ++m) y[m] = O[base + str * m];
       line_apply<NP, true>(y, z);
 #pragma unroll
-      for (int m = 0; m < NP; ++m) R[P(m, a, b)] = z[m];
-#pragma unroll
-      for (int m = 0; m < NP; ++m) y[m] = S[P(a, m, b)];
-      line_apply<NP, true>(y, z);
-#pragma unroll
-      for (int m = 0; m < NP; ++m) S[P(a, m, b)] = z[m];
+      for (int m = 0; m < NP; ++m) O[base + str * m] = z[m];
     }
     __syncthreads();
     // P4: sum the three directions, scale, convert, write
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
+      const int q = col + C::PK * k;
       const int p = a + NP * b + C::N2 * k;
-      const float2 zr = R[P(a, b, k)], zs = S[P(a, b, k)];
-      df::Acc acc = {zt[k].x, zt[k].y};
+      const float2 zr = R[q], zs = S[q], zt = T[q];
+      df::Acc acc = {zt.x, zt.y};
       df::acc_add(acc, zr.x, zr.y);
       df::acc_add(acc, zs.x, zs.y);
-      float2 v = df::norm(acc);
+      float2 v;
+      df::fast_two_sum(acc.s, acc.c, v.x, v.y);
       if (HELM) {
         const float2 Bv = act ? Bdf[e * C::N3 + p] : make_float2(0.0f, 0.0f);
-        df::Acc bu = df::mul_first(Bv.x, Bv.y, x[k].x, x[k].y);
-        const float2 buv = df::norm(bu);
+        const float2 buv = df::norm(df::mul_first(Bv.x, Bv.y, x[k].x, x[k].y));
         df::Acc o = df::mul_first(h1.x, h1.y, v.x, v.y);
         df::mac(o, h2.x, h2.y, buv.x, buv.y);
         v = df::norm(o);
@@ -271,13 +288,35 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
   }
 }
 
+int num_sms(int device) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n < 1) n = 152;
+  return n;
+}
+
+// Fixed grid of the assembled form: every CTA resident at once (one wave),
+// so the p.w partial sums come from a mesh-determined number of CTAs.
+template <int NP>
+int df_grid(const sem_mesh *m, bool assembled, unsigned *grid) {
+  using C = DfCfg<NP>;
+  int64_t blocks = (m->E + C::ELB - 1) / C::ELB;
+  if (assembled) {
+    auto kern = k_ax_df64<NP, true, false>;
+    if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    int per_sm = 0;
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS, C::SMEM));
+    blocks = std::min<int64_t>(blocks, (int64_t)std::max(per_sm, 1) * num_sms(m->device));
+  }
+  *grid = (unsigned)std::max<int64_t>(blocks, 1);
+  return SEM_OK;
+}
+
 template <int NP>
 int launch_np(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial, bool assembled,
               cudaStream_t st) {
   using C = DfCfg<NP>;
-  int64_t blocks = (m->E + C::ELB - 1) / C::ELB;
-  if (assembled) blocks = std::min<int64_t>(blocks, 152 * 16);
-  const unsigned grid = (unsigned)std::max<int64_t>(blocks, 1);
+  unsigned grid;
+  if (int rc = df_grid<NP>(m, assembled, &grid)) return rc;
   const float2 h1d = split_host(h1), h2d = split_host(h2);
   const bool helm = !(h1 == 1.0 && h2 == 0.0);
 #define LAUNCH(ASM, HLM)                                                                                    \
@@ -302,20 +341,19 @@ int launch_np(const sem_mesh *m, double h1, double h2, const double *u, double *
 }  // namespace
 
 int sem_df64_grid(const sem_mesh *m) {
-  // must match launch_np's assembled grid for every NP (used for partial sums)
-  int elb;
+  unsigned grid = 0;
+  int rc = SEM_OK;
   switch (m->n) {
-#define CASE(NPV)                 \
-  case NPV:                       \
-    elb = DfCfg<NPV>::ELB;        \
+#define CASE(NPV)                              \
+  case NPV:                                    \
+    rc = df_grid<NPV>(m, true, &grid);         \
     break;
     CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
 #undef CASE
     default:
       return 0;
   }
-  int64_t blocks = std::min<int64_t>((m->E + elb - 1) / elb, 152 * 16);
-  return (int)std::max<int64_t>(blocks, 1);
+  return rc == SEM_OK ? (int)grid : 0;
 }
 
 int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
