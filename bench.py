@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"])
+    ap.add_argument("--once", default="",
+                    help="profiling mode: comma list of kernels to launch once each on the workload "
+                         "(local_df64, asm_df64, local_fp64, asm_fp64, gs), then exit")
     return ap.parse_args()
 
 
@@ -174,6 +177,29 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+def run_once(sem, mesh, u, names):
+    """Launch each named kernel once (for ncu captures of single launches)."""
+    import torch
+    wg = torch.zeros_like(u)
+    uL = torch.empty(mesh.n_local, dtype=torch.float64, device="cuda")
+    sem.sem_scatter(mesh, u, uL)
+    wL = torch.empty_like(uL)
+    P = {"df64": sem.SEM_PREC_DF64, "fp64": sem.SEM_PREC_FP64}
+    for name in names:
+        kind, prec = name.split("_")
+        if kind == "local":
+            sem.sem_ax_apply(mesh, 1.0, 0.0, uL, wL, precision=P[prec])
+        elif kind == "asm":
+            sem.sem_ax_assembled_add(mesh, 1.0, 0.0, u, wg, precision=P[prec])
+        elif kind == "gs":  # name "gs_x"
+            sem.sem_gs_op(mesh, wL, True)
+        else:
+            raise ValueError(name)
+    torch.cuda.synchronize()
+    print(json.dumps({"once": names, "workload": "ok"}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -207,6 +233,8 @@ def main():
     ug_host = workloads.unique_field(mesh.n_unique)
     u = torch.from_numpy(ug_host).cuda()
     wg = torch.empty_like(u)
+    if args.once:
+        return run_once(sem, mesh, u, args.once.split(","))
     precs = {"df64": sem.SEM_PREC_DF64, "fp64": sem.SEM_PREC_FP64}
     head = args.precision
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
