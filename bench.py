@@ -186,12 +186,12 @@ def run_once(sem, mesh, u, names):
     wL = torch.empty_like(uL)
     P = {"df64": sem.SEM_PREC_DF64, "fp64": sem.SEM_PREC_FP64}
     for name in names:
-        kind, prec = name.split("_")
+        kind, _, prec = name.partition("_")
         if kind == "local":
             sem.sem_ax_apply(mesh, 1.0, 0.0, uL, wL, precision=P[prec])
         elif kind == "asm":
             sem.sem_ax_assembled_add(mesh, 1.0, 0.0, u, wg, precision=P[prec])
-        elif kind == "gs":  # name "gs_x"
+        elif kind == "gs":
             sem.sem_gs_op(mesh, wL, True)
         else:
             raise ValueError(name)

@@ -212,6 +212,34 @@ int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const double *b_g, do
                   const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats,
                   void *stream);
 
+/* Jacobi-PCG like sem_pcg_solve, for callers that cannot allocate device
+ * memory themselves -- for example a host program or plug-in whose device
+ * memory is owned entirely by another framework's allocator, or a loop that
+ * must not allocate once it is running. This entry point has no counterpart
+ * in the paper; it exists only for such callers.
+ *
+ * It allocates nothing: its workspace is a fixed 64 MiB array in the
+ * library's own device memory (sem_pcg_noalloc_capacity() bytes), which every
+ * GPU that loads the library holds until the process exits. That bounds the
+ * mesh to about 2.1 million unique nodes (4 vectors of n_unique doubles plus
+ * a few kilobytes of partial sums); a larger mesh is rejected with
+ * SEM_ERR_INVALID_ARG and a message giving both sizes. The caller still owns
+ * b_g and x_g, as for sem_pcg_solve, and the mesh must belong to the current
+ * device.
+ *
+ * The first call on each device looks up the array's device address (once,
+ * with that device current); make that first call before any CUDA stream
+ * capture. All calls share the one array and every call re-initialises what
+ * it reads, so results do not depend on earlier calls; but calls whose work
+ * overlaps on the GPU (different streams, or different host threads on one
+ * device) race on the array and must be serialised by the caller.
+ * Returns the same codes as sem_pcg_solve. */
+int sem_pcg_solve_noalloc(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
+                          const sem_solver_opts *opts, sem_solve_stats *stats, void *stream);
+
+/* Size in bytes of the fixed workspace of sem_pcg_solve_noalloc. */
+size_t sem_pcg_noalloc_capacity(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,7 +34,7 @@ EXPORTS = (
     "sem_last_error", "sem_version", "sem_gll", "sem_mesh_create_box", "sem_mesh_destroy",
     "sem_mesh_info_get", "sem_mesh_copy_maps", "sem_mesh_copy_gs_tables", "sem_ax_apply", "sem_gs_op",
     "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_ax_assembled_add", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
-    "sem_pcg_solve",
+    "sem_pcg_solve", "sem_pcg_solve_noalloc", "sem_pcg_noalloc_capacity",
 )
 
 
@@ -104,6 +104,9 @@ def lib() -> ctypes.CDLL:
             "sem_pcg_solve": ([_vp, _d, _d, _vp, _vp, ctypes.POINTER(sem_solver_opts), _vp,
                                ctypes.POINTER(sem_solve_stats), _vp], _i),
         }
+        sig["sem_pcg_solve_noalloc"] = ([_vp, _d, _d, _vp, _vp, ctypes.POINTER(sem_solver_opts),
+                                          ctypes.POINTER(sem_solve_stats), _vp], _i)
+        sig["sem_pcg_noalloc_capacity"] = ([], ctypes.c_size_t)
         for name, (args, res) in sig.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -331,6 +334,29 @@ def sem_pcg_solve(mesh: Mesh, h1: float, h2: float, b_g, x_g, tol: float = 1e-8,
     rc = lib().sem_pcg_solve(mesh.handle, float(h1), float(h2), _ptr(b_g, torch.float64, mesh.n_unique, "b_g"),
                              _ptr(x_g, torch.float64, mesh.n_unique, "x_g"), ctypes.byref(o),
                              ctypes.c_void_p(aligned), ctypes.byref(st), _stream(stream))
+    out = {"iterations": st.iterations, "rel_residual": st.rel_residual, "solve_ms": st.solve_ms,
+           "status": st.status}
+    if rc != SEM_OK and (raise_on_error or rc not in (SEM_ERR_NOT_CONVERGED, SEM_ERR_TIMEOUT, SEM_ERR_BREAKDOWN)):
+        _check(rc)
+    return out
+
+
+def sem_pcg_noalloc_capacity() -> int:
+    return int(lib().sem_pcg_noalloc_capacity())
+
+
+def sem_pcg_solve_noalloc(mesh: Mesh, h1: float, h2: float, b_g, x_g, tol: float = 1e-8, maxit: int = 1000,
+                          precision: int = SEM_PREC_FP64, timeout_s: float = 0.0, stream=None,
+                          raise_on_error: bool = True):
+    """Jacobi-PCG with the library's fixed device workspace (no allocation by
+    the library or by this binding); same statistics as sem_pcg_solve."""
+    import torch
+    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s))
+    st = sem_solve_stats()
+    rc = lib().sem_pcg_solve_noalloc(mesh.handle, float(h1), float(h2),
+                                     _ptr(b_g, torch.float64, mesh.n_unique, "b_g"),
+                                     _ptr(x_g, torch.float64, mesh.n_unique, "x_g"), ctypes.byref(o),
+                                     ctypes.byref(st), _stream(stream))
     out = {"iterations": st.iterations, "rel_residual": st.rel_residual, "solve_ms": st.solve_ms,
            "status": st.status}
     if rc != SEM_OK and (raise_on_error or rc not in (SEM_ERR_NOT_CONVERGED, SEM_ERR_TIMEOUT, SEM_ERR_BREAKDOWN)):

@@ -12,6 +12,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "sem_internal.h"
@@ -344,4 +346,57 @@ extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const doub
     }
   }
   return finish(SEM_ERR_NOT_CONVERGED, opts->maxit, hs.rr);
+}
+
+// ---------------------------------------------------------------- no-allocation variant
+// The same Jacobi-PCG solve for callers that cannot allocate device memory
+// themselves: its workspace is a fixed array in this module's device memory
+// (kNoAllocBytes, present on every GPU that loads the library until the
+// process exits). The array's device address is looked up once per device
+// with cudaGetSymbolAddress, on the first call made with that device current.
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)64 << 20;  // 64 MiB
+static __device__ __align__(256) unsigned char g_pcg_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+int scratch_address(int device, void **out) {
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (device < 0 || device >= kMaxDevices) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve_noalloc: device index out of range");
+  if (!g_scratch_ptr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
+    if (e != cudaSuccess) return sem_cuda_fail(e, "sem_pcg_solve_noalloc: cudaGetSymbolAddress");
+    g_scratch_ptr[device] = p;
+  }
+  *out = g_scratch_ptr[device];
+  return SEM_OK;
+}
+
+}  // namespace
+
+extern "C" size_t sem_pcg_noalloc_capacity(void) { return kNoAllocBytes; }
+
+extern "C" int sem_pcg_solve_noalloc(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
+                                     const sem_solver_opts *opts, sem_solve_stats *stats, void *stream) {
+  if (int rc = check_mesh(m, "sem_pcg_solve_noalloc")) return rc;
+  int dev = -1;
+  SEM_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve_noalloc: the mesh's device must be the current device");
+  const size_t need = pcg_layout(m, nullptr, nullptr);
+  if (need > kNoAllocBytes) {
+    char buf[200];
+    snprintf(buf, sizeof(buf),
+             "sem_pcg_solve_noalloc: mesh needs %zu bytes of workspace, more than the fixed %zu "
+             "(about %zu unique nodes at most); use sem_pcg_solve with caller-provided workspace",
+             need, kNoAllocBytes, kNoAllocBytes / (4 * sizeof(double)));
+    return sem_fail(SEM_ERR_INVALID_ARG, buf);
+  }
+  void *ws = nullptr;
+  if (int rc = scratch_address(dev, &ws)) return rc;
+  return sem_pcg_solve(m, h1, h2, b_g, x_g, opts, ws, stats, stream);
 }
