@@ -110,6 +110,10 @@ typedef struct {
   int maxit;       /* > 0 */
   int precision;   /* SEM_PREC_* */
   double timeout_s;/* <= 0: no limit */
+  int mask_mode;   /* 0: solve on the free nodes of the mesh's Dirichlet mask;
+                      1: no mask -- the pure-Neumann (singular) operator, for
+                      the pressure Poisson problem; b must be orthogonal to the
+                      constant vector and x is determined up to a constant */
 } sem_solver_opts;
 
 typedef struct {
@@ -211,6 +215,60 @@ int sem_pcg_workspace_bytes(const sem_mesh *m, size_t *bytes);
 int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
                   const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats,
                   void *stream);
+
+/* ------------------------------------------------------------------------
+ * Rayleigh-Benard convection time step (Boussinesq equations, Sec. 4.1,
+ * Eqs. (1)-(3); periodic x, y and isothermal no-slip plates, Sec. 4.4).
+ * The paper names no splitting scheme; the step is the BDF2/EXT2 high-order
+ * splitting in weak form:
+ *   explicit (t^n, GLL collocation): N_T = -u.grad T, N_u = -(u.grad)u + T z,
+ *     wall term W = nu sum_walls (phi n . curl curl u), EXT X* = a1 X^n + a2 X^{n-1};
+ *   T:  (b0/dt B + kappa A) T^{n+1} = Q^T B[(b1 T^n + b2 T^{n-1})/dt + N_T*],
+ *       T = 1 - z/Lz on the plates (lifting), kappa = 1/sqrt(Ra Pr);
+ *   p:  A p = Q^T[(grad phi, f*)] - W*, f* = (b1 u^n + b2 u^{n-1})/dt + N_u*,
+ *       pure Neumann, right-hand side and p with zero mean;
+ *   u:  (b0/dt B + nu A) u^{n+1} = M Q^T[B (f* - grad p)], u = 0 on the plates,
+ *       nu = sqrt(Pr/Ra).
+ * The first step uses history levels equal to the initial state. Explicit
+ * terms are binary64 kernels; the five solves are sem_pcg_solve (x0 = 0).
+ * ------------------------------------------------------------------------ */
+typedef struct sem_rbc sem_rbc; /* opaque; owns its fields and scratch */
+
+typedef struct {
+  double Ra, Pr, dt;
+  double tol;     /* relative residual of every solve */
+  int maxit;      /* per solve */
+  int precision;  /* SEM_PREC_* of the operator inside the solves */
+} sem_rbc_params;
+
+typedef struct {
+  int step;                  /* steps completed */
+  int iters_T, iters_p, iters_u[3];
+  double step_ms;            /* host wall time of the step */
+  int status;                /* SEM_OK or SEM_ERR_NOT_CONVERGED (a solve hit maxit) */
+} sem_step_stats;
+
+typedef struct {
+  double *u, *v, *w, *T, *p; /* device U-vectors of the current state (owned by the handle) */
+  int64_t n_unique;
+  int step;
+} sem_rbc_view;
+
+/* Create the state on mesh m (which must outlive it): u = 0, T = 1 - z/Lz
+ * plus T_pert_g (device U-vector, added on the free nodes; NULL for none),
+ * p = 0. The mesh must have Dirichlet plates at z = 0 and z = Lz and be
+ * periodic (or walled on both sides) in x and y. Synchronises the stream. */
+int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, const double *T_pert_g, void *stream,
+                   sem_rbc **out);
+
+/* Advance one BDF2/EXT2 step; fills *st. Returns SEM_OK, SEM_ERR_NOT_CONVERGED
+ * (the step completed but a solve hit maxit) or an error. */
+int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *st, void *stream);
+
+/* Device views of the current fields (valid until the next step or destroy). */
+int sem_rbc_fields(const sem_rbc *s, sem_rbc_view *view);
+
+int sem_rbc_destroy(sem_rbc *s);
 
 /* Jacobi-PCG like sem_pcg_solve, for callers that cannot allocate device
  * memory themselves -- for example a host program or plug-in whose device

@@ -79,6 +79,12 @@ def lib():
         L.or_gather_sum.restype = None
         L.or_scatter.argtypes = [ctypes.c_int64, _i64p, _dp, _dp]
         L.or_scatter.restype = None
+        L.or_jacobian.argtypes = [ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+        L.or_jacobian.restype = None
+        L.or_ref_grad.argtypes = [ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp]
+        L.or_ref_grad.restype = None
+        L.or_ref_div_t.argtypes = [ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp]
+        L.or_ref_div_t.restype = None
         L.or_num_threads.argtypes = []
         L.or_num_threads.restype = ctypes.c_int
         _lib = L

@@ -357,3 +357,71 @@ int or_num_threads(void) { return omp_get_max_threads(); }
 #else
 int or_num_threads(void) { return 1; }
 #endif
+
+/* Jacobian of the isoparametric map at every node: J[(3c + a) nL + l] =
+ * dx_c/dr_a (D applied to the node coordinates, as in or_geom). */
+void or_jacobian(int64_t E, int N, const double *D, const double *X, const double *Y, const double *Z,
+                 double *J) {
+  const int n = N + 1;
+  const int64_t nL = E * n * n * n;
+  const double *xc[3] = {X, Y, Z};
+  for (int64_t e = 0; e < E; ++e)
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          int64_t base = e * n * n * n, l = base + i + n * j + n * n * k;
+          for (int c = 0; c < 3; ++c) {
+            double dr = 0, ds = 0, dt = 0;
+            for (int m = 0; m < n; ++m) {
+              dr += D[i * n + m] * xc[c][base + m + n * j + n * n * k];
+              ds += D[j * n + m] * xc[c][base + i + n * m + n * n * k];
+              dt += D[k * n + m] * xc[c][base + i + n * j + n * n * m];
+            }
+            J[(3 * c + 0) * nL + l] = dr;
+            J[(3 * c + 1) * nL + l] = ds;
+            J[(3 * c + 2) * nL + l] = dt;
+          }
+        }
+}
+
+/* Reference-space derivatives of an E-vector: d[a nL + l] = (D_a f)_l,
+ * a = r, s, t. */
+void or_ref_grad(int64_t E, int N, const double *D, const double *f, double *d) {
+  const int n = N + 1;
+  const int64_t nL = E * n * n * n;
+  for (int64_t e = 0; e < E; ++e)
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          int64_t base = e * n * n * n, l = base + i + n * j + n * n * k;
+          double dr = 0, ds = 0, dt = 0;
+          for (int m = 0; m < n; ++m) {
+            dr += D[i * n + m] * f[base + m + n * j + n * n * k];
+            ds += D[j * n + m] * f[base + i + n * m + n * n * k];
+            dt += D[k * n + m] * f[base + i + n * j + n * n * m];
+          }
+          d[0 * nL + l] = dr;
+          d[1 * nL + l] = ds;
+          d[2 * nL + l] = dt;
+        }
+}
+
+/* Transposed reference derivatives: out_l = sum_a (D_a^T v_a)_l for three
+ * E-vectors v_r, v_s, v_t stored as v[a nL + l]. */
+void or_ref_div_t(int64_t E, int N, const double *D, const double *v, double *out) {
+  const int n = N + 1;
+  const int64_t nL = E * n * n * n;
+  for (int64_t e = 0; e < E; ++e)
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          int64_t base = e * n * n * n, l = base + i + n * j + n * n * k;
+          double s = 0;
+          for (int m = 0; m < n; ++m) {
+            s += D[m * n + i] * v[0 * nL + base + m + n * j + n * n * k];
+            s += D[m * n + j] * v[1 * nL + base + i + n * m + n * n * k];
+            s += D[m * n + k] * v[2 * nL + base + i + n * j + n * n * m];
+          }
+          out[l] = s;
+        }
+}

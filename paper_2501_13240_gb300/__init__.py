@@ -35,6 +35,7 @@ EXPORTS = (
     "sem_mesh_info_get", "sem_mesh_copy_maps", "sem_mesh_copy_gs_tables", "sem_ax_apply", "sem_gs_op",
     "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_ax_assembled_add", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
     "sem_pcg_solve", "sem_pcg_solve_noalloc", "sem_pcg_noalloc_capacity",
+    "sem_rbc_create", "sem_bdf_ext_step", "sem_rbc_fields", "sem_rbc_destroy",
 )
 
 
@@ -61,12 +62,27 @@ class sem_mesh_info(ctypes.Structure):
 
 class sem_solver_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
-                ("timeout_s", ctypes.c_double)]
+                ("timeout_s", ctypes.c_double), ("mask_mode", ctypes.c_int)]
 
 
 class sem_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("status", ctypes.c_int)]
+
+
+class sem_rbc_params(ctypes.Structure):
+    _fields_ = [("Ra", ctypes.c_double), ("Pr", ctypes.c_double), ("dt", ctypes.c_double), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class sem_step_stats(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int), ("iters_T", ctypes.c_int), ("iters_p", ctypes.c_int),
+                ("iters_u", ctypes.c_int * 3), ("step_ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class sem_rbc_view(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p), ("T", ctypes.c_void_p),
+                ("p", ctypes.c_void_p), ("n_unique", ctypes.c_int64), ("step", ctypes.c_int)]
 
 
 _lib = None
@@ -107,6 +123,10 @@ def lib() -> ctypes.CDLL:
         sig["sem_pcg_solve_noalloc"] = ([_vp, _d, _d, _vp, _vp, ctypes.POINTER(sem_solver_opts),
                                           ctypes.POINTER(sem_solve_stats), _vp], _i)
         sig["sem_pcg_noalloc_capacity"] = ([], ctypes.c_size_t)
+        sig["sem_rbc_create"] = ([_vp, ctypes.POINTER(sem_rbc_params), _vp, _vp, ctypes.POINTER(_vp)], _i)
+        sig["sem_bdf_ext_step"] = ([_vp, ctypes.POINTER(sem_step_stats), _vp], _i)
+        sig["sem_rbc_fields"] = ([_vp, ctypes.POINTER(sem_rbc_view)], _i)
+        sig["sem_rbc_destroy"] = ([_vp], _i)
         for name, (args, res) in sig.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -315,7 +335,7 @@ def sem_pcg_workspace_bytes(mesh: Mesh) -> int:
 
 def sem_pcg_solve(mesh: Mesh, h1: float, h2: float, b_g, x_g, tol: float = 1e-8, maxit: int = 1000,
                   precision: int = SEM_PREC_FP64, timeout_s: float = 0.0, workspace=None, stream=None,
-                  raise_on_error: bool = True):
+                  raise_on_error: bool = True, mask_mode: int = 0):
     """Jacobi-PCG; returns a dict of the solve statistics. ``workspace`` is a
     uint8 CUDA tensor of at least sem_pcg_workspace_bytes(mesh) bytes (allocated
     here through torch when None)."""
@@ -329,7 +349,7 @@ def sem_pcg_solve(mesh: Mesh, h1: float, h2: float, b_g, x_g, tol: float = 1e-8,
     aligned = (base + 255) & ~255
     if aligned + need > base + workspace.numel():
         raise ValueError("workspace too small after 256-byte alignment (allocate 256 extra bytes)")
-    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s))
+    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s), int(mask_mode))
     st = sem_solve_stats()
     rc = lib().sem_pcg_solve(mesh.handle, float(h1), float(h2), _ptr(b_g, torch.float64, mesh.n_unique, "b_g"),
                              _ptr(x_g, torch.float64, mesh.n_unique, "x_g"), ctypes.byref(o),
@@ -351,7 +371,7 @@ def sem_pcg_solve_noalloc(mesh: Mesh, h1: float, h2: float, b_g, x_g, tol: float
     """Jacobi-PCG with the library's fixed device workspace (no allocation by
     the library or by this binding); same statistics as sem_pcg_solve."""
     import torch
-    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s))
+    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s), 0)
     st = sem_solve_stats()
     rc = lib().sem_pcg_solve_noalloc(mesh.handle, float(h1), float(h2),
                                      _ptr(b_g, torch.float64, mesh.n_unique, "b_g"),
@@ -362,3 +382,49 @@ def sem_pcg_solve_noalloc(mesh: Mesh, h1: float, h2: float, b_g, x_g, tol: float
     if rc != SEM_OK and (raise_on_error or rc not in (SEM_ERR_NOT_CONVERGED, SEM_ERR_TIMEOUT, SEM_ERR_BREAKDOWN)):
         _check(rc)
     return out
+
+
+class RBC:
+    """Owns a ``sem_rbc`` handle (Rayleigh-Benard BDF2/EXT2 state on a mesh)."""
+
+    def __init__(self, handle, mesh: Mesh):
+        self._h = handle
+        self.mesh = mesh  # keeps the mesh alive
+
+    def destroy(self):
+        if self._h is not None:
+            lib().sem_rbc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sem_rbc_create(mesh: Mesh, Ra: float, Pr: float, dt: float, tol: float = 1e-10, maxit: int = 5000,
+                   precision: int = SEM_PREC_DF64, T_pert=None, stream=None) -> RBC:
+    import torch
+    prm = sem_rbc_params(float(Ra), float(Pr), float(dt), float(tol), int(maxit), int(precision))
+    pert = _ptr(T_pert, torch.float64, mesh.n_unique, "T_pert") if T_pert is not None else None
+    h = ctypes.c_void_p()
+    _check(lib().sem_rbc_create(mesh.handle, ctypes.byref(prm), pert, _stream(stream), ctypes.byref(h)))
+    return RBC(h, mesh)
+
+
+def sem_bdf_ext_step(s: RBC, stream=None, raise_on_error: bool = True) -> dict:
+    st = sem_step_stats()
+    rc = lib().sem_bdf_ext_step(s._h, ctypes.byref(st), _stream(stream))
+    if rc != SEM_OK and (raise_on_error or rc != SEM_ERR_NOT_CONVERGED):
+        _check(rc)
+    return {"step": st.step, "iters_T": st.iters_T, "iters_p": st.iters_p, "iters_u": list(st.iters_u),
+            "step_ms": st.step_ms, "status": st.status}
+
+
+def sem_rbc_fields(s: RBC) -> dict:
+    """Copies of the current fields (u, v, w, T, p) as torch tensors."""
+    v = sem_rbc_view()
+    _check(lib().sem_rbc_fields(s._h, ctypes.byref(v)))
+    n = int(v.n_unique)
+    return {k: _device_copy(getattr(v, k), n) for k in ("u", "v", "w", "T", "p")}

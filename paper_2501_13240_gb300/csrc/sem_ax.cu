@@ -128,11 +128,11 @@ __global__ void __launch_bounds__(AxCfg<NP>::THREADS)
 
 template <int NP, bool ASSEMBLED>
 int launch_fp64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
-                unsigned grid, cudaStream_t st) {
+                unsigned grid, cudaStream_t st, const int32_t *map) {
   using C = AxCfg<NP>;
   auto kern = k_ax_fp64<NP, ASSEMBLED>;
   if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-  kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->dD, m->G, m->B, h1, h2, u, w, m->l2gm, pw_partial);
+  kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->dD, m->G, m->B, h1, h2, u, w, map, pw_partial);
   SEM_LAUNCH_CHECK("k_ax_fp64");
   return SEM_OK;
 }
@@ -149,19 +149,19 @@ unsigned ax_grid(const sem_mesh *m, bool assembled) {
 
 template <int NP>
 int dispatch_np(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
-                bool assembled, int precision, cudaStream_t st) {
-  if (precision == SEM_PREC_DF64) return sem_launch_ax_df64(m, h1, h2, u, w, pw_partial, assembled, st);
+                bool assembled, int precision, cudaStream_t st, const int32_t *map) {
+  if (precision == SEM_PREC_DF64) return sem_launch_ax_df64(m, h1, h2, u, w, pw_partial, assembled, st, map);
   unsigned grid = ax_grid<NP>(m, assembled);
-  if (assembled) return launch_fp64<NP, true>(m, h1, h2, u, w, pw_partial, grid, st);
-  return launch_fp64<NP, false>(m, h1, h2, u, w, nullptr, grid, st);
+  if (assembled) return launch_fp64<NP, true>(m, h1, h2, u, w, pw_partial, grid, st, map);
+  return launch_fp64<NP, false>(m, h1, h2, u, w, nullptr, grid, st, map);
 }
 
 int dispatch(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial, bool assembled,
-             int precision, cudaStream_t st) {
+             int precision, cudaStream_t st, const int32_t *map) {
   switch (m->n) {
 #define CASE(NPV) \
   case NPV:       \
-    return dispatch_np<NPV>(m, h1, h2, u, w, pw_partial, assembled, precision, st);
+    return dispatch_np<NPV>(m, h1, h2, u, w, pw_partial, assembled, precision, st, map);
     CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
 #undef CASE
     default:
@@ -198,12 +198,12 @@ __global__ void k_diag_local(int n, int64_t E, const double *__restrict__ Dg, co
 
 int sem_launch_ax_local(const sem_mesh *m, double h1, double h2, const double *u, double *w, int precision,
                         cudaStream_t st) {
-  return dispatch(m, h1, h2, u, w, nullptr, false, precision, st);
+  return dispatch(m, h1, h2, u, w, nullptr, false, precision, st, m->l2gm);
 }
 
 int sem_launch_ax_assembled(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
-                            double *pw_partial, int precision, cudaStream_t st) {
-  return dispatch(m, h1, h2, u_g, w_g, pw_partial, true, precision, st);
+                            double *pw_partial, int precision, cudaStream_t st, const int32_t *map) {
+  return dispatch(m, h1, h2, u_g, w_g, pw_partial, true, precision, st, map ? map : m->l2gm);
 }
 
 int sem_ax_assembled_blocks(const sem_mesh *m, int precision) {

@@ -313,7 +313,7 @@ int df_grid(const sem_mesh *m, bool assembled, unsigned *grid) {
 
 template <int NP>
 int launch_np(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial, bool assembled,
-              cudaStream_t st) {
+              cudaStream_t st, const int32_t *map) {
   using C = DfCfg<NP>;
   unsigned grid;
   if (int rc = df_grid<NP>(m, assembled, &grid)) return rc;
@@ -324,7 +324,7 @@ int launch_np(const sem_mesh *m, double h1, double h2, const double *u, double *
     auto kern = k_ax_df64<NP, ASM, HLM>;                                                                    \
     if (C::SMEM > 48 * 1024)                                                                                \
       SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));          \
-    kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->Gdf, m->Bdf, h1d, h2d, u, w, m->l2gm, pw_partial);     \
+    kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->Gdf, m->Bdf, h1d, h2d, u, w, map, pw_partial);          \
   } while (0)
   if (assembled) {
     if (helm) LAUNCH(true, true);
@@ -357,12 +357,12 @@ int sem_df64_grid(const sem_mesh *m) {
 }
 
 int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
-                       bool assembled, cudaStream_t st) {
+                       bool assembled, cudaStream_t st, const int32_t *map) {
   if (int rc = ensure_tables(m->device)) return rc;
   switch (m->n) {
 #define CASE(NPV) \
   case NPV:       \
-    return launch_np<NPV>(m, h1, h2, u, w, pw_partial, assembled, st);
+    return launch_np<NPV>(m, h1, h2, u, w, pw_partial, assembled, st, map);
     CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
 #undef CASE
     default:

@@ -62,12 +62,14 @@ int sem_gll_host(int N, double *xi, double *rho, double *D);
 // kernels launched from other translation units
 int sem_launch_ax_local(const sem_mesh *m, double h1, double h2, const double *u, double *w,
                         int precision, cudaStream_t st);
+// map: local-to-unique map to gather/scatter through (nullptr: the masked
+// map l2gm; m->l2g for the unmasked operator)
 int sem_launch_ax_assembled(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
-                            double *pw_partial, int precision, cudaStream_t st);
+                            double *pw_partial, int precision, cudaStream_t st, const int32_t *map = nullptr);
 int sem_ax_assembled_blocks(const sem_mesh *m, int precision);
 int sem_df64_grid(const sem_mesh *m);
 int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
-                       bool assembled, cudaStream_t st);
+                       bool assembled, cudaStream_t st, const int32_t *map);
 int sem_launch_gs(const sem_mesh *m, double *v, int apply_mask, cudaStream_t st);
 int sem_launch_gather(const sem_mesh *m, const double *vL, double *vg, cudaStream_t st);
 int sem_launch_scatter(const sem_mesh *m, const double *vg, double *vL, cudaStream_t st);

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kUpdThreads)
 __global__ void k_jacobi_inv(int n, int64_t nU, const int32_t *__restrict__ off, const int32_t *__restrict__ perm,
                              const uint8_t *__restrict__ mask, const double *__restrict__ Dg,
                              const double *__restrict__ G, const double *__restrict__ B, double h1, double h2,
-                             double *__restrict__ dinv) {
+                             int use_mask, double *__restrict__ dinv) {
   const int n3 = n * n * n;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
     double tot = 0.0;
@@ -169,7 +169,7 @@ __global__ void k_jacobi_inv(int n, int64_t nU, const int32_t *__restrict__ off,
       s += 2.0 * dj * dk * Ge[4 * n3 + q];
       tot += h1 * s + h2 * B[l];
     }
-    dinv[g] = mask[g] ? 1.0 / tot : 0.0;
+    dinv[g] = (!use_mask || mask[g]) ? 1.0 / tot : 0.0;
   }
 }
 
@@ -267,7 +267,7 @@ extern "C" int sem_jacobi_inv(const sem_mesh *m, double h1, double h2, double *d
   if (int rc = check_mesh(m, "sem_jacobi_inv")) return rc;
   if (bad_ptr(dinv_g)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_jacobi_inv: NULL or misaligned vector");
   k_jacobi_inv<<<grid_for(m->n_unique, 256), 256, 0, as_stream(stream)>>>(
-      m->n, m->n_unique, m->gs_off, m->gs_perm, m->mask, m->dD, m->G, m->B, h1, h2, dinv_g);
+      m->n, m->n_unique, m->gs_off, m->gs_perm, m->mask, m->dD, m->G, m->B, h1, h2, 1, dinv_g);
   SEM_LAUNCH_CHECK("k_jacobi_inv");
   return SEM_OK;
 }
@@ -289,6 +289,7 @@ extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const doub
   if (!(opts->tol >= 0.0) || opts->maxit < 1) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: bad tol or maxit");
   if (opts->precision != SEM_PREC_FP64 && opts->precision != SEM_PREC_DF64)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: unknown precision");
+  if (opts->mask_mode != 0 && opts->mask_mode != 1) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: bad mask_mode");
   if (!(h1 >= 0.0) || !(h2 >= 0.0) || (h1 == 0.0 && h2 == 0.0))
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: need h1 >= 0, h2 >= 0, not both zero");
   const auto t0 = std::chrono::steady_clock::now();
@@ -303,7 +304,11 @@ extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const doub
   stats->status = SEM_OK;
 
   int rc;
-  if ((rc = sem_jacobi_inv(m, h1, h2, wk.dinv, stream)) != SEM_OK) return rc;
+  const bool masked = opts->mask_mode == 0;
+  const int32_t *map = masked ? m->l2gm : m->l2g;
+  k_jacobi_inv<<<grid_for(m->n_unique, 256), 256, 0, st>>>(m->n, m->n_unique, m->gs_off, m->gs_perm, m->mask, m->dD,
+                                                            m->G, m->B, h1, h2, masked ? 1 : 0, wk.dinv);
+  SEM_LAUNCH_CHECK("k_jacobi_inv");
   k_pcg_init<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, x_g, wk.r, wk.p, wk.dinv, wk.part_a, wk.part_b);
   k_pcg_init_finish<<<1, kUpdThreads, 0, st>>>(wk.part_a, wk.part_b, kUpdBlocks, wk.s);
   SEM_LAUNCH_CHECK("k_pcg_init");
@@ -330,7 +335,8 @@ extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const doub
   for (int it = 1; it <= opts->maxit; ++it) {
     const int par = (it - 1) & 1;
     SEM_CUDA(cudaMemsetAsync(wk.w, 0, sizeof(double) * nU, st));
-    if ((rc = sem_launch_ax_assembled(m, h1, h2, wk.p, wk.w, wk.pw_part, opts->precision, st)) != SEM_OK) return rc;
+    if ((rc = sem_launch_ax_assembled(m, h1, h2, wk.p, wk.w, wk.pw_part, opts->precision, st, map)) != SEM_OK)
+      return rc;
     k_pcg_update1<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, x_g, wk.r, wk.p, wk.w, wk.dinv, wk.pw_part, n_pw, wk.s, par,
                                                       wk.part_a, wk.part_b);
     k_pcg_update2<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, wk.r, wk.p, wk.dinv, wk.part_a, wk.part_b, kUpdBlocks, wk.s,

@@ -1,0 +1,569 @@
+// One BDF2/EXT2 time step of the Boussinesq equations (Sec. 4.1, Eqs. (1)-(3))
+// for Rayleigh-Benard convection: periodic x, y; isothermal no-slip plates
+// (Sec. 4.4). The paper gives no splitting scheme (it names NekRS and its
+// pressure Poisson solve, Sec. 2.2); this follows the high-order splitting of
+// the spectral-element textbook it cites, in weak form, step n -> n+1:
+//   explicit terms at t^n collocated at the GLL nodes: N_T = -u.grad T,
+//     N_u = -(u.grad)u + T z, wall term W = nu sum_walls (phi n.curl curl u)
+//     with element-local derivatives; EXT2 X* = 2 X^n - X^{n-1};
+//   T:  (b0/dt B + kappa A) T = Q^T B[(2T^n - T^{n-1}/2)/dt + N_T*], lifting 1 - z/Lz;
+//   p:  A p = Q^T[sum_a D_a^T (B sum_c dr_a/dx_c f*_c)] - W*, means removed,
+//       f* = (2u^n - u^{n-1}/2)/dt + N_u*;
+//   u:  (b0/dt B + nu A) u_c = M Q^T[B f*_c - B dp/dx_c];
+// BDF2 (3/2, 2, -1/2), EXT2 (2, -1); the first step is BDF1/EXT1 ((1, 1, 0), (1, 0)),
+// since BDF2 started from history levels equal to the initial state is first order.
+// Explicit terms run in binary64 kernels; the five solves use sem_pcg_solve.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "sem_internal.h"
+
+struct sem_rbc {
+  const sem_mesh *m = nullptr;
+  sem_rbc_params prm;
+  double nu = 0, kappa = 0;
+  int step = 0;
+  int64_t nL = 0, nU = 0;
+  // U-vectors
+  double *u[3] = {}, *up[3] = {}, *T = nullptr, *Tp = nullptr, *p = nullptr, *W = nullptr, *Wp = nullptr;
+  double *Tb = nullptr, *rhs = nullptr, *x = nullptr, *Tn = nullptr, *un[3] = {};
+  // E-vectors
+  double *uL[3] = {}, *upL[3] = {}, *TL = nullptr, *TpL = nullptr, *g[3] = {}, *om[3] = {};
+  double *NT = nullptr, *NTp = nullptr, *Nu[3] = {}, *Nup[3] = {}, *fs[3] = {}, *tmpL = nullptr;
+  double *R = nullptr;  // [E][9][n3] dr_a/dx_c
+  double *scal = nullptr;  // reduction partials + result
+  double *drho = nullptr;  // GLL weights on the device
+  int *dnel = nullptr;     // element counts on the device
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  std::vector<void *> owned;
+};
+
+namespace {
+
+constexpr int kRedBlocks = 152 * 2;
+struct StepCoef {
+  double b0, b1, b2, a1, a2;
+};
+StepCoef coefficients(int step) {
+  if (step == 0) return {1.0, 1.0, 0.0, 1.0, 0.0};  // BDF1/EXT1
+  return {1.5, 2.0, -0.5, 2.0, -1.0};               // BDF2/EXT2
+}
+
+// ---------------------------------------------------------------- kernels
+// inverse Jacobian dr_a/dx_c at every node, R[(9e + 3a + c) n3 + q]
+__global__ void k_inv_jacobian(int n, int64_t E, const double *__restrict__ D, const double *__restrict__ X,
+                               const double *__restrict__ Y, const double *__restrict__ Z, double *__restrict__ R) {
+  const int n3 = n * n * n;
+  const int64_t nL = E * n3;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = l / n3;
+    const int q = (int)(l - e * n3);
+    const int i = q % n, j = (q / n) % n, k = q / (n * n);
+    const int64_t base = e * n3;
+    const double *xc[3] = {X + base, Y + base, Z + base};
+    double J[3][3];
+    for (int c = 0; c < 3; ++c) {
+      double a = 0, b = 0, d = 0;
+      for (int m = 0; m < n; ++m) {
+        a = fma(D[i * n + m], xc[c][m + n * (j + n * k)], a);
+        b = fma(D[j * n + m], xc[c][i + n * (m + n * k)], b);
+        d = fma(D[k * n + m], xc[c][i + n * (j + n * m)], d);
+      }
+      J[c][0] = a;
+      J[c][1] = b;
+      J[c][2] = d;
+    }
+    const double C00 = J[1][1] * J[2][2] - J[1][2] * J[2][1], C01 = J[1][2] * J[2][0] - J[1][0] * J[2][2],
+                 C02 = J[1][0] * J[2][1] - J[1][1] * J[2][0], C10 = J[0][2] * J[2][1] - J[0][1] * J[2][2],
+                 C11 = J[0][0] * J[2][2] - J[0][2] * J[2][0], C12 = J[0][1] * J[2][0] - J[0][0] * J[2][1],
+                 C20 = J[0][1] * J[1][2] - J[0][2] * J[1][1], C21 = J[0][2] * J[1][0] - J[0][0] * J[1][2],
+                 C22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double inv = 1.0 / (J[0][0] * C00 + J[0][1] * C01 + J[0][2] * C02);
+    const double Rm[9] = {C00 * inv, C10 * inv, C20 * inv, C01 * inv, C11 * inv,
+                          C21 * inv, C02 * inv, C12 * inv, C22 * inv};  // [a][c]
+    for (int t = 0; t < 9; ++t) R[(9 * e + t) * n3 + q] = Rm[t];
+  }
+}
+
+// physical gradient of an E-vector: g_c = sum_a dr_a/dx_c (D_a f)
+__global__ void k_grad(int n, int64_t E, const double *__restrict__ D, const double *__restrict__ R,
+                       const double *__restrict__ f, double *__restrict__ gx, double *__restrict__ gy,
+                       double *__restrict__ gz) {
+  const int n3 = n * n * n;
+  const int64_t nL = E * n3;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = l / n3;
+    const int q = (int)(l - e * n3);
+    const int i = q % n, j = (q / n) % n, k = q / (n * n);
+    const double *fe = f + e * n3;
+    double dr = 0, ds = 0, dt = 0;
+    for (int m = 0; m < n; ++m) {
+      dr = fma(D[i * n + m], fe[m + n * (j + n * k)], dr);
+      ds = fma(D[j * n + m], fe[i + n * (m + n * k)], ds);
+      dt = fma(D[k * n + m], fe[i + n * (j + n * m)], dt);
+    }
+    const double *Re = R + 9 * e * n3 + q;
+    gx[l] = Re[0 * n3] * dr + Re[3 * n3] * ds + Re[6 * n3] * dt;
+    gy[l] = Re[1 * n3] * dr + Re[4 * n3] * ds + Re[7 * n3] * dt;
+    gz[l] = Re[2 * n3] * dr + Re[5 * n3] * ds + Re[8 * n3] * dt;
+  }
+}
+
+// out = -(u . grad f) (+ add if given)
+__global__ void k_neg_adv(int64_t nL, const double *__restrict__ u0, const double *__restrict__ u1,
+                          const double *__restrict__ u2, const double *__restrict__ g0, const double *__restrict__ g1,
+                          const double *__restrict__ g2, const double *__restrict__ add, double *__restrict__ out) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
+    double v = -(u0[l] * g0[l] + u1[l] * g1[l] + u2[l] * g2[l]);
+    if (add) v += add[l];
+    out[l] = v;
+  }
+}
+
+// accumulate the curl of u from grad u_c: om_x = dw/dy - dv/dz, om_y = du/dz - dw/dx, om_z = dv/dx - du/dy
+__global__ void k_curl_acc(int64_t nL, int c, const double *__restrict__ g0, const double *__restrict__ g1,
+                           const double *__restrict__ g2, double *__restrict__ ox, double *__restrict__ oy,
+                           double *__restrict__ oz) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
+    if (c == 0) {
+      ox[l] = 0.0;
+      oy[l] = g2[l];
+      oz[l] = -g1[l];
+    } else if (c == 1) {
+      ox[l] -= g2[l];
+      oz[l] += g0[l];
+    } else {
+      ox[l] += g1[l];
+      oy[l] -= g0[l];
+    }
+  }
+}
+
+// wall term on one face direction d / side: out_l += nu rho_a rho_b (+-x_a x x_b) . curl(om)
+// (elements touching the wall; element-local derivatives of om)
+__global__ void k_wall(int n, const int *__restrict__ nel, int d, int side, double nu, const double *__restrict__ D,
+                       const double *__restrict__ rho, const double *__restrict__ R, const double *__restrict__ X,
+                       const double *__restrict__ Y, const double *__restrict__ Z, const double *__restrict__ ox,
+                       const double *__restrict__ oy, const double *__restrict__ oz, double *__restrict__ out) {
+  const int n3 = n * n * n, n2 = n * n;
+  const int ne[3] = {nel[0], nel[1], nel[2]};
+  const int other[2] = {d == 0 ? 1 : 0, d == 2 ? 1 : 2};  // the two element indices across the face
+  const int64_t nface_el = (int64_t)ne[other[0]] * ne[other[1]];
+  const int64_t total = nface_el * n2;
+  const int a = (d + 1) % 3, b = (d + 2) % 3;  // tangential directions with x_a x x_b along +r_d
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t fe = t / n2;
+    const int fq = (int)(t - fe * n2);
+    int eix[3];
+    eix[d] = side ? ne[d] - 1 : 0;
+    eix[other[0]] = (int)(fe % ne[other[0]]);
+    eix[other[1]] = (int)(fe / ne[other[0]]);
+    const int64_t e = eix[0] + (int64_t)ne[0] * (eix[1] + (int64_t)ne[1] * eix[2]);
+    int loc[3];
+    loc[d] = side ? n - 1 : 0;
+    loc[other[0]] = fq % n;
+    loc[other[1]] = fq / n;
+    const int q = loc[0] + n * (loc[1] + n * loc[2]);
+    const int64_t base = e * n3;
+    // reference derivatives of om and of the coordinates at this node
+    const double *fld[6] = {ox + base, oy + base, oz + base, X + base, Y + base, Z + base};
+    double dref[6][3];
+    for (int f = 0; f < 6; ++f)
+      for (int r = 0; r < 3; ++r) dref[f][r] = 0.0;
+    for (int m = 0; m < n; ++m) {
+      const int qr = m + n * (loc[1] + n * loc[2]);
+      const int qs = loc[0] + n * (m + n * loc[2]);
+      const int qt = loc[0] + n * (loc[1] + n * m);
+      const double a0 = D[loc[0] * n + m], a1 = D[loc[1] * n + m], a2 = D[loc[2] * n + m];
+      for (int f = 0; f < 6; ++f) {
+        dref[f][0] = fma(a0, fld[f][qr], dref[f][0]);
+        dref[f][1] = fma(a1, fld[f][qs], dref[f][1]);
+        dref[f][2] = fma(a2, fld[f][qt], dref[f][2]);
+      }
+    }
+    const double *Re = R + 9 * e * n3 + q;
+    double go[3][3];  // go[i][c] = d om_i / d x_c
+    for (int i = 0; i < 3; ++i)
+      for (int c = 0; c < 3; ++c)
+        go[i][c] = Re[(0 + c) * n3] * dref[i][0] + Re[(3 + c) * n3] * dref[i][1] + Re[(6 + c) * n3] * dref[i][2];
+    const double cc[3] = {go[2][1] - go[1][2], go[0][2] - go[2][0], go[1][0] - go[0][1]};
+    // x_a x x_b from the coordinate derivatives (dref[3 + comp][dir])
+    const double xa[3] = {dref[3][a], dref[4][a], dref[5][a]};
+    const double xb[3] = {dref[3][b], dref[4][b], dref[5][b]};
+    const double area[3] = {xa[1] * xb[2] - xa[2] * xb[1], xa[2] * xb[0] - xa[0] * xb[2], xa[0] * xb[1] - xa[1] * xb[0]};
+    const double sgn = side ? 1.0 : -1.0;
+    const double wt = rho[loc[a]] * rho[loc[b]];
+    out[base + q] += nu * sgn * wt * (area[0] * cc[0] + area[1] * cc[1] + area[2] * cc[2]);
+  }
+}
+
+// weak divergence: out = sum_a D_a^T v_a with v_a = B sum_c dr_a/dx_c f_c
+__global__ void k_weak_div_v(int n, int64_t E, const double *__restrict__ R, const double *__restrict__ B,
+                             const double *__restrict__ f0, const double *__restrict__ f1, const double *__restrict__ f2,
+                             double *__restrict__ v0, double *__restrict__ v1, double *__restrict__ v2) {
+  const int n3 = n * n * n;
+  const int64_t nL = E * n3;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = l / n3;
+    const int q = (int)(l - e * n3);
+    const double *Re = R + 9 * e * n3 + q;
+    const double fb0 = f0[l], fb1 = f1[l], fb2 = f2[l], bw = B[l];
+    v0[l] = bw * (Re[0 * n3] * fb0 + Re[1 * n3] * fb1 + Re[2 * n3] * fb2);
+    v1[l] = bw * (Re[3 * n3] * fb0 + Re[4 * n3] * fb1 + Re[5 * n3] * fb2);
+    v2[l] = bw * (Re[6 * n3] * fb0 + Re[7 * n3] * fb1 + Re[8 * n3] * fb2);
+  }
+}
+
+__global__ void k_dt_sum(int n, int64_t E, const double *__restrict__ D, const double *__restrict__ v0,
+                         const double *__restrict__ v1, const double *__restrict__ v2, double *__restrict__ out) {
+  const int n3 = n * n * n;
+  const int64_t nL = E * n3;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = l / n3;
+    const int q = (int)(l - e * n3);
+    const int i = q % n, j = (q / n) % n, k = q / (n * n);
+    const int64_t base = e * n3;
+    double s = 0.0;
+    for (int m = 0; m < n; ++m) {
+      s = fma(D[m * n + i], v0[base + m + n * (j + n * k)], s);
+      s = fma(D[m * n + j], v1[base + i + n * (m + n * k)], s);
+      s = fma(D[m * n + k], v2[base + i + n * (j + n * m)], s);
+    }
+    out[l] = s;
+  }
+}
+
+// Q^T with optional mask: vg[g] = (mask ? mask[g] : 1) * sum of copies
+__global__ void k_gather_m(int64_t nU, const int32_t *__restrict__ off, const int32_t *__restrict__ perm,
+                           const uint8_t *__restrict__ mask, const double *__restrict__ vL, double *__restrict__ vg) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int32_t t = off[g]; t < off[g + 1]; ++t) s += vL[perm[t]];
+    vg[g] = (mask && !mask[g]) ? 0.0 : s;
+  }
+}
+
+// T right-hand side (local): B ((b1 T + b2 Tp)/dt + a1 NT + a2 NTp) - H(Tb)
+__global__ void k_rhsT(int64_t nL, double dt, StepCoef k, const double *__restrict__ B, const double *__restrict__ TL,
+                       const double *__restrict__ TpL, const double *__restrict__ NT, const double *__restrict__ NTp,
+                       const double *__restrict__ HTb, double *__restrict__ out) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x)
+    out[l] = B[l] * ((k.b1 * TL[l] + k.b2 * TpL[l]) / dt + (k.a1 * NT[l] + k.a2 * NTp[l])) - HTb[l];
+}
+
+// f* = (b1 u + b2 up)/dt + a1 Nu + a2 Nup
+__global__ void k_fstar(int64_t nL, double dt, StepCoef k, const double *__restrict__ uL,
+                        const double *__restrict__ upL, const double *__restrict__ N, const double *__restrict__ Np,
+                        double *__restrict__ out) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x)
+    out[l] = (k.b1 * uL[l] + k.b2 * upL[l]) / dt + (k.a1 * N[l] + k.a2 * Np[l]);
+}
+
+// B (f - g)
+__global__ void k_bdiff(int64_t nL, const double *__restrict__ B, const double *__restrict__ f,
+                        const double *__restrict__ g, double *__restrict__ out) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x)
+    out[l] = B[l] * (f[l] - g[l]);
+}
+
+// y = a x + b y2 + c z (U-vectors; any pointer may alias y)
+__global__ void k_axpbypcz(int64_t n, double a, const double *x, double b, const double *y2, double c,
+                           const double *z, double *y) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    double v = a * x[g];
+    if (y2) v += b * y2[g];
+    if (z) v += c * z[g];
+    y[g] = v;
+  }
+}
+
+__global__ void k_lifting(int64_t nL, double Lz, const int32_t *__restrict__ l2g, const double *__restrict__ Z,
+                          double *__restrict__ Tb) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x)
+    Tb[l2g[l]] = 1.0 - Z[l] / Lz;  // every copy writes the same value
+}
+
+__global__ void k_add_masked(int64_t nU, const uint8_t *__restrict__ mask, const double *__restrict__ a,
+                             double *__restrict__ y) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x)
+    if (mask[g]) y[g] += a[g];
+}
+
+// fixed-order sum: partials, then one block finishes and stores sum / n
+__global__ void k_sum_part(int64_t n, const double *__restrict__ x, double *__restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    s += x[g];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_mean_finish(int np, int64_t n, const double *__restrict__ part, double *__restrict__ mean) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < np; ++b) t += part[b];
+    *mean = t / (double)n;
+  }
+}
+
+__global__ void k_sub_scalar(int64_t n, const double *__restrict__ s, double *__restrict__ x) {
+  const double v = *s;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    x[g] -= v;
+}
+
+// ---------------------------------------------------------------- host helpers
+int remove_mean(sem_rbc *s, double *x, cudaStream_t st) {
+  k_sum_part<<<kRedBlocks, 256, 0, st>>>(s->nU, x, s->scal);
+  k_mean_finish<<<1, 32, 0, st>>>(kRedBlocks, s->nU, s->scal, s->scal + kRedBlocks);
+  k_sub_scalar<<<grid_for(s->nU, 256), 256, 0, st>>>(s->nU, s->scal + kRedBlocks, x);
+  SEM_LAUNCH_CHECK("remove_mean");
+  return SEM_OK;
+}
+
+int grad(sem_rbc *s, const double *f, double **out, cudaStream_t st) {
+  const sem_mesh *m = s->m;
+  k_grad<<<grid_for(s->nL, 256), 256, 0, st>>>(m->n, m->E, m->dD, s->R, f, out[0], out[1], out[2]);
+  SEM_LAUNCH_CHECK("k_grad");
+  return SEM_OK;
+}
+
+int gather(sem_rbc *s, const double *vL, double *vg, bool masked, cudaStream_t st) {
+  const sem_mesh *m = s->m;
+  k_gather_m<<<grid_for(s->nU, 256), 256, 0, st>>>(s->nU, m->gs_off, m->gs_perm, masked ? m->mask : nullptr, vL, vg);
+  SEM_LAUNCH_CHECK("k_gather_m");
+  return SEM_OK;
+}
+
+int solve(sem_rbc *s, double h1, double h2, const double *b, double *x, int mask_mode, int *iters,
+          cudaStream_t st) {
+  sem_solver_opts o;
+  o.tol = s->prm.tol;
+  o.maxit = s->prm.maxit;
+  o.precision = s->prm.precision;
+  o.timeout_s = 0.0;
+  o.mask_mode = mask_mode;
+  sem_solve_stats stt;
+  int rc = sem_pcg_solve(s->m, h1, h2, b, x, &o, s->ws, &stt, (void *)st);
+  *iters = stt.iterations;
+  return rc;
+}
+
+void free_rbc(sem_rbc *s) {
+  if (!s) return;
+  for (void *p : s->owned) cudaFree(p);
+  delete s;
+}
+
+}  // namespace
+
+extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, const double *T_pert_g, void *stream,
+                              sem_rbc **out) {
+  if (!m || !prm || !out) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: NULL argument");
+  *out = nullptr;
+  if (!(prm->Ra > 0) || !(prm->Pr > 0) || !(prm->dt > 0) || !(prm->tol > 0) || prm->maxit < 1)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: Ra, Pr, dt, tol must be > 0 and maxit >= 1");
+  if (prm->precision != SEM_PREC_FP64 && prm->precision != SEM_PREC_DF64)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: unknown precision");
+  int dev = -1;
+  SEM_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: the mesh's device must be current");
+  if (m->periodic[2] || !m->dirichlet[4] || !m->dirichlet[5])
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: the mesh needs Dirichlet plates at z = 0 and z = Lz");
+  if ((!m->periodic[0] && !(m->dirichlet[0] && m->dirichlet[1])) ||
+      (!m->periodic[1] && !(m->dirichlet[2] && m->dirichlet[3])))
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: x and y must be periodic or walls on both sides");
+  cudaStream_t st = as_stream(stream);
+  sem_rbc *s = new sem_rbc();
+  s->m = m;
+  s->prm = *prm;
+  s->nu = sqrt(prm->Pr / prm->Ra);
+  s->kappa = 1.0 / sqrt(prm->Ra * prm->Pr);
+  s->nL = m->n_local;
+  s->nU = m->n_unique;
+  auto alloc = [&](double **p, int64_t count) -> int {
+    cudaError_t e = cudaMalloc((void **)p, sizeof(double) * (size_t)std::max<int64_t>(count, 1));
+    if (e != cudaSuccess) return sem_cuda_fail(e, "sem_rbc_create: cudaMalloc");
+    s->owned.push_back(*p);
+    return SEM_OK;
+  };
+  int rc = SEM_OK;
+  double **uvecs[] = {&s->u[0], &s->u[1], &s->u[2], &s->up[0], &s->up[1], &s->up[2], &s->T, &s->Tp, &s->p,
+                      &s->W, &s->Wp, &s->Tb, &s->rhs, &s->x, &s->Tn, &s->un[0], &s->un[1], &s->un[2]};
+  for (double **p : uvecs)
+    if (!rc) rc = alloc(p, s->nU);
+  double **evecs[] = {&s->uL[0], &s->uL[1], &s->uL[2], &s->upL[0], &s->upL[1], &s->upL[2], &s->TL, &s->TpL,
+                      &s->g[0],  &s->g[1],  &s->g[2],  &s->om[0],  &s->om[1],  &s->om[2],  &s->NT, &s->NTp,
+                      &s->Nu[0], &s->Nu[1], &s->Nu[2], &s->Nup[0], &s->Nup[1], &s->Nup[2], &s->fs[0], &s->fs[1],
+                      &s->fs[2], &s->tmpL};
+  for (double **p : evecs)
+    if (!rc) rc = alloc(p, s->nL);
+  if (!rc) rc = alloc(&s->R, 9 * s->nL);
+  if (!rc) rc = alloc(&s->scal, kRedBlocks + 8);
+  if (!rc) rc = alloc(&s->drho, SEM_MAXNP);
+  if (!rc) {
+    cudaError_t e = cudaMalloc((void **)&s->dnel, sizeof(int) * 3);
+    if (e != cudaSuccess) rc = sem_cuda_fail(e, "sem_rbc_create: cudaMalloc");
+    else s->owned.push_back(s->dnel);
+  }
+  if (!rc) rc = sem_pcg_workspace_bytes(m, &s->ws_bytes);
+  if (!rc) {
+    cudaError_t e = cudaMalloc(&s->ws, s->ws_bytes);
+    if (e != cudaSuccess) rc = sem_cuda_fail(e, "sem_rbc_create: cudaMalloc(workspace)");
+    else s->owned.push_back(s->ws);
+  }
+  if (rc) {
+    free_rbc(s);
+    return rc;
+  }
+  cudaMemcpyAsync(s->drho, m->rho, sizeof(double) * m->n, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s->dnel, m->nel, sizeof(int) * 3, cudaMemcpyHostToDevice, st);
+  k_inv_jacobian<<<grid_for(s->nL, 256), 256, 0, st>>>(m->n, m->E, m->dD, m->X, m->Y, m->Z, s->R);
+  k_lifting<<<grid_for(s->nL, 256), 256, 0, st>>>(s->nL, m->L[2], m->l2g, m->Z, s->Tb);
+  cudaMemcpyAsync(s->T, s->Tb, sizeof(double) * s->nU, cudaMemcpyDeviceToDevice, st);
+  if (T_pert_g) k_add_masked<<<grid_for(s->nU, 256), 256, 0, st>>>(s->nU, m->mask, T_pert_g, s->T);
+  for (int c = 0; c < 3; ++c) cudaMemsetAsync(s->u[c], 0, sizeof(double) * s->nU, st);
+  cudaMemsetAsync(s->p, 0, sizeof(double) * s->nU, st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    rc = sem_cuda_fail(e, "sem_rbc_create: set-up kernels");
+    free_rbc(s);
+    return rc;
+  }
+  *out = s;
+  return SEM_OK;
+}
+
+extern "C" int sem_rbc_destroy(sem_rbc *s) {
+  free_rbc(s);
+  return SEM_OK;
+}
+
+extern "C" int sem_rbc_fields(const sem_rbc *s, sem_rbc_view *v) {
+  if (!s || !v) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_fields: NULL argument");
+  v->u = s->u[0];
+  v->v = s->u[1];
+  v->w = s->u[2];
+  v->T = s->T;
+  v->p = s->p;
+  v->n_unique = s->nU;
+  v->step = s->step;
+  return SEM_OK;
+}
+
+extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
+  if (!s || !stt) return sem_fail(SEM_ERR_INVALID_ARG, "sem_bdf_ext_step: NULL argument");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = as_stream(stream);
+  const sem_mesh *m = s->m;
+  const int64_t nL = s->nL, nU = s->nU;
+  const double dt = s->prm.dt;
+  const unsigned gl = grid_for(nL, 256), gu = grid_for(nU, 256);
+  int rc;
+  stt->status = SEM_OK;
+  // level-n fields at the local nodes
+  for (int c = 0; c < 3; ++c)
+    if ((rc = sem_launch_scatter(m, s->u[c], s->uL[c], st))) return rc;
+  if ((rc = sem_launch_scatter(m, s->T, s->TL, st))) return rc;
+  // explicit terms: N_T, N_u, curl u, wall term
+  if ((rc = grad(s, s->TL, s->g, st))) return rc;
+  k_neg_adv<<<gl, 256, 0, st>>>(nL, s->uL[0], s->uL[1], s->uL[2], s->g[0], s->g[1], s->g[2], nullptr, s->NT);
+  for (int c = 0; c < 3; ++c) {
+    if ((rc = grad(s, s->uL[c], s->g, st))) return rc;
+    k_neg_adv<<<gl, 256, 0, st>>>(nL, s->uL[0], s->uL[1], s->uL[2], s->g[0], s->g[1], s->g[2],
+                                  c == 2 ? s->TL : nullptr, s->Nu[c]);
+    k_curl_acc<<<gl, 256, 0, st>>>(nL, c, s->g[0], s->g[1], s->g[2], s->om[0], s->om[1], s->om[2]);
+  }
+  SEM_LAUNCH_CHECK("explicit terms");
+  SEM_CUDA(cudaMemsetAsync(s->tmpL, 0, sizeof(double) * nL, st));
+  for (int d = 0; d < 3; ++d) {  // one launch per wall face: a face writes each of its nodes once
+    if (m->periodic[d]) continue;
+    for (int side = 0; side < 2; ++side) {
+      if (!m->dirichlet[2 * d + side]) continue;
+      const int o0 = d == 0 ? 1 : 0, o1 = d == 2 ? 1 : 2;
+      const int64_t tot = (int64_t)m->nel[o0] * m->nel[o1] * m->n * m->n;
+      k_wall<<<grid_for(tot, 128), 128, 0, st>>>(m->n, s->dnel, d, side, s->nu, m->dD, s->drho, s->R, m->X, m->Y,
+                                                 m->Z, s->om[0], s->om[1], s->om[2], s->tmpL);
+    }
+  }
+  SEM_LAUNCH_CHECK("k_wall");
+  if ((rc = gather(s, s->tmpL, s->W, false, st))) return rc;
+  if (s->step == 0) {  // history = initial state
+    for (int c = 0; c < 3; ++c) {
+      SEM_CUDA(cudaMemcpyAsync(s->up[c], s->u[c], sizeof(double) * nU, cudaMemcpyDeviceToDevice, st));
+      SEM_CUDA(cudaMemcpyAsync(s->Nup[c], s->Nu[c], sizeof(double) * nL, cudaMemcpyDeviceToDevice, st));
+    }
+    SEM_CUDA(cudaMemcpyAsync(s->Tp, s->T, sizeof(double) * nU, cudaMemcpyDeviceToDevice, st));
+    SEM_CUDA(cudaMemcpyAsync(s->NTp, s->NT, sizeof(double) * nL, cudaMemcpyDeviceToDevice, st));
+    SEM_CUDA(cudaMemcpyAsync(s->Wp, s->W, sizeof(double) * nU, cudaMemcpyDeviceToDevice, st));
+  }
+  for (int c = 0; c < 3; ++c)
+    if ((rc = sem_launch_scatter(m, s->up[c], s->upL[c], st))) return rc;
+  if ((rc = sem_launch_scatter(m, s->Tp, s->TpL, st))) return rc;
+
+  // temperature: lifting Tb, theta = T - Tb on the free nodes
+  const StepCoef kc = coefficients(s->step);
+  const double b0dt = kc.b0 / dt;
+  if ((rc = sem_launch_scatter(m, s->Tb, s->fs[0], st))) return rc;                      // Tb (local)
+  if ((rc = sem_launch_ax_local(m, s->kappa, b0dt, s->fs[0], s->fs[1], SEM_PREC_FP64, st))) return rc;  // H Tb
+  k_rhsT<<<gl, 256, 0, st>>>(nL, dt, kc, m->B, s->TL, s->TpL, s->NT, s->NTp, s->fs[1], s->tmpL);
+  if ((rc = gather(s, s->tmpL, s->rhs, true, st))) return rc;
+  rc = solve(s, s->kappa, b0dt, s->rhs, s->x, 0, &stt->iters_T, st);
+  if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
+  if (rc) stt->status = rc;
+  k_axpbypcz<<<gu, 256, 0, st>>>(nU, 1.0, s->Tb, 1.0, s->x, 0.0, nullptr, s->Tn);
+
+  // pressure
+  for (int c = 0; c < 3; ++c)
+    k_fstar<<<gl, 256, 0, st>>>(nL, dt, kc, s->uL[c], s->upL[c], s->Nu[c], s->Nup[c], s->fs[c]);
+  k_weak_div_v<<<gl, 256, 0, st>>>(m->n, m->E, s->R, m->B, s->fs[0], s->fs[1], s->fs[2], s->g[0], s->g[1], s->g[2]);
+  k_dt_sum<<<gl, 256, 0, st>>>(m->n, m->E, m->dD, s->g[0], s->g[1], s->g[2], s->tmpL);
+  SEM_LAUNCH_CHECK("weak divergence");
+  if ((rc = gather(s, s->tmpL, s->rhs, false, st))) return rc;
+  k_axpbypcz<<<gu, 256, 0, st>>>(nU, 1.0, s->rhs, -kc.a1, s->W, -kc.a2, s->Wp, s->rhs);
+  if ((rc = remove_mean(s, s->rhs, st))) return rc;
+  rc = solve(s, 1.0, 0.0, s->rhs, s->p, 1, &stt->iters_p, st);
+  if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
+  if (rc) stt->status = rc;
+  if ((rc = remove_mean(s, s->p, st))) return rc;
+
+  // velocity
+  if ((rc = sem_launch_scatter(m, s->p, s->tmpL, st))) return rc;
+  if ((rc = grad(s, s->tmpL, s->g, st))) return rc;
+  for (int c = 0; c < 3; ++c) {
+    k_bdiff<<<gl, 256, 0, st>>>(nL, m->B, s->fs[c], s->g[c], s->tmpL);
+    if ((rc = gather(s, s->tmpL, s->rhs, true, st))) return rc;
+    rc = solve(s, s->nu, b0dt, s->rhs, s->un[c], 0, &stt->iters_u[c], st);
+    if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
+    if (rc) stt->status = rc;
+  }
+  // rotate histories
+  for (int c = 0; c < 3; ++c) {
+    std::swap(s->up[c], s->u[c]);
+    std::swap(s->u[c], s->un[c]);
+    std::swap(s->Nup[c], s->Nu[c]);
+  }
+  std::swap(s->Tp, s->T);
+  std::swap(s->T, s->Tn);
+  std::swap(s->NTp, s->NT);
+  std::swap(s->Wp, s->W);
+  s->step += 1;
+  SEM_CUDA(cudaStreamSynchronize(st));
+  stt->step = s->step;
+  stt->step_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return stt->status;
+}

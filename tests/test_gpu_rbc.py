@@ -1,0 +1,102 @@
+"""GPU parity of the BDF2/EXT2 Rayleigh-Benard step (Sec. 4.1, Eqs. (1)-(3);
+Sec. 4.4 plates and periodicity) against the oracle's identical scheme, on
+seeded perturbed initial states, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import rbc
+import workloads
+
+torch = pytest.importorskip("torch")
+import paper_2501_13240_gb300 as sem  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_err(a, b):
+    s = np.abs(b).max()
+    return np.abs(np.asarray(a) - b).max() / (s if s > 0 else 1.0)
+
+
+def meshes(nel, N, stretch):
+    kw = dict(periodic=(1, 1, 0), dirichlet=(0, 0, 0, 0, 1, 1), z_stretch=stretch)
+    return oracle.box_mesh(nel, N, **kw), sem.sem_mesh_create_box(nel, N, **kw)
+
+
+def fields(st):
+    f = sem.sem_rbc_fields(st)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in f.items()}
+
+
+def test_conduction_state_fixed_point_gpu():
+    om, gm = meshes((3, 3, 3), 5, 2.0)
+    st = sem.sem_rbc_create(gm, 1e8, 0.7, 1e-3, tol=1e-12)
+    z = np.zeros(om.n_unique)
+    z[om.l2g] = om.Z
+    pex = z - z * z / 2
+    pex -= pex.mean()
+    for _ in range(3):
+        s = sem.sem_bdf_ext_step(st)
+        f = fields(st)
+        assert np.abs(f["T"] - (1.0 - z)).max() < 1e-12
+        assert max(np.abs(f[c]).max() for c in "uvw") < 1e-12
+        assert np.abs(f["p"] - pex).max() < 1e-10
+    assert s["step"] == 3
+    st.destroy()
+    gm.destroy()
+
+
+@pytest.mark.parametrize("prec", [sem.SEM_PREC_FP64, sem.SEM_PREC_DF64], ids=["fp64", "df64"])
+@pytest.mark.parametrize("nel,N,stretch", [((3, 3, 3), 5, 2.0), ((2, 3, 4), 7, 1.3)])
+def test_perturbed_steps_match_oracle(nel, N, stretch, prec):
+    om, gm = meshes(nel, N, stretch)
+    Ra, Pr, dt, tol = 1e5, 0.7, 2e-3, 1e-12
+    pert = workloads.perturbation(om.n_unique, 1e-2, seed=2)
+    R = rbc.RBC(om, Ra, Pr, dt, tol=tol)
+    s = R.initial_state(pert)
+    st = sem.sem_rbc_create(gm, Ra, Pr, dt, tol=tol, precision=prec, T_pert=torch.from_numpy(pert).cuda())
+    for k in range(4):
+        s = R.step(s)
+        g = sem.sem_bdf_ext_step(st)
+        assert g["status"] == 0
+        assert abs(g["iters_T"] - s.iters["T"]) <= 2 and abs(g["iters_p"] - s.iters["p"]) <= 3, (g, s.iters)
+        f = fields(st)
+        assert rel_err(f["T"], s.T) < 1e-10
+        assert rel_err(f["p"], s.p) < 1e-8, k
+        for c, name in enumerate("uvw"):
+            assert rel_err(f[name], s.u[c]) < 1e-8, (k, name)
+    st.destroy()
+    gm.destroy()
+
+
+def test_rbc_mesh_requirements():
+    gm = sem.sem_mesh_create_box((2, 2, 2), 3)  # walls everywhere but no periodicity: allowed
+    st = sem.sem_rbc_create(gm, 1e6, 1.0, 1e-3)
+    st.destroy()
+    gm.destroy()
+    gm = sem.sem_mesh_create_box((2, 2, 2), 3, periodic=(1, 1, 1), dirichlet=(0,) * 6)
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_rbc_create(gm, 1e6, 1.0, 1e-3)
+    assert ei.value.code == sem.SEM_ERR_INVALID_ARG
+    gm.destroy()
+
+
+def test_rbc_32_workload_step():
+    """One step of the 32^3-element, N = 7 tanh-stretched RBC workload
+    (Ra = 1e8, Pr = 0.7, dt = 1e-3, seeded 1e-3 perturbation)."""
+    w = workloads.RBC_32
+    gm = sem.mesh_from_workload(w)
+    pert = workloads.perturbation(gm.n_unique, 1e-3, seed=2)
+    st = sem.sem_rbc_create(gm, 1e8, 0.7, 1e-3, tol=1e-8, T_pert=torch.from_numpy(pert).cuda())
+    for _ in range(2):
+        g = sem.sem_bdf_ext_step(st)
+        assert g["status"] == 0, g
+    f = sem.sem_rbc_fields(st)
+    T = f["T"]
+    assert torch.isfinite(T).all() and float(T.min()) > -0.01 and float(T.max()) < 1.01
+    for c in "uvw":
+        assert torch.isfinite(f[c]).all()
+    st.destroy()
+    gm.destroy()

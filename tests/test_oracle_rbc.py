@@ -1,0 +1,119 @@
+"""Pins of the oracle's Rayleigh-Benard BDF2/EXT2 step (Sec. 4.1, Eqs. (1)-(3);
+plates and periodicity of Sec. 4.4): exact steady states, second-order
+temporal accuracy on an exact solution, the wall term on an analytic field,
+and the weak divergence against dense brute force. CPU only."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import rbc
+from bruteforce import gll_numpy
+
+
+def rbc_mesh(nel=(3, 3, 3), N=5, stretch=2.0):
+    return oracle.box_mesh(nel, N, periodic=(1, 1, 0), dirichlet=(0, 0, 0, 0, 1, 1), z_stretch=stretch)
+
+
+def zg(m):
+    z = np.zeros(m.n_unique)
+    z[m.l2g] = m.Z
+    return z
+
+
+def test_conduction_state_is_a_fixed_point():
+    """u = 0, T = 1 - z, p = z - z^2/2 (+c) solve Eqs. (1)-(3) exactly (the
+    initial state of Sec. 4.4 without perturbation)."""
+    m = rbc_mesh()
+    R = rbc.RBC(m, 1e8, 0.7, 1e-3, tol=1e-13)
+    s = R.initial_state()
+    z = zg(m)
+    pex = z - z * z / 2
+    pex -= pex.mean()
+    for _ in range(3):
+        s = R.step(s)
+        assert np.abs(s.T - (1.0 - z)).max() < 1e-13
+        assert max(np.abs(c).max() for c in s.u) < 1e-13
+        assert np.abs(s.p - pex).max() < 1e-11
+
+
+def test_second_order_in_time_on_diffusing_profile():
+    """T = 1 - z + a exp(-kappa pi^2 t) sin(pi z), u = 0 solves the system
+    (buoyancy balanced by a hydrostatic pressure). BDF2/EXT2 error ~ dt^2."""
+    Ra, Pr, a, tend = 100.0, 1.0, 0.3, 0.24
+    kappa = 1.0 / np.sqrt(Ra * Pr)
+    m = rbc_mesh((2, 2, 4), 8, stretch=0.0)
+    z = zg(m)
+    errs = []
+    for nsteps in (6, 12, 24):
+        dt = tend / nsteps
+        R = rbc.RBC(m, Ra, Pr, dt, tol=1e-13)
+        s = R.initial_state(a * np.sin(np.pi * z))
+        for _ in range(nsteps):
+            s = R.step(s)
+        exact = 1.0 - z + a * np.exp(-kappa * np.pi ** 2 * tend) * np.sin(np.pi * z)
+        errs.append(np.abs(s.T - exact).max())
+        assert max(np.abs(c).max() for c in s.u) < 1e-9
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.0 < r1 < 5.0 and 3.0 < r2 < 5.0, errs
+
+
+def test_wall_term_on_analytic_field():
+    """u = (x z, 0, 0) has curl curl u = (0, 0, 1): the wall term is
+    nu * (-1 on z = 0, +1 on z = Lz) times the surface quadrature weights."""
+    L = (1.0, 1.5, 0.8)
+    nel, N, nu = (3, 2, 2), 4, 0.37
+    m = oracle.box_mesh(nel, N, L, periodic=(0, 0, 0), dirichlet=(0, 0, 0, 0, 1, 1))
+    g = rbc.geometry(m)
+    u = [m.X * m.Z, np.zeros(m.n_local), np.zeros(m.n_local)]
+    W = rbc.wall_term(m, g, u, nu)
+    hx, hy = L[0] / nel[0], L[1] / nel[1]
+    _, rho, _ = gll_numpy(N)
+    n = N + 1
+    ref = np.zeros(m.n_local)
+    e = np.arange(m.E)
+    ez = e // (nel[0] * nel[1])
+    for el in e:
+        for k, sgn, hit in ((0, -1.0, ez[el] == 0), (N, 1.0, ez[el] == nel[2] - 1)):
+            if not hit:
+                continue
+            for j in range(n):
+                for i in range(n):
+                    ref[el * n ** 3 + i + n * j + n * n * k] += sgn * nu * rho[i] * rho[j] * hx * hy / 4
+    np.testing.assert_allclose(W, oracle.gather_sum(m, ref), rtol=0, atol=1e-12)
+
+
+def test_weak_divergence_matches_dense():
+    from bruteforce import element_matrices  # noqa: F401 (same construction)
+    m = oracle.box_mesh((2, 1, 2), 4, deform_amp=0.05, kappa=np.array([[1.0, 2, 1], [2, 1, 1], [1, 1, 2]]),
+                        phi=np.array([0.3, 1.7, 4.1]))
+    g = rbc.geometry(m)
+    rng = np.random.default_rng(9)
+    f = [rng.standard_normal(m.n_local) for _ in range(3)]
+    got = rbc.weak_div(m, g, f)
+    _, rho, D = gll_numpy(m.N)
+    n = m.N + 1
+    I = np.eye(n)
+    grads = (np.kron(I, np.kron(I, D)), np.kron(I, np.kron(D, I)), np.kron(D, np.kron(I, I)))
+    ref = np.zeros(m.n_local)
+    for el in range(m.E):
+        sl = slice(el * n ** 3, (el + 1) * n ** 3)
+        Jm = np.zeros((n ** 3, 3, 3))
+        for c, xc in enumerate((m.X[sl], m.Y[sl], m.Z[sl])):
+            for a in range(3):
+                Jm[:, c, a] = grads[a] @ xc
+        Rm = np.linalg.inv(Jm)
+        w = np.kron(np.kron(rho, rho), rho) * np.linalg.det(Jm)
+        for c in range(3):
+            Gc = sum(Rm[:, a, c][:, None] * grads[a] for a in range(3))  # d phi / dx_c at nodes
+            ref[sl] += Gc.T @ (w * f[c][sl])
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_gradient_exact_for_polynomials():
+    m = oracle.box_mesh((2, 3, 2), 5, L=(1.0, 2.0, 0.7), z_stretch=1.3)
+    g = rbc.geometry(m)
+    f = m.X ** 2 * m.Y + m.Z ** 3 - 2.0 * m.X * m.Z
+    gr = rbc.grad(m, g, f)
+    np.testing.assert_allclose(gr[0], 2 * m.X * m.Y - 2 * m.Z, atol=1e-11)
+    np.testing.assert_allclose(gr[1], m.X ** 2, atol=1e-11)
+    np.testing.assert_allclose(gr[2], 3 * m.Z ** 2 - 2 * m.X, atol=1e-11)
