@@ -60,13 +60,13 @@ __device__ __forceinline__ double sum_partials(const double *__restrict__ part, 
 }
 
 __global__ void __launch_bounds__(kUpdThreads)
-    k_pcg_init(int64_t nU, const double *__restrict__ b, double *__restrict__ x, double *__restrict__ r,
-               double *__restrict__ p, const double *__restrict__ dinv, double *__restrict__ part_a,
-               double *__restrict__ part_b) {
+    k_pcg_init(int64_t nU, const double *__restrict__ b, double inv_scale, double *__restrict__ x,
+               double *__restrict__ r, double *__restrict__ p, const double *__restrict__ dinv,
+               double *__restrict__ part_a, double *__restrict__ part_b) {
   __shared__ double red[32];
   double rz = 0.0, bb = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
-    const double bv = b[g];
+    const double bv = b[g] * inv_scale;
     const double z = dinv[g] * bv;
     x[g] = 0.0;
     r[g] = bv;
@@ -140,6 +140,29 @@ __global__ void __launch_bounds__(kUpdThreads)
   }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x)
     p[g] = fma(beta, p[g], dinv[g] * r[g]);
+}
+
+// partial sums of b.b (for the scale of the system)
+__global__ void __launch_bounds__(kUpdThreads)
+    k_norm2_part(int64_t nU, const double *__restrict__ b, double *__restrict__ part) {
+  __shared__ double red[32];
+  double bb = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x)
+    bb = fma(b[g], b[g], bb);
+  bb = block_sum(bb, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = bb;
+}
+
+__global__ void __launch_bounds__(kUpdThreads)
+    k_sum_finish(const double *__restrict__ part, int n, PcgScalars *s) {
+  __shared__ double red[32];
+  const double v = sum_partials(part, n, red);
+  if (threadIdx.x == 0) s->bb = v;
+}
+
+__global__ void k_scale(int64_t n, double a, double *__restrict__ x) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    x[g] *= a;
 }
 
 // dinv[g] = mask[g] / sum over copies of the local diagonal
@@ -309,14 +332,29 @@ extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const doub
   k_jacobi_inv<<<grid_for(m->n_unique, 256), 256, 0, st>>>(m->n, m->n_unique, m->gs_off, m->gs_perm, m->mask, m->dD,
                                                             m->G, m->B, h1, h2, masked ? 1 : 0, wk.dinv);
   SEM_LAUNCH_CHECK("k_jacobi_inv");
-  k_pcg_init<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, x_g, wk.r, wk.p, wk.dinv, wk.part_a, wk.part_b);
+  // Solve the system scaled by an exact power of two so that ||b|| ~ 1: the
+  // iteration is unchanged in binary64 (power-of-two scaling is exact) and
+  // the double-float operator stays inside the binary32 exponent range.
+  PcgScalars hs;
+  k_norm2_part<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, wk.part_a);
+  k_sum_finish<<<1, kUpdThreads, 0, st>>>(wk.part_a, kUpdBlocks, wk.s);
+  SEM_LAUNCH_CHECK("k_norm2_part");
+  SEM_CUDA(cudaMemcpyAsync(&hs, wk.s, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  SEM_CUDA(cudaStreamSynchronize(st));
+  double scale = 1.0;
+  if (hs.bb > 0.0 && std::isfinite(hs.bb)) scale = std::ldexp(1.0, std::ilogb(sqrt(hs.bb)));
+  k_pcg_init<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, 1.0 / scale, x_g, wk.r, wk.p, wk.dinv, wk.part_a,
+                                                 wk.part_b);
   k_pcg_init_finish<<<1, kUpdThreads, 0, st>>>(wk.part_a, wk.part_b, kUpdBlocks, wk.s);
   SEM_LAUNCH_CHECK("k_pcg_init");
-  PcgScalars hs;
   SEM_CUDA(cudaMemcpyAsync(&hs, wk.s, sizeof(hs), cudaMemcpyDeviceToHost, st));
   SEM_CUDA(cudaStreamSynchronize(st));
   const double bnorm = sqrt(hs.bb);
   auto finish = [&](int status, int it, double rr) {
+    if (scale != 1.0 && it > 0) {
+      k_scale<<<grid_for(nU, 256), 256, 0, st>>>(nU, scale, x_g);
+      cudaStreamSynchronize(st);
+    }
     stats->iterations = it;
     stats->rel_residual = (bnorm > 0.0) ? sqrt(rr) / bnorm : 0.0;
     stats->solve_ms =
