@@ -55,13 +55,16 @@ enum {
 /* Arithmetic used by the operator and solver kernels. */
 enum {
   SEM_PREC_FP64 = 0, /* native binary64 FMA */
-  SEM_PREC_DF64 = 1  /* binary64-accurate double-float: each value carried as an
+  SEM_PREC_DF64 = 1, /* binary64-accurate double-float: each value carried as an
                         unevaluated sum of two binary32 (hi + lo) and combined
                         with error-free transformations (Dekker 1971; Knuth's
                         TwoSum; Joldes, Muller & Popescu 2017). About 2^-44
                         relative accuracy per operator application; inputs,
                         outputs and intermediate values must stay within
                         |x| in [2^-80, 2^100] (binary32 exponent range). */
+  SEM_PREC_FP32 = 2, /* binary32 (multigrid smoothing levels) */
+  SEM_PREC_BF16 = 3  /* geometric factors stored as bfloat16, binary32 arithmetic
+                        (multigrid smoothing levels) */
 };
 
 typedef struct sem_mesh sem_mesh; /* opaque */
@@ -215,6 +218,58 @@ int sem_pcg_workspace_bytes(const sem_mesh *m, size_t *bytes);
 int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
                   const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats,
                   void *stream);
+
+/* ------------------------------------------------------------------------
+ * p-multigrid preconditioned flexible CG. Sec. 2.2: NekRS preconditions its
+ * pressure Poisson solve with p-multigrid and 4th-kind Chebyshev-accelerated
+ * smoothers, running most preconditioner work in FP32. Here: levels of
+ * decreasing order on the same elements (each re-discretised on its own GLL
+ * points with the same box description), element-wise tensor-product
+ * Lagrange prolongation P and restriction R = P^T, 4th-kind Chebyshev-Jacobi
+ * smoothing (Lottes 2022 recurrence) in binary32 (geometry in binary32 or
+ * bfloat16), lambda_max from power iteration on D^{-1}A started from the
+ * alternating lattice vector (-1)^(I+J+K), and a binary64 Jacobi-PCG solve on
+ * the coarsest level. The outer iteration is flexible CG (Polak-Ribiere beta)
+ * with the fine operator in the precision of the solver options.
+ * ------------------------------------------------------------------------ */
+typedef struct sem_pmg sem_pmg; /* opaque; owns its level meshes and scratch */
+
+typedef struct {
+  int nlevels;            /* 2..4 */
+  int orders[4];          /* orders[0] = the fine mesh's N, strictly decreasing, >= 1 */
+  int smoother_precision; /* SEM_PREC_FP32 or SEM_PREC_BF16 */
+  int cheb_degree;        /* Chebyshev degree (operator applications per smoothing), >= 1 */
+  double lambda_safety;   /* factor on the power-iteration estimate of lambda_max (e.g. 1.1) */
+  int power_its;          /* power iterations (e.g. 20) */
+  double coarse_tol;      /* relative tolerance of the coarsest-level solve */
+  int coarse_maxit;
+} sem_pmg_opts;
+
+/* Build the hierarchy for the operator h1 A + h2 B on mesh m (which must
+ * outlive it). Level meshes are created with the description of m at the
+ * coarser orders. Synchronises the stream. */
+int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem_pmg_opts *opts, void *stream,
+                   sem_pmg **out);
+
+/* lambda_max estimate of D^{-1}A on level l (after the safety factor). */
+int sem_pmg_lambda(const sem_pmg *p, int level, double *lambda);
+
+/* One V-cycle: z_g ~ A^{-1} r_g on the fine level (device U-vectors, binary64
+ * in and out; r_g should vanish on Dirichlet nodes). */
+int sem_pmg_vcycle(sem_pmg *p, const double *r_g, double *z_g, void *stream);
+
+/* Prolongation (level l+1 -> l) and restriction (l -> l+1) of binary64
+ * device U-vectors, for tests of the transfer operators. */
+int sem_pmg_prolong(sem_pmg *p, int level, const double *uc_g, double *uf_g, void *stream);
+int sem_pmg_restrict(sem_pmg *p, int level, const double *rf_g, double *rc_g, void *stream);
+
+/* Flexible CG preconditioned by one V-cycle per iteration, x0 = 0; stops after
+ * the first iteration with ||r||_2 <= tol ||b||_2 (opts.mask_mode must be 0;
+ * opts.precision selects the fine operator: SEM_PREC_FP64 or SEM_PREC_DF64). */
+int sem_pmg_pcg_solve(sem_pmg *p, const double *b_g, double *x_g, const sem_solver_opts *opts,
+                      sem_solve_stats *stats, void *stream);
+
+int sem_pmg_destroy(sem_pmg *p);
 
 /* ------------------------------------------------------------------------
  * Rayleigh-Benard convection time step (Boussinesq equations, Sec. 4.1,

@@ -28,6 +28,8 @@ SEM_ERR_IO = -6
 SEM_ERR_NOMEM = -7
 SEM_PREC_FP64 = 0
 SEM_PREC_DF64 = 1
+SEM_PREC_FP32 = 2
+SEM_PREC_BF16 = 3
 
 # every symbol include/sem.h declares
 EXPORTS = (
@@ -36,6 +38,8 @@ EXPORTS = (
     "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_ax_assembled_add", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
     "sem_pcg_solve", "sem_pcg_solve_noalloc", "sem_pcg_noalloc_capacity",
     "sem_rbc_create", "sem_bdf_ext_step", "sem_rbc_fields", "sem_rbc_destroy",
+    "sem_pmg_create", "sem_pmg_lambda", "sem_pmg_vcycle", "sem_pmg_prolong", "sem_pmg_restrict",
+    "sem_pmg_pcg_solve", "sem_pmg_destroy",
 )
 
 
@@ -68,6 +72,12 @@ class sem_solver_opts(ctypes.Structure):
 class sem_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("status", ctypes.c_int)]
+
+
+class sem_pmg_opts(ctypes.Structure):
+    _fields_ = [("nlevels", ctypes.c_int), ("orders", ctypes.c_int * 4), ("smoother_precision", ctypes.c_int),
+                ("cheb_degree", ctypes.c_int), ("lambda_safety", ctypes.c_double), ("power_its", ctypes.c_int),
+                ("coarse_tol", ctypes.c_double), ("coarse_maxit", ctypes.c_int)]
 
 
 class sem_rbc_params(ctypes.Structure):
@@ -127,6 +137,14 @@ def lib() -> ctypes.CDLL:
         sig["sem_bdf_ext_step"] = ([_vp, ctypes.POINTER(sem_step_stats), _vp], _i)
         sig["sem_rbc_fields"] = ([_vp, ctypes.POINTER(sem_rbc_view)], _i)
         sig["sem_rbc_destroy"] = ([_vp], _i)
+        sig["sem_pmg_create"] = ([_vp, _d, _d, ctypes.POINTER(sem_pmg_opts), _vp, ctypes.POINTER(_vp)], _i)
+        sig["sem_pmg_lambda"] = ([_vp, _i, ctypes.POINTER(_d)], _i)
+        sig["sem_pmg_vcycle"] = ([_vp, _vp, _vp, _vp], _i)
+        sig["sem_pmg_prolong"] = ([_vp, _i, _vp, _vp, _vp], _i)
+        sig["sem_pmg_restrict"] = ([_vp, _i, _vp, _vp, _vp], _i)
+        sig["sem_pmg_pcg_solve"] = ([_vp, _vp, _vp, ctypes.POINTER(sem_solver_opts), ctypes.POINTER(sem_solve_stats),
+                                     _vp], _i)
+        sig["sem_pmg_destroy"] = ([_vp], _i)
         for name, (args, res) in sig.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -428,3 +446,83 @@ def sem_rbc_fields(s: RBC) -> dict:
     _check(lib().sem_rbc_fields(s._h, ctypes.byref(v)))
     n = int(v.n_unique)
     return {k: _device_copy(getattr(v, k), n) for k in ("u", "v", "w", "T", "p")}
+
+
+class PMG:
+    """Owns a ``sem_pmg`` handle (p-multigrid hierarchy on a fine mesh)."""
+
+    def __init__(self, handle, mesh: Mesh, orders):
+        self._h = handle
+        self.mesh = mesh
+        self.orders = tuple(orders)
+
+    def destroy(self):
+        if self._h is not None:
+            lib().sem_pmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def lam(self, level: int) -> float:
+        v = ctypes.c_double()
+        _check(lib().sem_pmg_lambda(self._h, int(level), ctypes.byref(v)))
+        return float(v.value)
+
+
+def sem_pmg_create(mesh: Mesh, h1: float = 1.0, h2: float = 0.0, orders=(7, 3, 1), smoother_precision=SEM_PREC_FP32,
+                   cheb_degree: int = 2, lambda_safety: float = 1.1, power_its: int = 20, coarse_tol: float = 1e-10,
+                   coarse_maxit: int = 2000, stream=None) -> PMG:
+    o = sem_pmg_opts()
+    o.nlevels = len(orders)
+    for t, N in enumerate(orders):
+        o.orders[t] = int(N)
+    o.smoother_precision = int(smoother_precision)
+    o.cheb_degree = int(cheb_degree)
+    o.lambda_safety = float(lambda_safety)
+    o.power_its = int(power_its)
+    o.coarse_tol = float(coarse_tol)
+    o.coarse_maxit = int(coarse_maxit)
+    h = ctypes.c_void_p()
+    _check(lib().sem_pmg_create(mesh.handle, float(h1), float(h2), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+    return PMG(h, mesh, orders)
+
+
+def sem_pmg_vcycle(P: PMG, r_g, z_g, stream=None):
+    import torch
+    n = P.mesh.n_unique
+    _check(lib().sem_pmg_vcycle(P._h, _ptr(r_g, torch.float64, n, "r_g"), _ptr(z_g, torch.float64, n, "z_g"),
+                                _stream(stream)))
+    return z_g
+
+
+def sem_pmg_prolong(P: PMG, level: int, uc_g, uf_g, stream=None):
+    import torch
+    _check(lib().sem_pmg_prolong(P._h, int(level), _ptr(uc_g, torch.float64, None, "uc_g"),
+                                 _ptr(uf_g, torch.float64, None, "uf_g"), _stream(stream)))
+    return uf_g
+
+
+def sem_pmg_restrict(P: PMG, level: int, rf_g, rc_g, stream=None):
+    import torch
+    _check(lib().sem_pmg_restrict(P._h, int(level), _ptr(rf_g, torch.float64, None, "rf_g"),
+                                  _ptr(rc_g, torch.float64, None, "rc_g"), _stream(stream)))
+    return rc_g
+
+
+def sem_pmg_pcg_solve(P: PMG, b_g, x_g, tol: float = 1e-8, maxit: int = 500, precision: int = SEM_PREC_DF64,
+                      timeout_s: float = 0.0, stream=None, raise_on_error: bool = True) -> dict:
+    import torch
+    n = P.mesh.n_unique
+    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s), 0)
+    st = sem_solve_stats()
+    rc = lib().sem_pmg_pcg_solve(P._h, _ptr(b_g, torch.float64, n, "b_g"), _ptr(x_g, torch.float64, n, "x_g"),
+                                 ctypes.byref(o), ctypes.byref(st), _stream(stream))
+    out = {"iterations": st.iterations, "rel_residual": st.rel_residual, "solve_ms": st.solve_ms,
+           "status": st.status}
+    if rc != SEM_OK and (raise_on_error or rc not in (SEM_ERR_NOT_CONVERGED, SEM_ERR_TIMEOUT, SEM_ERR_BREAKDOWN)):
+        _check(rc)
+    return out

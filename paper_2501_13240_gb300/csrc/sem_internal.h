@@ -12,6 +12,7 @@
 #define SEM_MAXNP (SEM_MAXN + 1)
 
 struct sem_mesh {
+  sem_box_desc desc;  // the description the mesh was built from
   int nel[3];
   int N;
   int n;          // N + 1

@@ -1,0 +1,798 @@
+// p-multigrid preconditioned flexible CG (Sec. 2.2: NekRS preconditions the
+// pressure Poisson solve with p-multigrid and 4th-kind Chebyshev-accelerated
+// smoothers, running most preconditioner work in FP32 to save bandwidth).
+//
+// Levels: the same elements at decreasing orders, each with its own mesh
+// (geometry re-evaluated at the level's GLL points). Smoothing levels run in
+// binary32 with geometric factors in binary32 or bfloat16; the coarsest level
+// is a binary64 Jacobi-PCG solve. Transfer operators: element-wise
+// tensor-product Lagrange interpolation P (coarse -> fine) and R = P^T.
+// Smoother: 4th-kind Chebyshev in D^{-1}A (Lottes 2022 recurrence):
+//   d_0 = 4/(3 lam) D^{-1} r_0;  for i = 1..k: x += d_{i-1}; (i < k) r -= A d_{i-1};
+//   d_i = (2i-1)/(2i+3) d_{i-1} + (8i+4)/((2i+3) lam) D^{-1} r_i.
+// Outer: flexible CG, beta = r.(z_new - z_old) / r.z_old.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "sem_df64.cuh"
+#include "sem_internal.h"
+
+namespace {
+
+struct PmgLevel {
+  sem_mesh *m = nullptr;
+  bool own = false;
+  float *Gf = nullptr;
+  __nv_bfloat16 *Gb = nullptr;
+  float *Bf = nullptr;
+  float *Df = nullptr;
+  float *dinv = nullptr;
+  float *minv = nullptr;  // 1 / multiplicity
+  float lam = 0.0f;
+  float *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *t = nullptr;
+};
+
+constexpr int kPart = 152 * 2;
+
+}  // namespace
+
+struct sem_pmg {
+  std::vector<PmgLevel> L;
+  float *J[3] = {};  // device interpolation matrices, level l+1 -> l, [n_f][n_c]
+  sem_pmg_opts o;
+  double h1 = 1.0, h2 = 0.0;
+  double *cb = nullptr, *cx = nullptr;  // coarsest level (binary64)
+  void *cws = nullptr;
+  double *r = nullptr, *z = nullptr, *zn = nullptr, *p = nullptr, *w = nullptr;  // outer FCG
+  double *part = nullptr, *pw_part = nullptr;
+  std::vector<void *> owned;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- binary32 operator
+template <int NP>
+struct F32Cfg {
+  static constexpr int N2 = NP * NP;
+  static constexpr int N3 = NP * NP * NP;
+  static constexpr int ELB = (N2 >= 256) ? 1 : (256 / N2);
+  static constexpr int THREADS = N2 * ELB;
+  static constexpr int SMEM = (NP * (NP + 1) + 3 * N3 * ELB) * (int)sizeof(float);
+};
+
+__device__ __forceinline__ float ldg_real(const float *p, int64_t i) { return p[i]; }
+__device__ __forceinline__ float ldg_real(const __nv_bfloat16 *p, int64_t i) { return __bfloat162float(p[i]); }
+
+// w[g] += h1 (A u)[g] + h2 (B u)[g] through map (-1 = skip), binary32
+template <int NP, typename GT>
+__global__ void __launch_bounds__(F32Cfg<NP>::THREADS)
+    k_ax32(int64_t E, const float *__restrict__ Df, const GT *__restrict__ G, const float *__restrict__ B, float h1,
+           float h2, const float *__restrict__ u, float *__restrict__ w, const int32_t *__restrict__ map) {
+  using C = F32Cfg<NP>;
+  extern __shared__ float smf[];
+  float *sD = smf;
+  const int tid = threadIdx.x;
+  const int le = tid / C::N2;
+  const int ij = tid - le * C::N2;
+  const int i = ij % NP, j = ij / NP;
+  float *s_u = smf + NP * (NP + 1) + le * 3 * C::N3;
+  float *s_r = s_u + C::N3;
+  float *s_s = s_r + C::N3;
+  for (int t = tid; t < NP * NP; t += C::THREADS) sD[(t / NP) * (NP + 1) + (t % NP)] = Df[t];
+  __syncthreads();
+  for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += (int64_t)gridDim.x * C::ELB) {
+    const int64_t e = e0 + le;
+    const bool act = e < E;
+    float ru[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int p = i + NP * j + C::N2 * k;
+      float v = 0.0f;
+      if (act) {
+        const int32_t g = map[e * C::N3 + p];
+        v = (g >= 0) ? u[g] : 0.0f;
+      }
+      ru[k] = v;
+      s_u[p] = v;
+    }
+    __syncthreads();
+    float rt[NP];
+    const int64_t gbase = (act ? e : 0) * 6 * C::N3;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int p = i + NP * j + C::N2 * k;
+      float ur = 0.0f, us = 0.0f, ut = 0.0f;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        ur = fmaf(sD[i * (NP + 1) + m], s_u[m + NP * j + C::N2 * k], ur);
+        us = fmaf(sD[j * (NP + 1) + m], s_u[i + NP * m + C::N2 * k], us);
+        ut = fmaf(sD[k * (NP + 1) + m], ru[m], ut);
+      }
+      float g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0;
+      if (act) {
+        g00 = ldg_real(G, gbase + p);
+        g01 = ldg_real(G, gbase + C::N3 + p);
+        g02 = ldg_real(G, gbase + 2 * C::N3 + p);
+        g11 = ldg_real(G, gbase + 3 * C::N3 + p);
+        g12 = ldg_real(G, gbase + 4 * C::N3 + p);
+        g22 = ldg_real(G, gbase + 5 * C::N3 + p);
+      }
+      s_r[p] = g00 * ur + g01 * us + g02 * ut;
+      s_s[p] = g01 * ur + g11 * us + g12 * ut;
+      rt[k] = g02 * ur + g12 * us + g22 * ut;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int p = i + NP * j + C::N2 * k;
+      float acc = 0.0f;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        acc = fmaf(sD[m * (NP + 1) + i], s_r[m + NP * j + C::N2 * k], acc);
+        acc = fmaf(sD[m * (NP + 1) + j], s_s[i + NP * m + C::N2 * k], acc);
+        acc = fmaf(sD[m * (NP + 1) + k], rt[m], acc);
+      }
+      float val = h1 * acc;
+      if (h2 != 0.0f && act) val = fmaf(h2 * B[e * C::N3 + p], ru[k], val);
+      if (act) {
+        const int32_t g = map[e * C::N3 + p];
+        if (g >= 0) atomicAdd(&w[g], val);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int NP>
+int launch_ax32_np(const PmgLevel &lv, int gprec, float h1, float h2, const float *u, float *w, cudaStream_t st) {
+  using C = F32Cfg<NP>;
+  const unsigned grid = (unsigned)std::max<int64_t>((lv.m->E + C::ELB - 1) / C::ELB, 1);
+  if (gprec == SEM_PREC_BF16) {
+    auto kern = k_ax32<NP, __nv_bfloat16>;
+    if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    kern<<<grid, C::THREADS, C::SMEM, st>>>(lv.m->E, lv.Df, lv.Gb, lv.Bf, h1, h2, u, w, lv.m->l2gm);
+  } else {
+    auto kern = k_ax32<NP, float>;
+    if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    kern<<<grid, C::THREADS, C::SMEM, st>>>(lv.m->E, lv.Df, lv.Gf, lv.Bf, h1, h2, u, w, lv.m->l2gm);
+  }
+  SEM_LAUNCH_CHECK("k_ax32");
+  return SEM_OK;
+}
+
+int launch_ax32(const PmgLevel &lv, int gprec, float h1, float h2, const float *u, float *w, cudaStream_t st) {
+  switch (lv.m->n) {
+#define CASE(NPV) \
+  case NPV:       \
+    return launch_ax32_np<NPV>(lv, gprec, h1, h2, u, w, st);
+    CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
+#undef CASE
+    default:
+      return sem_fail(SEM_ERR_INVALID_ARG, "pmg: unsupported order");
+  }
+}
+
+// ---------------------------------------------------------------- transfers
+// fine level uf = P uc: per fine element, interpolate the coarse element's
+// values (identical on shared nodes, so every copy stores the same value)
+__global__ void k_prolong(int nf, int nc, int64_t E, const float *__restrict__ J, const int32_t *__restrict__ mapc,
+                          const float *__restrict__ uc, const int32_t *__restrict__ mapf, float *__restrict__ uf) {
+  __shared__ float tile[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];
+  __shared__ float Js[SEM_MAXNP * SEM_MAXNP];
+  const int nc3 = nc * nc * nc, nf3 = nf * nf * nf;
+  for (int t = threadIdx.x; t < nf * nc; t += blockDim.x) Js[t] = J[t];
+  for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < nc3; t += blockDim.x) {
+      const int32_t g = mapc[e * nc3 + t];
+      tile[t] = g >= 0 ? uc[g] : 0.0f;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nf3; q += blockDim.x) {
+      const int i = q % nf, j = (q / nf) % nf, k = q / (nf * nf);
+      float s = 0.0f;
+      for (int c = 0; c < nc; ++c) {
+        float sb = 0.0f;
+        for (int b = 0; b < nc; ++b) {
+          float sa = 0.0f;
+          for (int a = 0; a < nc; ++a) sa = fmaf(Js[i * nc + a], tile[a + nc * (b + nc * c)], sa);
+          sb = fmaf(Js[j * nc + b], sa, sb);
+        }
+        s = fmaf(Js[k * nc + c], sb, s);
+      }
+      const int32_t g = mapf[e * nf3 + q];
+      if (g >= 0) uf[g] = s;
+    }
+  }
+}
+
+// coarse level rc += R rf = P^T rf: per element, J^T (x) J^T (x) J^T applied to
+// the fine element's rf / multiplicity, summed into the coarse vector
+__global__ void k_restrict(int nf, int nc, int64_t E, const float *__restrict__ J, const int32_t *__restrict__ mapf,
+                           const float *__restrict__ minvf, const float *__restrict__ rf,
+                           const int32_t *__restrict__ mapc, float *__restrict__ rc) {
+  __shared__ float tile[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];
+  __shared__ float Js[SEM_MAXNP * SEM_MAXNP];
+  const int nc3 = nc * nc * nc, nf3 = nf * nf * nf;
+  for (int t = threadIdx.x; t < nf * nc; t += blockDim.x) Js[t] = J[t];
+  for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < nf3; t += blockDim.x) {
+      const int32_t g = mapf[e * nf3 + t];
+      tile[t] = g >= 0 ? rf[g] * minvf[g] : 0.0f;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc3; q += blockDim.x) {
+      const int a = q % nc, b = (q / nc) % nc, c = q / (nc * nc);
+      float s = 0.0f;
+      for (int k = 0; k < nf; ++k) {
+        float sj = 0.0f;
+        for (int j = 0; j < nf; ++j) {
+          float si = 0.0f;
+          for (int i = 0; i < nf; ++i) si = fmaf(Js[i * nc + a], tile[i + nf * (j + nf * k)], si);
+          sj = fmaf(Js[j * nc + b], si, sj);
+        }
+        s = fmaf(Js[k * nc + c], sj, s);
+      }
+      const int32_t g = mapc[e * nc3 + q];
+      if (g >= 0) atomicAdd(&rc[g], s);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- vector kernels
+__global__ void k_cheb_start(int64_t n, const float *__restrict__ b, const float *__restrict__ dinv, float c0,
+                             float *__restrict__ x, float *__restrict__ r, float *__restrict__ d) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const float bv = b[g];
+    x[g] = 0.0f;
+    r[g] = bv;
+    d[g] = c0 * dinv[g] * bv;
+  }
+}
+
+__global__ void k_scaled(int64_t n, const float *__restrict__ r, const float *__restrict__ dinv, float c0,
+                         float *__restrict__ d) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    d[g] = c0 * dinv[g] * r[g];
+}
+
+// x += d;  d = c1 d + c2 dinv r
+__global__ void k_cheb_xd(int64_t n, float c1, float c2, const float *__restrict__ dinv, const float *__restrict__ r,
+                          float *__restrict__ x, float *__restrict__ d) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const float dv = d[g];
+    x[g] += dv;
+    d[g] = c1 * dv + c2 * dinv[g] * r[g];
+  }
+}
+
+__global__ void k_axpy_f(int64_t n, float a, const float *__restrict__ x, float *__restrict__ y) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    y[g] += a * x[g];
+}
+
+__global__ void k_copy_f(int64_t n, const float *__restrict__ x, float *__restrict__ y) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    y[g] = x[g];
+}
+
+// binary64 -> binary32 (leading 24 bits) with integer operations only
+__global__ void k_d2f(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    b[g] = df::from_f64(a[g]).x;
+}
+
+// binary32 -> binary64, exact, with integer operations only
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned fb = __float_as_uint(f);
+  const unsigned ef = (fb >> 23) & 0xFFu;
+  if (ef == 0u || ef == 255u) return (double)f;  // zero, subnormal, inf, nan: rare
+  const unsigned long long hi = (unsigned long long)((fb & 0x80000000u) | ((ef + 896u) << 20) | ((fb & 0x7FFFFFu) >> 3));
+  return __longlong_as_double((long long)((hi << 32) | ((unsigned long long)(fb & 7u) << 29)));
+}
+
+__global__ void k_f2d(int64_t n, const float *__restrict__ a, double *__restrict__ b) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    b[g] = f2d_bits(a[g]);
+}
+
+__global__ void k_g_to_f32(int64_t n, const double *__restrict__ G, float *__restrict__ Gf,
+                           __nv_bfloat16 *__restrict__ Gb) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const float v = (float)G[t];  // set-up only
+    if (Gf) Gf[t] = v;
+    if (Gb) Gb[t] = __float2bfloat16_rn(v);
+  }
+}
+
+__global__ void k_d2f_plain(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    b[g] = (float)a[g];  // set-up only
+}
+
+__global__ void k_minv(int64_t n, const double *__restrict__ mult, float *__restrict__ minv) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    minv[g] = (float)(1.0 / mult[g]);
+}
+
+// alternating lattice vector (-1)^(I+J+K) on free nodes
+__global__ void k_alt(int64_t n, int64_t nx, int64_t ny, const uint8_t *__restrict__ mask, float *__restrict__ v) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t I = g % nx, J = (g / nx) % ny, K = g / (nx * ny);
+    v[g] = mask[g] ? (((I + J + K) & 1) ? -1.0f : 1.0f) : 0.0f;
+  }
+}
+
+// w = dinv * w (in place), partial sums of w.w and v.v in binary64
+__global__ void k_power_step(int64_t n, const float *__restrict__ dinv, float *__restrict__ w,
+                             const float *__restrict__ v, double *__restrict__ part) {
+  __shared__ double red[2][32];
+  double ww = 0.0, vv = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const float x = dinv[g] * w[g];
+    w[g] = x;
+    ww += (double)x * (double)x;
+    vv += (double)v[g] * (double)v[g];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    ww += __shfl_xor_sync(0xffffffffu, ww, off);
+    vv += __shfl_xor_sync(0xffffffffu, vv, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = ww;
+    red[1][threadIdx.x >> 5] = vv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int t = 0; t < (int)(blockDim.x >> 5); ++t) {
+      a += red[0][t];
+      b += red[1][t];
+    }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void k_scale_f(int64_t n, float a, float *__restrict__ x) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    x[g] *= a;
+}
+
+// partial sums of (a.b, c.d) in binary64; c may be null
+__global__ void k_dots(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
+                       const double *__restrict__ c, const double *__restrict__ d, double *__restrict__ part) {
+  __shared__ double red[2][32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    s0 = fma(a[g], b[g], s0);
+    if (c) s1 = fma(c[g], d[g], s1);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s0;
+    red[1][threadIdx.x >> 5] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0, y = 0;
+    for (int t = 0; t < (int)(blockDim.x >> 5); ++t) {
+      x += red[0][t];
+      y += red[1][t];
+    }
+    part[2 * blockIdx.x] = x;
+    part[2 * blockIdx.x + 1] = y;
+  }
+}
+
+// x += alpha p; r -= alpha w
+__global__ void k_fcg_update(int64_t n, double alpha, const double *__restrict__ p, const double *__restrict__ w,
+                             double *__restrict__ x, double *__restrict__ r) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    x[g] = fma(alpha, p[g], x[g]);
+    r[g] = fma(-alpha, w[g], r[g]);
+  }
+}
+
+// p = z + beta p
+__global__ void k_xpby(int64_t n, const double *__restrict__ z, double beta, double *__restrict__ p) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    p[g] = fma(beta, p[g], z[g]);
+}
+
+__global__ void k_init_fcg(int64_t n, const double *__restrict__ b, const uint8_t *__restrict__ mask,
+                           double *__restrict__ x, double *__restrict__ r) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    x[g] = 0.0;
+    r[g] = mask[g] ? b[g] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- host helpers
+int sum_pairs(const double *dpart, double *a, double *b, cudaStream_t st) {
+  double h[2 * kPart];
+  SEM_CUDA(cudaMemcpyAsync(h, dpart, sizeof(h), cudaMemcpyDeviceToHost, st));
+  SEM_CUDA(cudaStreamSynchronize(st));
+  double x = 0, y = 0;
+  for (int t = 0; t < kPart; ++t) {
+    x += h[2 * t];
+    y += h[2 * t + 1];
+  }
+  *a = x;
+  *b = y;
+  return SEM_OK;
+}
+
+int interp_matrix(const sem_mesh *mf, const sem_mesh *mc, float *dJ, cudaStream_t st) {
+  const int nf = mf->n, nc = mc->n;
+  std::vector<float> J(nf * nc);
+  for (int i = 0; i < nf; ++i)
+    for (int m = 0; m < nc; ++m) {
+      long double v = 1.0L;
+      for (int j = 0; j < nc; ++j)
+        if (j != m) v *= ((long double)mf->xi[i] - mc->xi[j]) / ((long double)mc->xi[m] - mc->xi[j]);
+      J[i * nc + m] = (float)v;
+    }
+  SEM_CUDA(cudaMemcpyAsync(dJ, J.data(), sizeof(float) * nf * nc, cudaMemcpyHostToDevice, st));
+  SEM_CUDA(cudaStreamSynchronize(st));  // J lives on the host stack frame until copied
+  return SEM_OK;
+}
+
+int ax32(sem_pmg *P, int l, float h1s, const float *u, float *w, cudaStream_t st) {
+  return launch_ax32(P->L[l], P->o.smoother_precision, (float)(h1s * P->h1), (float)(h1s * P->h2), u, w, st);
+}
+
+// r = b - A x
+int residual(sem_pmg *P, int l, cudaStream_t st) {
+  PmgLevel &lv = P->L[l];
+  const int64_t n = lv.m->n_unique;
+  k_copy_f<<<grid_for(n, 256), 256, 0, st>>>(n, lv.b, lv.r);
+  return ax32(P, l, -1.0f, lv.x, lv.r, st);
+}
+
+// Chebyshev smoothing of A x = b on level l; zero initial guess when `zero`
+int smooth(sem_pmg *P, int l, bool zero, cudaStream_t st) {
+  PmgLevel &lv = P->L[l];
+  const int64_t n = lv.m->n_unique;
+  const unsigned g = grid_for(n, 256);
+  const float lam = lv.lam;
+  const float c0 = 4.0f / (3.0f * lam);
+  int rc;
+  if (zero) {
+    k_cheb_start<<<g, 256, 0, st>>>(n, lv.b, lv.dinv, c0, lv.x, lv.r, lv.d);
+  } else {
+    if ((rc = residual(P, l, st))) return rc;
+    k_scaled<<<g, 256, 0, st>>>(n, lv.r, lv.dinv, c0, lv.d);
+  }
+  for (int i = 1; i < P->o.cheb_degree; ++i) {
+    if ((rc = ax32(P, l, -1.0f, lv.d, lv.r, st))) return rc;  // r -= A d
+    const float c1 = (float)(2 * i - 1) / (float)(2 * i + 3);
+    const float c2 = (float)(8 * i + 4) / ((float)(2 * i + 3) * lam);
+    k_cheb_xd<<<g, 256, 0, st>>>(n, c1, c2, lv.dinv, lv.r, lv.x, lv.d);
+  }
+  k_axpy_f<<<g, 256, 0, st>>>(n, 1.0f, lv.d, lv.x);
+  SEM_LAUNCH_CHECK("chebyshev");
+  return SEM_OK;
+}
+
+int restrict_to(sem_pmg *P, int l, const float *rf, float *rc, cudaStream_t st) {
+  PmgLevel &f = P->L[l], &c = P->L[l + 1];
+  SEM_CUDA(cudaMemsetAsync(rc, 0, sizeof(float) * c.m->n_unique, st));
+  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 64);
+  k_restrict<<<grid, 128, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], f.m->l2gm, f.minv, rf, c.m->l2gm, rc);
+  SEM_LAUNCH_CHECK("k_restrict");
+  return SEM_OK;
+}
+
+int prolong_to(sem_pmg *P, int l, const float *uc, float *uf, cudaStream_t st) {
+  PmgLevel &f = P->L[l], &c = P->L[l + 1];
+  SEM_CUDA(cudaMemsetAsync(uf, 0, sizeof(float) * f.m->n_unique, st));
+  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 64);
+  k_prolong<<<grid, 256, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.m->l2gm, uc, f.m->l2gm, uf);
+  SEM_LAUNCH_CHECK("k_prolong");
+  return SEM_OK;
+}
+
+int coarse_solve(sem_pmg *P, cudaStream_t st) {
+  PmgLevel &lv = P->L.back();
+  const int64_t n = lv.m->n_unique;
+  k_f2d<<<grid_for(n, 256), 256, 0, st>>>(n, lv.b, P->cb);
+  sem_solver_opts o;
+  o.tol = P->o.coarse_tol;
+  o.maxit = P->o.coarse_maxit;
+  o.precision = SEM_PREC_FP64;
+  o.timeout_s = 0.0;
+  o.mask_mode = 0;
+  sem_solve_stats stt;
+  int rc = sem_pcg_solve(lv.m, P->h1, P->h2, P->cb, P->cx, &o, P->cws, &stt, (void *)st);
+  if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
+  k_d2f<<<grid_for(n, 256), 256, 0, st>>>(n, P->cx, lv.x);
+  SEM_LAUNCH_CHECK("coarse solve");
+  return SEM_OK;
+}
+
+// V-cycle on level l: L[l].x ~ A_l^{-1} L[l].b
+int vcycle(sem_pmg *P, int l, cudaStream_t st) {
+  if (l == (int)P->L.size() - 1) return coarse_solve(P, st);
+  int rc;
+  PmgLevel &lv = P->L[l];
+  const int64_t n = lv.m->n_unique;
+  if ((rc = smooth(P, l, true, st))) return rc;
+  if ((rc = residual(P, l, st))) return rc;
+  if ((rc = restrict_to(P, l, lv.r, P->L[l + 1].b, st))) return rc;
+  if ((rc = vcycle(P, l + 1, st))) return rc;
+  if ((rc = prolong_to(P, l, P->L[l + 1].x, lv.t, st))) return rc;
+  k_axpy_f<<<grid_for(n, 256), 256, 0, st>>>(n, 1.0f, lv.t, lv.x);
+  return smooth(P, l, false, st);
+}
+
+int power_lambda(sem_pmg *P, int l, cudaStream_t st) {
+  PmgLevel &lv = P->L[l];
+  const sem_mesh *m = lv.m;
+  const int64_t n = m->n_unique;
+  const int64_t nx = (int64_t)m->nel[0] * m->N + (m->periodic[0] ? 0 : 1);
+  const int64_t ny = (int64_t)m->nel[1] * m->N + (m->periodic[1] ? 0 : 1);
+  k_alt<<<grid_for(n, 256), 256, 0, st>>>(n, nx, ny, m->mask, lv.x);
+  double lam = 0.0;
+  for (int it = 0; it < P->o.power_its; ++it) {
+    SEM_CUDA(cudaMemsetAsync(lv.t, 0, sizeof(float) * n, st));
+    if (int rc = ax32(P, l, 1.0f, lv.x, lv.t, st)) return rc;
+    k_power_step<<<kPart, 256, 0, st>>>(n, lv.dinv, lv.t, lv.x, P->part);
+    SEM_LAUNCH_CHECK("power iteration");
+    double ww, vv;
+    if (int rc = sum_pairs(P->part, &ww, &vv, st)) return rc;
+    if (!(ww > 0.0) || !(vv > 0.0)) return sem_fail(SEM_ERR_BREAKDOWN, "pmg: power iteration degenerated");
+    lam = sqrt(ww / vv);
+    k_copy_f<<<grid_for(n, 256), 256, 0, st>>>(n, lv.t, lv.x);
+    k_scale_f<<<grid_for(n, 256), 256, 0, st>>>(n, (float)(1.0 / sqrt(ww)), lv.x);
+  }
+  lv.lam = (float)(P->o.lambda_safety * lam);
+  return SEM_OK;
+}
+
+void free_pmg(sem_pmg *P) {
+  if (!P) return;
+  for (auto &lv : P->L)
+    if (lv.own && lv.m) sem_mesh_destroy(lv.m);
+  for (void *q : P->owned) cudaFree(q);
+  delete P;
+}
+
+}  // namespace
+
+extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem_pmg_opts *o, void *stream,
+                              sem_pmg **out) {
+  if (!m || !o || !out) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: NULL argument");
+  *out = nullptr;
+  if (o->nlevels < 2 || o->nlevels > 4 || o->orders[0] != m->N)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: need 2..4 levels with orders[0] = the mesh's N");
+  for (int l = 1; l < o->nlevels; ++l)
+    if (o->orders[l] < 1 || o->orders[l] >= o->orders[l - 1])
+      return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: orders must decrease strictly and stay >= 1");
+  if (o->smoother_precision != SEM_PREC_FP32 && o->smoother_precision != SEM_PREC_BF16)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: smoother precision must be FP32 or BF16");
+  if (o->cheb_degree < 1 || !(o->lambda_safety >= 1.0) || o->power_its < 1 || !(o->coarse_tol > 0) ||
+      o->coarse_maxit < 1 || !(h1 > 0) || !(h2 >= 0))
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: bad option value");
+  cudaStream_t st = as_stream(stream);
+  sem_pmg *P = new sem_pmg();
+  P->o = *o;
+  P->h1 = h1;
+  P->h2 = h2;
+  int rc = SEM_OK;
+  auto alloc = [&](void **p, size_t bytes) -> int {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return sem_cuda_fail(e, "sem_pmg_create: cudaMalloc");
+    P->owned.push_back(*p);
+    return SEM_OK;
+  };
+  P->L.resize(o->nlevels);
+  for (int l = 0; l < o->nlevels && !rc; ++l) {
+    PmgLevel &lv = P->L[l];
+    if (l == 0) {
+      lv.m = const_cast<sem_mesh *>(m);
+    } else {
+      sem_box_desc d = m->desc;
+      d.N = o->orders[l];
+      rc = sem_mesh_create_box(&d, stream, &lv.m);
+      if (rc) break;
+      lv.own = true;
+    }
+    const int64_t nL = lv.m->n_local, nU = lv.m->n_unique;
+    const bool coarsest = l == o->nlevels - 1;
+    if (!coarsest) {
+      if (o->smoother_precision == SEM_PREC_BF16) rc = rc ? rc : alloc((void **)&lv.Gb, sizeof(__nv_bfloat16) * 6 * nL);
+      else rc = rc ? rc : alloc((void **)&lv.Gf, sizeof(float) * 6 * nL);
+      rc = rc ? rc : alloc((void **)&lv.Bf, sizeof(float) * nL);
+      rc = rc ? rc : alloc((void **)&lv.Df, sizeof(float) * lv.m->n * lv.m->n);
+      rc = rc ? rc : alloc((void **)&lv.dinv, sizeof(float) * nU);
+      rc = rc ? rc : alloc((void **)&lv.r, sizeof(float) * nU);
+      rc = rc ? rc : alloc((void **)&lv.d, sizeof(float) * nU);
+      rc = rc ? rc : alloc((void **)&lv.t, sizeof(float) * nU);
+      rc = rc ? rc : alloc((void **)&lv.minv, sizeof(float) * nU);
+    }
+    rc = rc ? rc : alloc((void **)&lv.b, sizeof(float) * nU);
+    rc = rc ? rc : alloc((void **)&lv.x, sizeof(float) * nU);
+  }
+  if (!rc) rc = alloc((void **)&P->part, sizeof(double) * 2 * kPart);
+  if (rc) {
+    free_pmg(P);
+    return rc;
+  }
+  // per-level binary32 data
+  for (int l = 0; l + 1 < o->nlevels && !rc; ++l) {
+    PmgLevel &lv = P->L[l];
+    const sem_mesh *lm = lv.m;
+    k_g_to_f32<<<grid_for(6 * lm->n_local, 256), 256, 0, st>>>(6 * lm->n_local, lm->G, lv.Gf, lv.Gb);
+    k_d2f_plain<<<grid_for(lm->n_local, 256), 256, 0, st>>>(lm->n_local, lm->B, lv.Bf);
+    k_d2f_plain<<<1, 128, 0, st>>>(lm->n * lm->n, lm->dD, lv.Df);
+    k_minv<<<grid_for(lm->n_unique, 256), 256, 0, st>>>(lm->n_unique, lm->mult, lv.minv);
+    // Jacobi diagonal (binary64) -> binary32
+    double *dd = nullptr;
+    if (cudaMalloc(&dd, sizeof(double) * lm->n_unique) != cudaSuccess) {
+      rc = sem_fail(SEM_ERR_NOMEM, "sem_pmg_create: cudaMalloc(diag)");
+      break;
+    }
+    rc = sem_jacobi_inv(lm, h1, h2, dd, stream);
+    k_d2f_plain<<<grid_for(lm->n_unique, 256), 256, 0, st>>>(lm->n_unique, dd, lv.dinv);
+    cudaStreamSynchronize(st);
+    cudaFree(dd);
+    if (!rc) rc = power_lambda(P, l, st);
+  }
+  for (int l = 0; l + 1 < o->nlevels && !rc; ++l) {
+    rc = alloc((void **)&P->J[l], sizeof(float) * P->L[l].m->n * P->L[l + 1].m->n);
+    if (!rc) rc = interp_matrix(P->L[l].m, P->L[l + 1].m, P->J[l], st);
+  }
+  // coarsest level binary64 vectors and solver workspace
+  const sem_mesh *cm = P->L.back().m;
+  size_t cwb = 0;
+  if (!rc) rc = sem_pcg_workspace_bytes(cm, &cwb);
+  if (!rc) rc = alloc((void **)&P->cb, sizeof(double) * cm->n_unique);
+  if (!rc) rc = alloc((void **)&P->cx, sizeof(double) * cm->n_unique);
+  if (!rc) rc = alloc(&P->cws, cwb);
+  // outer FCG vectors on the fine level
+  const int64_t nU = m->n_unique;
+  double **vecs[] = {&P->r, &P->z, &P->zn, &P->p, &P->w};
+  for (double **v : vecs)
+    if (!rc) rc = alloc((void **)v, sizeof(double) * nU);
+  if (!rc) {
+    const int npw = std::max(sem_ax_assembled_blocks(m, SEM_PREC_FP64), sem_ax_assembled_blocks(m, SEM_PREC_DF64));
+    rc = alloc((void **)&P->pw_part, sizeof(double) * std::max(npw, 1));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (!rc && e != cudaSuccess) rc = sem_cuda_fail(e, "sem_pmg_create");
+  if (rc) {
+    free_pmg(P);
+    return rc;
+  }
+  *out = P;
+  return SEM_OK;
+}
+
+extern "C" int sem_pmg_destroy(sem_pmg *P) {
+  free_pmg(P);
+  return SEM_OK;
+}
+
+extern "C" int sem_pmg_lambda(const sem_pmg *P, int level, double *lambda) {
+  if (!P || !lambda || level < 0 || level + 1 >= (int)P->L.size())
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_lambda: bad argument (smoothing levels only)");
+  *lambda = P->L[level].lam;
+  return SEM_OK;
+}
+
+extern "C" int sem_pmg_vcycle(sem_pmg *P, const double *r_g, double *z_g, void *stream) {
+  if (!P || !r_g || !z_g) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_vcycle: NULL argument");
+  cudaStream_t st = as_stream(stream);
+  PmgLevel &lv = P->L[0];
+  const int64_t n = lv.m->n_unique;
+  k_d2f<<<grid_for(n, 256), 256, 0, st>>>(n, r_g, lv.b);
+  if (int rc = vcycle(P, 0, st)) return rc;
+  k_f2d<<<grid_for(n, 256), 256, 0, st>>>(n, lv.x, z_g);
+  SEM_LAUNCH_CHECK("sem_pmg_vcycle");
+  return SEM_OK;
+}
+
+extern "C" int sem_pmg_prolong(sem_pmg *P, int level, const double *uc_g, double *uf_g, void *stream) {
+  if (!P || !uc_g || !uf_g || level < 0 || level + 1 >= (int)P->L.size())
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_prolong: bad argument");
+  cudaStream_t st = as_stream(stream);
+  PmgLevel &f = P->L[level], &c = P->L[level + 1];
+  k_d2f<<<grid_for(c.m->n_unique, 256), 256, 0, st>>>(c.m->n_unique, uc_g, c.b);
+  if (int rc = prolong_to(P, level, c.b, f.b, st)) return rc;
+  k_f2d<<<grid_for(f.m->n_unique, 256), 256, 0, st>>>(f.m->n_unique, f.b, uf_g);
+  SEM_LAUNCH_CHECK("sem_pmg_prolong");
+  return SEM_OK;
+}
+
+extern "C" int sem_pmg_restrict(sem_pmg *P, int level, const double *rf_g, double *rc_g, void *stream) {
+  if (!P || !rf_g || !rc_g || level < 0 || level + 1 >= (int)P->L.size())
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_restrict: bad argument");
+  cudaStream_t st = as_stream(stream);
+  PmgLevel &f = P->L[level], &c = P->L[level + 1];
+  k_d2f<<<grid_for(f.m->n_unique, 256), 256, 0, st>>>(f.m->n_unique, rf_g, f.b);
+  if (int rc = restrict_to(P, level, f.b, c.b, st)) return rc;
+  k_f2d<<<grid_for(c.m->n_unique, 256), 256, 0, st>>>(c.m->n_unique, c.b, rc_g);
+  SEM_LAUNCH_CHECK("sem_pmg_restrict");
+  return SEM_OK;
+}
+
+extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, const sem_solver_opts *opts,
+                                 sem_solve_stats *stats, void *stream) {
+  if (!P || !b_g || !x_g || !opts || !stats) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_pcg_solve: NULL argument");
+  if (opts->mask_mode != 0 || (opts->precision != SEM_PREC_FP64 && opts->precision != SEM_PREC_DF64) ||
+      !(opts->tol >= 0.0) || opts->maxit < 1)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_pcg_solve: bad options");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = as_stream(stream);
+  const sem_mesh *m = P->L[0].m;
+  const int64_t n = m->n_unique;
+  const unsigned g = grid_for(n, 256);
+  int rc;
+  stats->iterations = 0;
+  stats->status = SEM_OK;
+  k_init_fcg<<<g, 256, 0, st>>>(n, b_g, m->mask, x_g, P->r);
+  k_dots<<<kPart, 256, 0, st>>>(n, P->r, P->r, nullptr, nullptr, P->part);
+  SEM_LAUNCH_CHECK("fcg init");
+  double bb, unused;
+  if ((rc = sum_pairs(P->part, &bb, &unused, st))) return rc;
+  const double bn = sqrt(bb);
+  auto finish = [&](int status, int it, double rr) {
+    stats->iterations = it;
+    stats->rel_residual = bn > 0 ? sqrt(rr) / bn : 0.0;
+    stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    stats->status = status;
+    if (status == SEM_ERR_NOT_CONVERGED) sem_fail(status, "sem_pmg_pcg_solve: maxit reached");
+    if (status == SEM_ERR_BREAKDOWN) sem_fail(status, "sem_pmg_pcg_solve: breakdown");
+    return status;
+  };
+  if (!(bn > 0.0)) return finish(std::isfinite(bb) ? SEM_OK : SEM_ERR_BREAKDOWN, 0, 0.0);
+  if ((rc = sem_pmg_vcycle(P, P->r, P->z, stream))) return rc;
+  SEM_CUDA(cudaMemcpyAsync(P->p, P->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  k_dots<<<kPart, 256, 0, st>>>(n, P->r, P->z, nullptr, nullptr, P->part);
+  double rz;
+  if ((rc = sum_pairs(P->part, &rz, &unused, st))) return rc;
+  const int npw = sem_ax_assembled_blocks(m, opts->precision);
+  double rr = bb;
+  for (int it = 1; it <= opts->maxit; ++it) {
+    SEM_CUDA(cudaMemsetAsync(P->w, 0, sizeof(double) * n, st));
+    if ((rc = sem_launch_ax_assembled(m, P->h1, P->h2, P->p, P->w, P->pw_part, opts->precision, st))) return rc;
+    std::vector<double> hp(npw);
+    SEM_CUDA(cudaMemcpyAsync(hp.data(), P->pw_part, sizeof(double) * npw, cudaMemcpyDeviceToHost, st));
+    SEM_CUDA(cudaStreamSynchronize(st));
+    double pw = 0.0;
+    for (double v : hp) pw += v;
+    if (!(pw > 0.0) || !std::isfinite(pw)) return finish(SEM_ERR_BREAKDOWN, it, rr);
+    const double alpha = rz / pw;
+    k_fcg_update<<<g, 256, 0, st>>>(n, alpha, P->p, P->w, x_g, P->r);
+    k_dots<<<kPart, 256, 0, st>>>(n, P->r, P->r, nullptr, nullptr, P->part);
+    SEM_LAUNCH_CHECK("fcg update");
+    if ((rc = sum_pairs(P->part, &rr, &unused, st))) return rc;
+    if (!std::isfinite(rr)) return finish(SEM_ERR_BREAKDOWN, it, rr);
+    if (sqrt(rr) <= opts->tol * bn) return finish(SEM_OK, it, rr);
+    if (opts->timeout_s > 0.0 &&
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > opts->timeout_s)
+      return finish(SEM_ERR_TIMEOUT, it, rr);
+    if ((rc = sem_pmg_vcycle(P, P->r, P->zn, stream))) return rc;
+    k_dots<<<kPart, 256, 0, st>>>(n, P->r, P->zn, P->r, P->z, P->part);
+    double rzn, rzo;
+    if ((rc = sum_pairs(P->part, &rzn, &rzo, st))) return rc;
+    const double beta = (rzn - rzo) / rz;
+    rz = rzn;
+    k_xpby<<<g, 256, 0, st>>>(n, P->zn, beta, P->p);
+    SEM_LAUNCH_CHECK("fcg direction");
+    std::swap(P->z, P->zn);
+  }
+  return finish(SEM_ERR_NOT_CONVERGED, opts->maxit, rr);
+}

@@ -438,6 +438,7 @@ extern "C" int sem_mesh_create_box(const sem_box_desc *d, void *stream, sem_mesh
   m->L[0] = d->Lx;
   m->L[1] = d->Ly;
   m->L[2] = d->Lz;
+  m->desc = *d;
   cudaGetDevice(&m->device);
   sem_gll_host(d->N, m->xi, m->rho, m->D);
 

@@ -1,0 +1,122 @@
+"""GPU parity of the p-multigrid preconditioner and the mixed-precision
+flexible CG (Sec. 2.2: p-multigrid, 4th-kind Chebyshev smoothing, FP32
+preconditioner) against the binary64 oracle. Smoothing levels run in binary32
+(or bfloat16 geometry), so component parity is checked at binary32 level and
+the solve against binary64 residuals and solutions."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import pmg
+
+torch = pytest.importorskip("torch")
+import paper_2501_13240_gb300 as sem  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+KAPPA = np.array([[1.0, 2.0, 1.0], [2.0, 1.0, 1.0], [1.0, 1.0, 2.0]])
+PHI = np.array([0.3, 1.7, 4.1])
+
+
+def rel_err(a, b):
+    s = np.abs(b).max()
+    return np.abs(np.asarray(a) - b).max() / (s if s > 0 else 1.0)
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+CASES = [(((4, 3, 3), 0.05), (7, 3, 1)), (((3, 3, 2), 0.0), (7, 3, 1)), (((2, 3, 2), 0.05), (6, 3, 1))]
+
+
+@pytest.fixture(scope="module", params=range(len(CASES)), ids=lambda i: "case%d" % i)
+def hier(request):
+    (nel, deform), orders = CASES[request.param]
+    box = dict(nel=nel, deform_amp=deform, kappa=KAPPA, phi=PHI)
+    pm = pmg.PMG(box, orders=orders)
+    gm = sem.sem_mesh_create_box(nel, orders[0], deform_amp=deform, kappa=KAPPA, phi=PHI)
+    gp = sem.sem_pmg_create(gm, orders=orders)
+    yield pm, gm, gp
+    gp.destroy()
+    gm.destroy()
+
+
+def test_lambda_estimates(hier):
+    pm, gm, gp = hier
+    for l in range(len(pm.levels) - 1):
+        assert abs(gp.lam(l) - pm.levels[l].lam) <= 1e-4 * pm.levels[l].lam
+
+
+def test_transfer_operators(hier):
+    pm, gm, gp = hier
+    rng = np.random.default_rng(4)
+    for l in range(len(pm.levels) - 1):
+        mf, mc = pm.levels[l].m, pm.levels[l + 1].m
+        uc = rng.standard_normal(mc.n_unique) * mc.mask
+        uf = torch.empty(mf.n_unique, dtype=torch.float64, device="cuda")
+        sem.sem_pmg_prolong(gp, l, dev(uc), uf)
+        assert rel_err(host(uf), pm.prolong(l, uc)) < 2e-6
+        rf = rng.standard_normal(mf.n_unique) * mf.mask
+        rc = torch.empty(mc.n_unique, dtype=torch.float64, device="cuda")
+        sem.sem_pmg_restrict(gp, l, dev(rf), rc)
+        assert rel_err(host(rc), pm.restrict(l, rf) * mc.mask) < 2e-6
+
+
+def test_vcycle(hier):
+    pm, gm, gp = hier
+    m = pm.levels[0].m
+    r = np.random.default_rng(6).standard_normal(m.n_unique) * m.mask
+    z = torch.empty(m.n_unique, dtype=torch.float64, device="cuda")
+    sem.sem_pmg_vcycle(gp, dev(r), z)
+    assert rel_err(host(z), pm.vcycle(r)) < 1e-4
+
+
+@pytest.mark.parametrize("prec", [sem.SEM_PREC_DF64, sem.SEM_PREC_FP64], ids=["df64", "fp64"])
+def test_mixed_solve_reaches_binary64_tolerance(hier, prec):
+    pm, gm, gp = hier
+    m = pm.levels[0].m
+    b = oracle.poisson_rhs(m) if m.detJ_min > 0 else None
+    x = torch.zeros(m.n_unique, dtype=torch.float64, device="cuda")
+    st = sem.sem_pmg_pcg_solve(gp, dev(b), x, tol=1e-8, maxit=200, precision=prec)
+    assert st["status"] == 0
+    xg = host(x)
+    true_res = np.linalg.norm(b - oracle.apply_assembled(m, xg)) / np.linalg.norm(b)
+    assert true_res < 1.05e-8, true_res
+    ref = pmg.fcg(pm, b, tol=1e-8)
+    assert abs(st["iterations"] - ref.iterations) <= 2, (st, ref.iterations)
+    tight = oracle.pcg(m, b, tol=1e-13, maxit=5000)
+    assert rel_err(xg, tight.x) < 1e-6
+
+
+def test_bf16_smoother_converges():
+    nel, N = (4, 4, 3), 7
+    gm = sem.sem_mesh_create_box(nel, N, deform_amp=0.05, kappa=KAPPA, phi=PHI)
+    om = oracle.box_mesh(nel, N, deform_amp=0.05, kappa=KAPPA, phi=PHI)
+    b = oracle.poisson_rhs(om)
+    it = {}
+    for name, sp in (("fp32", sem.SEM_PREC_FP32), ("bf16", sem.SEM_PREC_BF16)):
+        gp = sem.sem_pmg_create(gm, orders=(7, 3, 1), smoother_precision=sp)
+        x = torch.zeros(gm.n_unique, dtype=torch.float64, device="cuda")
+        st = sem.sem_pmg_pcg_solve(gp, dev(b), x, tol=1e-8)
+        assert st["status"] == 0
+        res = np.linalg.norm(b - oracle.apply_assembled(om, host(x))) / np.linalg.norm(b)
+        assert res < 1.05e-8
+        it[name] = st["iterations"]
+        gp.destroy()
+    assert it["bf16"] <= 2 * it["fp32"] + 2, it
+    gm.destroy()
+
+
+def test_pmg_invalid_options():
+    gm = sem.sem_mesh_create_box((2, 2, 2), 5)
+    for kw in (dict(orders=(7, 3)), dict(orders=(5, 5, 1)), dict(orders=(5, 2), smoother_precision=sem.SEM_PREC_FP64),
+               dict(orders=(5, 2), cheb_degree=0)):
+        with pytest.raises(sem.SemError):
+            sem.sem_pmg_create(gm, **kw)
+    gm.destroy()
