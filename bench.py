@@ -56,11 +56,13 @@ def parse():
     ap.add_argument("--workload", default="ax_gs_64")
     ap.add_argument("--no-pcg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-rbc", action="store_true")
+    ap.add_argument("--quick-pcg", action="store_true", help="skip the slow binary64 Jacobi-PCG reference solve")
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"])
     ap.add_argument("--once", default="",
                     help="profiling mode: comma list of kernels to launch once each on the workload "
-                         "(local_df64, asm_df64, local_fp64, asm_fp64, gs), then exit")
+                         "(local_df64, asm_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16), then exit")
     return ap.parse_args()
 
 
@@ -193,6 +195,13 @@ def run_once(sem, mesh, u, names):
             sem.sem_ax_assembled_add(mesh, 1.0, 0.0, u, wg, precision=P[prec])
         elif kind == "gs":
             sem.sem_gs_op(mesh, wL, True)
+        elif kind == "vcycle":
+            sp = {"fp32": sem.SEM_PREC_FP32, "bf16": sem.SEM_PREC_BF16}[prec]
+            P = sem.sem_pmg_create(mesh, orders=(mesh.N, 3, 1), smoother_precision=sp, coarse_tol=1e-6)
+            z = torch.empty_like(u)
+            sem.sem_pmg_vcycle(P, u, z)
+            torch.cuda.synchronize()
+            P.destroy()
         else:
             raise ValueError(name)
     torch.cuda.synchronize()
@@ -323,10 +332,10 @@ def main():
            "ms_per_step": e2e_ms}
     del pin_in, pin_out
 
-    # --- PCG solve time on the same mesh (manufactured-solution right-hand side)
+    # --- solve time on the same mesh (manufactured forcing): binary64 Jacobi-PCG
+    # against the mixed-precision p-multigrid flexible CG, all to 1e-8
     pcg = None
     if not args.no_pcg:
-        # b = M Q^T (B f), f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z), assembled on the device
         # (the forcing at the nodes is input synthesis; the weak form is the library's)
         X, Y, Z = (mesh.field(n) for n in ("X", "Y", "Z"))
         fL = 3.0 * np.pi ** 2 * torch.sin(np.pi * X) * torch.sin(np.pi * Y) * torch.sin(np.pi * Z)
@@ -334,16 +343,54 @@ def main():
         b = torch.empty_like(u)
         sem.sem_weak_rhs(mesh, fL, b)
         del fL
-        x = torch.zeros_like(u)
         pcg = {}
-        for name, prec in (("df64", sem.SEM_PREC_DF64), ("fp64", sem.SEM_PREC_FP64)):
+        sols = {}
+        runs = [("jacobi_fp64", "jacobi", sem.SEM_PREC_FP64, None),
+                ("jacobi_df64", "jacobi", sem.SEM_PREC_DF64, None),
+                ("pmg_fp32_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_FP32),
+                ("pmg_bf16_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_BF16)]
+        if args.quick_pcg:
+            runs = [r for r in runs if r[0] != "jacobi_fp64"]
+        for name, kind, prec, sprec in runs:
+            x = torch.zeros_like(u)
             torch.cuda.synchronize()
-            st = sem.sem_pcg_solve(mesh, 1.0, 0.0, b, x, tol=args.pcg_tol, maxit=20000, precision=prec,
-                                   raise_on_error=False)
-            pcg[name] = {"iterations": st["iterations"], "solve_ms": st["solve_ms"],
+            setup_ms = 0.0
+            if kind == "jacobi":
+                st = sem.sem_pcg_solve(mesh, 1.0, 0.0, b, x, tol=args.pcg_tol, maxit=20000, precision=prec,
+                                       raise_on_error=False)
+            else:
+                t0 = time.perf_counter()
+                P = sem.sem_pmg_create(mesh, orders=(w.N, 3, 1) if w.N > 3 else (w.N, 1), smoother_precision=sprec,
+                                       coarse_tol=1e-6)
+                setup_ms = 1e3 * (time.perf_counter() - t0)
+                st = sem.sem_pmg_pcg_solve(P, b, x, tol=args.pcg_tol, maxit=500, precision=prec, raise_on_error=False)
+                P.destroy()
+            # true residual with the binary64 operator
+            rr = torch.empty_like(u)
+            sem.sem_ax_assembled(mesh, 1.0, 0.0, x, rr, precision=sem.SEM_PREC_FP64)
+            true_res = float(torch.linalg.norm(b - rr) / torch.linalg.norm(b))
+            pcg[name] = {"iterations": st["iterations"], "solve_ms": st["solve_ms"], "setup_ms": setup_ms,
                          "ms_per_iteration": st["solve_ms"] / max(st["iterations"], 1),
-                         "rel_residual": st["rel_residual"], "status": st["status"]}
-        del b, x
+                         "rel_residual": st["rel_residual"], "true_rel_residual_fp64": true_res,
+                         "status": st["status"]}
+            sols[name] = x
+        ref = sols.get("jacobi_fp64", sols.get("jacobi_df64"))
+        for name, x in sols.items():
+            pcg[name]["solution_rel_diff_vs_fp64_jacobi"] = float((x - ref).abs().max() / ref.abs().max())
+        del b, sols
+
+    # --- one Rayleigh-Benard BDF2/EXT2 step (32^3 elements, Ra = 1e8, Pr = 0.7)
+    rbc = None
+    if not args.no_rbc:
+        rw = workloads.RBC_32
+        rm = sem.mesh_from_workload(rw)
+        pert = torch.from_numpy(workloads.perturbation(rm.n_unique, 1e-3)).cuda()
+        rs = sem.sem_rbc_create(rm, 1e8, 0.7, 1e-3, tol=1e-8, precision=sem.SEM_PREC_DF64, T_pert=pert)
+        steps = [sem.sem_bdf_ext_step(rs, raise_on_error=False) for _ in range(3)]
+        rbc = {"workload": rw.name, "steps": steps, "ms_per_step_after_first": float(
+            np.mean([s_["step_ms"] for s_ in steps[1:]]))}
+        rs.destroy()
+        rm.destroy()
 
     # --- CPU oracle baseline on rank 0
     cpu = None
@@ -361,7 +408,7 @@ def main():
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clocks,
-            "extra": {"precision": head, "per_precision": per, "pcg": pcg},
+            "extra": {"precision": head, "per_precision": per, "solves": pcg, "rbc_step": rbc},
         }
         print(json.dumps(line))
     mesh.destroy()
