@@ -43,8 +43,9 @@ BYTES_PER_POINT_AXGS = 62.7  # G 48 + l2g 4 + (u read + w write) 16 per unique n
 FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 rate (vector and tensor)
 DTYPES = {"df64": "f32x2 (double-float, binary64-accurate)", "fp64": "f64"}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the assembled
-# operator kernel (ncu, scaled from the 32^3-element case); None until measured
-TRAFFIC = {}
+# operator kernel on the 64^3 workload, scaled by points from the ncu capture
+# of the 32^3-element case (traffic grows with the points streamed)
+TRAFFIC = {"df64": 9.58e9}
 
 
 def parse():
