@@ -198,7 +198,7 @@ def run_once(sem, mesh, u, names):
             sem.sem_gs_op(mesh, wL, True)
         elif kind == "vcycle":
             sp = {"fp32": sem.SEM_PREC_FP32, "bf16": sem.SEM_PREC_BF16}[prec]
-            P = sem.sem_pmg_create(mesh, orders=(mesh.N, 3, 1), smoother_precision=sp, coarse_tol=1e-6)
+            P = sem.sem_pmg_create(mesh, orders=(mesh.N, 3, 1), smoother_precision=sp, coarse_tol=1e-2)
             z = torch.empty_like(u)
             sem.sem_pmg_vcycle(P, u, z)
             torch.cuda.synchronize()
@@ -362,7 +362,7 @@ def main():
             else:
                 t0 = time.perf_counter()
                 P = sem.sem_pmg_create(mesh, orders=(w.N, 3, 1) if w.N > 3 else (w.N, 1), smoother_precision=sprec,
-                                       coarse_tol=1e-6)
+                                       coarse_tol=1e-2)
                 setup_ms = 1e3 * (time.perf_counter() - t0)
                 st = sem.sem_pmg_pcg_solve(P, b, x, tol=args.pcg_tol, maxit=500, precision=prec, raise_on_error=False)
                 P.destroy()

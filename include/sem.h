@@ -228,8 +228,8 @@ int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const double *b_g, do
  * Lagrange prolongation P and restriction R = P^T, 4th-kind Chebyshev-Jacobi
  * smoothing (Lottes 2022 recurrence) in binary32 (geometry in binary32 or
  * bfloat16), lambda_max from power iteration on D^{-1}A started from the
- * alternating lattice vector (-1)^(I+J+K), and a binary64 Jacobi-PCG solve on
- * the coarsest level. The outer iteration is flexible CG (Polak-Ribiere beta)
+ * alternating lattice vector (-1)^(I+J+K), and a binary64-accurate
+ * (double-float operator) Jacobi-PCG solve on the coarsest level. The outer iteration is flexible CG (Polak-Ribiere beta)
  * with the fine operator in the precision of the solver options.
  * ------------------------------------------------------------------------ */
 typedef struct sem_pmg sem_pmg; /* opaque; owns its level meshes and scratch */

@@ -144,7 +144,10 @@ struct DfCfg {
   static constexpr int PJ = NP + 1;        // padded r-line stride (avoids bank conflicts)
   static constexpr int PK = NP * (NP + 1);
   static constexpr int TILE = NP * PK;     // float2 per tile
-  static constexpr int ELB = (N2 >= 128) ? 1 : (128 / N2 > 4 ? 4 : 128 / N2);
+  // at least 128 threads per CTA, shared tiles within 48 KB
+  static constexpr int ELB_T = (N2 >= 128) ? 1 : 128 / N2;
+  static constexpr int ELB_S = (48 * 1024) / (4 * NP * NP * (NP + 1) * (int)sizeof(float2));
+  static constexpr int ELB = ELB_T < ELB_S ? ELB_T : (ELB_S > 0 ? ELB_S : 1);
   static constexpr int THREADS = N2 * ELB;
   static constexpr int SMEM = 4 * TILE * ELB * (int)sizeof(float2);
 };

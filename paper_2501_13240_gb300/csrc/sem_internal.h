@@ -76,6 +76,10 @@ int sem_launch_gather(const sem_mesh *m, const double *vL, double *vg, cudaStrea
 int sem_launch_scatter(const sem_mesh *m, const double *vg, double *vL, cudaStream_t st);
 int sem_launch_diag_local(const sem_mesh *m, double h1, double h2, double *dL, cudaStream_t st);
 
+int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
+                     const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats, void *stream,
+                     int check_every);
+
 // grid helpers
 static inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 32) {
   int64_t b = (n + threads - 1) / threads;

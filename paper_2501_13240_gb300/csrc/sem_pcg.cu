@@ -100,7 +100,9 @@ __global__ void __launch_bounds__(kUpdThreads)
                   int n_pw, PcgScalars *s, int par, double *__restrict__ rz_part, double *__restrict__ rr_part) {
   __shared__ double red[32];
   const double pw = sum_partials(pw_part, n_pw, red);
-  const double alpha = s->rho[par] / pw;
+  // an exactly converged iterate (p = 0) gives p.w = 0: take no step; the host
+  // reports a breakdown only if the residual has not met the tolerance
+  const double alpha = (pw > 0.0) ? s->rho[par] / pw : 0.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     s->pw = pw;
     s->alpha = alpha;
@@ -129,7 +131,8 @@ __global__ void __launch_bounds__(kUpdThreads)
                   int par) {
   __shared__ double red[32];
   const double rz = sum_partials(rz_part, n_part, red);
-  const double beta = rz / s->rho[par];
+  const double rho_old = s->rho[par];
+  const double beta = (rho_old != 0.0) ? rz / rho_old : 0.0;
   if (blockIdx.x == 0) {  // only block 0 needs r.r (block-uniform branch)
     const double rr = sum_partials(rr_part, n_part, red);
     if (threadIdx.x == 0) {
@@ -304,7 +307,18 @@ extern "C" int sem_pcg_workspace_bytes(const sem_mesh *m, size_t *bytes) {
 
 extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
                              const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats, void *stream) {
+  return sem_pcg_solve_ex(m, h1, h2, b_g, x_g, opts, workspace, stats, stream, 1);
+}
+
+// check_every: the host reads the scalars (stopping test, breakdown) only every
+// check_every iterations; the step lengths are computed on the device, so the
+// iteration itself is unchanged. A solve may then run up to check_every - 1
+// iterations past the first one that meets the tolerance.
+int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
+                     const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats, void *stream,
+                     int check_every) {
   if (int rc = check_mesh(m, "sem_pcg_solve")) return rc;
+  if (check_every < 1) check_every = 1;
   if (bad_ptr(b_g) || bad_ptr(x_g)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: NULL or misaligned vector");
   if (!opts || !stats) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: NULL opts or stats");
   if (!workspace || ((uintptr_t)workspace & 255))
@@ -320,6 +334,9 @@ extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const doub
   PcgWork wk;
   pcg_layout(m, (char *)workspace, &wk);
   const int n_pw = sem_ax_assembled_blocks(m, opts->precision);
+  // update kernels: no more CTAs than the vector needs (each CTA re-sums the
+  // partials of the previous kernel, so fewer CTAs also means less of that)
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kUpdBlocks, (m->n_unique + 2047) / 2048));
   const int64_t nU = m->n_unique;
   stats->iterations = 0;
   stats->rel_residual = 0.0;
@@ -375,15 +392,15 @@ extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const doub
     SEM_CUDA(cudaMemsetAsync(wk.w, 0, sizeof(double) * nU, st));
     if ((rc = sem_launch_ax_assembled(m, h1, h2, wk.p, wk.w, wk.pw_part, opts->precision, st, map)) != SEM_OK)
       return rc;
-    k_pcg_update1<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, x_g, wk.r, wk.p, wk.w, wk.dinv, wk.pw_part, n_pw, wk.s, par,
-                                                      wk.part_a, wk.part_b);
-    k_pcg_update2<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, wk.r, wk.p, wk.dinv, wk.part_a, wk.part_b, kUpdBlocks, wk.s,
-                                                      par);
+    k_pcg_update1<<<nblk, kUpdThreads, 0, st>>>(nU, x_g, wk.r, wk.p, wk.w, wk.dinv, wk.pw_part, n_pw, wk.s, par,
+                                                wk.part_a, wk.part_b);
+    k_pcg_update2<<<nblk, kUpdThreads, 0, st>>>(nU, wk.r, wk.p, wk.dinv, wk.part_a, wk.part_b, nblk, wk.s, par);
     SEM_LAUNCH_CHECK("pcg iteration");
+    if (it % check_every != 0 && it != opts->maxit) continue;
     SEM_CUDA(cudaMemcpyAsync(&hs, wk.s, sizeof(hs), cudaMemcpyDeviceToHost, st));
     SEM_CUDA(cudaStreamSynchronize(st));
+    if (std::isfinite(hs.rr) && sqrt(hs.rr) <= thresh) return finish(SEM_OK, it, hs.rr);
     if (!(hs.pw > 0.0) || !std::isfinite(hs.pw) || !std::isfinite(hs.rr)) return finish(SEM_ERR_BREAKDOWN, it, hs.rr);
-    if (sqrt(hs.rr) <= thresh) return finish(SEM_OK, it, hs.rr);
     if (opts->timeout_s > 0.0) {
       double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (el > opts->timeout_s) return finish(SEM_ERR_TIMEOUT, it, hs.rr);

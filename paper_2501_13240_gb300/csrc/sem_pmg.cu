@@ -5,7 +5,7 @@
 // Levels: the same elements at decreasing orders, each with its own mesh
 // (geometry re-evaluated at the level's GLL points). Smoothing levels run in
 // binary32 with geometric factors in binary32 or bfloat16; the coarsest level
-// is a binary64 Jacobi-PCG solve. Transfer operators: element-wise
+// is a binary64-accurate (double-float operator) Jacobi-PCG solve. Transfer operators: element-wise
 // tensor-product Lagrange interpolation P (coarse -> fine) and R = P^T.
 // Smoother: 4th-kind Chebyshev in D^{-1}A (Lottes 2022 recurrence):
 //   d_0 = 4/(3 lam) D^{-1} r_0;  for i = 1..k: x += d_{i-1}; (i < k) r -= A d_{i-1};
@@ -63,15 +63,19 @@ struct F32Cfg {
   static constexpr int N3 = NP * NP * NP;
   static constexpr int ELB = (N2 >= 256) ? 1 : (256 / N2);
   static constexpr int THREADS = N2 * ELB;
-  static constexpr int SMEM = (NP * (NP + 1) + 3 * N3 * ELB) * (int)sizeof(float);
+  static constexpr int SMEM = (NP * (NP + 1) + 4 * N3 * ELB) * (int)sizeof(float);
+  static constexpr int MINB = (NP <= 8) ? 4 : 2;  // resident CTAs per SM the registers must allow
 };
 
-__device__ __forceinline__ float ldg_real(const float *p, int64_t i) { return p[i]; }
+__device__ __forceinline__ float ldg_real(const float *p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float ldg_real(const __nv_bfloat16 *p, int64_t i) { return __bfloat162float(p[i]); }
 
-// w[g] += h1 (A u)[g] + h2 (B u)[g] through map (-1 = skip), binary32
+// w[g] += h1 (A u)[g] + h2 (B u)[g] through map (-1 = skip), binary32. The
+// kernel is bound by memory: the u column and the t-direction flux stay in
+// shared memory (not registers) so that four CTAs fit per SM, and the gather
+// indices of the next element are prefetched.
 template <int NP, typename GT>
-__global__ void __launch_bounds__(F32Cfg<NP>::THREADS)
+__global__ void __launch_bounds__(F32Cfg<NP>::THREADS, F32Cfg<NP>::MINB)
     k_ax32(int64_t E, const float *__restrict__ Df, const GT *__restrict__ G, const float *__restrict__ B, float h1,
            float h2, const float *__restrict__ u, float *__restrict__ w, const int32_t *__restrict__ map) {
   using C = F32Cfg<NP>;
@@ -81,39 +85,38 @@ __global__ void __launch_bounds__(F32Cfg<NP>::THREADS)
   const int le = tid / C::N2;
   const int ij = tid - le * C::N2;
   const int i = ij % NP, j = ij / NP;
-  float *s_u = smf + NP * (NP + 1) + le * 3 * C::N3;
+  float *s_u = smf + NP * (NP + 1) + le * 4 * C::N3;
   float *s_r = s_u + C::N3;
   float *s_s = s_r + C::N3;
+  float *s_t = s_s + C::N3;
   for (int t = tid; t < NP * NP; t += C::THREADS) sD[(t / NP) * (NP + 1) + (t % NP)] = Df[t];
+  const int64_t estride = (int64_t)gridDim.x * C::ELB;
+  int32_t gi[NP];
+  {
+    const int64_t e = (int64_t)blockIdx.x * C::ELB + le;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) gi[k] = (e < E) ? map[e * C::N3 + i + NP * j + C::N2 * k] : -1;
+  }
   __syncthreads();
-  for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += (int64_t)gridDim.x * C::ELB) {
+  for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += estride) {
     const int64_t e = e0 + le;
     const bool act = e < E;
-    float ru[NP];
+    int32_t go[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      const int p = i + NP * j + C::N2 * k;
-      float v = 0.0f;
-      if (act) {
-        const int32_t g = map[e * C::N3 + p];
-        v = (g >= 0) ? u[g] : 0.0f;
-      }
-      ru[k] = v;
-      s_u[p] = v;
+      go[k] = gi[k];
+      s_u[i + NP * j + C::N2 * k] = (gi[k] >= 0) ? u[gi[k]] : 0.0f;
+    }
+    {
+      const int64_t en = e + estride;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) gi[k] = (en < E) ? map[en * C::N3 + i + NP * j + C::N2 * k] : -1;
     }
     __syncthreads();
-    float rt[NP];
     const int64_t gbase = (act ? e : 0) * 6 * C::N3;
-#pragma unroll
+#pragma unroll 2
     for (int k = 0; k < NP; ++k) {
       const int p = i + NP * j + C::N2 * k;
-      float ur = 0.0f, us = 0.0f, ut = 0.0f;
-#pragma unroll
-      for (int m = 0; m < NP; ++m) {
-        ur = fmaf(sD[i * (NP + 1) + m], s_u[m + NP * j + C::N2 * k], ur);
-        us = fmaf(sD[j * (NP + 1) + m], s_u[i + NP * m + C::N2 * k], us);
-        ut = fmaf(sD[k * (NP + 1) + m], ru[m], ut);
-      }
       float g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0;
       if (act) {
         g00 = ldg_real(G, gbase + p);
@@ -123,12 +126,19 @@ __global__ void __launch_bounds__(F32Cfg<NP>::THREADS)
         g12 = ldg_real(G, gbase + 4 * C::N3 + p);
         g22 = ldg_real(G, gbase + 5 * C::N3 + p);
       }
+      float ur = 0.0f, us = 0.0f, ut = 0.0f;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        ur = fmaf(sD[i * (NP + 1) + m], s_u[m + NP * j + C::N2 * k], ur);
+        us = fmaf(sD[j * (NP + 1) + m], s_u[i + NP * m + C::N2 * k], us);
+        ut = fmaf(sD[k * (NP + 1) + m], s_u[i + NP * j + C::N2 * m], ut);
+      }
       s_r[p] = g00 * ur + g01 * us + g02 * ut;
       s_s[p] = g01 * ur + g11 * us + g12 * ut;
-      rt[k] = g02 * ur + g12 * us + g22 * ut;
+      s_t[p] = g02 * ur + g12 * us + g22 * ut;
     }
     __syncthreads();
-#pragma unroll
+#pragma unroll 2
     for (int k = 0; k < NP; ++k) {
       const int p = i + NP * j + C::N2 * k;
       float acc = 0.0f;
@@ -136,14 +146,11 @@ __global__ void __launch_bounds__(F32Cfg<NP>::THREADS)
       for (int m = 0; m < NP; ++m) {
         acc = fmaf(sD[m * (NP + 1) + i], s_r[m + NP * j + C::N2 * k], acc);
         acc = fmaf(sD[m * (NP + 1) + j], s_s[i + NP * m + C::N2 * k], acc);
-        acc = fmaf(sD[m * (NP + 1) + k], rt[m], acc);
+        acc = fmaf(sD[m * (NP + 1) + k], s_t[i + NP * j + C::N2 * m], acc);
       }
       float val = h1 * acc;
-      if (h2 != 0.0f && act) val = fmaf(h2 * B[e * C::N3 + p], ru[k], val);
-      if (act) {
-        const int32_t g = map[e * C::N3 + p];
-        if (g >= 0) atomicAdd(&w[g], val);
-      }
+      if (h2 != 0.0f && act) val = fmaf(h2 * B[e * C::N3 + p], s_u[p], val);
+      if (go[k] >= 0) atomicAdd(&w[go[k]], val);
     }
     __syncthreads();
   }
@@ -179,69 +186,86 @@ int launch_ax32(const PmgLevel &lv, int gprec, float h1, float h2, const float *
 }
 
 // ---------------------------------------------------------------- transfers
-// fine level uf = P uc: per fine element, interpolate the coarse element's
-// values (identical on shared nodes, so every copy stores the same value)
+// One CTA of nf^2 threads per element; thread (i, j) owns the fine column
+// (i, j, :). Sum factorisation: nc + nc^2 + nc^3 multiply-adds per column
+// stage instead of nc^3 per fine point.
+// fine level uf = P uc (identical values on shared nodes, every copy stores)
 __global__ void k_prolong(int nf, int nc, int64_t E, const float *__restrict__ J, const int32_t *__restrict__ mapc,
                           const float *__restrict__ uc, const int32_t *__restrict__ mapf, float *__restrict__ uf) {
   __shared__ float tile[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];
   __shared__ float Js[SEM_MAXNP * SEM_MAXNP];
   const int nc3 = nc * nc * nc, nf3 = nf * nf * nf;
-  for (int t = threadIdx.x; t < nf * nc; t += blockDim.x) Js[t] = J[t];
+  const int tid = threadIdx.x, i = tid % nf, j = tid / nf;
+  for (int t = tid; t < nf * nc; t += blockDim.x) Js[t] = J[t];
   for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
     __syncthreads();
-    for (int t = threadIdx.x; t < nc3; t += blockDim.x) {
+    for (int t = tid; t < nc3; t += blockDim.x) {
       const int32_t g = mapc[e * nc3 + t];
       tile[t] = g >= 0 ? uc[g] : 0.0f;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < nf3; q += blockDim.x) {
-      const int i = q % nf, j = (q / nf) % nf, k = q / (nf * nf);
-      float s = 0.0f;
-      for (int c = 0; c < nc; ++c) {
-        float sb = 0.0f;
-        for (int b = 0; b < nc; ++b) {
-          float sa = 0.0f;
-          for (int a = 0; a < nc; ++a) sa = fmaf(Js[i * nc + a], tile[a + nc * (b + nc * c)], sa);
-          sb = fmaf(Js[j * nc + b], sa, sb);
-        }
-        s = fmaf(Js[k * nc + c], sb, s);
+    float t2[SEM_MAXNP];
+    for (int c = 0; c < nc; ++c) {
+      float sb = 0.0f;
+      for (int b = 0; b < nc; ++b) {
+        float sa = 0.0f;
+        for (int a = 0; a < nc; ++a) sa = fmaf(Js[i * nc + a], tile[a + nc * (b + nc * c)], sa);
+        sb = fmaf(Js[j * nc + b], sa, sb);
       }
-      const int32_t g = mapf[e * nf3 + q];
+      t2[c] = sb;
+    }
+    for (int k = 0; k < nf; ++k) {
+      float s = 0.0f;
+      for (int c = 0; c < nc; ++c) s = fmaf(Js[k * nc + c], t2[c], s);
+      const int32_t g = mapf[e * nf3 + i + nf * (j + nf * k)];
       if (g >= 0) uf[g] = s;
     }
   }
 }
 
-// coarse level rc += R rf = P^T rf: per element, J^T (x) J^T (x) J^T applied to
-// the fine element's rf / multiplicity, summed into the coarse vector
+// coarse level rc += R rf = P^T rf: J^T (x) J^T (x) J^T of the fine element's
+// rf / multiplicity, summed into the coarse vector
 __global__ void k_restrict(int nf, int nc, int64_t E, const float *__restrict__ J, const int32_t *__restrict__ mapf,
                            const float *__restrict__ minvf, const float *__restrict__ rf,
                            const int32_t *__restrict__ mapc, float *__restrict__ rc) {
-  __shared__ float tile[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];
+  __shared__ float u1[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];  // [i][j][c]
+  __shared__ float u2[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];  // [i][b][c]
   __shared__ float Js[SEM_MAXNP * SEM_MAXNP];
   const int nc3 = nc * nc * nc, nf3 = nf * nf * nf;
-  for (int t = threadIdx.x; t < nf * nc; t += blockDim.x) Js[t] = J[t];
+  const int tid = threadIdx.x, i = tid % nf, j = tid / nf;
+  for (int t = tid; t < nf * nc; t += blockDim.x) Js[t] = J[t];
   for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
     __syncthreads();
-    for (int t = threadIdx.x; t < nf3; t += blockDim.x) {
-      const int32_t g = mapf[e * nf3 + t];
-      tile[t] = g >= 0 ? rf[g] * minvf[g] : 0.0f;
+    {
+      float v[SEM_MAXNP];
+      for (int k = 0; k < nf; ++k) {
+        const int32_t g = mapf[e * nf3 + i + nf * (j + nf * k)];
+        v[k] = g >= 0 ? rf[g] * minvf[g] : 0.0f;
+      }
+      for (int c = 0; c < nc; ++c) {
+        float s = 0.0f;
+        for (int k = 0; k < nf; ++k) s = fmaf(Js[k * nc + c], v[k], s);
+        u1[(i * nf + j) * nc + c] = s;
+      }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < nc3; q += blockDim.x) {
-      const int a = q % nc, b = (q / nc) % nc, c = q / (nc * nc);
-      float s = 0.0f;
-      for (int k = 0; k < nf; ++k) {
-        float sj = 0.0f;
-        for (int j = 0; j < nf; ++j) {
-          float si = 0.0f;
-          for (int i = 0; i < nf; ++i) si = fmaf(Js[i * nc + a], tile[i + nf * (j + nf * k)], si);
-          sj = fmaf(Js[j * nc + b], si, sj);
-        }
-        s = fmaf(Js[k * nc + c], sj, s);
+    if (tid < nf * nc) {  // thread (i, b)
+      const int ii = tid % nf, b = tid / nf;
+      for (int c = 0; c < nc; ++c) {
+        float s = 0.0f;
+        for (int jj = 0; jj < nf; ++jj) s = fmaf(Js[jj * nc + b], u1[(ii * nf + jj) * nc + c], s);
+        u2[(ii * nc + b) * nc + c] = s;
       }
-      const int32_t g = mapc[e * nc3 + q];
-      if (g >= 0) atomicAdd(&rc[g], s);
+    }
+    __syncthreads();
+    if (tid < nc * nc) {  // thread (a, b)
+      const int a = tid % nc, b = tid / nc;
+      for (int c = 0; c < nc; ++c) {
+        float s = 0.0f;
+        for (int ii = 0; ii < nf; ++ii) s = fmaf(Js[ii * nc + a], u2[(ii * nc + b) * nc + c], s);
+        const int32_t g = mapc[e * nc3 + a + nc * (b + nc * c)];
+        if (g >= 0) atomicAdd(&rc[g], s);
+      }
     }
   }
 }
@@ -488,8 +512,8 @@ int smooth(sem_pmg *P, int l, bool zero, cudaStream_t st) {
 int restrict_to(sem_pmg *P, int l, const float *rf, float *rc, cudaStream_t st) {
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   SEM_CUDA(cudaMemsetAsync(rc, 0, sizeof(float) * c.m->n_unique, st));
-  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 64);
-  k_restrict<<<grid, 128, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], f.m->l2gm, f.minv, rf, c.m->l2gm, rc);
+  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
+  k_restrict<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], f.m->l2gm, f.minv, rf, c.m->l2gm, rc);
   SEM_LAUNCH_CHECK("k_restrict");
   return SEM_OK;
 }
@@ -497,8 +521,8 @@ int restrict_to(sem_pmg *P, int l, const float *rf, float *rc, cudaStream_t st) 
 int prolong_to(sem_pmg *P, int l, const float *uc, float *uf, cudaStream_t st) {
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   SEM_CUDA(cudaMemsetAsync(uf, 0, sizeof(float) * f.m->n_unique, st));
-  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 64);
-  k_prolong<<<grid, 256, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.m->l2gm, uc, f.m->l2gm, uf);
+  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
+  k_prolong<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.m->l2gm, uc, f.m->l2gm, uf);
   SEM_LAUNCH_CHECK("k_prolong");
   return SEM_OK;
 }
@@ -510,11 +534,11 @@ int coarse_solve(sem_pmg *P, cudaStream_t st) {
   sem_solver_opts o;
   o.tol = P->o.coarse_tol;
   o.maxit = P->o.coarse_maxit;
-  o.precision = SEM_PREC_FP64;
+  o.precision = SEM_PREC_DF64;  // binary64-accurate; native FP64 is pipe-bound even at N = 1
   o.timeout_s = 0.0;
   o.mask_mode = 0;
   sem_solve_stats stt;
-  int rc = sem_pcg_solve(lv.m, P->h1, P->h2, P->cb, P->cx, &o, P->cws, &stt, (void *)st);
+  int rc = sem_pcg_solve_ex(lv.m, P->h1, P->h2, P->cb, P->cx, &o, P->cws, &stt, (void *)st, 8);
   if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
   k_d2f<<<grid_for(n, 256), 256, 0, st>>>(n, P->cx, lv.x);
   SEM_LAUNCH_CHECK("coarse solve");
