@@ -243,6 +243,8 @@ typedef struct {
   int power_its;          /* power iterations (e.g. 20) */
   double coarse_tol;      /* relative tolerance of the coarsest-level solve */
   int coarse_maxit;
+  int mask_mode;          /* 0: the mesh's Dirichlet mask; 1: pure Neumann (all levels
+                             unmasked, constant null space; for the pressure) */
 } sem_pmg_opts;
 
 /* Build the hierarchy for the operator h1 A + h2 B on mesh m (which must
@@ -264,7 +266,8 @@ int sem_pmg_prolong(sem_pmg *p, int level, const double *uc_g, double *uf_g, voi
 int sem_pmg_restrict(sem_pmg *p, int level, const double *rf_g, double *rc_g, void *stream);
 
 /* Flexible CG preconditioned by one V-cycle per iteration, x0 = 0; stops after
- * the first iteration with ||r||_2 <= tol ||b||_2 (opts.mask_mode must be 0;
+ * the first iteration with ||r||_2 <= tol ||b||_2 (opts.mask_mode must equal the
+ * hierarchy's mask_mode; for mask_mode 1, b must be orthogonal to constants;
  * opts.precision selects the fine operator: SEM_PREC_FP64 or SEM_PREC_DF64). */
 int sem_pmg_pcg_solve(sem_pmg *p, const double *b_g, double *x_g, const sem_solver_opts *opts,
                       sem_solve_stats *stats, void *stream);
@@ -294,6 +297,9 @@ typedef struct {
   double tol;     /* relative residual of every solve */
   int maxit;      /* per solve */
   int precision;  /* SEM_PREC_* of the operator inside the solves */
+  int pressure_pmg; /* 1: pressure by the p-multigrid flexible CG (pure Neumann
+                       hierarchy N -> N/2 -> ... -> 1, binary32 smoothing), the
+                       paper's choice of preconditioner; 0: Jacobi-PCG */
 } sem_rbc_params;
 
 typedef struct {

@@ -77,12 +77,12 @@ class sem_solve_stats(ctypes.Structure):
 class sem_pmg_opts(ctypes.Structure):
     _fields_ = [("nlevels", ctypes.c_int), ("orders", ctypes.c_int * 4), ("smoother_precision", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("lambda_safety", ctypes.c_double), ("power_its", ctypes.c_int),
-                ("coarse_tol", ctypes.c_double), ("coarse_maxit", ctypes.c_int)]
+                ("coarse_tol", ctypes.c_double), ("coarse_maxit", ctypes.c_int), ("mask_mode", ctypes.c_int)]
 
 
 class sem_rbc_params(ctypes.Structure):
     _fields_ = [("Ra", ctypes.c_double), ("Pr", ctypes.c_double), ("dt", ctypes.c_double), ("tol", ctypes.c_double),
-                ("maxit", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("maxit", ctypes.c_int), ("precision", ctypes.c_int), ("pressure_pmg", ctypes.c_int)]
 
 
 class sem_step_stats(ctypes.Structure):
@@ -422,9 +422,10 @@ class RBC:
 
 
 def sem_rbc_create(mesh: Mesh, Ra: float, Pr: float, dt: float, tol: float = 1e-10, maxit: int = 5000,
-                   precision: int = SEM_PREC_DF64, T_pert=None, stream=None) -> RBC:
+                   precision: int = SEM_PREC_DF64, T_pert=None, pressure_pmg: bool = True, stream=None) -> RBC:
     import torch
-    prm = sem_rbc_params(float(Ra), float(Pr), float(dt), float(tol), int(maxit), int(precision))
+    prm = sem_rbc_params(float(Ra), float(Pr), float(dt), float(tol), int(maxit), int(precision),
+                         int(bool(pressure_pmg)))
     pert = _ptr(T_pert, torch.float64, mesh.n_unique, "T_pert") if T_pert is not None else None
     h = ctypes.c_void_p()
     _check(lib().sem_rbc_create(mesh.handle, ctypes.byref(prm), pert, _stream(stream), ctypes.byref(h)))
@@ -475,7 +476,7 @@ class PMG:
 
 def sem_pmg_create(mesh: Mesh, h1: float = 1.0, h2: float = 0.0, orders=(7, 3, 1), smoother_precision=SEM_PREC_FP32,
                    cheb_degree: int = 2, lambda_safety: float = 1.1, power_its: int = 20, coarse_tol: float = 1e-10,
-                   coarse_maxit: int = 2000, stream=None) -> PMG:
+                   coarse_maxit: int = 2000, mask_mode: int = 0, stream=None) -> PMG:
     o = sem_pmg_opts()
     o.nlevels = len(orders)
     for t, N in enumerate(orders):
@@ -486,6 +487,7 @@ def sem_pmg_create(mesh: Mesh, h1: float = 1.0, h2: float = 0.0, orders=(7, 3, 1
     o.power_its = int(power_its)
     o.coarse_tol = float(coarse_tol)
     o.coarse_maxit = int(coarse_maxit)
+    o.mask_mode = int(mask_mode)
     h = ctypes.c_void_p()
     _check(lib().sem_pmg_create(mesh.handle, float(h1), float(h2), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
     return PMG(h, mesh, orders)
@@ -514,10 +516,10 @@ def sem_pmg_restrict(P: PMG, level: int, rf_g, rc_g, stream=None):
 
 
 def sem_pmg_pcg_solve(P: PMG, b_g, x_g, tol: float = 1e-8, maxit: int = 500, precision: int = SEM_PREC_DF64,
-                      timeout_s: float = 0.0, stream=None, raise_on_error: bool = True) -> dict:
+                      timeout_s: float = 0.0, stream=None, raise_on_error: bool = True, mask_mode: int = 0) -> dict:
     import torch
     n = P.mesh.n_unique
-    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s), 0)
+    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s), int(mask_mode))
     st = sem_solve_stats()
     rc = lib().sem_pmg_pcg_solve(P._h, _ptr(b_g, torch.float64, n, "b_g"), _ptr(x_g, torch.float64, n, "x_g"),
                                  ctypes.byref(o), ctypes.byref(st), _stream(stream))

@@ -80,6 +80,8 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
                      const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats, void *stream,
                      int check_every);
 
+int sem_jacobi_inv_mode(const sem_mesh *m, double h1, double h2, int use_mask, double *dinv_g, cudaStream_t st);
+
 // grid helpers
 static inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 32) {
   int64_t b = (n + threads - 1) / threads;

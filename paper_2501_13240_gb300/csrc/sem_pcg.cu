@@ -298,6 +298,13 @@ extern "C" int sem_jacobi_inv(const sem_mesh *m, double h1, double h2, double *d
   return SEM_OK;
 }
 
+int sem_jacobi_inv_mode(const sem_mesh *m, double h1, double h2, int use_mask, double *dinv_g, cudaStream_t st) {
+  k_jacobi_inv<<<grid_for(m->n_unique, 256), 256, 0, st>>>(m->n, m->n_unique, m->gs_off, m->gs_perm, m->mask, m->dD,
+                                                            m->G, m->B, h1, h2, use_mask, dinv_g);
+  SEM_LAUNCH_CHECK("k_jacobi_inv");
+  return SEM_OK;
+}
+
 extern "C" int sem_pcg_workspace_bytes(const sem_mesh *m, size_t *bytes) {
   if (int rc = check_mesh(m, "sem_pcg_workspace_bytes")) return rc;
   if (!bytes) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_workspace_bytes: NULL output");

@@ -28,6 +28,7 @@ namespace {
 struct PmgLevel {
   sem_mesh *m = nullptr;
   bool own = false;
+  const int32_t *map = nullptr;  // l2gm (Dirichlet mask) or l2g (pure Neumann)
   float *Gf = nullptr;
   __nv_bfloat16 *Gb = nullptr;
   float *Bf = nullptr;
@@ -163,11 +164,11 @@ int launch_ax32_np(const PmgLevel &lv, int gprec, float h1, float h2, const floa
   if (gprec == SEM_PREC_BF16) {
     auto kern = k_ax32<NP, __nv_bfloat16>;
     if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    kern<<<grid, C::THREADS, C::SMEM, st>>>(lv.m->E, lv.Df, lv.Gb, lv.Bf, h1, h2, u, w, lv.m->l2gm);
+    kern<<<grid, C::THREADS, C::SMEM, st>>>(lv.m->E, lv.Df, lv.Gb, lv.Bf, h1, h2, u, w, lv.map);
   } else {
     auto kern = k_ax32<NP, float>;
     if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    kern<<<grid, C::THREADS, C::SMEM, st>>>(lv.m->E, lv.Df, lv.Gf, lv.Bf, h1, h2, u, w, lv.m->l2gm);
+    kern<<<grid, C::THREADS, C::SMEM, st>>>(lv.m->E, lv.Df, lv.Gf, lv.Bf, h1, h2, u, w, lv.map);
   }
   SEM_LAUNCH_CHECK("k_ax32");
   return SEM_OK;
@@ -350,7 +351,7 @@ __global__ void k_minv(int64_t n, const double *__restrict__ mult, float *__rest
 __global__ void k_alt(int64_t n, int64_t nx, int64_t ny, const uint8_t *__restrict__ mask, float *__restrict__ v) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t I = g % nx, J = (g / nx) % ny, K = g / (nx * ny);
-    v[g] = mask[g] ? (((I + J + K) & 1) ? -1.0f : 1.0f) : 0.0f;
+    v[g] = (!mask || mask[g]) ? (((I + J + K) & 1) ? -1.0f : 1.0f) : 0.0f;
   }
 }
 
@@ -438,7 +439,7 @@ __global__ void k_init_fcg(int64_t n, const double *__restrict__ b, const uint8_
                            double *__restrict__ x, double *__restrict__ r) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     x[g] = 0.0;
-    r[g] = mask[g] ? b[g] : 0.0;
+    r[g] = (!mask || mask[g]) ? b[g] : 0.0;
   }
 }
 
@@ -513,7 +514,7 @@ int restrict_to(sem_pmg *P, int l, const float *rf, float *rc, cudaStream_t st) 
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   SEM_CUDA(cudaMemsetAsync(rc, 0, sizeof(float) * c.m->n_unique, st));
   const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
-  k_restrict<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], f.m->l2gm, f.minv, rf, c.m->l2gm, rc);
+  k_restrict<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], f.map, f.minv, rf, c.map, rc);
   SEM_LAUNCH_CHECK("k_restrict");
   return SEM_OK;
 }
@@ -522,8 +523,43 @@ int prolong_to(sem_pmg *P, int l, const float *uc, float *uf, cudaStream_t st) {
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   SEM_CUDA(cudaMemsetAsync(uf, 0, sizeof(float) * f.m->n_unique, st));
   const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
-  k_prolong<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.m->l2gm, uc, f.m->l2gm, uf);
+  k_prolong<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, uf);
   SEM_LAUNCH_CHECK("k_prolong");
+  return SEM_OK;
+}
+
+// subtract the mean of a binary64 vector (fixed-order partials, device scalar)
+__global__ void k_mean_part(int64_t n, const double *__restrict__ x, double *__restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    s += x[g];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sub_mean(int64_t n, int np, const double *__restrict__ part, double *__restrict__ x) {
+  __shared__ double mean;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < np; ++b) t += part[b];
+    mean = t / (double)n;
+  }
+  __syncthreads();
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    x[g] -= mean;
+}
+
+int remove_mean_d(sem_pmg *P, double *x, int64_t n, cudaStream_t st) {
+  k_mean_part<<<kPart, 256, 0, st>>>(n, x, P->part);
+  k_sub_mean<<<grid_for(n, 256), 256, 0, st>>>(n, kPart, P->part, x);
+  SEM_LAUNCH_CHECK("remove mean");
   return SEM_OK;
 }
 
@@ -531,12 +567,15 @@ int coarse_solve(sem_pmg *P, cudaStream_t st) {
   PmgLevel &lv = P->L.back();
   const int64_t n = lv.m->n_unique;
   k_f2d<<<grid_for(n, 256), 256, 0, st>>>(n, lv.b, P->cb);
+  if (P->o.mask_mode) {  // singular Neumann problem: make the right-hand side consistent
+    if (int rc = remove_mean_d(P, P->cb, n, st)) return rc;
+  }
   sem_solver_opts o;
   o.tol = P->o.coarse_tol;
   o.maxit = P->o.coarse_maxit;
   o.precision = SEM_PREC_DF64;  // binary64-accurate; native FP64 is pipe-bound even at N = 1
   o.timeout_s = 0.0;
-  o.mask_mode = 0;
+  o.mask_mode = P->o.mask_mode;
   sem_solve_stats stt;
   int rc = sem_pcg_solve_ex(lv.m, P->h1, P->h2, P->cb, P->cx, &o, P->cws, &stt, (void *)st, 8);
   if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
@@ -566,7 +605,7 @@ int power_lambda(sem_pmg *P, int l, cudaStream_t st) {
   const int64_t n = m->n_unique;
   const int64_t nx = (int64_t)m->nel[0] * m->N + (m->periodic[0] ? 0 : 1);
   const int64_t ny = (int64_t)m->nel[1] * m->N + (m->periodic[1] ? 0 : 1);
-  k_alt<<<grid_for(n, 256), 256, 0, st>>>(n, nx, ny, m->mask, lv.x);
+  k_alt<<<grid_for(n, 256), 256, 0, st>>>(n, nx, ny, P->o.mask_mode ? nullptr : m->mask, lv.x);
   double lam = 0.0;
   for (int it = 0; it < P->o.power_its; ++it) {
     SEM_CUDA(cudaMemsetAsync(lv.t, 0, sizeof(float) * n, st));
@@ -605,6 +644,7 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
       return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: orders must decrease strictly and stay >= 1");
   if (o->smoother_precision != SEM_PREC_FP32 && o->smoother_precision != SEM_PREC_BF16)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: smoother precision must be FP32 or BF16");
+  if (o->mask_mode != 0 && o->mask_mode != 1) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: bad mask_mode");
   if (o->cheb_degree < 1 || !(o->lambda_safety >= 1.0) || o->power_its < 1 || !(o->coarse_tol > 0) ||
       o->coarse_maxit < 1 || !(h1 > 0) || !(h2 >= 0))
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: bad option value");
@@ -628,10 +668,13 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
     } else {
       sem_box_desc d = m->desc;
       d.N = o->orders[l];
+      if (o->mask_mode)
+        for (int f = 0; f < 6; ++f) d.dirichlet[f] = 0;
       rc = sem_mesh_create_box(&d, stream, &lv.m);
       if (rc) break;
       lv.own = true;
     }
+    lv.map = o->mask_mode ? lv.m->l2g : lv.m->l2gm;
     const int64_t nL = lv.m->n_local, nU = lv.m->n_unique;
     const bool coarsest = l == o->nlevels - 1;
     if (!coarsest) {
@@ -667,7 +710,7 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
       rc = sem_fail(SEM_ERR_NOMEM, "sem_pmg_create: cudaMalloc(diag)");
       break;
     }
-    rc = sem_jacobi_inv(lm, h1, h2, dd, stream);
+    rc = sem_jacobi_inv_mode(lm, h1, h2, o->mask_mode ? 0 : 1, dd, st);
     k_d2f_plain<<<grid_for(lm->n_unique, 256), 256, 0, st>>>(lm->n_unique, dd, lv.dinv);
     cudaStreamSynchronize(st);
     cudaFree(dd);
@@ -755,7 +798,7 @@ extern "C" int sem_pmg_restrict(sem_pmg *P, int level, const double *rf_g, doubl
 extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, const sem_solver_opts *opts,
                                  sem_solve_stats *stats, void *stream) {
   if (!P || !b_g || !x_g || !opts || !stats) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_pcg_solve: NULL argument");
-  if (opts->mask_mode != 0 || (opts->precision != SEM_PREC_FP64 && opts->precision != SEM_PREC_DF64) ||
+  if (opts->mask_mode != P->o.mask_mode || (opts->precision != SEM_PREC_FP64 && opts->precision != SEM_PREC_DF64) ||
       !(opts->tol >= 0.0) || opts->maxit < 1)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_pcg_solve: bad options");
   const auto t0 = std::chrono::steady_clock::now();
@@ -766,7 +809,7 @@ extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, con
   int rc;
   stats->iterations = 0;
   stats->status = SEM_OK;
-  k_init_fcg<<<g, 256, 0, st>>>(n, b_g, m->mask, x_g, P->r);
+  k_init_fcg<<<g, 256, 0, st>>>(n, b_g, P->o.mask_mode ? nullptr : m->mask, x_g, P->r);
   k_dots<<<kPart, 256, 0, st>>>(n, P->r, P->r, nullptr, nullptr, P->part);
   SEM_LAUNCH_CHECK("fcg init");
   double bb, unused;
@@ -791,7 +834,8 @@ extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, con
   double rr = bb;
   for (int it = 1; it <= opts->maxit; ++it) {
     SEM_CUDA(cudaMemsetAsync(P->w, 0, sizeof(double) * n, st));
-    if ((rc = sem_launch_ax_assembled(m, P->h1, P->h2, P->p, P->w, P->pw_part, opts->precision, st))) return rc;
+    if ((rc = sem_launch_ax_assembled(m, P->h1, P->h2, P->p, P->w, P->pw_part, opts->precision, st, P->L[0].map)))
+      return rc;
     std::vector<double> hp(npw);
     SEM_CUDA(cudaMemcpyAsync(hp.data(), P->pw_part, sizeof(double) * npw, cudaMemcpyDeviceToHost, st));
     SEM_CUDA(cudaStreamSynchronize(st));

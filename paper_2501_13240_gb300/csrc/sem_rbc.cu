@@ -14,6 +14,7 @@
 // since BDF2 started from history levels equal to the initial state is first order.
 // Explicit terms run in binary64 kernels; the five solves use sem_pcg_solve.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <chrono>
@@ -41,6 +42,7 @@ struct sem_rbc {
   int *dnel = nullptr;     // element counts on the device
   void *ws = nullptr;
   size_t ws_bytes = 0;
+  sem_pmg *pmg = nullptr;  // pressure preconditioner (pure Neumann hierarchy)
   std::vector<void *> owned;
 };
 
@@ -364,6 +366,7 @@ int solve(sem_rbc *s, double h1, double h2, const double *b, double *x, int mask
 
 void free_rbc(sem_rbc *s) {
   if (!s) return;
+  if (s->pmg) sem_pmg_destroy(s->pmg);
   for (void *p : s->owned) cudaFree(p);
   delete s;
 }
@@ -437,6 +440,28 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
   if (T_pert_g) k_add_masked<<<grid_for(s->nU, 256), 256, 0, st>>>(s->nU, m->mask, T_pert_g, s->T);
   for (int c = 0; c < 3; ++c) cudaMemsetAsync(s->u[c], 0, sizeof(double) * s->nU, st);
   cudaMemsetAsync(s->p, 0, sizeof(double) * s->nU, st);
+  if (prm->pressure_pmg && m->N > 1) {
+    sem_pmg_opts po;
+    memset(&po, 0, sizeof(po));
+    int c = m->N, nl = 0;
+    po.orders[nl++] = c;
+    while (c > 1 && nl < 4) {
+      c = std::max(1, c / 2);
+      po.orders[nl++] = c;
+    }
+    po.nlevels = nl;
+    po.smoother_precision = SEM_PREC_FP32;
+    po.cheb_degree = 2;
+    po.lambda_safety = 1.1;
+    po.power_its = 20;
+    po.coarse_tol = 1e-2;
+    po.coarse_maxit = 2000;
+    po.mask_mode = 1;
+    if ((rc = sem_pmg_create(m, 1.0, 0.0, &po, stream, &s->pmg))) {
+      free_rbc(s);
+      return rc;
+    }
+  }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -536,7 +561,19 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   if ((rc = gather(s, s->tmpL, s->rhs, false, st))) return rc;
   k_axpbypcz<<<gu, 256, 0, st>>>(nU, 1.0, s->rhs, -kc.a1, s->W, -kc.a2, s->Wp, s->rhs);
   if ((rc = remove_mean(s, s->rhs, st))) return rc;
-  rc = solve(s, 1.0, 0.0, s->rhs, s->p, 1, &stt->iters_p, st);
+  if (s->pmg) {
+    sem_solver_opts o;
+    o.tol = s->prm.tol;
+    o.maxit = s->prm.maxit;
+    o.precision = s->prm.precision;
+    o.timeout_s = 0.0;
+    o.mask_mode = 1;
+    sem_solve_stats ps;
+    rc = sem_pmg_pcg_solve(s->pmg, s->rhs, s->p, &o, &ps, (void *)st);
+    stt->iters_p = ps.iterations;
+  } else {
+    rc = solve(s, 1.0, 0.0, s->rhs, s->p, 1, &stt->iters_p, st);
+  }
   if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
   if (rc) stt->status = rc;
   if ((rc = remove_mean(s, s->p, st))) return rc;

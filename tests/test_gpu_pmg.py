@@ -120,3 +120,27 @@ def test_pmg_invalid_options():
         with pytest.raises(sem.SemError):
             sem.sem_pmg_create(gm, **kw)
     gm.destroy()
+
+
+def test_neumann_hierarchy_pressure_problem():
+    """Pure-Neumann hierarchy (the pressure problem of the time step): the
+    mixed solve reaches the tolerance and agrees with Jacobi-PCG up to the
+    constant null space."""
+    kw = dict(periodic=(1, 1, 0), dirichlet=(0, 0, 0, 0, 1, 1), z_stretch=2.0)
+    gm = sem.sem_mesh_create_box((4, 4, 4), 7, **kw)
+    rng = np.random.default_rng(11)
+    b = rng.standard_normal(gm.n_unique)
+    b -= b.mean()
+    P = sem.sem_pmg_create(gm, orders=(7, 3, 1), mask_mode=1, coarse_tol=1e-2)
+    x = torch.zeros(gm.n_unique, dtype=torch.float64, device="cuda")
+    st = sem.sem_pmg_pcg_solve(P, dev(b), x, tol=1e-10, mask_mode=1)
+    assert st["status"] == 0
+    xr = torch.zeros_like(x)
+    st2 = sem.sem_pcg_solve(gm, 1.0, 0.0, dev(b), xr, tol=1e-10, maxit=5000, mask_mode=1)
+    assert st2["status"] == 0 and st["iterations"] * 5 < st2["iterations"]
+    a, c = host(x), host(xr)
+    a -= a.mean()
+    c -= c.mean()
+    assert rel_err(a, c) < 1e-7
+    P.destroy()
+    gm.destroy()
