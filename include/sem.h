@@ -331,6 +331,23 @@ int sem_rbc_fields(const sem_rbc *s, sem_rbc_view *view);
 
 int sem_rbc_destroy(sem_rbc *s);
 
+/* ------------------------------------------------------------------------
+ * Multi-rank partition (host only). Sec. 2.2: one rank per GPU; shared
+ * surface values are summed across ranks. Rank r of P owns the element
+ * planes ez in [r nelz/P, (r+1) nelz/P), i.e. elements [e_begin, e_end) in
+ * the element numbering of this header. Direct stiffness summation then is a
+ * rank-local Q Q^T plus a sum, over the ranks sharing it, of the partial sums
+ * at each interface node (a unique node that another rank also holds).
+ * ------------------------------------------------------------------------ */
+/* Element range of a rank and the number of its interface nodes.
+ * SEM_ERR_INVALID_ARG unless 1 <= nranks <= nelz and 0 <= rank < nranks. */
+int sem_partition_info(const sem_box_desc *desc, int nranks, int rank, int64_t *e_begin, int64_t *e_end,
+                       int64_t *n_interface);
+
+/* The rank's interface nodes (unique ids, ascending) into gids[n_interface]
+ * and, if nshare is not NULL, the number of ranks holding each. */
+int sem_partition_interface(const sem_box_desc *desc, int nranks, int rank, int64_t *gids, int32_t *nshare);
+
 /* Jacobi-PCG like sem_pcg_solve, for callers that cannot allocate device
  * memory themselves -- for example a host program or plug-in whose device
  * memory is owned entirely by another framework's allocator, or a loop that

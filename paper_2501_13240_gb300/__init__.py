@@ -39,7 +39,7 @@ EXPORTS = (
     "sem_pcg_solve", "sem_pcg_solve_noalloc", "sem_pcg_noalloc_capacity",
     "sem_rbc_create", "sem_bdf_ext_step", "sem_rbc_fields", "sem_rbc_destroy",
     "sem_pmg_create", "sem_pmg_lambda", "sem_pmg_vcycle", "sem_pmg_prolong", "sem_pmg_restrict",
-    "sem_pmg_pcg_solve", "sem_pmg_destroy",
+    "sem_pmg_pcg_solve", "sem_pmg_destroy", "sem_partition_info", "sem_partition_interface",
 )
 
 
@@ -145,6 +145,9 @@ def lib() -> ctypes.CDLL:
         sig["sem_pmg_pcg_solve"] = ([_vp, _vp, _vp, ctypes.POINTER(sem_solver_opts), ctypes.POINTER(sem_solve_stats),
                                      _vp], _i)
         sig["sem_pmg_destroy"] = ([_vp], _i)
+        sig["sem_partition_info"] = ([ctypes.POINTER(sem_box_desc), _i, _i, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], _i)
+        sig["sem_partition_interface"] = ([ctypes.POINTER(sem_box_desc), _i, _i, _vp, _vp], _i)
         for name, (args, res) in sig.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -257,8 +260,8 @@ def _device_copy(ptr: int, n: int, typestr: str = "<f8"):
     return torch.as_tensor(_DeviceView(ptr, n, typestr), device="cuda").clone()
 
 
-def sem_mesh_create_box(nel, N=7, L=(1.0, 1.0, 1.0), periodic=(0, 0, 0), dirichlet=(1, 1, 1, 1, 1, 1),
-                        z_stretch=0.0, deform_amp=0.0, kappa=None, phi=None, stream=None) -> Mesh:
+def box_desc(nel, N=7, L=(1.0, 1.0, 1.0), periodic=(0, 0, 0), dirichlet=(1, 1, 1, 1, 1, 1), z_stretch=0.0,
+             deform_amp=0.0, kappa=None, phi=None) -> sem_box_desc:
     d = sem_box_desc()
     d.nelx, d.nely, d.nelz = (int(v) for v in nel)
     d.N = int(N)
@@ -275,9 +278,32 @@ def sem_mesh_create_box(nel, N=7, L=(1.0, 1.0, 1.0), periodic=(0, 0, 0), dirichl
         d.kappa[t] = float(kap[t])
     for t in range(3):
         d.phi[t] = float(ph[t])
+    return d
+
+
+def sem_mesh_create_box(nel, N=7, L=(1.0, 1.0, 1.0), periodic=(0, 0, 0), dirichlet=(1, 1, 1, 1, 1, 1),
+                        z_stretch=0.0, deform_amp=0.0, kappa=None, phi=None, stream=None) -> Mesh:
+    d = box_desc(nel, N, L, periodic, dirichlet, z_stretch, deform_amp, kappa, phi)
     h = ctypes.c_void_p()
     _check(lib().sem_mesh_create_box(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
     return Mesh(h)
+
+
+def sem_partition_info(desc: sem_box_desc, nranks: int, rank: int):
+    """(e_begin, e_end, n_interface) of a rank of the element-slab partition."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sem_partition_info(ctypes.byref(desc), int(nranks), int(rank), ctypes.byref(a), ctypes.byref(b),
+                                    ctypes.byref(c)))
+    return int(a.value), int(b.value), int(c.value)
+
+
+def sem_partition_interface(desc: sem_box_desc, nranks: int, rank: int):
+    """(gids int64[n], nshare int32[n]) of a rank's interface nodes."""
+    _, _, n = sem_partition_info(desc, nranks, rank)
+    g = np.zeros(max(n, 1), dtype=np.int64)
+    c = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib().sem_partition_interface(ctypes.byref(desc), int(nranks), int(rank), g.ctypes.data, c.ctypes.data))
+    return g[:n], c[:n]
 
 
 def mesh_from_workload(w, stream=None) -> Mesh:

@@ -1,0 +1,97 @@
+"""Multi-rank direct stiffness summation on CPU ranks (gloo): the element-slab
+partition's interface maps against brute force (bit-exact), and the summed
+result against the single-partition Q Q^T (Sec. 2.2: one rank per GPU,
+shared surface values summed across ranks)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CASES = [dict(nel=(3, 2, 4), N=3, periodic=(0, 0, 0), dirichlet=(1,) * 6),
+         dict(nel=(2, 3, 6), N=4, periodic=(1, 1, 1), dirichlet=(0,) * 6),
+         dict(nel=(2, 2, 5), N=2, periodic=(1, 1, 0), dirichlet=(0, 0, 0, 0, 1, 1))]
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, case, queue):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        import paper_2501_13240_gb300 as sem
+        om = oracle.box_mesh(case["nel"], case["N"], periodic=case["periodic"], dirichlet=case["dirichlet"])
+        desc = sem.box_desc(case["nel"], case["N"], periodic=case["periodic"], dirichlet=case["dirichlet"])
+        n3 = (case["N"] + 1) ** 3
+        e0, e1, ni = sem.sem_partition_info(desc, world, rank)
+        mine = slice(e0 * n3, e1 * n3)
+        gids, nshare = sem.sem_partition_interface(desc, world, rank)
+        # brute force: unique ids this rank holds that another rank also holds
+        own = np.unique(om.l2g[mine])
+        other = np.unique(np.concatenate([om.l2g[: e0 * n3], om.l2g[e1 * n3:]]))
+        brute = np.intersect1d(own, other)
+        maps_ok = np.array_equal(gids, brute)
+        holders = np.zeros(om.n_unique, dtype=np.int32)
+        for q in range(world):
+            a, b, _ = sem.sem_partition_info(desc, world, q)
+            holders[np.unique(om.l2g[a * n3:b * n3])] += 1
+        share_ok = np.array_equal(nshare, holders[gids])
+        # rank-local partial sums, then exchange of the interface partial sums
+        v = np.random.default_rng(17).standard_normal(om.n_local)
+        part = np.zeros(om.n_unique)
+        np.add.at(part, om.l2g[mine], v[mine])
+        allg = np.unique(np.concatenate([sem.sem_partition_interface(desc, world, q)[0] for q in range(world)]))
+        buf = torch.zeros(len(allg), dtype=torch.float64)
+        idx = np.searchsorted(allg, gids)
+        buf[idx] = torch.from_numpy(part[gids])
+        dist.all_reduce(buf)
+        part[gids] = buf.numpy()[idx]
+        got = part[om.l2g[mine]]
+        ref = oracle.qqt(om, v)[mine]
+        err = float(np.abs(got - ref).max() / np.abs(ref).max())
+        queue.put((rank, bool(maps_ok), bool(share_ok), err, int(ni)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_partitioned_gather_scatter(world, case):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, CASES[case], q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, maps_ok, share_ok, err, ni in sorted(res):
+        assert maps_ok and share_ok, (rank, ni)
+        assert err < 1e-14, (rank, err)
+        assert ni > 0
+
+
+def test_partition_rejects_bad_arguments():
+    import paper_2501_13240_gb300 as sem
+    d = sem.box_desc((2, 2, 2), 3)
+    with pytest.raises(sem.SemError):
+        sem.sem_partition_info(d, 3, 0)  # more ranks than element planes
+    with pytest.raises(sem.SemError):
+        sem.sem_partition_info(d, 2, 2)
+    assert sem.sem_partition_info(d, 1, 0) == (0, 8, 0)
