@@ -1,0 +1,67 @@
+"""Pins of the oracle's discrete adjoint of the frozen-velocity temperature
+steps and of the bottom-wall Nusselt functional (Sec. 4.1 Eq. (2); plates of
+Sec. 4.4): Nu_b = 1 for conduction, linearity of the functional, the adjoint
+against the dense Jacobian built column by column, and central finite
+differences. CPU only."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import adjoint, rbc
+
+
+def rbc_mesh(nel=(2, 2, 3), N=4, stretch=1.5):
+    return oracle.box_mesh(nel, N, periodic=(1, 1, 0), dirichlet=(0, 0, 0, 0, 1, 1), z_stretch=stretch)
+
+
+def velocities(m, K, amp=0.3, seed=4):
+    rng = np.random.default_rng(seed)
+    return [[amp * rng.standard_normal(m.n_unique) * m.mask for _ in range(3)] for _ in range(K)]
+
+
+def test_nusselt_of_conduction_is_one():
+    m = rbc_mesh()
+    g = rbc.geometry(m)
+    z = np.zeros(m.n_unique)
+    z[m.l2g] = m.Z
+    assert abs(adjoint.nusselt_bottom(m, g, 1.0 - z) - 1.0) < 1e-13
+    # twice the gradient -> twice the flux; and the gradient vector is the functional
+    assert abs(adjoint.nusselt_bottom(m, g, 2.0 * (1.0 - z)) - 2.0) < 1e-13
+    c = adjoint.nusselt_bottom_grad(m, g)
+    T = np.random.default_rng(1).standard_normal(m.n_unique)
+    assert abs(np.dot(c, T) - adjoint.nusselt_bottom(m, g, T)) < 1e-12 * np.abs(c).sum()
+
+
+def test_adjoint_equals_dense_jacobian():
+    m = rbc_mesh((2, 2, 2), 3, 1.0)
+    K, kappa, dt = 4, 0.05, 0.01
+    ta = adjoint.TAdv(m, kappa, dt)
+    us = velocities(m, K)
+    T0 = ta.Tb + 0.1 * np.random.default_rng(2).standard_normal(m.n_unique) * ta.mk
+    c = adjoint.nusselt_bottom_grad(m, ta.g)
+    base = np.dot(c, ta.forward(T0, us))
+    free = np.nonzero(m.mask)[0]
+    jac = np.zeros(len(free))  # dJ/dT0 by perturbing one free node at a time (J is affine)
+    for t, i in enumerate(free):
+        T1 = T0.copy()
+        T1[i] += 1.0
+        jac[t] = np.dot(c, ta.forward(T1, us)) - base
+    grad = ta.adjoint(c, us)
+    np.testing.assert_allclose(grad[free], jac, rtol=0, atol=1e-10 * np.abs(jac).max())
+    assert np.all(grad[m.mask == 0] == 0.0)
+
+
+def test_adjoint_against_central_differences():
+    m = rbc_mesh((2, 2, 3), 4, 1.5)
+    K, kappa, dt = 6, 0.02, 0.005
+    ta = adjoint.TAdv(m, kappa, dt)
+    us = velocities(m, K, amp=0.5, seed=7)
+    T0 = ta.Tb.copy()
+    J = lambda T: adjoint.nusselt_bottom(m, ta.g, ta.forward(T, us))  # noqa: E731
+    grad = ta.adjoint(adjoint.nusselt_bottom_grad(m, ta.g), us)
+    rng = np.random.default_rng(11)
+    eps = 1e-6
+    for _ in range(4):
+        d = rng.standard_normal(m.n_unique) * ta.mk
+        fd = (J(T0 + eps * d) - J(T0 - eps * d)) / (2 * eps)
+        assert abs(fd - np.dot(grad, d)) <= 1e-6 * (abs(fd) + 1e-12), (fd, np.dot(grad, d))
