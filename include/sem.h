@@ -313,6 +313,7 @@ typedef struct {
   double *u, *v, *w, *T, *p; /* device U-vectors of the current state (owned by the handle) */
   int64_t n_unique;
   int step;
+  double *u_prev, *v_prev, *w_prev; /* the velocity one step earlier (zero before the first step) */
 } sem_rbc_view;
 
 /* Create the state on mesh m (which must outlive it): u = 0, T = 1 - z/Lz
@@ -330,6 +331,86 @@ int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *st, void *stream);
 int sem_rbc_fields(const sem_rbc *s, sem_rbc_view *view);
 
 int sem_rbc_destroy(sem_rbc *s);
+
+/* State snapshots for checkpoint/restart. The state after a step is u, v, w,
+ * their previous level, T, T^{n-1}, p, the previous wall term (U-vectors),
+ * the previous advection terms of T, u, v, w (E-vectors) and the step
+ * counter; every other array is rebuilt each step, so restoring a snapshot
+ * and stepping again reproduces the original run bit for bit.
+ * sem_rbc_state_bytes: size of a snapshot (64-byte header + the arrays).
+ * sem_rbc_save_state / sem_rbc_load_state: copy to / from a caller-owned
+ * device buffer of that size; both synchronise the stream. Loading a
+ * snapshot of another mesh size returns SEM_ERR_INVALID_ARG. */
+int sem_rbc_state_bytes(const sem_rbc *s, size_t *bytes);
+int sem_rbc_save_state(const sem_rbc *s, void *dev_buf, void *stream);
+int sem_rbc_load_state(sem_rbc *s, const void *dev_buf, void *stream);
+
+/* The same snapshot in a file: the 8 bytes "SEMRBC01", the snapshot, then
+ * its FNV-1a 64-bit checksum (little-endian). sem_rbc_load returns SEM_ERR_IO
+ * for a missing, truncated or corrupted file or one of another mesh size, and
+ * then leaves the state unchanged. Both use the default stream. */
+int sem_rbc_save(const sem_rbc *s, const char *path);
+int sem_rbc_load(sem_rbc *s, const char *path);
+
+/* ------------------------------------------------------------------------
+ * Temperature transport with a prescribed velocity history and its discrete
+ * adjoint. The step is the temperature update of sem_bdf_ext_step (Sec. 4.1,
+ * Eq. (2); BDF2/EXT2 of Sec. 2.2, BDF1/EXT1 at n = 0, lifting Tb = 1 - z/Lz)
+ * with the velocity u^n given as data:
+ *   T^{n+1} = Tb + H^{-1} M [Q^T B((b1 Q T^n + b2 Q T^{n-1})/dt + a1 N^n + a2 N^{n-1}) - Q^T H_L Q Tb],
+ *   N^n = -(u^n . grad)(Q T^n),  H = kappa A + (b0/dt) B.
+ * With u frozen, T^K is affine in T^0, and the transposed step gives the
+ * exact gradient of a linear functional of T^K. The paper has no adjoint;
+ * these calls add differentiation of its temperature step.
+ * U-vectors: n_unique doubles; E-vectors: n_local doubles; all device
+ * arrays, caller-owned. Every call synchronises the stream.
+ * ------------------------------------------------------------------------ */
+typedef struct sem_tadv sem_tadv; /* opaque; owns its scratch */
+
+typedef struct {
+  double kappa;  /* diffusivity (1/sqrt(Ra Pr) for the Boussinesq scaling) */
+  double dt;
+  double tol;    /* relative residual of each Helmholtz solve */
+  int maxit;
+  int precision; /* SEM_PREC_FP64 or SEM_PREC_DF64 operator in the solves */
+} sem_tadv_params;
+
+/* The mesh must have Dirichlet plates at z = 0 and z = Lz. */
+int sem_tadv_create(const sem_mesh *m, const sem_tadv_params *prm, void *stream, sem_tadv **out);
+int sem_tadv_destroy(sem_tadv *t);
+
+/* A_b (the quadrature of 1 over the bottom plate) and the lifting Tb
+ * (device U-vector owned by the handle). Either output may be NULL. */
+int sem_tadv_info(const sem_tadv *t, double *area, const double **Tb);
+
+/* Forward step n >= 0. u[3]: host array of three device U-vectors (u^n).
+ * Tn: T^n; Tnm1, NTnm1: T^{n-1} (U) and N^{n-1} (E), ignored at n = 0.
+ * Writes Tnp1 (U) and NTn = N^n (E); *iters (may be NULL) gets the PCG
+ * iterations. Tnp1 must not alias an input. Returns SEM_OK,
+ * SEM_ERR_NOT_CONVERGED (the step completed with maxit iterations) or an
+ * error. */
+int sem_tadv_step(sem_tadv *t, int n, const double *const u[3], const double *Tn, const double *Tnm1,
+                  const double *NTnm1, double *Tnp1, double *NTn, int *iters, void *stream);
+
+/* Reverse of step n: with psi = H^{-1} M g_np1 and phi = B Q psi,
+ *   g_n   += Q^T [(b1/dt) phi + a1 L_n^T phi],
+ *   g_nm1 += Q^T [(b2/dt) phi + a2 L_{n-1}^T phi]     (n > 0 only),
+ * L_n = -(u^n . grad), so g_n is dJ/dT^n for J linear in T^K once every
+ * later step has been reversed. u_n: velocity u^n; u_nm1: u^{n-1} (NULL at
+ * n = 0). At n = 0 the Dirichlet entries of g_n are set to zero: g_0 is then
+ * the gradient with respect to the free values of T^0. Returns like
+ * sem_tadv_step. */
+int sem_tadv_adjoint_step(sem_tadv *t, int n, const double *const u_n[3], const double *const u_nm1[3],
+                          const double *g_np1, double *g_n, double *g_nm1, int *iters, void *stream);
+
+/* Bottom-plate Nusselt number of the U-vector T (a host double):
+ *   Nu_b = -(1/A_b) sum over the bottom-face nodes of rho_i rho_j |x_r x x_s| dT/dz,
+ * dT/dz from the element-local derivatives; 1 for T = 1 - z/Lz. */
+int sem_tadv_nusselt(sem_tadv *t, const double *T, double *nu, void *stream);
+
+/* c = scale * dNu_b/dT (U-vector; Nu_b is linear in T, so Nu_b(T) = c.T at
+ * scale 1). */
+int sem_tadv_nusselt_grad(sem_tadv *t, double scale, double *c, void *stream);
 
 /* ------------------------------------------------------------------------
  * Multi-rank partition (host only). Sec. 2.2: one rank per GPU; shared

@@ -38,6 +38,9 @@ EXPORTS = (
     "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_ax_assembled_add", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
     "sem_pcg_solve", "sem_pcg_solve_noalloc", "sem_pcg_noalloc_capacity",
     "sem_rbc_create", "sem_bdf_ext_step", "sem_rbc_fields", "sem_rbc_destroy",
+    "sem_rbc_state_bytes", "sem_rbc_save_state", "sem_rbc_load_state", "sem_rbc_save", "sem_rbc_load",
+    "sem_tadv_create", "sem_tadv_destroy", "sem_tadv_info", "sem_tadv_step", "sem_tadv_adjoint_step",
+    "sem_tadv_nusselt", "sem_tadv_nusselt_grad",
     "sem_pmg_create", "sem_pmg_lambda", "sem_pmg_vcycle", "sem_pmg_prolong", "sem_pmg_restrict",
     "sem_pmg_pcg_solve", "sem_pmg_destroy", "sem_partition_info", "sem_partition_interface",
 )
@@ -92,7 +95,13 @@ class sem_step_stats(ctypes.Structure):
 
 class sem_rbc_view(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p), ("T", ctypes.c_void_p),
-                ("p", ctypes.c_void_p), ("n_unique", ctypes.c_int64), ("step", ctypes.c_int)]
+                ("p", ctypes.c_void_p), ("n_unique", ctypes.c_int64), ("step", ctypes.c_int),
+                ("u_prev", ctypes.c_void_p), ("v_prev", ctypes.c_void_p), ("w_prev", ctypes.c_void_p)]
+
+
+class sem_tadv_params(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_double), ("dt", ctypes.c_double), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 _lib = None
@@ -137,6 +146,19 @@ def lib() -> ctypes.CDLL:
         sig["sem_bdf_ext_step"] = ([_vp, ctypes.POINTER(sem_step_stats), _vp], _i)
         sig["sem_rbc_fields"] = ([_vp, ctypes.POINTER(sem_rbc_view)], _i)
         sig["sem_rbc_destroy"] = ([_vp], _i)
+        sig["sem_rbc_state_bytes"] = ([_vp, ctypes.POINTER(ctypes.c_size_t)], _i)
+        sig["sem_rbc_save_state"] = ([_vp, _vp, _vp], _i)
+        sig["sem_rbc_load_state"] = ([_vp, _vp, _vp], _i)
+        sig["sem_rbc_save"] = ([_vp, ctypes.c_char_p], _i)
+        sig["sem_rbc_load"] = ([_vp, ctypes.c_char_p], _i)
+        _vp3 = ctypes.POINTER(_vp)
+        sig["sem_tadv_create"] = ([_vp, ctypes.POINTER(sem_tadv_params), _vp, ctypes.POINTER(_vp)], _i)
+        sig["sem_tadv_destroy"] = ([_vp], _i)
+        sig["sem_tadv_info"] = ([_vp, ctypes.POINTER(_d), ctypes.POINTER(_vp)], _i)
+        sig["sem_tadv_step"] = ([_vp, _i, _vp3, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i), _vp], _i)
+        sig["sem_tadv_adjoint_step"] = ([_vp, _i, _vp3, _vp3, _vp, _vp, _vp, ctypes.POINTER(_i), _vp], _i)
+        sig["sem_tadv_nusselt"] = ([_vp, _vp, ctypes.POINTER(_d), _vp], _i)
+        sig["sem_tadv_nusselt_grad"] = ([_vp, _d, _vp, _vp], _i)
         sig["sem_pmg_create"] = ([_vp, _d, _d, ctypes.POINTER(sem_pmg_opts), _vp, ctypes.POINTER(_vp)], _i)
         sig["sem_pmg_lambda"] = ([_vp, _i, ctypes.POINTER(_d)], _i)
         sig["sem_pmg_vcycle"] = ([_vp, _vp, _vp, _vp], _i)
@@ -468,11 +490,125 @@ def sem_bdf_ext_step(s: RBC, stream=None, raise_on_error: bool = True) -> dict:
 
 
 def sem_rbc_fields(s: RBC) -> dict:
-    """Copies of the current fields (u, v, w, T, p) as torch tensors."""
+    """Copies of the current fields (u, v, w, T, p, and the previous velocity
+    u_prev, v_prev, w_prev) as torch tensors."""
     v = sem_rbc_view()
     _check(lib().sem_rbc_fields(s._h, ctypes.byref(v)))
     n = int(v.n_unique)
-    return {k: _device_copy(getattr(v, k), n) for k in ("u", "v", "w", "T", "p")}
+    return {k: _device_copy(getattr(v, k), n) for k in ("u", "v", "w", "T", "p", "u_prev", "v_prev", "w_prev")}
+
+
+def sem_rbc_state_bytes(s: RBC) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().sem_rbc_state_bytes(s._h, ctypes.byref(n)))
+    return int(n.value)
+
+
+def sem_rbc_save_state(s: RBC, buf=None, stream=None):
+    """Snapshot of the state into a device uint8 tensor (allocated if None)."""
+    import torch
+    nb = sem_rbc_state_bytes(s)
+    if buf is None:
+        buf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    _check(lib().sem_rbc_save_state(s._h, _ptr(buf, torch.uint8, nb, "buf"), _stream(stream)))
+    return buf
+
+
+def sem_rbc_load_state(s: RBC, buf, stream=None):
+    import torch
+    _check(lib().sem_rbc_load_state(s._h, _ptr(buf, torch.uint8, sem_rbc_state_bytes(s), "buf"), _stream(stream)))
+
+
+def sem_rbc_save(s: RBC, path: str):
+    _check(lib().sem_rbc_save(s._h, os.fsencode(path)))
+
+
+def sem_rbc_load(s: RBC, path: str):
+    _check(lib().sem_rbc_load(s._h, os.fsencode(path)))
+
+
+class TAdv:
+    """Owns a ``sem_tadv`` handle (temperature transport with a given velocity)."""
+
+    def __init__(self, handle, mesh: Mesh):
+        self._h = handle
+        self.mesh = mesh
+
+    def destroy(self):
+        if self._h is not None:
+            lib().sem_tadv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def area(self) -> float:
+        a = ctypes.c_double()
+        _check(lib().sem_tadv_info(self._h, ctypes.byref(a), None))
+        return float(a.value)
+
+    def lifting(self):
+        """Copy of the lifting Tb = 1 - z/Lz (U-vector)."""
+        p = _vp()
+        _check(lib().sem_tadv_info(self._h, None, ctypes.byref(p)))
+        return _device_copy(p.value, self.mesh.n_unique)
+
+
+def sem_tadv_create(mesh: Mesh, kappa: float, dt: float, tol: float = 1e-13, maxit: int = 5000,
+                    precision: int = SEM_PREC_FP64, stream=None) -> TAdv:
+    prm = sem_tadv_params(float(kappa), float(dt), float(tol), int(maxit), int(precision))
+    h = ctypes.c_void_p()
+    _check(lib().sem_tadv_create(mesh.handle, ctypes.byref(prm), _stream(stream), ctypes.byref(h)))
+    return TAdv(h, mesh)
+
+
+def _vel(mesh: Mesh, u, name):
+    import torch
+    if u is None:
+        return None
+    if len(u) != 3:
+        raise ValueError(f"{name} must hold three U-vectors")
+    return (_vp * 3)(*[_ptr(c, torch.float64, mesh.n_unique, name).value for c in u])
+
+
+def _opt(t, n, name):
+    import torch
+    return _ptr(t, torch.float64, n, name) if t is not None else None
+
+
+def sem_tadv_step(t: TAdv, n: int, u, Tn, Tnm1, NTnm1, Tnp1, NTn, stream=None) -> int:
+    """Forward step n (see the header); returns the PCG iterations."""
+    m = t.mesh
+    it = _i()
+    _check(lib().sem_tadv_step(t._h, int(n), _vel(m, u, "u"), _opt(Tn, m.n_unique, "Tn"),
+                               _opt(Tnm1, m.n_unique, "Tnm1"), _opt(NTnm1, m.n_local, "NTnm1"),
+                               _opt(Tnp1, m.n_unique, "Tnp1"), _opt(NTn, m.n_local, "NTn"), ctypes.byref(it),
+                               _stream(stream)))
+    return int(it.value)
+
+
+def sem_tadv_adjoint_step(t: TAdv, n: int, u_n, u_nm1, g_np1, g_n, g_nm1, stream=None) -> int:
+    """Reverse of step n (see the header); returns the PCG iterations."""
+    m = t.mesh
+    it = _i()
+    _check(lib().sem_tadv_adjoint_step(t._h, int(n), _vel(m, u_n, "u_n"), _vel(m, u_nm1, "u_nm1"),
+                                       _opt(g_np1, m.n_unique, "g_np1"), _opt(g_n, m.n_unique, "g_n"),
+                                       _opt(g_nm1, m.n_unique, "g_nm1"), ctypes.byref(it), _stream(stream)))
+    return int(it.value)
+
+
+def sem_tadv_nusselt(t: TAdv, T, stream=None) -> float:
+    v = ctypes.c_double()
+    _check(lib().sem_tadv_nusselt(t._h, _opt(T, t.mesh.n_unique, "T"), ctypes.byref(v), _stream(stream)))
+    return float(v.value)
+
+
+def sem_tadv_nusselt_grad(t: TAdv, c, scale: float = 1.0, stream=None):
+    _check(lib().sem_tadv_nusselt_grad(t._h, float(scale), _opt(c, t.mesh.n_unique, "c"), _stream(stream)))
+    return c
 
 
 class PMG:

@@ -22,6 +22,7 @@
 #include <utility>
 #include <vector>
 
+#include "sem_fields.cuh"
 #include "sem_internal.h"
 
 struct sem_rbc {
@@ -58,76 +59,6 @@ StepCoef coefficients(int step) {
 }
 
 // ---------------------------------------------------------------- kernels
-// inverse Jacobian dr_a/dx_c at every node, R[(9e + 3a + c) n3 + q]
-__global__ void k_inv_jacobian(int n, int64_t E, const double *__restrict__ D, const double *__restrict__ X,
-                               const double *__restrict__ Y, const double *__restrict__ Z, double *__restrict__ R) {
-  const int n3 = n * n * n;
-  const int64_t nL = E * n3;
-  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = l / n3;
-    const int q = (int)(l - e * n3);
-    const int i = q % n, j = (q / n) % n, k = q / (n * n);
-    const int64_t base = e * n3;
-    const double *xc[3] = {X + base, Y + base, Z + base};
-    double J[3][3];
-    for (int c = 0; c < 3; ++c) {
-      double a = 0, b = 0, d = 0;
-      for (int m = 0; m < n; ++m) {
-        a = fma(D[i * n + m], xc[c][m + n * (j + n * k)], a);
-        b = fma(D[j * n + m], xc[c][i + n * (m + n * k)], b);
-        d = fma(D[k * n + m], xc[c][i + n * (j + n * m)], d);
-      }
-      J[c][0] = a;
-      J[c][1] = b;
-      J[c][2] = d;
-    }
-    const double C00 = J[1][1] * J[2][2] - J[1][2] * J[2][1], C01 = J[1][2] * J[2][0] - J[1][0] * J[2][2],
-                 C02 = J[1][0] * J[2][1] - J[1][1] * J[2][0], C10 = J[0][2] * J[2][1] - J[0][1] * J[2][2],
-                 C11 = J[0][0] * J[2][2] - J[0][2] * J[2][0], C12 = J[0][1] * J[2][0] - J[0][0] * J[2][1],
-                 C20 = J[0][1] * J[1][2] - J[0][2] * J[1][1], C21 = J[0][2] * J[1][0] - J[0][0] * J[1][2],
-                 C22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-    const double inv = 1.0 / (J[0][0] * C00 + J[0][1] * C01 + J[0][2] * C02);
-    const double Rm[9] = {C00 * inv, C10 * inv, C20 * inv, C01 * inv, C11 * inv,
-                          C21 * inv, C02 * inv, C12 * inv, C22 * inv};  // [a][c]
-    for (int t = 0; t < 9; ++t) R[(9 * e + t) * n3 + q] = Rm[t];
-  }
-}
-
-// physical gradient of an E-vector: g_c = sum_a dr_a/dx_c (D_a f)
-__global__ void k_grad(int n, int64_t E, const double *__restrict__ D, const double *__restrict__ R,
-                       const double *__restrict__ f, double *__restrict__ gx, double *__restrict__ gy,
-                       double *__restrict__ gz) {
-  const int n3 = n * n * n;
-  const int64_t nL = E * n3;
-  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = l / n3;
-    const int q = (int)(l - e * n3);
-    const int i = q % n, j = (q / n) % n, k = q / (n * n);
-    const double *fe = f + e * n3;
-    double dr = 0, ds = 0, dt = 0;
-    for (int m = 0; m < n; ++m) {
-      dr = fma(D[i * n + m], fe[m + n * (j + n * k)], dr);
-      ds = fma(D[j * n + m], fe[i + n * (m + n * k)], ds);
-      dt = fma(D[k * n + m], fe[i + n * (j + n * m)], dt);
-    }
-    const double *Re = R + 9 * e * n3 + q;
-    gx[l] = Re[0 * n3] * dr + Re[3 * n3] * ds + Re[6 * n3] * dt;
-    gy[l] = Re[1 * n3] * dr + Re[4 * n3] * ds + Re[7 * n3] * dt;
-    gz[l] = Re[2 * n3] * dr + Re[5 * n3] * ds + Re[8 * n3] * dt;
-  }
-}
-
-// out = -(u . grad f) (+ add if given)
-__global__ void k_neg_adv(int64_t nL, const double *__restrict__ u0, const double *__restrict__ u1,
-                          const double *__restrict__ u2, const double *__restrict__ g0, const double *__restrict__ g1,
-                          const double *__restrict__ g2, const double *__restrict__ add, double *__restrict__ out) {
-  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
-    double v = -(u0[l] * g0[l] + u1[l] * g1[l] + u2[l] * g2[l]);
-    if (add) v += add[l];
-    out[l] = v;
-  }
-}
-
 // accumulate the curl of u from grad u_c: om_x = dw/dy - dv/dz, om_y = du/dz - dw/dx, om_z = dv/dx - du/dy
 __global__ void k_curl_acc(int64_t nL, int c, const double *__restrict__ g0, const double *__restrict__ g1,
                            const double *__restrict__ g2, double *__restrict__ ox, double *__restrict__ oy,
@@ -206,51 +137,7 @@ __global__ void k_wall(int n, const int *__restrict__ nel, int d, int side, doub
 }
 
 // weak divergence: out = sum_a D_a^T v_a with v_a = B sum_c dr_a/dx_c f_c
-__global__ void k_weak_div_v(int n, int64_t E, const double *__restrict__ R, const double *__restrict__ B,
-                             const double *__restrict__ f0, const double *__restrict__ f1, const double *__restrict__ f2,
-                             double *__restrict__ v0, double *__restrict__ v1, double *__restrict__ v2) {
-  const int n3 = n * n * n;
-  const int64_t nL = E * n3;
-  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = l / n3;
-    const int q = (int)(l - e * n3);
-    const double *Re = R + 9 * e * n3 + q;
-    const double fb0 = f0[l], fb1 = f1[l], fb2 = f2[l], bw = B[l];
-    v0[l] = bw * (Re[0 * n3] * fb0 + Re[1 * n3] * fb1 + Re[2 * n3] * fb2);
-    v1[l] = bw * (Re[3 * n3] * fb0 + Re[4 * n3] * fb1 + Re[5 * n3] * fb2);
-    v2[l] = bw * (Re[6 * n3] * fb0 + Re[7 * n3] * fb1 + Re[8 * n3] * fb2);
-  }
-}
-
-__global__ void k_dt_sum(int n, int64_t E, const double *__restrict__ D, const double *__restrict__ v0,
-                         const double *__restrict__ v1, const double *__restrict__ v2, double *__restrict__ out) {
-  const int n3 = n * n * n;
-  const int64_t nL = E * n3;
-  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = l / n3;
-    const int q = (int)(l - e * n3);
-    const int i = q % n, j = (q / n) % n, k = q / (n * n);
-    const int64_t base = e * n3;
-    double s = 0.0;
-    for (int m = 0; m < n; ++m) {
-      s = fma(D[m * n + i], v0[base + m + n * (j + n * k)], s);
-      s = fma(D[m * n + j], v1[base + i + n * (m + n * k)], s);
-      s = fma(D[m * n + k], v2[base + i + n * (j + n * m)], s);
-    }
-    out[l] = s;
-  }
-}
-
 // Q^T with optional mask: vg[g] = (mask ? mask[g] : 1) * sum of copies
-__global__ void k_gather_m(int64_t nU, const int32_t *__restrict__ off, const int32_t *__restrict__ perm,
-                           const uint8_t *__restrict__ mask, const double *__restrict__ vL, double *__restrict__ vg) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int32_t t = off[g]; t < off[g + 1]; ++t) s += vL[perm[t]];
-    vg[g] = (mask && !mask[g]) ? 0.0 : s;
-  }
-}
-
 // T right-hand side (local): B ((b1 T + b2 Tp)/dt + a1 NT + a2 NTp) - H(Tb)
 __global__ void k_rhsT(int64_t nL, double dt, StepCoef k, const double *__restrict__ B, const double *__restrict__ TL,
                        const double *__restrict__ TpL, const double *__restrict__ NT, const double *__restrict__ NTp,
@@ -275,59 +162,7 @@ __global__ void k_bdiff(int64_t nL, const double *__restrict__ B, const double *
 }
 
 // y = a x + b y2 + c z (U-vectors; any pointer may alias y)
-__global__ void k_axpbypcz(int64_t n, double a, const double *x, double b, const double *y2, double c,
-                           const double *z, double *y) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    double v = a * x[g];
-    if (y2) v += b * y2[g];
-    if (z) v += c * z[g];
-    y[g] = v;
-  }
-}
-
-__global__ void k_lifting(int64_t nL, double Lz, const int32_t *__restrict__ l2g, const double *__restrict__ Z,
-                          double *__restrict__ Tb) {
-  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x)
-    Tb[l2g[l]] = 1.0 - Z[l] / Lz;  // every copy writes the same value
-}
-
-__global__ void k_add_masked(int64_t nU, const uint8_t *__restrict__ mask, const double *__restrict__ a,
-                             double *__restrict__ y) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x)
-    if (mask[g]) y[g] += a[g];
-}
-
-// fixed-order sum: partials, then one block finishes and stores sum / n
-__global__ void k_sum_part(int64_t n, const double *__restrict__ x, double *__restrict__ part) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    s += x[g];
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    part[blockIdx.x] = t;
-  }
-}
-
-__global__ void k_mean_finish(int np, int64_t n, const double *__restrict__ part, double *__restrict__ mean) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double t = 0.0;
-    for (int b = 0; b < np; ++b) t += part[b];
-    *mean = t / (double)n;
-  }
-}
-
-__global__ void k_sub_scalar(int64_t n, const double *__restrict__ s, double *__restrict__ x) {
-  const double v = *s;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    x[g] -= v;
-}
-
-// ---------------------------------------------------------------- host helpers
+// fixed-order sum: partials, then one block finishes and stores sum / n// ---------------------------------------------------------------- host helpers
 int remove_mean(sem_rbc *s, double *x, cudaStream_t st) {
   k_sum_part<<<kRedBlocks, 256, 0, st>>>(s->nU, x, s->scal);
   k_mean_finish<<<1, 32, 0, st>>>(kRedBlocks, s->nU, s->scal, s->scal + kRedBlocks);
@@ -438,8 +273,16 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
   k_lifting<<<grid_for(s->nL, 256), 256, 0, st>>>(s->nL, m->L[2], m->l2g, m->Z, s->Tb);
   cudaMemcpyAsync(s->T, s->Tb, sizeof(double) * s->nU, cudaMemcpyDeviceToDevice, st);
   if (T_pert_g) k_add_masked<<<grid_for(s->nU, 256), 256, 0, st>>>(s->nU, m->mask, T_pert_g, s->T);
-  for (int c = 0; c < 3; ++c) cudaMemsetAsync(s->u[c], 0, sizeof(double) * s->nU, st);
+  // every array a snapshot holds starts defined: u = 0 and zero history
+  for (int c = 0; c < 3; ++c) {
+    cudaMemsetAsync(s->u[c], 0, sizeof(double) * s->nU, st);
+    cudaMemsetAsync(s->up[c], 0, sizeof(double) * s->nU, st);
+    cudaMemsetAsync(s->Nup[c], 0, sizeof(double) * s->nL, st);
+  }
   cudaMemsetAsync(s->p, 0, sizeof(double) * s->nU, st);
+  cudaMemsetAsync(s->Tp, 0, sizeof(double) * s->nU, st);
+  cudaMemsetAsync(s->Wp, 0, sizeof(double) * s->nU, st);
+  cudaMemsetAsync(s->NTp, 0, sizeof(double) * s->nL, st);
   if (prm->pressure_pmg && m->N > 1) {
     sem_pmg_opts po;
     memset(&po, 0, sizeof(po));
@@ -487,6 +330,9 @@ extern "C" int sem_rbc_fields(const sem_rbc *s, sem_rbc_view *v) {
   v->p = s->p;
   v->n_unique = s->nU;
   v->step = s->step;
+  v->u_prev = s->up[0];
+  v->v_prev = s->up[1];
+  v->w_prev = s->up[2];
   return SEM_OK;
 }
 
@@ -603,4 +449,119 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   stt->step = s->step;
   stt->step_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return stt->status;
+}
+
+// ---------------------------------------------------------------- checkpoints
+// The state after a step: u, u^{n-1}, T, T^{n-1}, p, W^{n-1} (U-vectors),
+// N_T^{n-1}, N_u^{n-1} (E-vectors) and the step counter; the rest is rebuilt
+// every step. Layout: 64-byte header (step, n_unique, n_local) then the
+// arrays in that order.
+namespace {
+
+struct StateLayout {
+  std::vector<std::pair<double *, int64_t>> arrays;
+  size_t bytes;
+};
+
+StateLayout layout(const sem_rbc *s) {
+  StateLayout L;
+  double *uvec[] = {s->u[0], s->u[1], s->u[2], s->up[0], s->up[1], s->up[2], s->T, s->Tp, s->p, s->Wp};
+  for (double *p : uvec) L.arrays.push_back({p, s->nU});
+  double *evec[] = {s->NTp, s->Nup[0], s->Nup[1], s->Nup[2]};
+  for (double *p : evec) L.arrays.push_back({p, s->nL});
+  L.bytes = 64;
+  for (auto &a : L.arrays) L.bytes += sizeof(double) * (size_t)a.second;
+  return L;
+}
+
+uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t h) {
+  for (size_t t = 0; t < n; ++t) h = (h ^ p[t]) * 1099511628211ull;
+  return h;
+}
+
+}  // namespace
+
+extern "C" int sem_rbc_state_bytes(const sem_rbc *s, size_t *bytes) {
+  if (!s || !bytes) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_state_bytes: NULL argument");
+  *bytes = layout(s).bytes;
+  return SEM_OK;
+}
+
+extern "C" int sem_rbc_save_state(const sem_rbc *s, void *dev_buf, void *stream) {
+  if (!s || !dev_buf) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_save_state: NULL argument");
+  cudaStream_t st = as_stream(stream);
+  int64_t hdr[8] = {s->step, s->nU, s->nL, 0, 0, 0, 0, 0};
+  SEM_CUDA(cudaMemcpyAsync(dev_buf, hdr, sizeof(hdr), cudaMemcpyHostToDevice, st));
+  size_t off = 64;
+  for (auto &a : layout(s).arrays) {
+    SEM_CUDA(cudaMemcpyAsync((char *)dev_buf + off, a.first, sizeof(double) * a.second, cudaMemcpyDeviceToDevice, st));
+    off += sizeof(double) * a.second;
+  }
+  SEM_CUDA(cudaStreamSynchronize(st));  // the header lives on this stack frame
+  return SEM_OK;
+}
+
+extern "C" int sem_rbc_load_state(sem_rbc *s, const void *dev_buf, void *stream) {
+  if (!s || !dev_buf) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_load_state: NULL argument");
+  cudaStream_t st = as_stream(stream);
+  int64_t hdr[8];
+  SEM_CUDA(cudaMemcpyAsync(hdr, dev_buf, sizeof(hdr), cudaMemcpyDeviceToHost, st));
+  SEM_CUDA(cudaStreamSynchronize(st));
+  if (hdr[1] != s->nU || hdr[2] != s->nL || hdr[0] < 0)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_load_state: the snapshot belongs to another mesh");
+  size_t off = 64;
+  for (auto &a : layout(s).arrays) {
+    SEM_CUDA(cudaMemcpyAsync(a.first, (const char *)dev_buf + off, sizeof(double) * a.second,
+                             cudaMemcpyDeviceToDevice, st));
+    off += sizeof(double) * a.second;
+  }
+  SEM_CUDA(cudaStreamSynchronize(st));
+  s->step = (int)hdr[0];
+  return SEM_OK;
+}
+
+// File checkpoint: magic "SEMRBC01", the state header and arrays, then an
+// FNV-1a 64-bit checksum of everything before it.
+extern "C" int sem_rbc_save(const sem_rbc *s, const char *path) {
+  if (!s || !path) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_save: NULL argument");
+  const StateLayout L = layout(s);
+  std::vector<unsigned char> buf(8 + L.bytes);
+  memcpy(buf.data(), "SEMRBC01", 8);
+  int64_t hdr[8] = {s->step, s->nU, s->nL, 0, 0, 0, 0, 0};
+  memcpy(buf.data() + 8, hdr, 64);
+  size_t off = 8 + 64;
+  for (auto &a : L.arrays) {
+    SEM_CUDA(cudaMemcpy(buf.data() + off, a.first, sizeof(double) * a.second, cudaMemcpyDeviceToHost));
+    off += sizeof(double) * a.second;
+  }
+  const uint64_t h = fnv1a(buf.data(), buf.size(), 1469598103934665603ull);
+  FILE *f = fopen(path, "wb");
+  if (!f) return sem_fail(SEM_ERR_IO, std::string("sem_rbc_save: cannot open ") + path);
+  const bool ok = fwrite(buf.data(), 1, buf.size(), f) == buf.size() && fwrite(&h, sizeof(h), 1, f) == 1;
+  if (fclose(f) != 0 || !ok) return sem_fail(SEM_ERR_IO, std::string("sem_rbc_save: write failed: ") + path);
+  return SEM_OK;
+}
+
+extern "C" int sem_rbc_load(sem_rbc *s, const char *path) {
+  if (!s || !path) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_load: NULL argument");
+  const StateLayout L = layout(s);
+  std::vector<unsigned char> buf(8 + L.bytes);
+  uint64_t h = 0;
+  FILE *f = fopen(path, "rb");
+  if (!f) return sem_fail(SEM_ERR_IO, std::string("sem_rbc_load: cannot open ") + path);
+  const bool ok = fread(buf.data(), 1, buf.size(), f) == buf.size() && fread(&h, sizeof(h), 1, f) == 1;
+  fclose(f);
+  if (!ok) return sem_fail(SEM_ERR_IO, "sem_rbc_load: file truncated or of another mesh");
+  if (memcmp(buf.data(), "SEMRBC01", 8) != 0) return sem_fail(SEM_ERR_IO, "sem_rbc_load: not a checkpoint");
+  if (fnv1a(buf.data(), buf.size(), 1469598103934665603ull) != h) return sem_fail(SEM_ERR_IO, "sem_rbc_load: checksum mismatch");
+  int64_t hdr[8];
+  memcpy(hdr, buf.data() + 8, 64);
+  if (hdr[1] != s->nU || hdr[2] != s->nL) return sem_fail(SEM_ERR_IO, "sem_rbc_load: checkpoint of another mesh");
+  size_t off = 8 + 64;
+  for (auto &a : L.arrays) {
+    SEM_CUDA(cudaMemcpy(a.first, buf.data() + off, sizeof(double) * a.second, cudaMemcpyHostToDevice));
+    off += sizeof(double) * a.second;
+  }
+  s->step = (int)hdr[0];
+  return SEM_OK;
 }
