@@ -154,6 +154,20 @@ int sem_mesh_destroy(sem_mesh *m);
 /* Fill *info with sizes and device views. */
 int sem_mesh_info_get(const sem_mesh *m, sem_mesh_info *info);
 
+/* Deterministic assembly (on = 1) or atomic assembly (on = 0, the default).
+ * The assembled operators (sem_ax_assembled*, the PCG and p-multigrid
+ * solves) add each element's contribution to a unique node with FP64/FP32
+ * atomics by default, so sums over a node's copies come in a run-dependent
+ * order and results agree run to run only to rounding. In deterministic mode
+ * they write element results to an E-vector (8 bytes per local node, owned
+ * by the mesh) and sum each node's copies in ascending copy order: results
+ * are bitwise reproducible, at the cost of that scratch and one more pass
+ * over it. p-multigrid hierarchies take the setting of their fine mesh when
+ * they are created. Applications of operators on one deterministic mesh
+ * share the scratch and must not overlap on the GPU (one stream, or
+ * serialised by the caller). Turning it off synchronises the device. */
+int sem_mesh_set_deterministic(sem_mesh *m, int on);
+
 /* Copy l2g (n_local int32) and mask (n_unique uint8) to host arrays; either
  * may be NULL. Synchronous. */
 int sem_mesh_copy_maps(const sem_mesh *m, int32_t *l2g_host, uint8_t *mask_host);
@@ -335,20 +349,25 @@ int sem_rbc_destroy(sem_rbc *s);
 /* State snapshots for checkpoint/restart. The state after a step is u, v, w,
  * their previous level, T, T^{n-1}, p, the previous wall term (U-vectors),
  * the previous advection terms of T, u, v, w (E-vectors) and the step
- * counter; every other array is rebuilt each step, so restoring a snapshot
- * and stepping again reproduces the original run bit for bit.
- * sem_rbc_state_bytes: size of a snapshot (64-byte header + the arrays).
+ * counter; every other array is rebuilt each step. Restoring a snapshot and
+ * stepping again reproduces the original run bit for bit when the mesh is in
+ * deterministic mode (sem_mesh_set_deterministic), otherwise to rounding.
+ * sem_rbc_state_bytes: size of a snapshot: a header of eight int64 (step,
+ * n_unique, n_local, E, N, format version 1, the bits of dt, 0) then the
+ * arrays.
  * sem_rbc_save_state / sem_rbc_load_state: copy to / from a caller-owned
  * device buffer of that size; both synchronise the stream. Loading a
- * snapshot of another mesh size returns SEM_ERR_INVALID_ARG. */
+ * snapshot whose header differs in anything but the step (another mesh, dt
+ * or format) returns SEM_ERR_INVALID_ARG. */
 int sem_rbc_state_bytes(const sem_rbc *s, size_t *bytes);
 int sem_rbc_save_state(const sem_rbc *s, void *dev_buf, void *stream);
 int sem_rbc_load_state(sem_rbc *s, const void *dev_buf, void *stream);
 
 /* The same snapshot in a file: the 8 bytes "SEMRBC01", the snapshot, then
  * its FNV-1a 64-bit checksum (little-endian). sem_rbc_load returns SEM_ERR_IO
- * for a missing, truncated or corrupted file or one of another mesh size, and
- * then leaves the state unchanged. Both use the default stream. */
+ * for a missing, truncated or corrupted file or one whose header differs in
+ * anything but the step, and then leaves the state unchanged. Both use the
+ * default stream. */
 int sem_rbc_save(const sem_rbc *s, const char *path);
 int sem_rbc_load(sem_rbc *s, const char *path);
 

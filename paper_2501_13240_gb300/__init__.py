@@ -34,7 +34,7 @@ SEM_PREC_BF16 = 3
 # every symbol include/sem.h declares
 EXPORTS = (
     "sem_last_error", "sem_version", "sem_gll", "sem_mesh_create_box", "sem_mesh_destroy",
-    "sem_mesh_info_get", "sem_mesh_copy_maps", "sem_mesh_copy_gs_tables", "sem_ax_apply", "sem_gs_op",
+    "sem_mesh_info_get", "sem_mesh_set_deterministic", "sem_mesh_copy_maps", "sem_mesh_copy_gs_tables", "sem_ax_apply", "sem_gs_op",
     "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_ax_assembled_add", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
     "sem_pcg_solve", "sem_pcg_solve_noalloc", "sem_pcg_noalloc_capacity",
     "sem_rbc_create", "sem_bdf_ext_step", "sem_rbc_fields", "sem_rbc_destroy",
@@ -125,6 +125,7 @@ def lib() -> ctypes.CDLL:
             "sem_mesh_create_box": ([ctypes.POINTER(sem_box_desc), _vp, ctypes.POINTER(_vp)], _i),
             "sem_mesh_destroy": ([_vp], _i),
             "sem_mesh_info_get": ([_vp, ctypes.POINTER(sem_mesh_info)], _i),
+            "sem_mesh_set_deterministic": ([_vp, _i], _i),
             "sem_mesh_copy_maps": ([_vp, _vp, _vp], _i),
             "sem_mesh_copy_gs_tables": ([_vp, _vp, _vp], _i),
             "sem_ax_apply": ([_vp, _d, _d, _vp, _vp, _i, _vp], _i),
@@ -304,11 +305,19 @@ def box_desc(nel, N=7, L=(1.0, 1.0, 1.0), periodic=(0, 0, 0), dirichlet=(1, 1, 1
 
 
 def sem_mesh_create_box(nel, N=7, L=(1.0, 1.0, 1.0), periodic=(0, 0, 0), dirichlet=(1, 1, 1, 1, 1, 1),
-                        z_stretch=0.0, deform_amp=0.0, kappa=None, phi=None, stream=None) -> Mesh:
+                        z_stretch=0.0, deform_amp=0.0, kappa=None, phi=None, stream=None,
+                        deterministic: bool = False) -> Mesh:
     d = box_desc(nel, N, L, periodic, dirichlet, z_stretch, deform_amp, kappa, phi)
     h = ctypes.c_void_p()
     _check(lib().sem_mesh_create_box(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
-    return Mesh(h)
+    m = Mesh(h)
+    if deterministic:
+        sem_mesh_set_deterministic(m, True)
+    return m
+
+
+def sem_mesh_set_deterministic(mesh: Mesh, on: bool = True):
+    _check(lib().sem_mesh_set_deterministic(mesh.handle, int(bool(on))))
 
 
 def sem_partition_info(desc: sem_box_desc, nranks: int, rank: int):

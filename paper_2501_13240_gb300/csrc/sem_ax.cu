@@ -29,7 +29,7 @@ template <int NP, bool ASSEMBLED>
 __global__ void __launch_bounds__(AxCfg<NP>::THREADS)
     k_ax_fp64(int64_t E, const double *__restrict__ Dg, const double *__restrict__ G, const double *__restrict__ B,
               double h1, double h2, const double *__restrict__ u, double *__restrict__ w,
-              const int32_t *__restrict__ l2gm, double *__restrict__ pw_partial) {
+              const int32_t *__restrict__ l2gm, double *__restrict__ pw_partial, double *__restrict__ wloc) {
   using C = AxCfg<NP>;
   extern __shared__ double smem[];
   double *sD = smem;  // [NP][NP+1]
@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(AxCfg<NP>::THREADS)
       if (act) {
         if (ASSEMBLED) {
           const int32_t g = l2gm[e * C::N3 + p];
-          if (g >= 0) atomicAdd(&w[g], val);
+          if (wloc) wloc[e * C::N3 + p] = (g >= 0) ? val : 0.0;
+          else if (g >= 0) atomicAdd(&w[g], val);
           pw = fma(ru[k], val, pw);
         } else {
           w[e * C::N3 + p] = val;
@@ -132,8 +133,10 @@ int launch_fp64(const sem_mesh *m, double h1, double h2, const double *u, double
   using C = AxCfg<NP>;
   auto kern = k_ax_fp64<NP, ASSEMBLED>;
   if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-  kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->dD, m->G, m->B, h1, h2, u, w, map, pw_partial);
+  double *wloc = ASSEMBLED ? (double *)m->det_w : nullptr;
+  kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->dD, m->G, m->B, h1, h2, u, w, map, pw_partial, wloc);
   SEM_LAUNCH_CHECK("k_ax_fp64");
+  if (wloc) return sem_launch_gather_add(m, wloc, w, st);
   return SEM_OK;
 }
 

@@ -156,7 +156,7 @@ template <int NP, bool ASSEMBLED, bool HELM>
 __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
     k_ax_df64(int64_t E, const float2 *__restrict__ Gdf, const float2 *__restrict__ Bdf, float2 h1, float2 h2,
               const double *__restrict__ u, double *__restrict__ w, const int32_t *__restrict__ l2gm,
-              double *__restrict__ pw_partial) {
+              double *__restrict__ pw_partial, double *__restrict__ wloc) {
   using C = DfCfg<NP>;
   extern __shared__ float2 sm2[];
   const int tid = threadIdx.x;
@@ -267,7 +267,8 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
         const double vd = df::to_f64(v.x, v.y);
         if (ASSEMBLED) {
           const int32_t g = l2gm[e * C::N3 + p];
-          if (g >= 0) atomicAdd(&w[g], vd);
+          if (wloc) wloc[e * C::N3 + p] = (g >= 0) ? vd : 0.0;
+          else if (g >= 0) atomicAdd(&w[g], vd);
           if (pw_partial) df::mac(pw, x[k].x, x[k].y, v.x, v.y);
         } else {
           w[e * C::N3 + p] = vd;
@@ -322,12 +323,13 @@ int launch_np(const sem_mesh *m, double h1, double h2, const double *u, double *
   if (int rc = df_grid<NP>(m, assembled, &grid)) return rc;
   const float2 h1d = split_host(h1), h2d = split_host(h2);
   const bool helm = !(h1 == 1.0 && h2 == 0.0);
+  double *wloc = assembled ? (double *)m->det_w : nullptr;
 #define LAUNCH(ASM, HLM)                                                                                    \
   do {                                                                                                      \
     auto kern = k_ax_df64<NP, ASM, HLM>;                                                                    \
     if (C::SMEM > 48 * 1024)                                                                                \
       SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));          \
-    kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->Gdf, m->Bdf, h1d, h2d, u, w, map, pw_partial);          \
+    kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->Gdf, m->Bdf, h1d, h2d, u, w, map, pw_partial, wloc);    \
   } while (0)
   if (assembled) {
     if (helm) LAUNCH(true, true);
@@ -338,6 +340,7 @@ int launch_np(const sem_mesh *m, double h1, double h2, const double *u, double *
   }
 #undef LAUNCH
   SEM_LAUNCH_CHECK("k_ax_df64");
+  if (wloc) return sem_launch_gather_add(m, wloc, w, st);
   return SEM_OK;
 }
 

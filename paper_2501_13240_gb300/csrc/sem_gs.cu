@@ -62,6 +62,31 @@ int sem_launch_gs(const sem_mesh *m, double *v, int apply_mask, cudaStream_t st)
   return SEM_OK;
 }
 
+namespace {
+template <typename T>
+__global__ void k_gather_add(int64_t nU, const int32_t *__restrict__ off, const int32_t *__restrict__ perm,
+                             const T *__restrict__ wL, T *__restrict__ w) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = off[g], b = off[g + 1];
+    T s = T(0);
+    for (int32_t t = a; t < b; ++t) s += wL[perm[t]];
+    w[g] += s;
+  }
+}
+}  // namespace
+
+int sem_launch_gather_add(const sem_mesh *m, const double *wL, double *w, cudaStream_t st) {
+  k_gather_add<double><<<grid_for(m->n_unique, 256), 256, 0, st>>>(m->n_unique, m->gs_off, m->gs_perm, wL, w);
+  SEM_LAUNCH_CHECK("k_gather_add");
+  return SEM_OK;
+}
+
+int sem_launch_gather_add_f(const sem_mesh *m, const float *wL, float *w, cudaStream_t st) {
+  k_gather_add<float><<<grid_for(m->n_unique, 256), 256, 0, st>>>(m->n_unique, m->gs_off, m->gs_perm, wL, w);
+  SEM_LAUNCH_CHECK("k_gather_add");
+  return SEM_OK;
+}
+
 int sem_launch_gather(const sem_mesh *m, const double *vL, double *vg, cudaStream_t st) {
   k_gather<<<grid_for(m->n_unique, 256), 256, 0, st>>>(m->n_unique, m->gs_off, m->gs_perm, vL, vg);
   SEM_LAUNCH_CHECK("k_gather");

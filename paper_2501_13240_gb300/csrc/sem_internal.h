@@ -39,6 +39,10 @@ struct sem_mesh {
   int32_t *gs_perm = nullptr;  // [n_local]
   double *dD = nullptr;     // device copy of D (n*n)
   int device = 0;
+  // deterministic assembly: when set, assembled operators write element
+  // results here (n_local doubles, or floats for binary32 levels) and sum the
+  // copies of each unique node in ascending copy order instead of with atomics
+  void *det_w = nullptr;
 };
 
 // thread-local error reporting
@@ -74,6 +78,10 @@ int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u,
 int sem_launch_gs(const sem_mesh *m, double *v, int apply_mask, cudaStream_t st);
 int sem_launch_gather(const sem_mesh *m, const double *vL, double *vg, cudaStream_t st);
 int sem_launch_scatter(const sem_mesh *m, const double *vg, double *vL, cudaStream_t st);
+// w[g] += sum over the copies of g (ascending) of wL; the deterministic
+// replacement of atomic assembly
+int sem_launch_gather_add(const sem_mesh *m, const double *wL, double *w, cudaStream_t st);
+int sem_launch_gather_add_f(const sem_mesh *m, const float *wL, float *w, cudaStream_t st);
 int sem_launch_diag_local(const sem_mesh *m, double h1, double h2, double *dL, cudaStream_t st);
 
 int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,

@@ -78,7 +78,8 @@ __device__ __forceinline__ float ldg_real(const __nv_bfloat16 *p, int64_t i) { r
 template <int NP, typename GT>
 __global__ void __launch_bounds__(F32Cfg<NP>::THREADS, F32Cfg<NP>::MINB)
     k_ax32(int64_t E, const float *__restrict__ Df, const GT *__restrict__ G, const float *__restrict__ B, float h1,
-           float h2, const float *__restrict__ u, float *__restrict__ w, const int32_t *__restrict__ map) {
+           float h2, const float *__restrict__ u, float *__restrict__ w, const int32_t *__restrict__ map,
+           float *__restrict__ wloc) {
   using C = F32Cfg<NP>;
   extern __shared__ float smf[];
   float *sD = smf;
@@ -151,7 +152,11 @@ __global__ void __launch_bounds__(F32Cfg<NP>::THREADS, F32Cfg<NP>::MINB)
       }
       float val = h1 * acc;
       if (h2 != 0.0f && act) val = fmaf(h2 * B[e * C::N3 + p], s_u[p], val);
-      if (go[k] >= 0) atomicAdd(&w[go[k]], val);
+      if (wloc) {
+        if (act) wloc[e * C::N3 + p] = (go[k] >= 0) ? val : 0.0f;
+      } else if (go[k] >= 0) {
+        atomicAdd(&w[go[k]], val);
+      }
     }
     __syncthreads();
   }
@@ -161,16 +166,18 @@ template <int NP>
 int launch_ax32_np(const PmgLevel &lv, int gprec, float h1, float h2, const float *u, float *w, cudaStream_t st) {
   using C = F32Cfg<NP>;
   const unsigned grid = (unsigned)std::max<int64_t>((lv.m->E + C::ELB - 1) / C::ELB, 1);
+  float *wloc = (float *)lv.m->det_w;
   if (gprec == SEM_PREC_BF16) {
     auto kern = k_ax32<NP, __nv_bfloat16>;
     if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    kern<<<grid, C::THREADS, C::SMEM, st>>>(lv.m->E, lv.Df, lv.Gb, lv.Bf, h1, h2, u, w, lv.map);
+    kern<<<grid, C::THREADS, C::SMEM, st>>>(lv.m->E, lv.Df, lv.Gb, lv.Bf, h1, h2, u, w, lv.map, wloc);
   } else {
     auto kern = k_ax32<NP, float>;
     if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    kern<<<grid, C::THREADS, C::SMEM, st>>>(lv.m->E, lv.Df, lv.Gf, lv.Bf, h1, h2, u, w, lv.map);
+    kern<<<grid, C::THREADS, C::SMEM, st>>>(lv.m->E, lv.Df, lv.Gf, lv.Bf, h1, h2, u, w, lv.map, wloc);
   }
   SEM_LAUNCH_CHECK("k_ax32");
+  if (wloc) return sem_launch_gather_add_f(lv.m, wloc, w, st);
   return SEM_OK;
 }
 
@@ -228,7 +235,7 @@ __global__ void k_prolong(int nf, int nc, int64_t E, const float *__restrict__ J
 // rf / multiplicity, summed into the coarse vector
 __global__ void k_restrict(int nf, int nc, int64_t E, const float *__restrict__ J, const int32_t *__restrict__ mapf,
                            const float *__restrict__ minvf, const float *__restrict__ rf,
-                           const int32_t *__restrict__ mapc, float *__restrict__ rc) {
+                           const int32_t *__restrict__ mapc, float *__restrict__ rc, float *__restrict__ wloc) {
   __shared__ float u1[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];  // [i][j][c]
   __shared__ float u2[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];  // [i][b][c]
   __shared__ float Js[SEM_MAXNP * SEM_MAXNP];
@@ -264,8 +271,10 @@ __global__ void k_restrict(int nf, int nc, int64_t E, const float *__restrict__ 
       for (int c = 0; c < nc; ++c) {
         float s = 0.0f;
         for (int ii = 0; ii < nf; ++ii) s = fmaf(Js[ii * nc + a], u2[(ii * nc + b) * nc + c], s);
-        const int32_t g = mapc[e * nc3 + a + nc * (b + nc * c)];
-        if (g >= 0) atomicAdd(&rc[g], s);
+        const int64_t lc = e * nc3 + a + nc * (b + nc * c);
+        const int32_t g = mapc[lc];
+        if (wloc) wloc[lc] = (g >= 0) ? s : 0.0f;
+        else if (g >= 0) atomicAdd(&rc[g], s);
       }
     }
   }
@@ -514,8 +523,11 @@ int restrict_to(sem_pmg *P, int l, const float *rf, float *rc, cudaStream_t st) 
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   SEM_CUDA(cudaMemsetAsync(rc, 0, sizeof(float) * c.m->n_unique, st));
   const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
-  k_restrict<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], f.map, f.minv, rf, c.map, rc);
+  float *wloc = (float *)c.m->det_w;
+  k_restrict<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], f.map, f.minv, rf, c.map, rc,
+                                                wloc);
   SEM_LAUNCH_CHECK("k_restrict");
+  if (wloc) return sem_launch_gather_add_f(c.m, wloc, rc, st);
   return SEM_OK;
 }
 
@@ -673,6 +685,7 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
       rc = sem_mesh_create_box(&d, stream, &lv.m);
       if (rc) break;
       lv.own = true;
+      if (m->det_w && (rc = sem_mesh_set_deterministic(lv.m, 1))) break;
     }
     lv.map = o->mask_mode ? lv.m->l2g : lv.m->l2gm;
     const int64_t nL = lv.m->n_local, nU = lv.m->n_unique;

@@ -454,8 +454,8 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
 // ---------------------------------------------------------------- checkpoints
 // The state after a step: u, u^{n-1}, T, T^{n-1}, p, W^{n-1} (U-vectors),
 // N_T^{n-1}, N_u^{n-1} (E-vectors) and the step counter; the rest is rebuilt
-// every step. Layout: 64-byte header (step, n_unique, n_local) then the
-// arrays in that order.
+// every step. Layout: 64-byte header of eight int64 (step, n_unique, n_local,
+// E, N, format version, the bits of dt, 0) then the arrays in that order.
 namespace {
 
 struct StateLayout {
@@ -474,6 +474,22 @@ StateLayout layout(const sem_rbc *s) {
   return L;
 }
 
+constexpr int64_t kStateVersion = 1;
+
+void make_header(const sem_rbc *s, int64_t hdr[8]) {
+  int64_t dtbits;
+  memcpy(&dtbits, &s->prm.dt, sizeof(dtbits));
+  const int64_t h[8] = {s->step, s->nU, s->nL, s->m->E, s->m->N, kStateVersion, dtbits, 0};
+  memcpy(hdr, h, sizeof(h));
+}
+
+// a header fits this state if everything but the step counter matches
+bool header_fits(const sem_rbc *s, const int64_t hdr[8]) {
+  int64_t mine[8];
+  make_header(s, mine);
+  return hdr[0] >= 0 && hdr[0] <= INT32_MAX && memcmp(hdr + 1, mine + 1, 7 * sizeof(int64_t)) == 0;
+}
+
 uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t h) {
   for (size_t t = 0; t < n; ++t) h = (h ^ p[t]) * 1099511628211ull;
   return h;
@@ -490,7 +506,8 @@ extern "C" int sem_rbc_state_bytes(const sem_rbc *s, size_t *bytes) {
 extern "C" int sem_rbc_save_state(const sem_rbc *s, void *dev_buf, void *stream) {
   if (!s || !dev_buf) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_save_state: NULL argument");
   cudaStream_t st = as_stream(stream);
-  int64_t hdr[8] = {s->step, s->nU, s->nL, 0, 0, 0, 0, 0};
+  int64_t hdr[8];
+  make_header(s, hdr);
   SEM_CUDA(cudaMemcpyAsync(dev_buf, hdr, sizeof(hdr), cudaMemcpyHostToDevice, st));
   size_t off = 64;
   for (auto &a : layout(s).arrays) {
@@ -507,8 +524,8 @@ extern "C" int sem_rbc_load_state(sem_rbc *s, const void *dev_buf, void *stream)
   int64_t hdr[8];
   SEM_CUDA(cudaMemcpyAsync(hdr, dev_buf, sizeof(hdr), cudaMemcpyDeviceToHost, st));
   SEM_CUDA(cudaStreamSynchronize(st));
-  if (hdr[1] != s->nU || hdr[2] != s->nL || hdr[0] < 0)
-    return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_load_state: the snapshot belongs to another mesh");
+  if (!header_fits(s, hdr))
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_load_state: the snapshot belongs to another mesh, dt or format");
   size_t off = 64;
   for (auto &a : layout(s).arrays) {
     SEM_CUDA(cudaMemcpyAsync(a.first, (const char *)dev_buf + off, sizeof(double) * a.second,
@@ -527,7 +544,8 @@ extern "C" int sem_rbc_save(const sem_rbc *s, const char *path) {
   const StateLayout L = layout(s);
   std::vector<unsigned char> buf(8 + L.bytes);
   memcpy(buf.data(), "SEMRBC01", 8);
-  int64_t hdr[8] = {s->step, s->nU, s->nL, 0, 0, 0, 0, 0};
+  int64_t hdr[8];
+  make_header(s, hdr);
   memcpy(buf.data() + 8, hdr, 64);
   size_t off = 8 + 64;
   for (auto &a : L.arrays) {
@@ -556,7 +574,7 @@ extern "C" int sem_rbc_load(sem_rbc *s, const char *path) {
   if (fnv1a(buf.data(), buf.size(), 1469598103934665603ull) != h) return sem_fail(SEM_ERR_IO, "sem_rbc_load: checksum mismatch");
   int64_t hdr[8];
   memcpy(hdr, buf.data() + 8, 64);
-  if (hdr[1] != s->nU || hdr[2] != s->nL) return sem_fail(SEM_ERR_IO, "sem_rbc_load: checkpoint of another mesh");
+  if (!header_fits(s, hdr)) return sem_fail(SEM_ERR_IO, "sem_rbc_load: checkpoint of another mesh, dt or format");
   size_t off = 8 + 64;
   for (auto &a : L.arrays) {
     SEM_CUDA(cudaMemcpy(a.first, buf.data() + off, sizeof(double) * a.second, cudaMemcpyHostToDevice));

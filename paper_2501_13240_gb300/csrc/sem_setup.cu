@@ -339,7 +339,8 @@ __global__ void k_sort_segments(int64_t nU, const int32_t *off, int32_t *perm, d
 // ---------------------------------------------------------------- host
 static void free_mesh(sem_mesh *m) {
   if (!m) return;
-  void *ptrs[] = {m->X, m->Y, m->Z, m->G, m->Gdf, m->B, m->Bdf, m->l2g, m->l2gm, m->mask, m->mult, m->gs_off, m->gs_perm, m->dD};
+  void *ptrs[] = {m->X,    m->Y,    m->Z,      m->G,      m->Gdf,  m->B,     m->Bdf, m->l2g,
+                  m->l2gm, m->mask, m->mult,   m->gs_off, m->gs_perm, m->dD, m->det_w};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete m;
@@ -512,6 +513,22 @@ extern "C" int sem_mesh_create_box(const sem_box_desc *d, void *stream, sem_mesh
 
 extern "C" int sem_mesh_destroy(sem_mesh *m) {
   free_mesh(m);
+  return SEM_OK;
+}
+
+extern "C" int sem_mesh_set_deterministic(sem_mesh *m, int on) {
+  if (!m) return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_set_deterministic: NULL mesh");
+  if (on && !m->det_w) {
+    cudaError_t e = cudaMalloc(&m->det_w, sizeof(double) * (size_t)std::max<int64_t>(m->n_local, 1));
+    if (e != cudaSuccess) {
+      m->det_w = nullptr;
+      return sem_cuda_fail(e, "sem_mesh_set_deterministic: cudaMalloc");
+    }
+  } else if (!on && m->det_w) {
+    SEM_CUDA(cudaDeviceSynchronize());  // no launch in flight may still use the scratch
+    cudaFree(m->det_w);
+    m->det_w = nullptr;
+  }
   return SEM_OK;
 }
 
