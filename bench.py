@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-pcg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rbc", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--quick-pcg", action="store_true", help="skip the slow binary64 Jacobi-PCG reference solve")
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"])
@@ -393,6 +394,50 @@ def main():
         rs.destroy()
         rm.destroy()
 
+    # --- adjoint: gradient of the bottom-plate Nusselt number after K = 20
+    # steps with respect to T^0 (16^3 elements, N = 7, Ra = 1e7, Pr = 1),
+    # velocity history checkpointed every 5 steps; deterministic assembly so
+    # that replayed segments equal the original run bit for bit
+    adj = None
+    if not args.no_adjoint:
+        from paper_2501_13240_gb300 import adjoint as gadj
+        aw = workloads.ADJOINT_16
+        am = sem.mesh_from_workload(aw, deterministic=True)
+        Ra, Pr, dt, K = 1e7, 1.0, 2e-3, 20
+        pert = torch.from_numpy(workloads.perturbation(am.n_unique, 1e-2, seed=2)).cuda()
+        rs = sem.sem_rbc_create(am, Ra, Pr, dt, tol=1e-10, precision=sem.SEM_PREC_DF64, T_pert=pert)
+        T0 = sem.sem_rbc_fields(rs)["T"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist = gadj.VelocityHistory(rs, K, 5)
+        torch.cuda.synchronize()
+        run_ms = 1e3 * (time.perf_counter() - t0)
+        ta = sem.sem_tadv_create(am, 1.0 / np.sqrt(Ra * Pr), dt, tol=1e-13, precision=sem.SEM_PREC_DF64)
+        x = T0.clone().requires_grad_(True)
+        t0 = time.perf_counter()
+        nu = gadj.nusselt_after(x, hist, ta)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        nu.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        mask = torch.from_numpy(am.maps()[1].astype(np.float64)).cuda()
+        rng = np.random.default_rng(31)
+        fd_err = []
+        for _ in range(2):
+            d = torch.from_numpy(rng.standard_normal(am.n_unique)).cuda() * mask
+            fp = float(gadj.nusselt_after(T0 + 1e-6 * d, hist, ta))
+            fm = float(gadj.nusselt_after(T0 - 1e-6 * d, hist, ta))
+            fd = (fp - fm) / 2e-6
+            fd_err.append(abs(fd - float(torch.dot(x.grad, d))) / abs(fd))
+        adj = {"workload": aw.name, "K": K, "checkpoint_every": 5, "Nu_b": float(nu.detach()),
+               "rbc_run_ms": run_ms, "forward_ms": 1e3 * (t1 - t0), "backward_ms": 1e3 * (t2 - t1),
+               "rbc_steps_replayed": hist.n_replayed, "fd_rel_err_2_directions": fd_err}
+        del hist, x, T0
+        ta.destroy()
+        rs.destroy()
+        am.destroy()
+
     # --- CPU oracle baseline on rank 0
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
@@ -409,7 +454,8 @@ def main():
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clocks,
-            "extra": {"precision": head, "per_precision": per, "solves": pcg, "rbc_step": rbc},
+            "extra": {"precision": head, "per_precision": per, "solves": pcg, "rbc_step": rbc,
+                      "adjoint": adj},
         }
         print(json.dumps(line))
     mesh.destroy()

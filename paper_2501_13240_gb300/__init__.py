@@ -337,12 +337,12 @@ def sem_partition_interface(desc: sem_box_desc, nranks: int, rank: int):
     return g[:n], c[:n]
 
 
-def mesh_from_workload(w, stream=None) -> Mesh:
+def mesh_from_workload(w, stream=None, deterministic: bool = False) -> Mesh:
     """Mesh of a ``workloads.BoxWorkload`` (sizes and seeded deformation)."""
     from workloads import deformation_params
     kappa, phi = deformation_params(w.deform_seed)
     return sem_mesh_create_box(w.nel, w.N, w.L, w.periodic, w.dirichlet, w.z_stretch, w.deform_amp, kappa, phi,
-                               stream)
+                               stream, deterministic=deterministic)
 
 
 def sem_ax_apply(mesh: Mesh, h1: float, h2: float, u_L, w_L, precision: int = SEM_PREC_FP64, stream=None):
