@@ -199,11 +199,11 @@ def run_once(sem, mesh, u, names):
             sem.sem_gs_op(mesh, wL, True)
         elif kind == "vcycle":
             sp = {"fp32": sem.SEM_PREC_FP32, "bf16": sem.SEM_PREC_BF16}[prec]
-            P = sem.sem_pmg_create(mesh, orders=(mesh.N, 3, 1), smoother_precision=sp, coarse_tol=1e-2)
+            H = sem.sem_pmg_create(mesh, orders=(mesh.N, 3, 1), smoother_precision=sp, coarse_tol=1e-2)
             z = torch.empty_like(u)
-            sem.sem_pmg_vcycle(P, u, z)
+            sem.sem_pmg_vcycle(H, u, z)
             torch.cuda.synchronize()
-            P.destroy()
+            H.destroy()
         else:
             raise ValueError(name)
     torch.cuda.synchronize()

@@ -17,11 +17,13 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "sem_df64.cuh"
 #include "sem_internal.h"
+#include "sem_tma.cuh"
 
 namespace {
 
@@ -37,6 +39,8 @@ struct PmgLevel {
   float *minv = nullptr;  // 1 / multiplicity
   float lam = 0.0f;
   float *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *t = nullptr;
+  int *err = nullptr;  // set by a kernel whose shared-memory copies did not land (then the persistent
+                       // TMA operator is used; NULL selects the plain operator)
 };
 
 constexpr int kPart = 152 * 2;
@@ -52,6 +56,7 @@ struct sem_pmg {
   void *cws = nullptr;
   double *r = nullptr, *z = nullptr, *zn = nullptr, *p = nullptr, *w = nullptr;  // outer FCG
   double *part = nullptr, *pw_part = nullptr;
+  int *err = nullptr;  // device flag of the persistent operator (a bulk copy that never landed)
   std::vector<void *> owned;
 };
 
@@ -70,6 +75,9 @@ struct F32Cfg {
 
 __device__ __forceinline__ float ldg_real(const float *p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float ldg_real(const __nv_bfloat16 *p, int64_t i) { return __bfloat162float(p[i]); }
+// plain (generic) loads, for values staged in shared memory
+__device__ __forceinline__ float lds_real(const float *p, int i) { return p[i]; }
+__device__ __forceinline__ float lds_real(const __nv_bfloat16 *p, int i) { return __bfloat162float(p[i]); }
 
 // w[g] += h1 (A u)[g] + h2 (B u)[g] through map (-1 = skip), binary32. The
 // kernel is bound by memory: the u column and the t-direction flux stay in
@@ -162,9 +170,264 @@ __global__ void __launch_bounds__(F32Cfg<NP>::THREADS, F32Cfg<NP>::MINB)
   }
 }
 
+// Persistent form for even NP: each CTA walks element groups with a stride of
+// the grid, as a three-stage pipeline. The group's geometric factors and
+// gather indices (contiguous per element) come into shared memory by bulk
+// asynchronous copies (TMA) two groups ahead, in a ring of three buffers with
+// one mbarrier each; the gathered u values of the next group are copied into
+// shared memory by per-thread asynchronous copies one group ahead. Neither the
+// geometry stream nor the gather latency is then exposed to the arithmetic.
+// Each thread keeps its rows of D and D^T in registers, takes the t-direction
+// coefficients from constant memory (compile-time indices) and keeps its
+// t-column of u and of the t-flux in registers; r-lines are read with vector
+// loads. Dynamic shared memory: barriers | G[3][ELB][6][N3] |
+// map[3][ELB][N3] | u[2][ELB][N3] | r, s fluxes [ELB][2][N3].
+template <int NP, typename GT>
+struct TmaCfg {
+  static constexpr int N2 = NP * NP;
+  static constexpr int N3 = NP * NP * NP;
+  static constexpr int ELB = (N2 >= 64) ? 1 : 64 / N2;
+  static constexpr int THREADS = N2 * ELB;
+  static constexpr int STAGES = 3;
+  static constexpr int GELEM = 6 * N3 * (int)sizeof(GT);  // bytes of G per element
+  static constexpr int MELEM = N3 * 4;                     // bytes of map per element
+  static constexpr int OFF_G = 128;
+  static constexpr int OFF_M = OFF_G + STAGES * ELB * GELEM;
+  static constexpr int OFF_U = OFF_M + STAGES * ELB * MELEM;
+  static constexpr int OFF_T = OFF_U + 2 * ELB * N3 * 4;
+  static constexpr int SMEM = OFF_T + 2 * ELB * N3 * 4;
+  static_assert(GELEM % 16 == 0 && MELEM % 16 == 0, "bulk copies need 16-byte multiples");
+};
+
+// binary32 derivative matrices D (row-major) for NP = 2 .. SEM_MAXNP in
+// constant memory: with compile-time indices they are instruction operands
+__host__ __device__ constexpr int d32_off(int np) { return np <= 2 ? 0 : d32_off(np - 1) + (np - 1) * (np - 1); }
+__constant__ float c_D32[d32_off(SEM_MAXNP + 1)];
+std::mutex g_d32_mu;
+unsigned g_d32_ready = 0;  // bit per device
+
+int ensure_d32(int device) {
+  std::lock_guard<std::mutex> lk(g_d32_mu);
+  if (device < 32 && (g_d32_ready >> device) & 1u) return SEM_OK;
+  std::vector<float> tab(d32_off(SEM_MAXNP + 1));
+  for (int np = 2; np <= SEM_MAXNP; ++np) {
+    double xi[SEM_MAXNP], rho[SEM_MAXNP], D[SEM_MAXNP * SEM_MAXNP];
+    if (int rc = sem_gll_host(np - 1, xi, rho, D)) return rc;
+    for (int t = 0; t < np * np; ++t) tab[d32_off(np) + t] = (float)D[t];
+  }
+  SEM_CUDA(cudaMemcpyToSymbol(c_D32, tab.data(), sizeof(float) * tab.size()));
+  if (device < 32) g_d32_ready |= 1u << device;
+  return SEM_OK;
+}
+
+// a contiguous line of NP floats from shared memory (vector loads; NP even)
+template <int NP>
+__device__ __forceinline__ void load_line(const float *p, float (&v)[NP]) {
+  if constexpr (NP % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < NP / 4; ++q) {
+      const float4 t = reinterpret_cast<const float4 *>(p)[q];
+      v[4 * q] = t.x;
+      v[4 * q + 1] = t.y;
+      v[4 * q + 2] = t.z;
+      v[4 * q + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NP / 2; ++q) {
+      const float2 t = reinterpret_cast<const float2 *>(p)[q];
+      v[2 * q] = t.x;
+      v[2 * q + 1] = t.y;
+    }
+  }
+}
+
+// 4-byte asynchronous global -> shared copy, zero-filled when !valid
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+  const unsigned sa = tma::smem_u32(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int NP, typename GT>
+__global__ void __launch_bounds__(TmaCfg<NP, GT>::THREADS)
+    k_ax32_tma(int64_t E, const float *__restrict__ Df, const GT *__restrict__ G, const float *__restrict__ B,
+               float h1, float h2, const float *__restrict__ u, float *__restrict__ w,
+               const int32_t *__restrict__ map, float *__restrict__ wloc, int *__restrict__ err) {
+  using C = TmaCfg<NP, GT>;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);
+  GT *Gs = reinterpret_cast<GT *>(smraw + C::OFF_G);
+  int32_t *Ms = reinterpret_cast<int32_t *>(smraw + C::OFF_M);
+  float *Us = reinterpret_cast<float *>(smraw + C::OFF_U);
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x;
+  const int le = tid / C::N2;
+  const int ij = tid - le * C::N2;
+  const int i = ij % NP, j = ij / NP;
+  float *s_r = reinterpret_cast<float *>(smraw + C::OFF_T) + le * 2 * C::N3;
+  float *s_s = s_r + C::N3;
+  const float *cD = c_D32 + d32_off(NP);
+  float Dr[NP], Ds[NP], DrT[NP], DsT[NP];  // D[i][m], D[j][m], D[m][i], D[m][j]
+#pragma unroll
+  for (int m = 0; m < NP; ++m) {
+    Dr[m] = cD[i * NP + m];
+    Ds[m] = cD[j * NP + m];
+    DrT[m] = cD[m * NP + i];
+    DsT[m] = cD[m * NP + j];
+  }
+  const int64_t ngroups = (E + C::ELB - 1) / C::ELB;
+  const int64_t gstride = gridDim.x;
+  if (tid == 0) {
+    for (int b = 0; b < C::STAGES; ++b) tma::mbar_init(&bar[b], 1);
+    tma::fence_mbar_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  // thread 0: group g into ring slot b
+  auto issue = [&](int64_t g, int b) {
+    const int64_t e0 = g * C::ELB;
+    const unsigned ne = (unsigned)((E - e0) < C::ELB ? (E - e0) : C::ELB);
+    tma::mbar_arrive_expect_tx(&bar[b], ne * (unsigned)(C::GELEM + C::MELEM));
+    tma::bulk_g2s(Gs + (size_t)b * C::ELB * 6 * C::N3, G + e0 * 6 * C::N3, ne * C::GELEM, &bar[b]);
+    tma::bulk_g2s(Ms + (size_t)b * C::ELB * C::N3, map + e0 * C::N3, ne * C::MELEM, &bar[b]);
+  };
+  // every thread: asynchronous gather of its column of group g (map in slot b) into u buffer ub
+  auto gather = [&](int64_t g, int b, int ub, bool ok) {
+    const int64_t e = g * C::ELB + le;
+    const bool act = ok && e < E;
+    const int32_t *Me = Ms + (size_t)b * C::ELB * C::N3 + le * C::N3;
+    float *Ue = Us + (size_t)ub * C::ELB * C::N3 + le * C::N3;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int p = ij + C::N2 * k;
+      const int32_t gk = act ? Me[p] : -1;
+      cp_async4(Ue + p, gk >= 0 ? u + gk : u, gk >= 0);
+    }
+  };
+  // the wait for group number q (q-th group of this CTA) uses slot q % 3, phase (q / 3) & 1
+  auto wait_group = [&](int q) { return tma::mbar_wait(&bar[q % 3], (unsigned)(q / 3) & 1u, tma::kWaitLimit); };
+
+  const int64_t g0 = blockIdx.x;
+  int issued = 0;  // groups issued so far (thread 0's count; the same on every thread by construction)
+  if (tid == 0) {
+    if (g0 < ngroups) issue(g0, 0);
+    if (g0 + gstride < ngroups) issue(g0 + gstride, 1);
+  }
+  issued = (g0 < ngroups) + (g0 + gstride < ngroups);
+  if (g0 < ngroups) {
+    const bool ok = wait_group(0);
+    if (!ok) abort_flag = 1;
+    gather(g0, 0, 0, ok);
+  }
+  cp_async_commit();
+  int q = 0;
+  for (int64_t g = g0; g < ngroups; g += gstride, ++q) {
+    const int b = q % 3;
+    const int64_t gn = g + gstride, gnn = g + 2 * gstride;
+    if (gnn < ngroups) {  // slot (q + 2) % 3 was released by the previous iteration's final barrier
+      if (tid == 0) {
+        tma::fence_proxy_async();
+        issue(gnn, (q + 2) % 3);
+      }
+      ++issued;
+    }
+    if (gn < ngroups) {
+      const bool ok = wait_group(q + 1);
+      if (!ok) abort_flag = 1;
+      gather(gn, (q + 1) % 3, (q + 1) & 1, ok);
+    }
+    cp_async_commit();
+    cp_async_wait_prev();  // this thread's gathers of group g have landed
+    __syncthreads();
+    if (abort_flag) break;
+    const int64_t e = g * C::ELB + le;
+    const GT *Ge = Gs + (size_t)b * C::ELB * 6 * C::N3 + le * 6 * C::N3;
+    const int32_t *Me = Ms + (size_t)b * C::ELB * C::N3 + le * C::N3;
+    const float *s_u = Us + (size_t)(q & 1) * C::ELB * C::N3 + le * C::N3;
+    float ucol[NP], tt[NP];  // this thread's t-column of u, then of the t-flux
+#pragma unroll
+    for (int m = 0; m < NP; ++m) ucol[m] = s_u[ij + C::N2 * m];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int p = ij + C::N2 * k;
+      const float g00 = lds_real(Ge, p), g01 = lds_real(Ge, C::N3 + p), g02 = lds_real(Ge, 2 * C::N3 + p),
+                  g11 = lds_real(Ge, 3 * C::N3 + p), g12 = lds_real(Ge, 4 * C::N3 + p),
+                  g22 = lds_real(Ge, 5 * C::N3 + p);
+      float rl[NP];
+      load_line<NP>(s_u + NP * j + C::N2 * k, rl);
+      float ur = 0.0f, us = 0.0f, ut = 0.0f;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        ur = fmaf(Dr[m], rl[m], ur);
+        us = fmaf(Ds[m], s_u[i + NP * m + C::N2 * k], us);
+        ut = fmaf(cD[k * NP + m], ucol[m], ut);
+      }
+      s_r[p] = g00 * ur + g01 * us + g02 * ut;
+      s_s[p] = g01 * ur + g11 * us + g12 * ut;
+      tt[k] = g02 * ur + g12 * us + g22 * ut;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int p = ij + C::N2 * k;
+      float rl[NP];
+      load_line<NP>(s_r + NP * j + C::N2 * k, rl);
+      float acc = 0.0f;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        acc = fmaf(DrT[m], rl[m], acc);
+        acc = fmaf(DsT[m], s_s[i + NP * m + C::N2 * k], acc);
+        acc = fmaf(cD[m * NP + k], tt[m], acc);
+      }
+      float val = h1 * acc;
+      if (h2 != 0.0f && e < E) val = fmaf(h2 * B[e * C::N3 + p], s_u[p], val);
+      const int32_t gk = (e < E) ? Me[p] : -1;
+      if (wloc) {
+        if (e < E) wloc[e * C::N3 + p] = (gk >= 0) ? val : 0.0f;
+      } else if (gk >= 0) {
+        atomicAdd(&w[gk], val);
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait_all();
+  if (abort_flag && tid == 0) {  // let the bulk copies still in flight land before the CTA exits
+    for (int t = q; t < issued; ++t) wait_group(t);
+    atomicExch(err, 1);
+  }
+}
+
+template <int NP, typename GT>
+int launch_ax32_tma(const PmgLevel &lv, const GT *Gp, float h1, float h2, const float *u, float *w, int *err,
+                    cudaStream_t st) {
+  using C = TmaCfg<NP, GT>;
+  if (int rc = ensure_d32(lv.m->device)) return rc;
+  auto kern = k_ax32_tma<NP, GT>;
+  if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  int per_sm = 0, nsm = 0;
+  SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS, C::SMEM));
+  SEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, lv.m->device));
+  const int64_t ngroups = (lv.m->E + C::ELB - 1) / C::ELB;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)std::max(per_sm, 1) * nsm));
+  kern<<<grid, C::THREADS, C::SMEM, st>>>(lv.m->E, lv.Df, Gp, lv.Bf, h1, h2, u, w, lv.map, (float *)lv.m->det_w,
+                                           err);
+  SEM_LAUNCH_CHECK("k_ax32_tma");
+  if (lv.m->det_w) return sem_launch_gather_add_f(lv.m, (const float *)lv.m->det_w, w, st);
+  return SEM_OK;
+}
+
 template <int NP>
 int launch_ax32_np(const PmgLevel &lv, int gprec, float h1, float h2, const float *u, float *w, cudaStream_t st) {
   using C = F32Cfg<NP>;
+  if constexpr (NP % 2 == 0 && NP >= 4) {
+    if (lv.err) {
+      if (gprec == SEM_PREC_BF16) return launch_ax32_tma<NP, __nv_bfloat16>(lv, lv.Gb, h1, h2, u, w, lv.err, st);
+      return launch_ax32_tma<NP, float>(lv, lv.Gf, h1, h2, u, w, lv.err, st);
+    }
+  }
   const unsigned grid = (unsigned)std::max<int64_t>((lv.m->E + C::ELB - 1) / C::ELB, 1);
   float *wloc = (float *)lv.m->det_w;
   if (gprec == SEM_PREC_BF16) {
@@ -645,6 +908,20 @@ void free_pmg(sem_pmg *P) {
 
 }  // namespace
 
+namespace {
+// read and clear the persistent operator's error flag (synchronises the stream)
+int check_err(sem_pmg *P, cudaStream_t st) {
+  int h = 0;
+  SEM_CUDA(cudaMemcpyAsync(&h, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SEM_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    cudaMemsetAsync(P->err, 0, sizeof(int), st);
+    return sem_fail(SEM_ERR_CUDA, "pmg: a bulk shared-memory copy did not complete within its wait limit");
+  }
+  return SEM_OK;
+}
+}  // namespace
+
 extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem_pmg_opts *o, void *stream,
                               sem_pmg **out) {
   if (!m || !o || !out) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: NULL argument");
@@ -705,10 +982,13 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
     rc = rc ? rc : alloc((void **)&lv.x, sizeof(float) * nU);
   }
   if (!rc) rc = alloc((void **)&P->part, sizeof(double) * 2 * kPart);
+  if (!rc) rc = alloc((void **)&P->err, sizeof(int));
   if (rc) {
     free_pmg(P);
     return rc;
   }
+  cudaMemsetAsync(P->err, 0, sizeof(int), st);
+  for (int l = 0; l + 1 < o->nlevels; ++l) P->L[l].err = P->err;
   // per-level binary32 data
   for (int l = 0; l + 1 < o->nlevels && !rc; ++l) {
     PmgLevel &lv = P->L[l];
@@ -752,6 +1032,7 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
   cudaError_t e = cudaGetLastError();
   if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (!rc && e != cudaSuccess) rc = sem_cuda_fail(e, "sem_pmg_create");
+  if (!rc) rc = check_err(P, st);
   if (rc) {
     free_pmg(P);
     return rc;
@@ -781,7 +1062,7 @@ extern "C" int sem_pmg_vcycle(sem_pmg *P, const double *r_g, double *z_g, void *
   if (int rc = vcycle(P, 0, st)) return rc;
   k_f2d<<<grid_for(n, 256), 256, 0, st>>>(n, lv.x, z_g);
   SEM_LAUNCH_CHECK("sem_pmg_vcycle");
-  return SEM_OK;
+  return check_err(P, st);
 }
 
 extern "C" int sem_pmg_prolong(sem_pmg *P, int level, const double *uc_g, double *uf_g, void *stream) {
