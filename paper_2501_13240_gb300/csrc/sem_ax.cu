@@ -206,10 +206,14 @@ int sem_launch_ax_local(const sem_mesh *m, double h1, double h2, const double *u
 
 int sem_launch_ax_assembled(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
                             double *pw_partial, int precision, cudaStream_t st, const int32_t *map) {
+  if (m->N == 1 && m->K1) return sem_launch_ax_n1(m, h1, h2, u_g, w_g, pw_partial, precision, st, map ? map : m->l2gm);
   return dispatch(m, h1, h2, u_g, w_g, pw_partial, true, precision, st, map ? map : m->l2gm);
 }
 
 int sem_ax_assembled_blocks(const sem_mesh *m, int precision) {
+  // element-matrix operator of N = 1 meshes: one element per thread, 128
+  // threads per CTA, at most 8 CTAs per SM (fewer p.w partials to sum)
+  if (m->N == 1 && m->K1) return (int)std::max<int64_t>(1, std::min<int64_t>((m->E + 127) / 128, 152 * 8));
   if (precision == SEM_PREC_DF64) return sem_df64_grid(m);
   switch (m->n) {
 #define CASE(NPV) \

@@ -43,6 +43,10 @@ struct sem_mesh {
   // results here (n_local doubles, or floats for binary32 levels) and sum the
   // copies of each unique node in ascending copy order instead of with atomics
   void *det_w = nullptr;
+  // N = 1 only: element stiffness matrices (upper triangle, [36][E]) in
+  // binary64 and double-float
+  double *K1 = nullptr;
+  float2 *K1df = nullptr;
 };
 
 // thread-local error reporting
@@ -81,6 +85,10 @@ int sem_launch_scatter(const sem_mesh *m, const double *vg, double *vL, cudaStre
 // w[g] += sum over the copies of g (ascending) of wL; the deterministic
 // replacement of atomic assembly
 int sem_launch_gather_add(const sem_mesh *m, const double *wL, double *w, cudaStream_t st);
+// N = 1 meshes: element matrices (set-up) and the assembled operator from them
+int sem_n1_prepare(sem_mesh *m, cudaStream_t st);
+int sem_launch_ax_n1(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g, double *pw_partial,
+                     int precision, cudaStream_t st, const int32_t *map);
 int sem_launch_gather_add_f(const sem_mesh *m, const float *wL, float *w, cudaStream_t st);
 int sem_launch_diag_local(const sem_mesh *m, double h1, double h2, double *dL, cudaStream_t st);
 

@@ -627,17 +627,25 @@ __global__ void k_alt(int64_t n, int64_t nx, int64_t ny, const uint8_t *__restri
   }
 }
 
-// w = dinv * w (in place), partial sums of w.w and v.v in binary64
+// y = a x
+__global__ void k_copy_scale_f(int64_t n, float a, const float *__restrict__ x, float *__restrict__ y) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    y[g] = a * x[g];
+}
+
+// w = dinv * w (in place), partial sums of w.w and v.v (binary32 per thread,
+// binary64 across threads: an eigenvalue estimate needs no more)
 __global__ void k_power_step(int64_t n, const float *__restrict__ dinv, float *__restrict__ w,
                              const float *__restrict__ v, double *__restrict__ part) {
   __shared__ double red[2][32];
-  double ww = 0.0, vv = 0.0;
+  float wwf = 0.0f, vvf = 0.0f;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const float x = dinv[g] * w[g];
     w[g] = x;
-    ww += (double)x * (double)x;
-    vv += (double)v[g] * (double)v[g];
+    wwf = fmaf(x, x, wwf);
+    vvf = fmaf(v[g], v[g], vvf);
   }
+  double ww = wwf, vv = vvf;
   for (int off = 16; off > 0; off >>= 1) {
     ww += __shfl_xor_sync(0xffffffffu, ww, off);
     vv += __shfl_xor_sync(0xffffffffu, vv, off);
@@ -658,10 +666,6 @@ __global__ void k_power_step(int64_t n, const float *__restrict__ dinv, float *_
   }
 }
 
-__global__ void k_scale_f(int64_t n, float a, float *__restrict__ x) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    x[g] *= a;
-}
 
 // partial sums of (a.b, c.d) in binary64; c may be null
 __global__ void k_dots(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
@@ -891,8 +895,7 @@ int power_lambda(sem_pmg *P, int l, cudaStream_t st) {
     if (int rc = sum_pairs(P->part, &ww, &vv, st)) return rc;
     if (!(ww > 0.0) || !(vv > 0.0)) return sem_fail(SEM_ERR_BREAKDOWN, "pmg: power iteration degenerated");
     lam = sqrt(ww / vv);
-    k_copy_f<<<grid_for(n, 256), 256, 0, st>>>(n, lv.t, lv.x);
-    k_scale_f<<<grid_for(n, 256), 256, 0, st>>>(n, (float)(1.0 / sqrt(ww)), lv.x);
+    k_copy_scale_f<<<grid_for(n, 256), 256, 0, st>>>(n, (float)(1.0 / sqrt(ww)), lv.t, lv.x);
   }
   lv.lam = (float)(P->o.lambda_safety * lam);
   return SEM_OK;

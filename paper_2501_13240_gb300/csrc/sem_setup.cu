@@ -340,7 +340,7 @@ __global__ void k_sort_segments(int64_t nU, const int32_t *off, int32_t *perm, d
 static void free_mesh(sem_mesh *m) {
   if (!m) return;
   void *ptrs[] = {m->X,    m->Y,    m->Z,      m->G,      m->Gdf,  m->B,     m->Bdf, m->l2g,
-                  m->l2gm, m->mask, m->mult,   m->gs_off, m->gs_perm, m->dD, m->det_w};
+                  m->l2gm, m->mask, m->mult,   m->gs_off, m->gs_perm, m->dD, m->det_w, m->K1, m->K1df};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete m;
@@ -503,9 +503,13 @@ extern "C" int sem_mesh_create_box(const sem_box_desc *d, void *stream, sem_mesh
     snprintf(buf, sizeof(buf), "sem_mesh_create_box: non-positive Jacobian (min det J = %g)", dmin);
     return sem_fail(SEM_ERR_INVALID_ARG, buf);
   }
-  if ((rc = build_gs_tables(m, st)) != SEM_OK) {
+  if ((rc = build_gs_tables(m, st)) != SEM_OK || (rc = sem_n1_prepare(m, st)) != SEM_OK) {
     free_mesh(m);
     return rc;
+  }
+  if (cudaError_t e2 = cudaStreamSynchronize(st)) {
+    free_mesh(m);
+    return sem_cuda_fail(e2, "sem_mesh_create_box: set-up");
   }
   *out = m;
   return SEM_OK;

@@ -44,6 +44,7 @@ MESHES = [
     dict(nel=(3, 2, 2), N=4, deform=0.05, L=(1.0, 2.0, 0.5)),
     dict(nel=(2, 3, 4), N=9, deform=0.04, periodic=(1, 1, 0), dirichlet=(0, 0, 0, 0, 1, 1), stretch=2.0),
     dict(nel=(1, 1, 1), N=1, deform=0.0),
+    dict(nel=(9, 7, 5), N=1, deform=0.05, periodic=(1, 0, 0), dirichlet=(0, 0, 1, 1, 1, 1)),  # element matrices
     dict(nel=(2, 2, 2), N=10, deform=0.05),
     dict(nel=(3, 3, 2), N=2, deform=0.05, periodic=(1, 0, 1), dirichlet=(0, 0, 1, 1, 0, 0)),
 ]
