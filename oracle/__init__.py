@@ -131,6 +131,7 @@ class Mesh:
     n_unique: int
     detJ_min: float
     L: tuple = (1.0, 1.0, 1.0)
+    z_stretch: float = 0.0
     _mult: Optional[np.ndarray] = field(default=None, repr=False)
 
     @property
@@ -188,7 +189,7 @@ def box_mesh(nel, N=7, L=(1.0, 1.0, 1.0), periodic=(0, 0, 0), dirichlet=(1, 1, 1
             raise ValueError(f"mesh has a non-positive Jacobian (min det J = {detmin})")
         G = G.reshape(6, nL)
     return Mesh(nel, N, tuple(periodic), tuple(dirichlet), xi, rho, D, X, Y, Z, G, B, l2g, mask, nU,
-                detmin, tuple(L))
+                detmin, tuple(L), float(z_stretch))
 
 
 def element_subset(w, elems):
