@@ -391,6 +391,23 @@ def main():
         steps = [sem.sem_bdf_ext_step(rs, raise_on_error=False) for _ in range(3)]
         rbc = {"workload": rw.name, "steps": steps, "ms_per_step_after_first": float(
             np.mean([s_["step_ms"] for s_ in steps[1:]]))}
+        # in-situ rendering of the temperature: bottom boundary-layer slice and a
+        # vertical slice, 4096 x 4096 pixels each, iso-levels 0.4 and 0.6
+        T = sem.sem_rbc_fields(rs)["T"]
+        render = {}
+        for name, axis, coord in (("bottom_bl_z0.01", 2, 0.01), ("vertical_y0.5", 1, 0.5)):
+            vals = torch.empty((4096, 4096), dtype=torch.float32, device="cuda")
+            rgba = torch.empty((4096, 4096, 4), dtype=torch.uint8, device="cuda")
+            for _ in range(2):
+                sem.sem_render_slice(rm, T, axis, coord, 4096, 4096, 0.0, 1.0, (0.4, 0.6), vals, rgba)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(5):
+                sem.sem_render_slice(rm, T, axis, coord, 4096, 4096, 0.0, 1.0, (0.4, 0.6), vals, rgba)
+            ms = 1e3 * (time.perf_counter() - t0) / 5
+            render[name] = {"ms": ms, "mpixel_per_s": 4096 * 4096 / (ms * 1e-3) / 1e6}
+            del vals, rgba
+        rbc["render_4096x4096"] = render
         rs.destroy()
         rm.destroy()
 

@@ -432,6 +432,41 @@ int sem_tadv_nusselt(sem_tadv *t, const double *T, double *nu, void *stream);
 int sem_tadv_nusselt_grad(sem_tadv *t, double scale, double *c, void *stream);
 
 /* ------------------------------------------------------------------------
+ * In-situ slice rendering (the paper's in-situ scenes, Sec. 5.3 and the
+ * figures of Sec. 4.5: temperature slices through the plate boundary layers
+ * and vertical slices with iso-levels, rendered from GPU-resident data; here
+ * as CUDA kernels into a caller-owned device image, no graphics API).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int axis;          /* plane normal: 0 (x = coord), 1 (y = coord), 2 (z = coord) */
+  double coord;      /* 0 <= coord <= L[axis], in the undeformed box (on a deformed mesh the
+                        plane of the reference lattice) */
+  int width, height; /* pixels along the two other axes in increasing order
+                        (axis 0: y, z; 1: x, z; 2: x, y); 1 .. 32768 each */
+  double vmin, vmax; /* colour-map range, vmax > vmin */
+  int n_iso;         /* 0 .. 8 contour levels */
+  double iso[8];
+} sem_slice_desc;
+
+/* Render the unique-node field u_g (device, n_unique doubles) on the slice.
+ * Pixel (px, py) is centred at ((px + 1/2) L_first / width, (py + 1/2)
+ * L_second / height); row 0 is the low end; both outputs are row-major
+ * [py][px], caller-owned device memory: values (width * height binary32, the
+ * SEM polynomial of the element containing the pixel centre: normal-direction
+ * sum in binary64, in-plane sum in binary32) and rgba (width * height * 4
+ * bytes: piecewise-linear cool-warm colour map of (v - vmin) / (vmax - vmin)
+ * clamped to [0, 1], blue (59, 76, 192) - grey (221, 221, 221) - red
+ * (180, 4, 38), each channel rounded half up; NaN magenta; black where the
+ * sign of v - level changes towards the right or upper neighbour). Allocates
+ * a small table per call; synchronises the stream. */
+int sem_render_slice(const sem_mesh *m, const double *u_g, const sem_slice_desc *desc, float *values,
+                     uint8_t *rgba, void *stream);
+
+/* Write a host RGBA image (row 0 = low end) as a binary PPM (RGB, top row =
+ * high end). SEM_ERR_IO if the file cannot be written. */
+int sem_write_ppm(const char *path, const uint8_t *rgba_host, int width, int height);
+
+/* ------------------------------------------------------------------------
  * Multi-rank partition (host only). Sec. 2.2: one rank per GPU; shared
  * surface values are summed across ranks. Rank r of P owns the element
  * planes ez in [r nelz/P, (r+1) nelz/P), i.e. elements [e_begin, e_end) in

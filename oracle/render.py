@@ -70,28 +70,32 @@ def in_plane_axes(axis: int):
     return [a for a in range(3) if a != axis]
 
 
-def slice_values(m: Mesh, u_g: np.ndarray, axis: int, coord: float, W: int, H: int) -> np.ndarray:
-    """[H, W] values of the unique-node field u_g on the slice."""
+def slice_values(m: Mesh, u_g: np.ndarray, axis: int, coord: float, W: int, H: int, pixels=None) -> np.ndarray:
+    """[H, W] values of the unique-node field u_g on the slice, or the values
+    at the listed (px, py) pixels only (for images too large to evaluate
+    whole here)."""
     n = m.N + 1
     a, b = in_plane_axes(axis)
-    xa = (np.arange(W) + 0.5) * m.L[a] / W
-    xb = (np.arange(H) + 0.5) * m.L[b] / H
-    ka, sa = locate(interfaces(m, a), xa)
-    kb, sb = locate(interfaces(m, b), xb)
+    whole = pixels is None
+    if whole:
+        pixels = [(px, py) for py in range(H) for px in range(W)]
+    px = np.array([p[0] for p in pixels], dtype=np.int64)
+    py = np.array([p[1] for p in pixels], dtype=np.int64)
+    ka, sa = locate(interfaces(m, a), (px + 0.5) * m.L[a] / W)
+    kb, sb = locate(interfaces(m, b), (py + 0.5) * m.L[b] / H)
     kc, sc = locate(interfaces(m, axis), np.array([coord], dtype=np.float64))
     la, lb, lc = lagrange(m.xi, sa), lagrange(m.xi, sb), lagrange(m.xi, sc)[0]
-    uL = u_g[m.l2g].reshape(m.E, n, n, n)  # [e, k, j, i]
-    out = np.zeros((H, W))
-    for py in range(H):
-        for px in range(W):
-            ek = [0, 0, 0]
-            ek[a], ek[b], ek[axis] = ka[px], kb[py], kc[0]
-            e = ek[0] + m.nel[0] * (ek[1] + m.nel[1] * ek[2])
-            basis = [None, None, None]
-            basis[a], basis[b], basis[axis] = la[px], lb[py], lc
-            # v = sum_{ijk} u[e, k, j, i] l_i(x) l_j(y) l_k(z)
-            out[py, px] = np.einsum("kji,i,j,k->", uL[e], basis[0], basis[1], basis[2])
-    return out
+    out = np.zeros(len(pixels))
+    for t in range(len(pixels)):
+        ek = [0, 0, 0]
+        ek[a], ek[b], ek[axis] = ka[t], kb[t], kc[0]
+        e = ek[0] + m.nel[0] * (ek[1] + m.nel[1] * ek[2])
+        ue = u_g[m.l2g[e * n ** 3:(e + 1) * n ** 3]].reshape(n, n, n)  # [k, j, i]
+        basis = [None, None, None]
+        basis[a], basis[b], basis[axis] = la[t], lb[t], lc
+        # v = sum_{ijk} u[k, j, i] l_i(x) l_j(y) l_k(z)
+        out[t] = np.einsum("kji,i,j,k->", ue, basis[0], basis[1], basis[2])
+    return out.reshape(H, W) if whole else out
 
 
 def colorize(v: np.ndarray, vmin: float, vmax: float, iso=()) -> np.ndarray:

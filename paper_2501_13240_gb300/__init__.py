@@ -40,7 +40,7 @@ EXPORTS = (
     "sem_rbc_create", "sem_bdf_ext_step", "sem_rbc_fields", "sem_rbc_destroy",
     "sem_rbc_state_bytes", "sem_rbc_save_state", "sem_rbc_load_state", "sem_rbc_save", "sem_rbc_load",
     "sem_tadv_create", "sem_tadv_destroy", "sem_tadv_info", "sem_tadv_step", "sem_tadv_adjoint_step",
-    "sem_tadv_nusselt", "sem_tadv_nusselt_grad",
+    "sem_tadv_nusselt", "sem_tadv_nusselt_grad", "sem_render_slice", "sem_write_ppm",
     "sem_pmg_create", "sem_pmg_lambda", "sem_pmg_vcycle", "sem_pmg_prolong", "sem_pmg_restrict",
     "sem_pmg_pcg_solve", "sem_pmg_destroy", "sem_partition_info", "sem_partition_interface",
 )
@@ -97,6 +97,12 @@ class sem_rbc_view(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p), ("T", ctypes.c_void_p),
                 ("p", ctypes.c_void_p), ("n_unique", ctypes.c_int64), ("step", ctypes.c_int),
                 ("u_prev", ctypes.c_void_p), ("v_prev", ctypes.c_void_p), ("w_prev", ctypes.c_void_p)]
+
+
+class sem_slice_desc(ctypes.Structure):
+    _fields_ = [("axis", ctypes.c_int), ("coord", ctypes.c_double), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("vmin", ctypes.c_double), ("vmax", ctypes.c_double), ("n_iso", ctypes.c_int),
+                ("iso", ctypes.c_double * 8)]
 
 
 class sem_tadv_params(ctypes.Structure):
@@ -160,6 +166,8 @@ def lib() -> ctypes.CDLL:
         sig["sem_tadv_adjoint_step"] = ([_vp, _i, _vp3, _vp3, _vp, _vp, _vp, ctypes.POINTER(_i), _vp], _i)
         sig["sem_tadv_nusselt"] = ([_vp, _vp, ctypes.POINTER(_d), _vp], _i)
         sig["sem_tadv_nusselt_grad"] = ([_vp, _d, _vp, _vp], _i)
+        sig["sem_render_slice"] = ([_vp, _vp, ctypes.POINTER(sem_slice_desc), _vp, _vp, _vp], _i)
+        sig["sem_write_ppm"] = ([ctypes.c_char_p, _vp, _i, _i], _i)
         sig["sem_pmg_create"] = ([_vp, _d, _d, ctypes.POINTER(sem_pmg_opts), _vp, ctypes.POINTER(_vp)], _i)
         sig["sem_pmg_lambda"] = ([_vp, _i, ctypes.POINTER(_d)], _i)
         sig["sem_pmg_vcycle"] = ([_vp, _vp, _vp, _vp], _i)
@@ -618,6 +626,37 @@ def sem_tadv_nusselt(t: TAdv, T, stream=None) -> float:
 def sem_tadv_nusselt_grad(t: TAdv, c, scale: float = 1.0, stream=None):
     _check(lib().sem_tadv_nusselt_grad(t._h, float(scale), _opt(c, t.mesh.n_unique, "c"), _stream(stream)))
     return c
+
+
+def sem_render_slice(mesh: Mesh, u_g, axis: int, coord: float, width: int, height: int, vmin: float = 0.0,
+                     vmax: float = 1.0, iso=(), values=None, rgba=None, stream=None):
+    """Slice image of a unique-node field: (values [H, W] float32, rgba [H, W, 4] uint8), device tensors."""
+    import torch
+    d = sem_slice_desc()
+    d.axis, d.coord, d.width, d.height = int(axis), float(coord), int(width), int(height)
+    d.vmin, d.vmax = float(vmin), float(vmax)
+    iso = list(iso)
+    if len(iso) > 8:
+        raise ValueError("at most 8 iso-levels")
+    d.n_iso = len(iso)
+    for q, lvl in enumerate(iso):
+        d.iso[q] = float(lvl)
+    if values is None:
+        values = torch.empty((height, width), dtype=torch.float32, device="cuda")
+    if rgba is None:
+        rgba = torch.empty((height, width, 4), dtype=torch.uint8, device="cuda")
+    _check(lib().sem_render_slice(mesh.handle, _ptr(u_g, torch.float64, mesh.n_unique, "u_g"), ctypes.byref(d),
+                                  _ptr(values, torch.float32, width * height, "values"),
+                                  _ptr(rgba, torch.uint8, width * height * 4, "rgba"), _stream(stream)))
+    return values, rgba
+
+
+def sem_write_ppm(path: str, rgba_host):
+    """Write an [H, W, 4] uint8 host array (row 0 = low end) as a PPM file."""
+    a = np.ascontiguousarray(rgba_host, dtype=np.uint8)
+    if a.ndim != 3 or a.shape[2] != 4:
+        raise ValueError("rgba must be [H, W, 4]")
+    _check(lib().sem_write_ppm(os.fsencode(path), a.ctypes.data, a.shape[1], a.shape[0]))
 
 
 class PMG:

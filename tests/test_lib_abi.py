@@ -47,3 +47,20 @@ def test_library_gll_rejects_bad_order(N):
     with pytest.raises(sem.SemError) as ei:
         sem.sem_gll(N)
     assert ei.value.code == sem.SEM_ERR_INVALID_ARG
+
+
+def test_write_ppm_host_only(tmp_path):
+    """The PPM writer is host code: it runs without a GPU."""
+    import paper_2501_13240_gb300 as sem
+    img = np.zeros((2, 3, 4), dtype=np.uint8)
+    img[0, :, 0] = 255   # bottom row red
+    img[1, :, 2] = 255   # top row blue
+    path = tmp_path / "x.ppm"
+    sem.sem_write_ppm(str(path), img)
+    data = path.read_bytes()
+    head = b"P6\n3 2\n255\n"
+    assert data[:len(head)] == head
+    body = np.frombuffer(data[len(head):], dtype=np.uint8).reshape(2, 3, 3)
+    assert (body[0, :, 2] == 255).all() and (body[1, :, 0] == 255).all()  # top row first in the file
+    with pytest.raises(sem.SemError):
+        sem.sem_write_ppm(str(tmp_path / "missing_dir" / "y.ppm"), img)
