@@ -214,6 +214,23 @@ int sem_weak_rhs(const sem_mesh *m, const double *f_L, double *b_g, void *stream
 int sem_ax_assembled_add(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
                          int precision, void *stream);
 
+/* The assembled operator of sem_ax_assembled on vectors in HOST memory:
+ * w_host = M Q^T (h1 A_L + h2 B_L) Q M u_host, with the host<->device copies
+ * pipelined against the arithmetic. The elements are cut into `nchunks` slabs
+ * of element layers along z (0: 8; clamped to [1, nelz]; 1 for N = 1 meshes
+ * and meshes in deterministic mode); unique nodes are numbered plane by plane
+ * in z, so a slab reads and writes only its own lattice planes. While the
+ * caller's stream applies the operator to one slab, a copy-in stream brings
+ * the planes of the next slab and a copy-out stream returns the planes of
+ * finished slabs (both streams created and destroyed by the call).
+ * u_dev, w_dev: caller-owned device scratch of n_unique doubles each
+ * (w_dev ends holding the result too). u_host, w_host: n_unique doubles;
+ * page-locked (pinned) host memory lets the copies overlap, pageable memory
+ * works but serialises them. The call waits for work already queued on
+ * `stream` and synchronises it before returning. */
+int sem_ax_assembled_host(const sem_mesh *m, double h1, double h2, const double *u_host, double *w_host,
+                          int precision, double *u_dev, double *w_dev, int nchunks, void *stream);
+
 /* Masked inverse of the assembled diagonal of h1 A + h2 B (the Jacobi
  * preconditioner, including the D_ii D_jj G_rs cross terms at element
  * boundaries): dinv_g[g] = mask[g] / (Q^T diag_L)[g]. Device U-vector out. */

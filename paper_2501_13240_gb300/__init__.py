@@ -35,7 +35,7 @@ SEM_PREC_BF16 = 3
 EXPORTS = (
     "sem_last_error", "sem_version", "sem_gll", "sem_mesh_create_box", "sem_mesh_destroy",
     "sem_mesh_info_get", "sem_mesh_set_deterministic", "sem_mesh_copy_maps", "sem_mesh_copy_gs_tables", "sem_ax_apply", "sem_gs_op",
-    "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_ax_assembled_add", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
+    "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_ax_assembled_add", "sem_ax_assembled_host", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
     "sem_pcg_solve", "sem_pcg_solve_noalloc", "sem_pcg_noalloc_capacity",
     "sem_rbc_create", "sem_bdf_ext_step", "sem_rbc_fields", "sem_rbc_destroy",
     "sem_rbc_state_bytes", "sem_rbc_save_state", "sem_rbc_load_state", "sem_rbc_save", "sem_rbc_load",
@@ -140,6 +140,7 @@ def lib() -> ctypes.CDLL:
             "sem_scatter": ([_vp, _vp, _vp, _vp], _i),
             "sem_ax_assembled": ([_vp, _d, _d, _vp, _vp, _i, _vp], _i),
             "sem_ax_assembled_add": ([_vp, _d, _d, _vp, _vp, _i, _vp], _i),
+            "sem_ax_assembled_host": ([_vp, _d, _d, _vp, _vp, _i, _vp, _vp, _i, _vp], _i),
             "sem_jacobi_inv": ([_vp, _d, _d, _vp, _vp], _i),
             "sem_weak_rhs": ([_vp, _vp, _vp, _vp], _i),
             "sem_pcg_workspace_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], _i),
@@ -394,6 +395,23 @@ def sem_ax_assembled_add(mesh: Mesh, h1: float, h2: float, u_g, w_g, precision: 
                                       _ptr(u_g, torch.float64, mesh.n_unique, "u_g"),
                                       _ptr(w_g, torch.float64, mesh.n_unique, "w_g"), int(precision), _stream(stream)))
     return w_g
+
+
+def sem_ax_assembled_host(mesh: Mesh, h1: float, h2: float, u_host, w_host, u_dev, w_dev,
+                          precision: int = SEM_PREC_DF64, nchunks: int = 0, stream=None):
+    """Assembled operator on host vectors (CPU torch tensors, ideally pinned),
+    transfers pipelined against the arithmetic; u_dev, w_dev are device scratch."""
+    import torch
+    for t, nm in ((u_host, "u_host"), (w_host, "w_host")):
+        if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() \
+                or t.numel() != mesh.n_unique:
+            raise TypeError(f"{nm} must be a contiguous float64 CPU tensor of n_unique elements")
+    _check(lib().sem_ax_assembled_host(mesh.handle, float(h1), float(h2), ctypes.c_void_p(u_host.data_ptr()),
+                                       ctypes.c_void_p(w_host.data_ptr()), int(precision),
+                                       _ptr(u_dev, torch.float64, mesh.n_unique, "u_dev"),
+                                       _ptr(w_dev, torch.float64, mesh.n_unique, "w_dev"), int(nchunks),
+                                       _stream(stream)))
+    return w_host
 
 
 def sem_jacobi_inv(mesh: Mesh, h1: float, h2: float, dinv_g, stream=None):
