@@ -420,8 +420,8 @@ def main():
             t0 = time.perf_counter()
             for _ in range(5):
                 sem.sem_render_slice(rm, T, axis, coord, 4096, 4096, 0.0, 1.0, (0.4, 0.6), vals, rgba)
-            ms = 1e3 * (time.perf_counter() - t0) / 5
-            render[name] = {"ms": ms, "mpixel_per_s": 4096 * 4096 / (ms * 1e-3) / 1e6}
+            rms = 1e3 * (time.perf_counter() - t0) / 5
+            render[name] = {"ms": rms, "mpixel_per_s": 4096 * 4096 / (rms * 1e-3) / 1e6}
             del vals, rgba
         rbc["render_4096x4096"] = render
         rs.destroy()
