@@ -154,6 +154,14 @@ int sem_mesh_destroy(sem_mesh *m);
 /* Fill *info with sizes and device views. */
 int sem_mesh_info_get(const sem_mesh *m, sem_mesh_info *info);
 
+/* Audit the index tables on the host: l2g in range, l2gm = l2g on free
+ * nodes and -1 on Dirichlet nodes, CSR offsets increasing from 0 to n_local,
+ * the CSR permutation a permutation whose segments hold exactly the copies of
+ * their node in ascending order, multiplicities equal to the copy counts.
+ * SEM_ERR_INVALID_ARG names the first violation. Copies the tables to host
+ * memory (synchronous). */
+int sem_mesh_validate(const sem_mesh *m);
+
 /* Deterministic assembly (on = 1) or atomic assembly (on = 0, the default).
  * The assembled operators (sem_ax_assembled*, the PCG and p-multigrid
  * solves) add each element's contribution to a unique node with FP64/FP32

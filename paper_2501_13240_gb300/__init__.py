@@ -34,7 +34,7 @@ SEM_PREC_BF16 = 3
 # every symbol include/sem.h declares
 EXPORTS = (
     "sem_last_error", "sem_version", "sem_gll", "sem_mesh_create_box", "sem_mesh_destroy",
-    "sem_mesh_info_get", "sem_mesh_set_deterministic", "sem_mesh_copy_maps", "sem_mesh_copy_gs_tables", "sem_ax_apply", "sem_gs_op",
+    "sem_mesh_info_get", "sem_mesh_set_deterministic", "sem_mesh_validate", "sem_mesh_copy_maps", "sem_mesh_copy_gs_tables", "sem_ax_apply", "sem_gs_op",
     "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_ax_assembled_add", "sem_ax_assembled_host", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
     "sem_pcg_solve", "sem_pcg_solve_noalloc", "sem_pcg_noalloc_capacity",
     "sem_rbc_create", "sem_bdf_ext_step", "sem_rbc_fields", "sem_rbc_destroy",
@@ -132,6 +132,7 @@ def lib() -> ctypes.CDLL:
             "sem_mesh_destroy": ([_vp], _i),
             "sem_mesh_info_get": ([_vp, ctypes.POINTER(sem_mesh_info)], _i),
             "sem_mesh_set_deterministic": ([_vp, _i], _i),
+            "sem_mesh_validate": ([_vp], _i),
             "sem_mesh_copy_maps": ([_vp, _vp, _vp], _i),
             "sem_mesh_copy_gs_tables": ([_vp, _vp, _vp], _i),
             "sem_ax_apply": ([_vp, _d, _d, _vp, _vp, _i, _vp], _i),
@@ -323,6 +324,10 @@ def sem_mesh_create_box(nel, N=7, L=(1.0, 1.0, 1.0), periodic=(0, 0, 0), dirichl
     if deterministic:
         sem_mesh_set_deterministic(m, True)
     return m
+
+
+def sem_mesh_validate(mesh: Mesh):
+    _check(lib().sem_mesh_validate(mesh.handle))
 
 
 def sem_mesh_set_deterministic(mesh: Mesh, on: bool = True):

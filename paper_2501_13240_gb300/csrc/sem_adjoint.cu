@@ -266,6 +266,7 @@ extern "C" int sem_tadv_destroy(sem_tadv *t) {
 
 extern "C" int sem_tadv_step(sem_tadv *t, int n, const double *const u[3], const double *Tn, const double *Tnm1,
                              const double *NTnm1, double *Tnp1, double *NTn, int *iters, void *stream) {
+  SemRange nvtx_range("sem_tadv_step");
   if (!t || !u || n < 0) return sem_fail(SEM_ERR_INVALID_ARG, "sem_tadv_step: NULL handle/velocity or n < 0");
   if (bad(u[0]) || bad(u[1]) || bad(u[2]) || bad(Tn) || bad(Tnp1) || bad(NTn) ||
       (n > 0 && (bad(Tnm1) || bad(NTnm1))))
@@ -301,6 +302,7 @@ extern "C" int sem_tadv_step(sem_tadv *t, int n, const double *const u[3], const
 
 extern "C" int sem_tadv_adjoint_step(sem_tadv *t, int n, const double *const u_n[3], const double *const u_nm1[3],
                                      const double *g_np1, double *g_n, double *g_nm1, int *iters, void *stream) {
+  SemRange nvtx_range("sem_tadv_adjoint_step");
   if (!t || !u_n || n < 0) return sem_fail(SEM_ERR_INVALID_ARG, "sem_tadv_adjoint_step: NULL handle/velocity or n < 0");
   if (bad(u_n[0]) || bad(u_n[1]) || bad(u_n[2]) || bad(g_np1) || bad(g_n) ||
       (n > 0 && (!u_nm1 || bad(u_nm1[0]) || bad(u_nm1[1]) || bad(u_nm1[2]) || bad(g_nm1))))

@@ -58,6 +58,7 @@ sem_mesh sub_range(const sem_mesh *m, int64_t e0, int64_t e1) {
 
 extern "C" int sem_ax_assembled_host(const sem_mesh *m, double h1, double h2, const double *u_host, double *w_host,
                                      int precision, double *u_dev, double *w_dev, int nchunks, void *stream) {
+  SemRange nvtx_range("sem_ax_assembled_host");
   if (!m || !u_host || !w_host || !u_dev || !w_dev)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_host: NULL argument");
   if ((((uintptr_t)u_dev) | ((uintptr_t)w_dev)) & 7 || u_dev == w_dev)

@@ -6,7 +6,18 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sem.h"
+
+// NVTX range over an entry point (visible in Nsight timelines; a no-op when
+// no tool is attached)
+struct SemRange {
+  explicit SemRange(const char *name) { nvtxRangePushA(name); }
+  ~SemRange() { nvtxRangePop(); }
+  SemRange(const SemRange &) = delete;
+  SemRange &operator=(const SemRange &) = delete;
+};
 
 #define SEM_MAXN 10
 #define SEM_MAXNP (SEM_MAXN + 1)

@@ -241,6 +241,7 @@ bool bad_ptr(const void *p) { return p == nullptr || ((uintptr_t)p & 7) != 0; }
 
 extern "C" int sem_ax_apply(const sem_mesh *m, double h1, double h2, const double *u_L, double *w_L, int precision,
                             void *stream) {
+  SemRange nvtx_range("sem_ax_apply");
   if (int rc = check_mesh(m, "sem_ax_apply")) return rc;
   if (bad_ptr(u_L) || bad_ptr(w_L)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_apply: NULL or misaligned vector");
   if (u_L == w_L) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_apply: u_L and w_L must not overlap");
@@ -250,6 +251,7 @@ extern "C" int sem_ax_apply(const sem_mesh *m, double h1, double h2, const doubl
 }
 
 extern "C" int sem_gs_op(const sem_mesh *m, double *v_L, int apply_mask, void *stream) {
+  SemRange nvtx_range("sem_gs_op");
   if (int rc = check_mesh(m, "sem_gs_op")) return rc;
   if (bad_ptr(v_L)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_gs_op: NULL or misaligned vector");
   return sem_launch_gs(m, v_L, apply_mask, as_stream(stream));
@@ -269,6 +271,7 @@ extern "C" int sem_scatter(const sem_mesh *m, const double *v_g, double *v_L, vo
 
 extern "C" int sem_ax_assembled(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g, int precision,
                                 void *stream) {
+  SemRange nvtx_range("sem_ax_assembled");
   if (int rc = check_mesh(m, "sem_ax_assembled")) return rc;
   if (bad_ptr(u_g) || bad_ptr(w_g)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled: NULL or misaligned vector");
   if (u_g == w_g) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled: u_g and w_g must not overlap");
@@ -324,6 +327,7 @@ extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const doub
 int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
                      const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats, void *stream,
                      int check_every) {
+  SemRange nvtx_range("sem_pcg_solve_ex");
   if (int rc = check_mesh(m, "sem_pcg_solve")) return rc;
   if (check_every < 1) check_every = 1;
   if (bad_ptr(b_g) || bad_ptr(x_g)) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: NULL or misaligned vector");

@@ -1057,6 +1057,7 @@ extern "C" int sem_pmg_lambda(const sem_pmg *P, int level, double *lambda) {
 }
 
 extern "C" int sem_pmg_vcycle(sem_pmg *P, const double *r_g, double *z_g, void *stream) {
+  SemRange nvtx_range("sem_pmg_vcycle");
   if (!P || !r_g || !z_g) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_vcycle: NULL argument");
   cudaStream_t st = as_stream(stream);
   PmgLevel &lv = P->L[0];
@@ -1094,6 +1095,7 @@ extern "C" int sem_pmg_restrict(sem_pmg *P, int level, const double *rf_g, doubl
 
 extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, const sem_solver_opts *opts,
                                  sem_solve_stats *stats, void *stream) {
+  SemRange nvtx_range("sem_pmg_pcg_solve");
   if (!P || !b_g || !x_g || !opts || !stats) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_pcg_solve: NULL argument");
   if (opts->mask_mode != P->o.mask_mode || (opts->precision != SEM_PREC_FP64 && opts->precision != SEM_PREC_DF64) ||
       !(opts->tol >= 0.0) || opts->maxit < 1)

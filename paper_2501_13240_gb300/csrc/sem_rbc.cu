@@ -337,6 +337,7 @@ extern "C" int sem_rbc_fields(const sem_rbc *s, sem_rbc_view *v) {
 }
 
 extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
+  SemRange nvtx_range("sem_bdf_ext_step");
   if (!s || !stt) return sem_fail(SEM_ERR_INVALID_ARG, "sem_bdf_ext_step: NULL argument");
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = as_stream(stream);

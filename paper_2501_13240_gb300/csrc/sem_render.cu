@@ -134,6 +134,7 @@ int locate_basis(const sem_mesh *m, const std::vector<double> &xk, double x, dou
 
 extern "C" int sem_render_slice(const sem_mesh *m, const double *u_g, const sem_slice_desc *d, float *values,
                                 uint8_t *rgba, void *stream) {
+  SemRange nvtx_range("sem_render_slice");
   if (!m || !u_g || !d || !values || !rgba) return sem_fail(SEM_ERR_INVALID_ARG, "sem_render_slice: NULL argument");
   if (d->axis < 0 || d->axis > 2 || !(d->coord >= 0.0) || !(d->coord <= m->L[d->axis]))
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_render_slice: axis must be 0..2 and 0 <= coord <= L[axis]");

@@ -408,6 +408,7 @@ static int build_gs_tables(sem_mesh *m, cudaStream_t st) {
 }
 
 extern "C" int sem_mesh_create_box(const sem_box_desc *d, void *stream, sem_mesh **out) {
+  SemRange nvtx_range("sem_mesh_create_box");
   if (!d || !out) return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_create_box: NULL argument");
   *out = nullptr;
   if (d->N < 1 || d->N > SEM_MAXN) return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_create_box: N must be in [1, 10]");
@@ -517,6 +518,46 @@ extern "C" int sem_mesh_create_box(const sem_box_desc *d, void *stream, sem_mesh
 
 extern "C" int sem_mesh_destroy(sem_mesh *m) {
   free_mesh(m);
+  return SEM_OK;
+}
+
+// Host-side audit of a mesh's index tables (the stand-in for a memory
+// checker: every index a kernel follows is checked before it is trusted).
+extern "C" int sem_mesh_validate(const sem_mesh *m) {
+  if (!m) return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_validate: NULL mesh");
+  const int64_t nL = m->n_local, nU = m->n_unique;
+  std::vector<int32_t> l2g(nL), l2gm(nL), off(nU + 1), perm(nL);
+  std::vector<uint8_t> mask(nU);
+  std::vector<double> mult(nU);
+  SEM_CUDA(cudaMemcpy(l2g.data(), m->l2g, sizeof(int32_t) * nL, cudaMemcpyDeviceToHost));
+  SEM_CUDA(cudaMemcpy(l2gm.data(), m->l2gm, sizeof(int32_t) * nL, cudaMemcpyDeviceToHost));
+  SEM_CUDA(cudaMemcpy(off.data(), m->gs_off, sizeof(int32_t) * (nU + 1), cudaMemcpyDeviceToHost));
+  SEM_CUDA(cudaMemcpy(perm.data(), m->gs_perm, sizeof(int32_t) * nL, cudaMemcpyDeviceToHost));
+  SEM_CUDA(cudaMemcpy(mask.data(), m->mask, nU, cudaMemcpyDeviceToHost));
+  SEM_CUDA(cudaMemcpy(mult.data(), m->mult, sizeof(double) * nU, cudaMemcpyDeviceToHost));
+  char msg[160];
+  auto bad = [&](const char *what, int64_t i) {
+    snprintf(msg, sizeof(msg), "sem_mesh_validate: %s at index %lld", what, (long long)i);
+    return sem_fail(SEM_ERR_INVALID_ARG, msg);
+  };
+  for (int64_t l = 0; l < nL; ++l) {
+    if (l2g[l] < 0 || l2g[l] >= nU) return bad("l2g out of range", l);
+    const int32_t want = mask[l2g[l]] ? l2g[l] : -1;
+    if (l2gm[l] != want) return bad("l2gm disagrees with l2g and the mask", l);
+  }
+  if (off[0] != 0 || off[nU] != nL) return bad("CSR offsets do not span the local nodes", 0);
+  std::vector<uint8_t> seen(nL, 0);
+  for (int64_t g = 0; g < nU; ++g) {
+    if (off[g + 1] <= off[g]) return bad("unique node without a copy (CSR offsets not increasing)", g);
+    if (mult[g] != (double)(off[g + 1] - off[g])) return bad("multiplicity differs from the copy count", g);
+    for (int32_t t = off[g]; t < off[g + 1]; ++t) {
+      const int32_t l = perm[t];
+      if (l < 0 || l >= nL || seen[l]) return bad("CSR permutation out of range or repeated", t);
+      seen[l] = 1;
+      if (l2g[l] != g) return bad("CSR segment holds a copy of another node", t);
+      if (t > off[g] && perm[t - 1] >= l) return bad("CSR segment not in ascending copy order", t);
+    }
+  }
   return SEM_OK;
 }
 

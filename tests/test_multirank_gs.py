@@ -95,3 +95,56 @@ def test_partition_rejects_bad_arguments():
     with pytest.raises(sem.SemError):
         sem.sem_partition_info(d, 2, 2)
     assert sem.sem_partition_info(d, 1, 0) == (0, 8, 0)
+
+
+def _worker_failing(rank, world, port, queue):
+    """Rank 1 fails (raises) after joining and before the interface exchange;
+    rank 0 must learn of it on the host instead of hanging: first from a
+    missing heartbeat in the rendezvous store, then from its exchange ending
+    with an error within the process group's timeout."""
+    import datetime
+    import sys
+    import time
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    store = dist.distributed_c10d._get_default_store()
+    if rank == 1:
+        queue.put((1, "failing", 0.0))
+        queue.close()
+        queue.join_thread()  # the message is out before the process dies
+        os._exit(3)  # dies with no exchange in flight
+    t0 = time.monotonic()
+    heartbeat_missing = False
+    try:
+        store.wait(["heartbeat/1/step0"], datetime.timedelta(seconds=3))
+    except Exception:
+        heartbeat_missing = True
+    exchange_failed = False
+    try:
+        buf = torch.zeros(8, dtype=torch.float64)
+        dist.all_reduce(buf)
+    except Exception:
+        exchange_failed = True
+    queue.put((0, f"heartbeat_missing={heartbeat_missing} exchange_failed={exchange_failed}",
+               time.monotonic() - t0))
+    queue.close()
+    queue.join_thread()
+    os._exit(0)  # skip the process-group teardown, which would wait for the dead peer
+
+
+def test_failed_rank_is_detected_on_the_host():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_failing, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict((r, (msg, t)) for r, msg, t in (q.get(timeout=120) for _ in range(2)))
+    for p in procs:
+        p.join(timeout=60)
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0
+    msg, elapsed = res[0]
+    assert msg == "heartbeat_missing=True exchange_failed=True", msg
+    assert elapsed < 30.0
