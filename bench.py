@@ -211,6 +211,46 @@ def run_once(sem, mesh, u, names):
     return 0
 
 
+def run_solves(sem, mesh, w, runs, tol):
+    """Solve the manufactured Poisson problem on `mesh` with each listed
+    solver to `tol`; iterations, times, true binary64 residuals and the
+    difference to the first (reference) solution."""
+    import torch
+    # (the forcing at the nodes is input synthesis; the weak form is the library's)
+    X, Y, Z = (mesh.field(n) for n in ("X", "Y", "Z"))
+    fL = 3.0 * np.pi ** 2 * torch.sin(np.pi * X) * torch.sin(np.pi * Y) * torch.sin(np.pi * Z)
+    del X, Y, Z
+    b = torch.empty(mesh.n_unique, dtype=torch.float64, device="cuda")
+    sem.sem_weak_rhs(mesh, fL, b)
+    del fL
+    out, sols = {}, {}
+    for name, kind, prec, sprec in runs:
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        setup_ms = 0.0
+        if kind == "jacobi":
+            st = sem.sem_pcg_solve(mesh, 1.0, 0.0, b, x, tol=tol, maxit=20000, precision=prec, raise_on_error=False)
+        else:
+            t0 = time.perf_counter()
+            P = sem.sem_pmg_create(mesh, orders=(w.N, 3, 1) if w.N > 3 else (w.N, 1), smoother_precision=sprec,
+                                   coarse_tol=1e-2)
+            setup_ms = 1e3 * (time.perf_counter() - t0)
+            st = sem.sem_pmg_pcg_solve(P, b, x, tol=tol, maxit=500, precision=prec, raise_on_error=False)
+            P.destroy()
+        rr = torch.empty_like(b)  # true residual with the binary64 operator
+        sem.sem_ax_assembled(mesh, 1.0, 0.0, x, rr, precision=sem.SEM_PREC_FP64)
+        true_res = float(torch.linalg.norm(b - rr) / torch.linalg.norm(b))
+        out[name] = {"iterations": st["iterations"], "solve_ms": st["solve_ms"], "setup_ms": setup_ms,
+                     "ms_per_iteration": st["solve_ms"] / max(st["iterations"], 1),
+                     "rel_residual": st["rel_residual"], "true_rel_residual_fp64": true_res, "status": st["status"]}
+        sols[name] = x
+    ref_name = runs[0][0]
+    ref = sols[ref_name]
+    for name, x in sols.items():
+        out[name]["solution_rel_diff_vs_" + ref_name] = float((x - ref).abs().max() / ref.abs().max())
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -354,48 +394,25 @@ def main():
     # against the mixed-precision p-multigrid flexible CG, all to 1e-8
     pcg = None
     if not args.no_pcg:
-        # (the forcing at the nodes is input synthesis; the weak form is the library's)
-        X, Y, Z = (mesh.field(n) for n in ("X", "Y", "Z"))
-        fL = 3.0 * np.pi ** 2 * torch.sin(np.pi * X) * torch.sin(np.pi * Y) * torch.sin(np.pi * Z)
-        del X, Y, Z
-        b = torch.empty_like(u)
-        sem.sem_weak_rhs(mesh, fL, b)
-        del fL
-        pcg = {}
-        sols = {}
         runs = [("jacobi_fp64", "jacobi", sem.SEM_PREC_FP64, None),
                 ("jacobi_df64", "jacobi", sem.SEM_PREC_DF64, None),
                 ("pmg_fp32_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_FP32),
                 ("pmg_bf16_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_BF16)]
         if args.quick_pcg:
             runs = [r for r in runs if r[0] != "jacobi_fp64"]
-        for name, kind, prec, sprec in runs:
-            x = torch.zeros_like(u)
-            torch.cuda.synchronize()
-            setup_ms = 0.0
-            if kind == "jacobi":
-                st = sem.sem_pcg_solve(mesh, 1.0, 0.0, b, x, tol=args.pcg_tol, maxit=20000, precision=prec,
-                                       raise_on_error=False)
-            else:
-                t0 = time.perf_counter()
-                P = sem.sem_pmg_create(mesh, orders=(w.N, 3, 1) if w.N > 3 else (w.N, 1), smoother_precision=sprec,
-                                       coarse_tol=1e-2)
-                setup_ms = 1e3 * (time.perf_counter() - t0)
-                st = sem.sem_pmg_pcg_solve(P, b, x, tol=args.pcg_tol, maxit=500, precision=prec, raise_on_error=False)
-                P.destroy()
-            # true residual with the binary64 operator
-            rr = torch.empty_like(u)
-            sem.sem_ax_assembled(mesh, 1.0, 0.0, x, rr, precision=sem.SEM_PREC_FP64)
-            true_res = float(torch.linalg.norm(b - rr) / torch.linalg.norm(b))
-            pcg[name] = {"iterations": st["iterations"], "solve_ms": st["solve_ms"], "setup_ms": setup_ms,
-                         "ms_per_iteration": st["solve_ms"] / max(st["iterations"], 1),
-                         "rel_residual": st["rel_residual"], "true_rel_residual_fp64": true_res,
-                         "status": st["status"]}
-            sols[name] = x
-        ref = sols.get("jacobi_fp64", sols.get("jacobi_df64"))
-        for name, x in sols.items():
-            pcg[name]["solution_rel_diff_vs_fp64_jacobi"] = float((x - ref).abs().max() / ref.abs().max())
-        del b, sols
+        pcg = run_solves(sem, mesh, w, runs, args.pcg_tol)
+    # the mixed-precision configuration on its own mesh: the 64^3 construction
+    # at 48^3 elements (37.9 M unknowns); reference = double-float Jacobi-PCG
+    pcg48 = None
+    if not args.no_pcg:
+        w48 = workloads.PMG_48
+        m48 = sem.mesh_from_workload(w48)
+        pcg48 = run_solves(sem, m48, w48, [("jacobi_df64", "jacobi", sem.SEM_PREC_DF64, None),
+                                           ("pmg_fp32_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_FP32),
+                                           ("pmg_bf16_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_BF16)],
+                           args.pcg_tol)
+        pcg48["workload"] = w48.name
+        m48.destroy()
 
     # --- one Rayleigh-Benard BDF2/EXT2 step (32^3 elements, Ra = 1e8, Pr = 0.7)
     rbc = None
@@ -487,7 +504,7 @@ def main():
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clocks,
-            "extra": {"precision": head, "per_precision": per, "solves": pcg, "rbc_step": rbc,
+            "extra": {"precision": head, "per_precision": per, "solves": pcg, "solves_pmg_48": pcg48, "rbc_step": rbc,
                       "adjoint": adj},
         }
         print(json.dumps(line))
