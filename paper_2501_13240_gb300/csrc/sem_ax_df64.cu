@@ -171,8 +171,9 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
   df::Acc pw = {0.0f, 0.0f};
   const int64_t estride = (int64_t)gridDim.x * C::ELB;
 
-  // gather indices of this thread's column, prefetched one element ahead
-  int32_t gi[NP];
+  // gather indices of this thread's column, prefetched one element ahead;
+  // go keeps the current element's for the scatter at the end
+  int32_t gi[NP], go[NP];
   int64_t e = (int64_t)blockIdx.x * C::ELB + le;
   if (ASSEMBLED) {
 #pragma unroll
@@ -188,7 +189,10 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
         const int p = a + NP * b + C::N2 * k;
-        if (ASSEMBLED) v[k] = (gi[k] >= 0) ? u[gi[k]] : 0.0;
+        if (ASSEMBLED) {
+          go[k] = gi[k];
+          v[k] = (gi[k] >= 0) ? u[gi[k]] : 0.0;
+        }
         else v[k] = act ? u[e * C::N3 + p] : 0.0;
       }
       if (ASSEMBLED) {
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
       if (act) {
         const double vd = df::to_f64(v.x, v.y);
         if (ASSEMBLED) {
-          const int32_t g = l2gm[e * C::N3 + p];
+          const int32_t g = go[k];
           if (wloc) wloc[e * C::N3 + p] = (g >= 0) ? vd : 0.0;
           else if (g >= 0) atomicAdd(&w[g], vd);
           if (pw_partial) df::mac(pw, x[k].x, x[k].y, v.x, v.y);
