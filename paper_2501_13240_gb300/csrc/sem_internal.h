@@ -100,6 +100,12 @@ int sem_launch_gather_add(const sem_mesh *m, const double *wL, double *w, cudaSt
 int sem_n1_prepare(sem_mesh *m, cudaStream_t st);
 int sem_launch_ax_n1(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g, double *pw_partial,
                      int precision, cudaStream_t st, const int32_t *map);
+// Jacobi-PCG on an N = 1 mesh in one cooperative launch (the p-multigrid
+// coarsest level); synchronises the stream
+size_t sem_pcg_n1_workspace_bytes(const sem_mesh *m);
+int sem_pcg_n1_persistent(const sem_mesh *m, double h1, double h2, const double *b, double *x, const double *dinv,
+                          const int32_t *map, double tol, int maxit, void *work, int *iters, double *rel,
+                          cudaStream_t st);
 int sem_launch_gather_add_f(const sem_mesh *m, const float *wL, float *w, cudaStream_t st);
 int sem_launch_diag_local(const sem_mesh *m, double h1, double h2, double *dL, cudaStream_t st);
 

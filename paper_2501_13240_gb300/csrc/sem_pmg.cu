@@ -53,6 +53,7 @@ struct sem_pmg {
   sem_pmg_opts o;
   double h1 = 1.0, h2 = 0.0;
   double *cb = nullptr, *cx = nullptr;  // coarsest level (binary64)
+  double *cdinv = nullptr;              // its Jacobi inverse (persistent coarse solver)
   void *cws = nullptr;
   double *r = nullptr, *z = nullptr, *zn = nullptr, *p = nullptr, *w = nullptr;  // outer FCG
   double *part = nullptr, *pw_part = nullptr;
@@ -460,15 +461,23 @@ int launch_ax32(const PmgLevel &lv, int gprec, float h1, float h2, const float *
 // One CTA of nf^2 threads per element; thread (i, j) owns the fine column
 // (i, j, :). Sum factorisation: nc + nc^2 + nc^3 multiply-adds per column
 // stage instead of nc^3 per fine point.
-// fine level uf = P uc (identical values on shared nodes, every copy stores)
+// Fine level uf = P uc (identical values on shared nodes, every copy stores).
+// Accumulate form (own != nullptr): uf += P uc and r = b, written by the one
+// copy that owns each unique node: the copy whose local index is below N in
+// every direction, or N at the last element of a non-periodic direction.
+struct Owner {
+  int nel[3], per[3];
+};
 __global__ void k_prolong(int nf, int nc, int64_t E, const float *__restrict__ J, const int32_t *__restrict__ mapc,
-                          const float *__restrict__ uc, const int32_t *__restrict__ mapf, float *__restrict__ uf) {
+                          const float *__restrict__ uc, const int32_t *__restrict__ mapf, float *__restrict__ uf,
+                          int accumulate, Owner ow, const float *__restrict__ bf, float *__restrict__ rf) {
   __shared__ float tile[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];
   __shared__ float Js[SEM_MAXNP * SEM_MAXNP];
   const int nc3 = nc * nc * nc, nf3 = nf * nf * nf;
   const int tid = threadIdx.x, i = tid % nf, j = tid / nf;
   for (int t = tid; t < nf * nc; t += blockDim.x) Js[t] = J[t];
   for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    const int64_t ex = e % ow.nel[0], ey = (e / ow.nel[0]) % ow.nel[1], ez = e / ((int64_t)ow.nel[0] * ow.nel[1]);
     __syncthreads();
     for (int t = tid; t < nc3; t += blockDim.x) {
       const int32_t g = mapc[e * nc3 + t];
@@ -489,7 +498,15 @@ __global__ void k_prolong(int nf, int nc, int64_t E, const float *__restrict__ J
       float s = 0.0f;
       for (int c = 0; c < nc; ++c) s = fmaf(Js[k * nc + c], t2[c], s);
       const int32_t g = mapf[e * nf3 + i + nf * (j + nf * k)];
-      if (g >= 0) uf[g] = s;
+      if (g < 0) continue;
+      if (!accumulate) {
+        uf[g] = s;
+      } else if ((i < nf - 1 || (!ow.per[0] && ex == ow.nel[0] - 1)) &&
+                 (j < nf - 1 || (!ow.per[1] && ey == ow.nel[1] - 1)) &&
+                 (k < nf - 1 || (!ow.per[2] && ez == ow.nel[2] - 1))) {
+        uf[g] += s;
+        rf[g] = bf[g];
+      }
     }
   }
 }
@@ -624,6 +641,47 @@ __global__ void k_alt(int64_t n, int64_t nx, int64_t ny, const uint8_t *__restri
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t I = g % nx, J = (g / nx) % ny, K = g / (nx * ny);
     v[g] = (!mask || mask[g]) ? (((I + J + K) & 1) ? -1.0f : 1.0f) : 0.0f;
+  }
+}
+
+// Degree-2 Chebyshev smoothing with fused vector passes (c1 = 1/5,
+// c2 = 12/(5 lam) of the recurrence); the same roundings as the general path.
+// pre, part 1: b (from binary64 when b64 is given), r = b, d = c0 dinv b
+__global__ void k_pre2a(int64_t n, const double *__restrict__ b64, float *__restrict__ b, const float *__restrict__ dinv,
+                        float c0, float *__restrict__ r, float *__restrict__ d) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    float bv;
+    if (b64) {
+      bv = df::from_f64(b64[g]).x;
+      b[g] = bv;
+    } else {
+      bv = b[g];
+    }
+    r[g] = bv;
+    d[g] = c0 * dinv[g] * bv;
+  }
+}
+
+// pre, part 2 (r = b - A d): x = d + (c1 d + c2 dinv r), then r = b for the residual
+__global__ void k_pre2b(int64_t n, float c1, float c2, const float *__restrict__ dinv, const float *__restrict__ b,
+                        float *__restrict__ r, const float *__restrict__ d, float *__restrict__ x) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const float dv = d[g];
+    const float d1 = c1 * dv + c2 * dinv[g] * r[g];
+    x[g] = 0.0f + dv + d1;
+    r[g] = b[g];
+  }
+}
+
+// post (r = b - A x - A d): x = (x + d) + (c1 d + c2 dinv r); written to z64 in binary64 when given
+__global__ void k_post2(int64_t n, float c1, float c2, const float *__restrict__ dinv, const float *__restrict__ r,
+                        const float *__restrict__ d, float *__restrict__ x, double *__restrict__ z64) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const float dv = d[g];
+    const float d1 = c1 * dv + c2 * dinv[g] * r[g];
+    const float xv = (x[g] + dv) + d1;
+    if (z64) z64[g] = f2d_bits(xv);
+    else x[g] = xv;
   }
 }
 
@@ -798,12 +856,32 @@ int restrict_to(sem_pmg *P, int l, const float *rf, float *rc, cudaStream_t st) 
   return SEM_OK;
 }
 
+Owner owner_of(const sem_mesh *m) {
+  Owner o;
+  for (int d = 0; d < 3; ++d) {
+    o.nel[d] = m->nel[d];
+    o.per[d] = m->periodic[d];
+  }
+  return o;
+}
+
 int prolong_to(sem_pmg *P, int l, const float *uc, float *uf, cudaStream_t st) {
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   SEM_CUDA(cudaMemsetAsync(uf, 0, sizeof(float) * f.m->n_unique, st));
   const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
-  k_prolong<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, uf);
+  k_prolong<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, uf, 0,
+                                              owner_of(f.m), nullptr, nullptr);
   SEM_LAUNCH_CHECK("k_prolong");
+  return SEM_OK;
+}
+
+// x += P uc and r = b on level l (each unique node once, by its owner copy)
+int prolong_add(sem_pmg *P, int l, const float *uc, float *x, const float *b, float *r, cudaStream_t st) {
+  PmgLevel &f = P->L[l], &c = P->L[l + 1];
+  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
+  k_prolong<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, x, 1,
+                                              owner_of(f.m), b, r);
+  SEM_LAUNCH_CHECK("k_prolong (accumulate)");
   return SEM_OK;
 }
 
@@ -849,14 +927,20 @@ int coarse_solve(sem_pmg *P, cudaStream_t st) {
   if (P->o.mask_mode) {  // singular Neumann problem: make the right-hand side consistent
     if (int rc = remove_mean_d(P, P->cb, n, st)) return rc;
   }
-  sem_solver_opts o;
-  o.tol = P->o.coarse_tol;
-  o.maxit = P->o.coarse_maxit;
-  o.precision = SEM_PREC_DF64;  // binary64-accurate; native FP64 is pipe-bound even at N = 1
-  o.timeout_s = 0.0;
-  o.mask_mode = P->o.mask_mode;
-  sem_solve_stats stt;
-  int rc = sem_pcg_solve_ex(lv.m, P->h1, P->h2, P->cb, P->cx, &o, P->cws, &stt, (void *)st, 8);
+  int rc;
+  if (P->cdinv) {  // N = 1 element matrices, atomic assembly: one persistent launch
+    rc = sem_pcg_n1_persistent(lv.m, P->h1, P->h2, P->cb, P->cx, P->cdinv, lv.map, P->o.coarse_tol,
+                               P->o.coarse_maxit, P->cws, nullptr, nullptr, st);
+  } else {
+    sem_solver_opts o;
+    o.tol = P->o.coarse_tol;
+    o.maxit = P->o.coarse_maxit;
+    o.precision = SEM_PREC_DF64;  // binary64-accurate; native FP64 is pipe-bound even at N = 1
+    o.timeout_s = 0.0;
+    o.mask_mode = P->o.mask_mode;
+    sem_solve_stats stt;
+    rc = sem_pcg_solve_ex(lv.m, P->h1, P->h2, P->cb, P->cx, &o, P->cws, &stt, (void *)st, 8);
+  }
   if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
   k_d2f<<<grid_for(n, 256), 256, 0, st>>>(n, P->cx, lv.x);
   SEM_LAUNCH_CHECK("coarse solve");
@@ -876,6 +960,35 @@ int vcycle(sem_pmg *P, int l, cudaStream_t st) {
   if ((rc = prolong_to(P, l, P->L[l + 1].x, lv.t, st))) return rc;
   k_axpy_f<<<grid_for(n, 256), 256, 0, st>>>(n, 1.0f, lv.t, lv.x);
   return smooth(P, l, false, st);
+}
+
+// The V-cycle for degree-2 smoothing with fused vector passes (the same
+// operations in the same order as vcycle; 8 instead of 17 streaming passes
+// over the level's vectors). Level 0 may read its right-hand side in binary64
+// (in64) and write the correction in binary64 (out64).
+int vcycle2(sem_pmg *P, int l, cudaStream_t st, const double *in64, double *out64) {
+  if (l == (int)P->L.size() - 1) return coarse_solve(P, st);
+  int rc;
+  PmgLevel &lv = P->L[l];
+  const int64_t n = lv.m->n_unique;
+  const unsigned g = grid_for(n, 256);
+  const float lam = lv.lam;
+  const float c0 = 4.0f / (3.0f * lam);
+  const float c1 = 1.0f / 5.0f, c2 = 12.0f / (5.0f * lam);
+  k_pre2a<<<g, 256, 0, st>>>(n, in64, lv.b, lv.dinv, c0, lv.r, lv.d);
+  if ((rc = ax32(P, l, -1.0f, lv.d, lv.r, st))) return rc;  // r = b - A d
+  k_pre2b<<<g, 256, 0, st>>>(n, c1, c2, lv.dinv, lv.b, lv.r, lv.d, lv.x);
+  SEM_LAUNCH_CHECK("pre-smoothing");
+  if ((rc = ax32(P, l, -1.0f, lv.x, lv.r, st))) return rc;  // r = b - A x
+  if ((rc = restrict_to(P, l, lv.r, P->L[l + 1].b, st))) return rc;
+  if ((rc = vcycle2(P, l + 1, st, nullptr, nullptr))) return rc;
+  if ((rc = prolong_add(P, l, P->L[l + 1].x, lv.x, lv.b, lv.r, st))) return rc;  // x += P xc, r = b
+  if ((rc = ax32(P, l, -1.0f, lv.x, lv.r, st))) return rc;                       // r = b - A x
+  k_scaled<<<g, 256, 0, st>>>(n, lv.r, lv.dinv, c0, lv.d);
+  if ((rc = ax32(P, l, -1.0f, lv.d, lv.r, st))) return rc;  // r -= A d
+  k_post2<<<g, 256, 0, st>>>(n, c1, c2, lv.dinv, lv.r, lv.d, lv.x, out64);
+  SEM_LAUNCH_CHECK("post-smoothing");
+  return SEM_OK;
 }
 
 int power_lambda(sem_pmg *P, int l, cudaStream_t st) {
@@ -1022,7 +1135,13 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
   if (!rc) rc = sem_pcg_workspace_bytes(cm, &cwb);
   if (!rc) rc = alloc((void **)&P->cb, sizeof(double) * cm->n_unique);
   if (!rc) rc = alloc((void **)&P->cx, sizeof(double) * cm->n_unique);
+  const bool persistent = cm->K1 && !cm->det_w;  // atomic assembly only: deterministic mode keeps its order
+  if (persistent) cwb = std::max(cwb, sem_pcg_n1_workspace_bytes(cm));
   if (!rc) rc = alloc(&P->cws, cwb);
+  if (!rc && persistent) {
+    rc = alloc((void **)&P->cdinv, sizeof(double) * cm->n_unique);
+    if (!rc) rc = sem_jacobi_inv_mode(cm, h1, h2, o->mask_mode ? 0 : 1, P->cdinv, st);
+  }
   // outer FCG vectors on the fine level
   const int64_t nU = m->n_unique;
   double **vecs[] = {&P->r, &P->z, &P->zn, &P->p, &P->w};
@@ -1062,6 +1181,10 @@ extern "C" int sem_pmg_vcycle(sem_pmg *P, const double *r_g, double *z_g, void *
   cudaStream_t st = as_stream(stream);
   PmgLevel &lv = P->L[0];
   const int64_t n = lv.m->n_unique;
+  if (P->o.cheb_degree == 2) {
+    if (int rc = vcycle2(P, 0, st, r_g, z_g)) return rc;
+    return check_err(P, st);
+  }
   k_d2f<<<grid_for(n, 256), 256, 0, st>>>(n, r_g, lv.b);
   if (int rc = vcycle(P, 0, st)) return rc;
   k_f2d<<<grid_for(n, 256), 256, 0, st>>>(n, lv.x, z_g);
