@@ -346,6 +346,8 @@ typedef struct {
   int iters_T, iters_p, iters_u[3];
   double step_ms;            /* host wall time of the step */
   int status;                /* SEM_OK or SEM_ERR_NOT_CONVERGED (a solve hit maxit) */
+  double ms_explicit, ms_T, ms_p, ms_u; /* host wall time of the phases: explicit terms and
+                                           wall term, temperature, pressure, velocity */
 } sem_step_stats;
 
 typedef struct {

@@ -90,7 +90,9 @@ class sem_rbc_params(ctypes.Structure):
 
 class sem_step_stats(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int), ("iters_T", ctypes.c_int), ("iters_p", ctypes.c_int),
-                ("iters_u", ctypes.c_int * 3), ("step_ms", ctypes.c_double), ("status", ctypes.c_int)]
+                ("iters_u", ctypes.c_int * 3), ("step_ms", ctypes.c_double), ("status", ctypes.c_int),
+                ("ms_explicit", ctypes.c_double), ("ms_T", ctypes.c_double), ("ms_p", ctypes.c_double),
+                ("ms_u", ctypes.c_double)]
 
 
 class sem_rbc_view(ctypes.Structure):
@@ -526,7 +528,8 @@ def sem_bdf_ext_step(s: RBC, stream=None, raise_on_error: bool = True) -> dict:
     if rc != SEM_OK and (raise_on_error or rc != SEM_ERR_NOT_CONVERGED):
         _check(rc)
     return {"step": st.step, "iters_T": st.iters_T, "iters_p": st.iters_p, "iters_u": list(st.iters_u),
-            "step_ms": st.step_ms, "status": st.status}
+            "step_ms": st.step_ms, "status": st.status, "ms_explicit": st.ms_explicit, "ms_T": st.ms_T,
+            "ms_p": st.ms_p, "ms_u": st.ms_u}
 
 
 def sem_rbc_fields(s: RBC) -> dict:

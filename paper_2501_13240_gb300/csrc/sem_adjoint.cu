@@ -34,6 +34,8 @@ struct sem_tadv {
   double *R = nullptr, *Tb = nullptr, *TbL = nullptr, *wb = nullptr;
   double *uL[3] = {}, *g[3] = {}, *aL = nullptr, *bL = nullptr, *rhs = nullptr, *x = nullptr;
   double *scal = nullptr;
+  double *dinv[2] = {};  // Jacobi inverses of H for the two BDF coefficients b0 (1 and 3/2)
+  double key[2] = {-1.0, -1.0};
   void *ws = nullptr;
   size_t ws_bytes = 0;
   std::vector<void *> owned;
@@ -153,7 +155,13 @@ int solve(sem_tadv *t, double h2, const double *b, double *x, int *iters, cudaSt
   o.timeout_s = 0.0;
   o.mask_mode = 0;
   sem_solve_stats stt;
-  int rc = sem_pcg_solve(t->m, t->prm.kappa, h2, b, x, &o, t->ws, &stt, (void *)st);
+  int slot = (t->key[0] == h2) ? 0 : (t->key[1] == h2) ? 1 : -1;
+  if (slot < 0) {  // not cached: fill the slot of this coefficient's step kind
+    slot = (h2 == t->key[0] || t->key[0] < 0.0) ? 0 : 1;
+    if (int rc = sem_jacobi_inv_mode(t->m, t->prm.kappa, h2, 1, t->dinv[slot], st)) return rc;
+    t->key[slot] = h2;
+  }
+  int rc = sem_pcg_solve_ex(t->m, t->prm.kappa, h2, b, x, &o, t->ws, &stt, (void *)st, 1, t->dinv[slot]);
   if (iters) *iters = stt.iterations;
   return rc;
 }
@@ -218,7 +226,7 @@ extern "C" int sem_tadv_create(const sem_mesh *m, const sem_tadv_params *prm, vo
     return SEM_OK;
   };
   int rc = SEM_OK;
-  double **uvecs[] = {&t->Tb, &t->rhs, &t->x};
+  double **uvecs[] = {&t->Tb, &t->rhs, &t->x, &t->dinv[0], &t->dinv[1]};
   for (double **p : uvecs)
     if (!rc) rc = alloc(p, t->nU);
   double **evecs[] = {&t->TbL, &t->wb, &t->uL[0], &t->uL[1], &t->uL[2],

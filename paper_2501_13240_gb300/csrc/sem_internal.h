@@ -109,9 +109,11 @@ int sem_pcg_n1_persistent(const sem_mesh *m, double h1, double h2, const double 
 int sem_launch_gather_add_f(const sem_mesh *m, const float *wL, float *w, cudaStream_t st);
 int sem_launch_diag_local(const sem_mesh *m, double h1, double h2, double *dL, cudaStream_t st);
 
+// dinv: the Jacobi inverse of (h1, h2) for the solve's mask mode, computed by
+// the caller and reused across solves (nullptr: computed here, each call)
 int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
                      const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats, void *stream,
-                     int check_every);
+                     int check_every, const double *dinv = nullptr);
 
 int sem_jacobi_inv_mode(const sem_mesh *m, double h1, double h2, int use_mask, double *dinv_g, cudaStream_t st);
 

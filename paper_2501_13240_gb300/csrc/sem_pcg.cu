@@ -326,7 +326,7 @@ extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const doub
 // iterations past the first one that meets the tolerance.
 int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
                      const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats, void *stream,
-                     int check_every) {
+                     int check_every, const double *dinv_given) {
   SemRange nvtx_range("sem_pcg_solve_ex");
   if (int rc = check_mesh(m, "sem_pcg_solve")) return rc;
   if (check_every < 1) check_every = 1;
@@ -357,9 +357,12 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
   int rc;
   const bool masked = opts->mask_mode == 0;
   const int32_t *map = masked ? m->l2gm : m->l2g;
-  k_jacobi_inv<<<grid_for(m->n_unique, 256), 256, 0, st>>>(m->n, m->n_unique, m->gs_off, m->gs_perm, m->mask, m->dD,
-                                                            m->G, m->B, h1, h2, masked ? 1 : 0, wk.dinv);
-  SEM_LAUNCH_CHECK("k_jacobi_inv");
+  const double *dinv = dinv_given ? dinv_given : wk.dinv;
+  if (!dinv_given) {
+    k_jacobi_inv<<<grid_for(m->n_unique, 256), 256, 0, st>>>(m->n, m->n_unique, m->gs_off, m->gs_perm, m->mask,
+                                                              m->dD, m->G, m->B, h1, h2, masked ? 1 : 0, wk.dinv);
+    SEM_LAUNCH_CHECK("k_jacobi_inv");
+  }
   // Solve the system scaled by an exact power of two so that ||b|| ~ 1: the
   // iteration is unchanged in binary64 (power-of-two scaling is exact) and
   // the double-float operator stays inside the binary32 exponent range.
@@ -371,7 +374,7 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
   SEM_CUDA(cudaStreamSynchronize(st));
   double scale = 1.0;
   if (hs.bb > 0.0 && std::isfinite(hs.bb)) scale = std::ldexp(1.0, std::ilogb(sqrt(hs.bb)));
-  k_pcg_init<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, 1.0 / scale, x_g, wk.r, wk.p, wk.dinv, wk.part_a,
+  k_pcg_init<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, 1.0 / scale, x_g, wk.r, wk.p, dinv, wk.part_a,
                                                  wk.part_b);
   k_pcg_init_finish<<<1, kUpdThreads, 0, st>>>(wk.part_a, wk.part_b, kUpdBlocks, wk.s);
   SEM_LAUNCH_CHECK("k_pcg_init");
@@ -403,9 +406,9 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
     SEM_CUDA(cudaMemsetAsync(wk.w, 0, sizeof(double) * nU, st));
     if ((rc = sem_launch_ax_assembled(m, h1, h2, wk.p, wk.w, wk.pw_part, opts->precision, st, map)) != SEM_OK)
       return rc;
-    k_pcg_update1<<<nblk, kUpdThreads, 0, st>>>(nU, x_g, wk.r, wk.p, wk.w, wk.dinv, wk.pw_part, n_pw, wk.s, par,
+    k_pcg_update1<<<nblk, kUpdThreads, 0, st>>>(nU, x_g, wk.r, wk.p, wk.w, dinv, wk.pw_part, n_pw, wk.s, par,
                                                 wk.part_a, wk.part_b);
-    k_pcg_update2<<<nblk, kUpdThreads, 0, st>>>(nU, wk.r, wk.p, wk.dinv, wk.part_a, wk.part_b, nblk, wk.s, par);
+    k_pcg_update2<<<nblk, kUpdThreads, 0, st>>>(nU, wk.r, wk.p, dinv, wk.part_a, wk.part_b, nblk, wk.s, par);
     SEM_LAUNCH_CHECK("pcg iteration");
     if (it % check_every != 0 && it != opts->maxit) continue;
     SEM_CUDA(cudaMemcpyAsync(&hs, wk.s, sizeof(hs), cudaMemcpyDeviceToHost, st));

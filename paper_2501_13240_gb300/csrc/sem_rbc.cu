@@ -44,6 +44,10 @@ struct sem_rbc {
   void *ws = nullptr;
   size_t ws_bytes = 0;
   sem_pmg *pmg = nullptr;  // pressure preconditioner (pure Neumann hierarchy)
+  // Jacobi inverses of the two Helmholtz operators, recomputed only when
+  // their coefficients change (the first step's BDF1 b0 differs)
+  double *dinvT = nullptr, *dinvU = nullptr;
+  double keyT[2] = {-1.0, -1.0}, keyU[2] = {-1.0, -1.0};
   std::vector<void *> owned;
 };
 
@@ -186,7 +190,7 @@ int gather(sem_rbc *s, const double *vL, double *vg, bool masked, cudaStream_t s
 }
 
 int solve(sem_rbc *s, double h1, double h2, const double *b, double *x, int mask_mode, int *iters,
-          cudaStream_t st) {
+          cudaStream_t st, double *dinv = nullptr, double *key = nullptr) {
   sem_solver_opts o;
   o.tol = s->prm.tol;
   o.maxit = s->prm.maxit;
@@ -194,7 +198,12 @@ int solve(sem_rbc *s, double h1, double h2, const double *b, double *x, int mask
   o.timeout_s = 0.0;
   o.mask_mode = mask_mode;
   sem_solve_stats stt;
-  int rc = sem_pcg_solve(s->m, h1, h2, b, x, &o, s->ws, &stt, (void *)st);
+  if (dinv && (key[0] != h1 || key[1] != h2)) {
+    if (int rc = sem_jacobi_inv_mode(s->m, h1, h2, mask_mode == 0 ? 1 : 0, dinv, st)) return rc;
+    key[0] = h1;
+    key[1] = h2;
+  }
+  int rc = sem_pcg_solve_ex(s->m, h1, h2, b, x, &o, s->ws, &stt, (void *)st, 1, dinv);
   *iters = stt.iterations;
   return rc;
 }
@@ -239,8 +248,10 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
     return SEM_OK;
   };
   int rc = SEM_OK;
-  double **uvecs[] = {&s->u[0], &s->u[1], &s->u[2], &s->up[0], &s->up[1], &s->up[2], &s->T, &s->Tp, &s->p,
-                      &s->W, &s->Wp, &s->Tb, &s->rhs, &s->x, &s->Tn, &s->un[0], &s->un[1], &s->un[2]};
+  double **uvecs[] = {&s->u[0],  &s->u[1], &s->u[2], &s->up[0], &s->up[1], &s->up[2],
+                      &s->T,     &s->Tp,   &s->p,    &s->W,     &s->Wp,    &s->Tb,
+                      &s->rhs,   &s->x,    &s->Tn,   &s->un[0], &s->un[1], &s->un[2],
+                      &s->dinvT, &s->dinvU};
   for (double **p : uvecs)
     if (!rc) rc = alloc(p, s->nU);
   double **evecs[] = {&s->uL[0], &s->uL[1], &s->uL[2], &s->upL[0], &s->upL[1], &s->upL[2], &s->TL, &s->TpL,
@@ -387,6 +398,14 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
     if ((rc = sem_launch_scatter(m, s->up[c], s->upL[c], st))) return rc;
   if ((rc = sem_launch_scatter(m, s->Tp, s->TpL, st))) return rc;
 
+  SEM_CUDA(cudaStreamSynchronize(st));
+  auto lap = [&, tl = t0]() mutable {
+    const auto now = std::chrono::steady_clock::now();
+    const double ms = std::chrono::duration<double, std::milli>(now - tl).count();
+    tl = now;
+    return ms;
+  };
+  stt->ms_explicit = lap();
   // temperature: lifting Tb, theta = T - Tb on the free nodes
   const StepCoef kc = coefficients(s->step);
   const double b0dt = kc.b0 / dt;
@@ -394,10 +413,12 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   if ((rc = sem_launch_ax_local(m, s->kappa, b0dt, s->fs[0], s->fs[1], SEM_PREC_FP64, st))) return rc;  // H Tb
   k_rhsT<<<gl, 256, 0, st>>>(nL, dt, kc, m->B, s->TL, s->TpL, s->NT, s->NTp, s->fs[1], s->tmpL);
   if ((rc = gather(s, s->tmpL, s->rhs, true, st))) return rc;
-  rc = solve(s, s->kappa, b0dt, s->rhs, s->x, 0, &stt->iters_T, st);
+  rc = solve(s, s->kappa, b0dt, s->rhs, s->x, 0, &stt->iters_T, st, s->dinvT, s->keyT);
   if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
   if (rc) stt->status = rc;
   k_axpbypcz<<<gu, 256, 0, st>>>(nU, 1.0, s->Tb, 1.0, s->x, 0.0, nullptr, s->Tn);
+  SEM_CUDA(cudaStreamSynchronize(st));
+  stt->ms_T = lap();
 
   // pressure
   for (int c = 0; c < 3; ++c)
@@ -424,6 +445,8 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
   if (rc) stt->status = rc;
   if ((rc = remove_mean(s, s->p, st))) return rc;
+  SEM_CUDA(cudaStreamSynchronize(st));
+  stt->ms_p = lap();
 
   // velocity
   if ((rc = sem_launch_scatter(m, s->p, s->tmpL, st))) return rc;
@@ -431,10 +454,12 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   for (int c = 0; c < 3; ++c) {
     k_bdiff<<<gl, 256, 0, st>>>(nL, m->B, s->fs[c], s->g[c], s->tmpL);
     if ((rc = gather(s, s->tmpL, s->rhs, true, st))) return rc;
-    rc = solve(s, s->nu, b0dt, s->rhs, s->un[c], 0, &stt->iters_u[c], st);
+    rc = solve(s, s->nu, b0dt, s->rhs, s->un[c], 0, &stt->iters_u[c], st, s->dinvU, s->keyU);
     if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
     if (rc) stt->status = rc;
   }
+  SEM_CUDA(cudaStreamSynchronize(st));
+  stt->ms_u = lap();
   // rotate histories
   for (int c = 0; c < 3; ++c) {
     std::swap(s->up[c], s->u[c]);
