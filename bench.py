@@ -46,6 +46,12 @@ DTYPES = {"df64": "f32x2 (double-float, binary64-accurate)", "fp64": "f64"}
 # operator kernel on the 64^3 workload, scaled by points from the ncu capture
 # of the 32^3-element case (traffic grows with the points streamed)
 TRAFFIC = {"df64": 9.22e9}
+# thread instructions per local point of the double-float assembled kernel
+# (smsp__inst_executed.sum x 32 / local points, same ncu capture), and the SM
+# issue limit: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (one warp
+# instruction per scheduler per clock)
+INST_PER_POINT = {"df64": 618.0}
+ISSUE_PEAK_TINST = 152 * 4 * 32 * 2.07e9 / 1e12
 
 
 def parse():
@@ -350,6 +356,12 @@ def main():
                 "algorithmic_bytes_per_launch": algo_bytes, "kernel_ms": kms,
                 "fp64_kernel": {"bound": "alu", "achieved_tflops": fp64_tf, "peak_tflops": FP64_PEAK_TFLOPS,
                                 "frac": fp64_tf / FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64 rate"}}
+    if head in INST_PER_POINT:  # what actually binds the double-float kernel: instruction issue
+        ti = INST_PER_POINT[head] * w.n_local / (kms * 1e-3) / 1e12
+        roofline["issue_view"] = {"bound": "alu", "achieved_tinst_per_s": ti, "peak_tinst_per_s": ISSUE_PEAK_TINST,
+                                  "frac": ti / ISSUE_PEAK_TINST,
+                                  "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz",
+                                  "inst_per_point_source": "ncu smsp__inst_executed.sum, ax_gs_32"}
 
     # --- end to end through the C ABI with host buffers
     pin_in = torch.from_numpy(ug_host).pin_memory()
