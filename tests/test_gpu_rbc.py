@@ -107,3 +107,38 @@ def test_rbc_32_workload_step():
         assert torch.isfinite(f[c]).all()
     st.destroy()
     gm.destroy()
+
+
+def test_rbc_32_workload_properties():
+    """Full-size properties of the 32^3-element stretched RBC workload: with
+    no perturbation the conduction state is a fixed point of the step; with
+    the seeded perturbation the velocity vanishes on the plates, the pressure
+    has zero mean and every field stays finite."""
+    w = workloads.RBC_32
+    gm = sem.mesh_from_workload(w)
+    st = sem.sem_rbc_create(gm, 1e8, 0.7, 1e-3, tol=1e-10)
+    for _ in range(2):
+        assert sem.sem_bdf_ext_step(st)["status"] == 0
+    f = sem.sem_rbc_fields(st)
+    l2g, mask = gm.maps()
+    Z = gm.field("Z").cpu().numpy()
+    z = np.zeros(gm.n_unique)
+    z[l2g] = Z
+    assert np.abs(f["T"].cpu().numpy() - (1.0 - z)).max() < 1e-10
+    assert max(float(f[c].abs().max()) for c in "uvw") < 1e-10
+    st.destroy()
+    pert = workloads.perturbation(gm.n_unique, 1e-3, seed=2)
+    st = sem.sem_rbc_create(gm, 1e8, 0.7, 1e-3, tol=1e-10, T_pert=torch.from_numpy(pert).cuda())
+    for _ in range(3):
+        assert sem.sem_bdf_ext_step(st)["status"] == 0
+    f = sem.sem_rbc_fields(st)
+    walls = mask == 0
+    for c in "uvw":
+        assert float(f[c].cpu().numpy()[walls].__abs__().max()) == 0.0
+    p = f["p"].cpu().numpy()
+    assert abs(p.mean()) < 1e-12 * max(1.0, np.abs(p).max())
+    for name in ("u", "v", "w", "T", "p"):
+        assert torch.isfinite(f[name]).all(), name
+    assert float(f["w"].abs().max()) > 0.0  # the perturbation has set the fluid moving
+    st.destroy()
+    gm.destroy()
