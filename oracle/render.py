@@ -117,3 +117,134 @@ def colorize(v: np.ndarray, vmin: float, vmax: float, iso=()) -> np.ndarray:
         line[:-1, :] |= d
     img[line] = (0, 0, 0, 255)
     return img
+
+
+# ---------------------------------------------------------------- 3-D scene
+# Readings for the overview scene (iso-surfaces T = 0.4, 0.6 in perspective,
+# with the box walls behind them):
+# * the field is resampled at the cell centres of an R_x x R_y x R_z grid of
+#   the undeformed box (x_i = (i + 1/2) L_x / R_x), each value the SEM
+#   polynomial there, and read back by trilinear interpolation (index
+#   coordinate g = x R / L - 1/2, clamped to [0, R - 1]);
+# * pinhole camera: f = (target - eye)/|.|, r = (f x up)/|.|, u = r x f; the
+#   ray through pixel (px, py) has direction f + s_x r + s_y u normalised,
+#   s_x = (2 (px + 1/2)/W - 1) tan(fov/2) W/H, s_y = (2 (py + 1/2)/H - 1)
+#   tan(fov/2) (row 0 at the bottom);
+# * the ray enters and leaves the box at t0 = max(0, slab entries) and t1 =
+#   min(slab exits); no intersection: white, depth -1;
+# * samples at t0 + s h, h = min_d L_d / R_d, s = 0 .. floor((t1 - t0)/h);
+#   the first sample interval in which v - level changes sign (>= 0 against
+#   < 0) for some level is the hit, at t = t_{s-1} + h a/(a - b) (a, b the
+#   values of v - level at the two ends), the earliest such t among levels;
+#   its colour is the colour map at the level, times the depth cue
+#   1 - (t - t_near)/(2 (t_far - t_near)) clamped to [1/2, 1] (t_near, t_far:
+#   nearest and farthest box corner from the eye); depth = t;
+# * a ray through the box without a hit shows the colour map of the last
+#   sample times 0.35 (the walls behind); depth -1.
+
+def resample(m: Mesh, u_g: np.ndarray, R) -> np.ndarray:
+    """[R_z, R_y, R_x] values of the field at the cell centres."""
+    n = m.N + 1
+    ks, ls = [], []
+    for d in range(3):
+        x = (np.arange(R[d]) + 0.5) * m.L[d] / R[d]
+        k, s = locate(interfaces(m, d), x)
+        ks.append(k)
+        ls.append(lagrange(m.xi, s))
+    uL = u_g[m.l2g].reshape(m.E, n, n, n)  # [e, k, j, i]
+    out = np.zeros((R[2], R[1], R[0]))
+    for c in range(R[2]):
+        for b in range(R[1]):
+            for a in range(R[0]):
+                e = ks[0][a] + m.nel[0] * (ks[1][b] + m.nel[1] * ks[2][c])
+                out[c, b, a] = np.einsum("kji,i,j,k->", uL[e], ls[0][a], ls[1][b], ls[2][c])
+    return out
+
+
+def trilinear(vol: np.ndarray, L, p) -> float:
+    R = (vol.shape[2], vol.shape[1], vol.shape[0])
+    i0, f = [0, 0, 0], [0.0, 0.0, 0.0]
+    for d in range(3):
+        g = min(max(p[d] * R[d] / L[d] - 0.5, 0.0), R[d] - 1.0)
+        i0[d] = min(int(np.floor(g)), R[d] - 2) if R[d] > 1 else 0
+        f[d] = g - i0[d] if R[d] > 1 else 0.0
+    v = 0.0
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                w = (f[0] if dx else 1 - f[0]) * (f[1] if dy else 1 - f[1]) * (f[2] if dz else 1 - f[2])
+                if w != 0.0:
+                    v += w * vol[i0[2] + dz, i0[1] + dy, i0[0] + dx]
+    return v
+
+
+def colour(v: float, vmin: float, vmax: float) -> np.ndarray:
+    t = min(max((v - vmin) / (vmax - vmin), 0.0), 1.0)
+    if t < 0.5:
+        return COOL + 2.0 * t * (MID - COOL)
+    return MID + (2.0 * t - 1.0) * (WARM - MID)
+
+
+def render_scene(vol: np.ndarray, L, eye, target, up, fov_deg, W, H, vmin, vmax, iso, pixels=None):
+    """(depth [H, W], rgba [H, W, 4]) of the iso-surface scene, or the values
+    at the listed pixels only."""
+    eye, target, up = (np.asarray(v, dtype=np.float64) for v in (eye, target, up))
+    fw = target - eye
+    fw /= np.linalg.norm(fw)
+    rt = np.cross(fw, up)
+    rt /= np.linalg.norm(rt)
+    uu = np.cross(rt, fw)
+    tanh_ = np.tan(np.radians(fov_deg) / 2.0)
+    R = (vol.shape[2], vol.shape[1], vol.shape[0])
+    h = min(L[d] / R[d] for d in range(3))
+    corners = [np.array([x, y, z]) for x in (0.0, L[0]) for y in (0.0, L[1]) for z in (0.0, L[2])]
+    dist = [float(np.linalg.norm(c - eye)) for c in corners]
+    tn, tf = min(dist), max(dist)
+    whole = pixels is None
+    if whole:
+        pixels = [(px, py) for py in range(H) for px in range(W)]
+    depth = np.full(len(pixels), -1.0)
+    rgba = np.zeros((len(pixels), 4), dtype=np.uint8)
+    for q, (px, py) in enumerate(pixels):
+        sx = (2.0 * (px + 0.5) / W - 1.0) * tanh_ * W / H
+        sy = (2.0 * (py + 0.5) / H - 1.0) * tanh_
+        dr = fw + sx * rt + sy * uu
+        dr /= np.linalg.norm(dr)
+        t0, t1 = 0.0, np.inf
+        for d in range(3):
+            if dr[d] != 0.0:
+                ta, tb = (0.0 - eye[d]) / dr[d], (L[d] - eye[d]) / dr[d]
+                t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+            elif not (0.0 <= eye[d] <= L[d]):
+                t1 = -1.0
+        if t1 < t0:
+            rgba[q] = (255, 255, 255, 255)
+            continue
+        S = int(np.floor((t1 - t0) / h))
+        prev = trilinear(vol, L, eye + t0 * dr)
+        hit = None
+        for s in range(1, S + 1):
+            ts = t0 + s * h
+            cur = trilinear(vol, L, eye + ts * dr)
+            best = None
+            for lvl in iso:
+                a, b = prev - lvl, cur - lvl
+                if (a >= 0.0) != (b >= 0.0):
+                    tq = ts - h + h * a / (a - b)
+                    if best is None or tq < best[0]:
+                        best = (tq, lvl)
+            if best is not None:
+                hit = best
+                break
+            prev = cur
+        if hit is not None:
+            shade = min(max(1.0 - (hit[0] - tn) / (2.0 * (tf - tn)), 0.5), 1.0)
+            c = colour(hit[1], vmin, vmax) * shade
+            depth[q] = hit[0]
+        else:
+            c = colour(prev, vmin, vmax) * 0.35
+        rgba[q, :3] = np.floor(c + 0.5).astype(np.uint8)
+        rgba[q, 3] = 255
+    if whole:
+        return depth.reshape(H, W), rgba.reshape(H, W, 4)
+    return depth, rgba
