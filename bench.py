@@ -452,6 +452,21 @@ def main():
             rms = 1e3 * (time.perf_counter() - t0) / 5
             render[name] = {"ms": rms, "mpixel_per_s": 4096 * 4096 / (rms * 1e-3) / 1e6}
             del vals, rgba
+        # the overview scene: iso-surfaces 0.4 and 0.6 in perspective, 4096 x 2048
+        # pixels, field resampled to 256^3
+        sv = torch.empty((256, 256, 256), dtype=torch.float32, device="cuda")
+        sd = torch.empty((2048, 4096), dtype=torch.float32, device="cuda")
+        sr = torch.empty((2048, 4096, 4), dtype=torch.uint8, device="cuda")
+        cam = ((2.2, -1.6, 1.6), (0.5, 0.5, 0.45), (0.0, 0.0, 1.0), 35.0)
+        for _ in range(2):
+            sem.sem_render_scene(rm, T, *cam, 4096, 2048, (256, 256, 256), 0.0, 1.0, (0.4, 0.6), sv, sd, sr)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            sem.sem_render_scene(rm, T, *cam, 4096, 2048, (256, 256, 256), 0.0, 1.0, (0.4, 0.6), sv, sd, sr)
+        rms = 1e3 * (time.perf_counter() - t0) / 3
+        render["iso_scene_4096x2048_grid256"] = {"ms": rms, "hit_fraction": float((sd >= 0).float().mean())}
+        del sv, sd, sr
         rbc["render_4096x4096"] = render
         rs.destroy()
         rm.destroy()

@@ -489,6 +489,36 @@ typedef struct {
 int sem_render_slice(const sem_mesh *m, const double *u_g, const sem_slice_desc *desc, float *values,
                      uint8_t *rgba, void *stream);
 
+/* The overview scene: iso-surfaces of a field in perspective, the box walls
+ * behind them. The field (u_g, device, n_unique doubles) is resampled at the
+ * cell centres of a grid[0] x grid[1] x grid[2] grid of the undeformed box
+ * (each value the SEM polynomial there, binary32) into `volume` (caller-owned
+ * device, [grid[2]][grid[1]][grid[0]] floats). Pinhole camera: f = target -
+ * eye, r = f x up, u = r x f (normalised); pixel (px, py) looks along f +
+ * s_x r + s_y u, s_x = (2 (px + 1/2)/width - 1) tan(fov/2) width/height,
+ * s_y = (2 (py + 1/2)/height - 1) tan(fov/2) (row 0 at the bottom). Each ray
+ * enters the box at t0 and leaves at t1 and is sampled every h = min(L_d /
+ * grid[d]) from t0 with trilinear interpolation of the grid; the first sample
+ * interval where v - level changes sign for some level is the hit, at the
+ * linearly interpolated t. depth (width * height floats) = t, or -1 without
+ * a hit; rgba = the colour map of sem_render_slice at the level times
+ * 1 - (t - t_near)/(2 (t_far - t_near)) clamped to [1/2, 1] (nearest and
+ * farthest box corner), rays through the box without a hit the colour map of
+ * their last sample times 0.35, rays missing the box white. Allocates a small
+ * table per call; synchronises the stream. */
+typedef struct {
+  double eye[3], target[3], up[3];
+  double fov_deg;    /* vertical field of view, (0, 179) degrees */
+  int width, height; /* 1 .. 16384 */
+  int grid[3];       /* resampling grid, 1 .. 2048 per axis */
+  double vmin, vmax; /* colour-map range, vmax > vmin */
+  int n_iso;         /* 1 .. 4 levels */
+  double iso[4];
+} sem_scene_desc;
+
+int sem_render_scene(const sem_mesh *m, const double *u_g, const sem_scene_desc *desc, float *volume,
+                     float *depth, uint8_t *rgba, void *stream);
+
 /* Write a host RGBA image (row 0 = low end) as a binary PPM (RGB, top row =
  * high end). SEM_ERR_IO if the file cannot be written. */
 int sem_write_ppm(const char *path, const uint8_t *rgba_host, int width, int height);

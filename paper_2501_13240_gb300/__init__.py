@@ -40,7 +40,7 @@ EXPORTS = (
     "sem_rbc_create", "sem_bdf_ext_step", "sem_rbc_fields", "sem_rbc_destroy",
     "sem_rbc_state_bytes", "sem_rbc_save_state", "sem_rbc_load_state", "sem_rbc_save", "sem_rbc_load",
     "sem_tadv_create", "sem_tadv_destroy", "sem_tadv_info", "sem_tadv_step", "sem_tadv_adjoint_step",
-    "sem_tadv_nusselt", "sem_tadv_nusselt_grad", "sem_render_slice", "sem_write_ppm",
+    "sem_tadv_nusselt", "sem_tadv_nusselt_grad", "sem_render_slice", "sem_render_scene", "sem_write_ppm",
     "sem_pmg_create", "sem_pmg_lambda", "sem_pmg_vcycle", "sem_pmg_prolong", "sem_pmg_restrict",
     "sem_pmg_pcg_solve", "sem_pmg_destroy", "sem_partition_info", "sem_partition_interface",
 )
@@ -107,6 +107,13 @@ class sem_slice_desc(ctypes.Structure):
                 ("iso", ctypes.c_double * 8)]
 
 
+class sem_scene_desc(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_double * 3), ("target", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
+                ("fov_deg", ctypes.c_double), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("grid", ctypes.c_int * 3), ("vmin", ctypes.c_double), ("vmax", ctypes.c_double),
+                ("n_iso", ctypes.c_int), ("iso", ctypes.c_double * 4)]
+
+
 class sem_tadv_params(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_double), ("dt", ctypes.c_double), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("precision", ctypes.c_int)]
@@ -171,6 +178,7 @@ def lib() -> ctypes.CDLL:
         sig["sem_tadv_nusselt"] = ([_vp, _vp, ctypes.POINTER(_d), _vp], _i)
         sig["sem_tadv_nusselt_grad"] = ([_vp, _d, _vp, _vp], _i)
         sig["sem_render_slice"] = ([_vp, _vp, ctypes.POINTER(sem_slice_desc), _vp, _vp, _vp], _i)
+        sig["sem_render_scene"] = ([_vp, _vp, ctypes.POINTER(sem_scene_desc), _vp, _vp, _vp, _vp], _i)
         sig["sem_write_ppm"] = ([ctypes.c_char_p, _vp, _i, _i], _i)
         sig["sem_pmg_create"] = ([_vp, _d, _d, ctypes.POINTER(sem_pmg_opts), _vp, ctypes.POINTER(_vp)], _i)
         sig["sem_pmg_lambda"] = ([_vp, _i, ctypes.POINTER(_d)], _i)
@@ -675,6 +683,37 @@ def sem_render_slice(mesh: Mesh, u_g, axis: int, coord: float, width: int, heigh
                                   _ptr(values, torch.float32, width * height, "values"),
                                   _ptr(rgba, torch.uint8, width * height * 4, "rgba"), _stream(stream)))
     return values, rgba
+
+
+def sem_render_scene(mesh: Mesh, u_g, eye, target, up, fov_deg: float, width: int, height: int, grid,
+                     vmin: float = 0.0, vmax: float = 1.0, iso=(0.4, 0.6), volume=None, depth=None, rgba=None,
+                     stream=None):
+    """Iso-surface scene: (volume [Rz, Ry, Rx] float32, depth [H, W] float32, rgba [H, W, 4] uint8), device."""
+    import torch
+    d = sem_scene_desc()
+    for q in range(3):
+        d.eye[q], d.target[q], d.up[q] = float(eye[q]), float(target[q]), float(up[q])
+        d.grid[q] = int(grid[q])
+    d.fov_deg, d.width, d.height = float(fov_deg), int(width), int(height)
+    d.vmin, d.vmax = float(vmin), float(vmax)
+    iso = list(iso)
+    if not 1 <= len(iso) <= 4:
+        raise ValueError("1 to 4 iso-levels")
+    d.n_iso = len(iso)
+    for q, lvl in enumerate(iso):
+        d.iso[q] = float(lvl)
+    nv = int(grid[0]) * int(grid[1]) * int(grid[2])
+    if volume is None:
+        volume = torch.empty((int(grid[2]), int(grid[1]), int(grid[0])), dtype=torch.float32, device="cuda")
+    if depth is None:
+        depth = torch.empty((height, width), dtype=torch.float32, device="cuda")
+    if rgba is None:
+        rgba = torch.empty((height, width, 4), dtype=torch.uint8, device="cuda")
+    _check(lib().sem_render_scene(mesh.handle, _ptr(u_g, torch.float64, mesh.n_unique, "u_g"), ctypes.byref(d),
+                                  _ptr(volume, torch.float32, nv, "volume"),
+                                  _ptr(depth, torch.float32, width * height, "depth"),
+                                  _ptr(rgba, torch.uint8, width * height * 4, "rgba"), _stream(stream)))
+    return volume, depth, rgba
 
 
 def sem_write_ppm(path: str, rgba_host):

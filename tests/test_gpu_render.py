@@ -2,7 +2,10 @@
 boundary-layer and vertical temperature slices with iso-levels, Sec. 5.3 and
 Sec. 4.5): slice values within the binary32 bound, RGBA bytes identical except
 at pixels whose colour or contour decision lies within rounding of a
-threshold, the full-size RBC mesh on sampled pixels, and argument checks."""
+threshold, the full-size RBC mesh on sampled pixels, and argument checks;
+and the iso-surface overview scene: the resampled grid within the binary32
+bound, hit/no-hit, depth and colour agreeing with the oracle's ray march on
+all but near-tie pixels."""
 import numpy as np
 import pytest
 
@@ -118,4 +121,54 @@ def test_edges_and_invalid_arguments(tmp_path):
     sem.sem_write_ppm(str(path), host(rgba))
     data = path.read_bytes()
     assert data.startswith(b"P6\n8 6\n255\n") and len(data) == len(b"P6\n8 6\n255\n") + 8 * 6 * 3
+    gm.destroy()
+
+
+# ------------------------------------------------------------ 3-D scene
+
+def scene_field(m):
+    u = np.zeros(m.n_unique)
+    u[m.l2g] = 1.0 - m.Z / m.L[2] + 0.15 * np.sin(3.1 * m.X + 0.4) * np.cos(2.3 * m.Y) * np.sin(np.pi * m.Z / m.L[2])
+    return u
+
+
+@pytest.mark.parametrize("spec", MESHES[:2], ids=["rbc_like_N5", "deformed_N7"])
+def test_scene_matches_oracle(spec):
+    om = oracle.box_mesh(**spec)
+    gm = sem.sem_mesh_create_box(**spec)
+    u = scene_field(om)
+    R, W, H = (14, 12, 16), 40, 30
+    cam = dict(eye=(2.2, -1.6, 1.4), target=(0.5, 0.5, 0.45), up=(0.0, 0.0, 1.0), fov_deg=35.0)
+    vol, depth, rgba = sem.sem_render_scene(gm, torch.from_numpy(u).cuda(), cam["eye"], cam["target"], cam["up"],
+                                            cam["fov_deg"], W, H, R, 0.0, 1.0, (0.4, 0.6))
+    ref_vol = render.resample(om, u, R)
+    assert np.abs(host(vol) - ref_vol).max() <= 4e-6 * np.abs(ref_vol).max()
+    ref_d, ref_img = render.render_scene(ref_vol, om.L, cam["eye"], cam["target"], cam["up"], cam["fov_deg"], W, H,
+                                         0.0, 1.0, (0.4, 0.6))
+    d, img = host(depth), host(rgba)
+    h = min(om.L[q] / R[q] for q in range(3))
+    same_status = (d >= 0) == (ref_d >= 0)
+    assert same_status.mean() >= 0.98
+    both = same_status & (d >= 0)
+    assert both.sum() > 0.08 * W * H  # the levels are in view (top of the box)
+    close = np.abs(d - ref_d) <= 1e-3 * h
+    assert close[both].mean() >= 0.98
+    chan = np.abs(img.astype(int) - ref_img.astype(int)).max(axis=-1)
+    assert (chan[same_status & (close | (d < 0))] <= 1).mean() >= 0.98
+    assert (img[..., 3] == 255).all()
+    gm.destroy()
+
+
+def test_scene_background_and_arguments():
+    spec = MESHES[0]
+    gm = sem.sem_mesh_create_box(**spec)
+    u = torch.ones(gm.n_unique, dtype=torch.float64, device="cuda") * 0.25
+    _, depth, rgba = sem.sem_render_scene(gm, u, (3.0, 3.0, 3.0), (6.0, 6.0, 6.0), (0, 0, 1), 40.0, 8, 6, (4, 4, 4))
+    assert (host(depth) == -1).all() and (host(rgba) == 255).all()
+    with pytest.raises(sem.SemError):
+        sem.sem_render_scene(gm, u, (0.5, 0.5, 3.0), (0.5, 0.5, 3.0), (0, 0, 1), 40.0, 8, 6, (4, 4, 4))  # eye = target
+    with pytest.raises(sem.SemError):
+        sem.sem_render_scene(gm, u, (0.5, 0.5, 3.0), (0.5, 0.5, 0.0), (0, 0, 1), 40.0, 8, 6, (4, 4, 4))  # up || view
+    with pytest.raises(sem.SemError):
+        sem.sem_render_scene(gm, u, (0.5, 0.5, 3.0), (0.5, 0.5, 0.0), (0, 1, 0), 40.0, 8, 6, (0, 4, 4))
     gm.destroy()
