@@ -272,6 +272,9 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        # replicas: the scaling run measures the headline step only (the
+        # solver, RBC, adjoint and rendering sections are single-GPU reports)
+        args.no_pcg = args.no_rbc = args.no_adjoint = True
 
     def barrier():
         if dist is not None:
