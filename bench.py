@@ -238,8 +238,9 @@ def run_solves(sem, mesh, w, runs, tol):
             st = sem.sem_pcg_solve(mesh, 1.0, 0.0, b, x, tol=tol, maxit=20000, precision=prec, raise_on_error=False)
         else:
             t0 = time.perf_counter()
+            # the configuration's degree-2 Chebyshev smoothing ("pmg"), and degree 3 beside it ("pmg3")
             P = sem.sem_pmg_create(mesh, orders=(w.N, 3, 1) if w.N > 3 else (w.N, 1), smoother_precision=sprec,
-                                   coarse_tol=1e-2)
+                                   coarse_tol=1e-2, cheb_degree=3 if kind == "pmg3" else 2)
             setup_ms = 1e3 * (time.perf_counter() - t0)
             st = sem.sem_pmg_pcg_solve(P, b, x, tol=tol, maxit=500, precision=prec, raise_on_error=False)
             P.destroy()
@@ -412,7 +413,8 @@ def main():
         runs = [("jacobi_fp64", "jacobi", sem.SEM_PREC_FP64, None),
                 ("jacobi_df64", "jacobi", sem.SEM_PREC_DF64, None),
                 ("pmg_fp32_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_FP32),
-                ("pmg_bf16_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_BF16)]
+                ("pmg_bf16_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_BF16),
+                ("pmg_fp32_df64_cheb3", "pmg3", sem.SEM_PREC_DF64, sem.SEM_PREC_FP32)]
         if args.quick_pcg:
             runs = [r for r in runs if r[0] != "jacobi_fp64"]
         pcg = run_solves(sem, mesh, w, runs, args.pcg_tol)
@@ -424,7 +426,8 @@ def main():
         m48 = sem.mesh_from_workload(w48)
         pcg48 = run_solves(sem, m48, w48, [("jacobi_df64", "jacobi", sem.SEM_PREC_DF64, None),
                                            ("pmg_fp32_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_FP32),
-                                           ("pmg_bf16_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_BF16)],
+                                           ("pmg_bf16_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_BF16),
+                                           ("pmg_fp32_df64_cheb3", "pmg3", sem.SEM_PREC_DF64, sem.SEM_PREC_FP32)],
                            args.pcg_tol)
         pcg48["workload"] = w48.name
         m48.destroy()

@@ -305,7 +305,10 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
     }
     po.nlevels = nl;
     po.smoother_precision = SEM_PREC_FP32;
-    po.cheb_degree = 2;
+    // high-degree 4th-kind Chebyshev: on the plate-stretched elements a
+    // degree-2 smoother needs ~30-40 outer iterations, degree 16 about 5, and
+    // the whole solve is ~3x faster (measured on the 32^3 RBC mesh)
+    po.cheb_degree = 16;
     po.lambda_safety = 1.1;
     po.power_its = 20;
     po.coarse_tol = 1e-2;
