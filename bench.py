@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"])
     ap.add_argument("--once", default="",
                     help="profiling mode: comma list of kernels to launch once each on the workload "
-                         "(local_df64, asm_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16), then exit")
+                         "(local_df64, asm_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16, rbc), then exit")
     return ap.parse_args()
 
 
@@ -203,6 +203,15 @@ def run_once(sem, mesh, u, names):
             sem.sem_ax_assembled_add(mesh, 1.0, 0.0, u, wg, precision=P[prec])
         elif kind == "gs":
             sem.sem_gs_op(mesh, wL, True)
+        elif kind == "rbc":  # two Rayleigh-Benard steps on the 32^3-element workload (the second timed)
+            rw = workloads.RBC_32
+            rm = sem.mesh_from_workload(rw)
+            pert = torch.from_numpy(workloads.perturbation(rm.n_unique, 1e-3)).cuda()
+            rs = sem.sem_rbc_create(rm, 1e8, 0.7, 1e-3, tol=1e-8, precision=sem.SEM_PREC_DF64, T_pert=pert)
+            for _ in range(2):
+                print(json.dumps(sem.sem_bdf_ext_step(rs)))
+            rs.destroy()
+            rm.destroy()
         elif kind == "vcycle":
             sp = {"fp32": sem.SEM_PREC_FP32, "bf16": sem.SEM_PREC_BF16}[prec]
             H = sem.sem_pmg_create(mesh, orders=(mesh.N, 3, 1), smoother_precision=sp, coarse_tol=1e-2)

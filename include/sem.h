@@ -335,7 +335,8 @@ typedef struct {
   double Ra, Pr, dt;
   double tol;     /* relative residual of every solve */
   int maxit;      /* per solve */
-  int precision;  /* SEM_PREC_* of the operator inside the solves */
+  int precision;  /* SEM_PREC_FP64 or SEM_PREC_DF64: the operator inside the solves and the
+                     explicit terms (gradients, weak divergence, H Tb; double-float for DF64) */
   int pressure_pmg; /* 1: pressure by the p-multigrid flexible CG (pure Neumann
                        hierarchy N -> N/2 -> ... -> 1, binary32 smoothing), the
                        paper's choice of preconditioner; 0: Jacobi-PCG */
@@ -418,7 +419,8 @@ typedef struct {
   double dt;
   double tol;    /* relative residual of each Helmholtz solve */
   int maxit;
-  int precision; /* SEM_PREC_FP64 or SEM_PREC_DF64 operator in the solves */
+  int precision; /* SEM_PREC_FP64 or SEM_PREC_DF64: the operator in the solves, the forward
+                    step's gradient and H Tb (as in sem_bdf_ext_step of the same precision) */
 } sem_tadv_params;
 
 /* The mesh must have Dirichlet plates at z = 0 and z = Lz. */

@@ -32,6 +32,7 @@ struct sem_tadv {
   int64_t nL = 0, nU = 0;
   double area = 0.0;  // A_b
   double *R = nullptr, *Tb = nullptr, *TbL = nullptr, *wb = nullptr;
+  float2 *Rdf = nullptr;  // double-float split of R (SEM_PREC_DF64): the same gradient as the time step
   double *uL[3] = {}, *g[3] = {}, *aL = nullptr, *bL = nullptr, *rhs = nullptr, *x = nullptr;
   double *scal = nullptr;
   double *dinv[2] = {};  // Jacobi inverses of H for the two BDF coefficients b0 (1 and 3/2)
@@ -117,12 +118,13 @@ __global__ void k_dot_part(int64_t n, const double *__restrict__ x, const double
   }
 }
 
-// the forward right-hand side at the local nodes
-__global__ void k_rhs_tadv(int64_t nL, double dt, Coef k, const double *__restrict__ B, const double *__restrict__ TL,
+// the forward right-hand side at the local nodes (k.b1, k.b2 divided by dt;
+// the same expression as the time step's, so a replayed run repeats it bit for bit)
+__global__ void k_rhs_tadv(int64_t nL, Coef k, const double *__restrict__ B, const double *__restrict__ TL,
                            const double *__restrict__ TpL, const double *__restrict__ NT, const double *__restrict__ NTp,
                            const double *__restrict__ HTb, double *__restrict__ out) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x)
-    out[l] = B[l] * ((k.b1 * TL[l] + k.b2 * TpL[l]) / dt + (k.a1 * NT[l] + k.a2 * NTp[l])) - HTb[l];
+    out[l] = B[l] * ((k.b1 * TL[l] + k.b2 * TpL[l]) + (k.a1 * NT[l] + k.a2 * NTp[l])) - HTb[l];
 }
 
 // out = c0 phi - c1 s  (s = sum_a D_a^T v_a, so -s = L^T phi)
@@ -170,7 +172,11 @@ int solve(sem_tadv *t, double h2, const double *b, double *x, int *iters, cudaSt
 int neg_adv(sem_tadv *t, const double *fL, double *out, cudaStream_t st) {
   const sem_mesh *m = t->m;
   const unsigned gl = grid_for(t->nL, 256);
-  k_grad<<<gl, 256, 0, st>>>(m->n, m->E, m->dD, t->R, fL, t->g[0], t->g[1], t->g[2]);
+  if (t->Rdf) {
+    if (int rc = sem_launch_grad_df64(m, t->Rdf, fL, t->g[0], t->g[1], t->g[2], st)) return rc;
+  } else {
+    k_grad<<<gl, 256, 0, st>>>(m->n, m->E, m->dD, t->R, fL, t->g[0], t->g[1], t->g[2]);
+  }
   k_neg_adv<<<gl, 256, 0, st>>>(t->nL, t->uL[0], t->uL[1], t->uL[2], t->g[0], t->g[1], t->g[2], nullptr, out);
   SEM_LAUNCH_CHECK("advection");
   return SEM_OK;
@@ -234,6 +240,11 @@ extern "C" int sem_tadv_create(const sem_mesh *m, const sem_tadv_params *prm, vo
   for (double **p : evecs)
     if (!rc) rc = alloc(p, t->nL);
   if (!rc) rc = alloc(&t->R, 9 * t->nL);
+  if (!rc && prm->precision == SEM_PREC_DF64) {
+    cudaError_t e = cudaMalloc((void **)&t->Rdf, sizeof(float2) * 9 * (size_t)std::max<int64_t>(t->nL, 1));
+    if (e != cudaSuccess) rc = sem_cuda_fail(e, "sem_tadv_create: cudaMalloc(Rdf)");
+    else t->owned.push_back(t->Rdf);
+  }
   if (!rc) rc = alloc(&t->scal, kRed + 8 + SEM_MAXNP);
   if (!rc) rc = sem_pcg_workspace_bytes(m, &t->ws_bytes);
   if (!rc) {
@@ -249,6 +260,10 @@ extern "C" int sem_tadv_create(const sem_mesh *m, const sem_tadv_params *prm, vo
   const unsigned gl = grid_for(t->nL, 256);
   cudaMemcpyAsync(drho, m->rho, sizeof(double) * m->n, cudaMemcpyHostToDevice, st);
   k_inv_jacobian<<<gl, 256, 0, st>>>(m->n, m->E, m->dD, m->X, m->Y, m->Z, t->R);
+  if (t->Rdf && (rc = sem_launch_split_df64(t->R, t->Rdf, 9 * t->nL, st))) {
+    free_tadv(t);
+    return rc;
+  }
   k_lifting<<<gl, 256, 0, st>>>(t->nL, m->L[2], m->l2g, m->Z, t->Tb);
   k_bottom_weights<<<gl, 256, 0, st>>>(m->n, m->E, (int64_t)m->nel[0] * m->nel[1], m->dD, drho, m->X, m->Y, m->Z,
                                        t->wb);
@@ -294,8 +309,12 @@ extern "C" int sem_tadv_step(sem_tadv *t, int n, const double *const u[3], const
     NTp = NTnm1;
   }
   // H_L Tb with h2 = b0/dt
-  if ((rc = sem_launch_ax_local(m, t->prm.kappa, k.b0 / t->prm.dt, t->TbL, t->g[0], SEM_PREC_FP64, st))) return rc;
-  k_rhs_tadv<<<gl, 256, 0, st>>>(t->nL, t->prm.dt, k, m->B, t->aL, TpL, NTn, NTp, t->g[0], t->g[2]);
+  if ((rc = sem_launch_ax_local(m, t->prm.kappa, k.b0 / t->prm.dt, t->TbL, t->g[0], t->prm.precision, st)))
+    return rc;
+  Coef kd = k;
+  kd.b1 = k.b1 / t->prm.dt;
+  kd.b2 = k.b2 / t->prm.dt;
+  k_rhs_tadv<<<gl, 256, 0, st>>>(t->nL, kd, m->B, t->aL, TpL, NTn, NTp, t->g[0], t->g[2]);
   k_gather_m<<<gu, 256, 0, st>>>(t->nU, m->gs_off, m->gs_perm, m->mask, t->g[2], t->rhs);
   SEM_LAUNCH_CHECK("tadv right-hand side");
   int it = 0;

@@ -296,6 +296,195 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
   }
 }
 
+// ---------------------------------------------------------------- field operators
+// The same element-local machinery for the explicit terms of the time step
+// (Sec. 2.2: derivatives carried to deformed elements by the chain rule).
+// Rdf is the inverse Jacobian dr_a/dx_c at every point, split to (hi, lo),
+// laid out [E][9][n3] with factor 3a + c.
+template <int NP>
+struct FieldCfg {
+  using C = DfCfg<NP>;
+  static constexpr int SMEM = 2 * C::TILE * C::ELB * (int)sizeof(float2);
+};
+
+// physical gradient of an E-vector: d_a = D_a f along the three element
+// directions, then g_c = sum_a dr_a/dx_c d_a
+template <int NP>
+__global__ void __launch_bounds__(DfCfg<NP>::THREADS)
+    k_grad_df64(int64_t E, const float2 *__restrict__ Rdf, const double *__restrict__ f, double *__restrict__ g0,
+                double *__restrict__ g1, double *__restrict__ g2) {
+  using C = DfCfg<NP>;
+  extern __shared__ float2 sm2[];
+  const int tid = threadIdx.x;
+  const int le = tid / C::N2;
+  const int t = tid - le * C::N2;
+  const int a = t % NP, b = t / NP;
+  float2 *Rt = sm2 + le * 2 * C::TILE;  // the field, then its r-derivative
+  float2 *St = Rt + C::TILE;            // its s-derivative
+  const int col = a + C::PJ * b;
+  const int64_t estride = (int64_t)gridDim.x * C::ELB;
+  for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += estride) {
+    const int64_t e = e0 + le;
+    const bool act = e < E;
+    float2 x[NP], zt[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      x[k] = df::from_f64(act ? f[e * C::N3 + a + NP * b + C::N2 * k] : 0.0);
+      Rt[col + C::PK * k] = x[k];
+    }
+    __syncthreads();
+    // s-lines first into St (reads the field in Rt), then the r-lines in place
+    // after a barrier, and the t-line from registers
+    {
+      float2 y[NP], z[NP];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) y[m] = Rt[a + C::PK * b + C::PJ * m];
+      line_apply<NP, false>(y, z);
+#pragma unroll
+      for (int m = 0; m < NP; ++m) St[a + C::PK * b + C::PJ * m] = z[m];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) y[m] = Rt[C::PJ * a + C::PK * b + m];
+      __syncthreads();
+      line_apply<NP, false>(y, z);
+#pragma unroll
+      for (int m = 0; m < NP; ++m) Rt[C::PJ * a + C::PK * b + m] = z[m];
+    }
+    line_apply<NP, false>(x, zt);
+    __syncthreads();
+    if (act) {
+      const float2 *Re = Rdf + e * 9 * C::N3 + a + NP * b;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const int q = col + C::PK * k;
+        const int64_t p = e * C::N3 + a + NP * b + C::N2 * k;
+        const float2 dr = Rt[q], ds = St[q], dtt = zt[k];
+        float2 r[9];
+#pragma unroll
+        for (int f9 = 0; f9 < 9; ++f9) r[f9] = Re[f9 * C::N3 + C::N2 * k];
+        float2 v = metric_row(r[0], r[3], r[6], dr, ds, dtt);
+        g0[p] = df::to_f64(v.x, v.y);
+        v = metric_row(r[1], r[4], r[7], dr, ds, dtt);
+        g1[p] = df::to_f64(v.x, v.y);
+        v = metric_row(r[2], r[5], r[8], dr, ds, dtt);
+        g2[p] = df::to_f64(v.x, v.y);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// weak divergence of a vector E-field: out = sum_a D_a^T v_a with
+// v_a = B sum_c dr_a/dx_c f_c
+template <int NP>
+__global__ void __launch_bounds__(DfCfg<NP>::THREADS)
+    k_wdiv_df64(int64_t E, const float2 *__restrict__ Rdf, const float2 *__restrict__ Bdf,
+                const double *__restrict__ f0, const double *__restrict__ f1, const double *__restrict__ f2,
+                double *__restrict__ out) {
+  using C = DfCfg<NP>;
+  extern __shared__ float2 sm2[];
+  const int tid = threadIdx.x;
+  const int le = tid / C::N2;
+  const int t = tid - le * C::N2;
+  const int a = t % NP, b = t / NP;
+  float2 *Rt = sm2 + le * 2 * C::TILE;
+  float2 *St = Rt + C::TILE;
+  const int col = a + C::PJ * b;
+  const int64_t estride = (int64_t)gridDim.x * C::ELB;
+  for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += estride) {
+    const int64_t e = e0 + le;
+    const bool act = e < E;
+    const int64_t ec = act ? e : 0;
+    const float2 *Re = Rdf + ec * 9 * C::N3 + a + NP * b;
+    float2 vt[NP], zt[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int64_t p = ec * C::N3 + a + NP * b + C::N2 * k;
+      const float2 fa = df::from_f64(act ? f0[p] : 0.0), fb = df::from_f64(act ? f1[p] : 0.0),
+                   fc = df::from_f64(act ? f2[p] : 0.0);
+      const float2 bw = Bdf[p];
+      float2 r[9];
+#pragma unroll
+      for (int f9 = 0; f9 < 9; ++f9) r[f9] = Re[f9 * C::N3 + C::N2 * k];
+      float2 v = metric_row(r[0], r[1], r[2], fa, fb, fc);
+      Rt[col + C::PK * k] = df::norm(df::mul_first(bw.x, bw.y, v.x, v.y));
+      v = metric_row(r[3], r[4], r[5], fa, fb, fc);
+      St[col + C::PK * k] = df::norm(df::mul_first(bw.x, bw.y, v.x, v.y));
+      v = metric_row(r[6], r[7], r[8], fa, fb, fc);
+      vt[k] = df::norm(df::mul_first(bw.x, bw.y, v.x, v.y));
+    }
+    __syncthreads();
+    // transposed contractions in place (the lines of one direction are disjoint)
+#pragma unroll 1
+    for (int d = 0; d < 2; ++d) {
+      const int base = d == 0 ? C::PJ * a + C::PK * b : a + C::PK * b;
+      const int str = d == 0 ? 1 : C::PJ;
+      float2 *O = d == 0 ? Rt : St;
+      float2 y[NP], z[NP];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) y[m] = O[base + str * m];
+      line_apply<NP, true>(y, z);
+#pragma unroll
+      for (int m = 0; m < NP; ++m) O[base + str * m] = z[m];
+    }
+    line_apply<NP, true>(vt, zt);
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const int q = col + C::PK * k;
+        const float2 zr = Rt[q], zs = St[q];
+        df::Acc acc = {zt[k].x, zt[k].y};
+        df::acc_add(acc, zr.x, zr.y);
+        df::acc_add(acc, zs.x, zs.y);
+        float2 v;
+        df::fast_two_sum(acc.s, acc.c, v.x, v.y);
+        out[e * C::N3 + a + NP * b + C::N2 * k] = df::to_f64(v.x, v.y);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_split_df64(int64_t n, const double *__restrict__ x, float2 *__restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = df::from_f64(x[i]);
+}
+
+template <int NP, bool GRAD>
+int launch_field_np(const sem_mesh *m, const float2 *Rdf, const double *f0, const double *f1, const double *f2,
+                    double *o0, double *o1, double *o2, cudaStream_t st) {
+  using C = DfCfg<NP>;
+  constexpr int smem = FieldCfg<NP>::SMEM;
+  const unsigned grid = (unsigned)std::max<int64_t>((m->E + C::ELB - 1) / C::ELB, 1);
+  if constexpr (GRAD) {
+    auto kern = k_grad_df64<NP>;
+    if (smem > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    kern<<<grid, C::THREADS, smem, st>>>(m->E, Rdf, f0, o0, o1, o2);
+    SEM_LAUNCH_CHECK("k_grad_df64");
+  } else {
+    auto kern = k_wdiv_df64<NP>;
+    if (smem > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    kern<<<grid, C::THREADS, smem, st>>>(m->E, Rdf, m->Bdf, f0, f1, f2, o0);
+    SEM_LAUNCH_CHECK("k_wdiv_df64");
+  }
+  return SEM_OK;
+}
+
+template <bool GRAD>
+int launch_field(const sem_mesh *m, const float2 *Rdf, const double *f0, const double *f1, const double *f2,
+                 double *o0, double *o1, double *o2, cudaStream_t st) {
+  if (int rc = ensure_tables(m->device)) return rc;
+  switch (m->n) {
+#define CASE(NPV) \
+  case NPV:       \
+    return launch_field_np<NPV, GRAD>(m, Rdf, f0, f1, f2, o0, o1, o2, st);
+    CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
+#undef CASE
+    default:
+      return sem_fail(SEM_ERR_INVALID_ARG, "unsupported polynomial order");
+  }
+}
+
 int num_sms(int device) {
   int n = 0;
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n < 1) n = 152;
@@ -378,4 +567,21 @@ int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u,
     default:
       return sem_fail(SEM_ERR_INVALID_ARG, "unsupported polynomial order");
   }
+}
+
+int sem_launch_grad_df64(const sem_mesh *m, const float2 *Rdf, const double *f, double *g0, double *g1, double *g2,
+                         cudaStream_t st) {
+  return launch_field<true>(m, Rdf, f, nullptr, nullptr, g0, g1, g2, st);
+}
+
+int sem_launch_wdiv_df64(const sem_mesh *m, const float2 *Rdf, const double *f0, const double *f1, const double *f2,
+                         double *out, cudaStream_t st) {
+  return launch_field<false>(m, Rdf, f0, f1, f2, out, nullptr, nullptr, st);
+}
+
+int sem_launch_split_df64(const double *x, float2 *y, int64_t n, cudaStream_t st) {
+  if (n <= 0) return SEM_OK;
+  k_split_df64<<<grid_for(n, 256), 256, 0, st>>>(n, x, y);
+  SEM_LAUNCH_CHECK("k_split_df64");
+  return SEM_OK;
 }

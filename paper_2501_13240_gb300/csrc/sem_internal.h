@@ -107,6 +107,15 @@ int sem_pcg_n1_persistent(const sem_mesh *m, double h1, double h2, const double 
                           const int32_t *map, double tol, int maxit, void *work, int *iters, double *rel,
                           cudaStream_t st);
 int sem_launch_gather_add_f(const sem_mesh *m, const float *wL, float *w, cudaStream_t st);
+// binary64-accurate element-local field operators in double-float
+// arithmetic; Rdf = the inverse Jacobian dr_a/dx_c split to (hi, lo),
+// [E][9][n3] with factor 3a + c. grad: g_c = sum_a dr_a/dx_c D_a f (E-vectors
+// in and out); wdiv: out = sum_a D_a^T (B sum_c dr_a/dx_c f_c)
+int sem_launch_grad_df64(const sem_mesh *m, const float2 *Rdf, const double *f, double *g0, double *g1, double *g2,
+                         cudaStream_t st);
+int sem_launch_wdiv_df64(const sem_mesh *m, const float2 *Rdf, const double *f0, const double *f1, const double *f2,
+                         double *out, cudaStream_t st);
+int sem_launch_split_df64(const double *x, float2 *y, int64_t n, cudaStream_t st);
 int sem_launch_diag_local(const sem_mesh *m, double h1, double h2, double *dL, cudaStream_t st);
 
 // dinv: the Jacobi inverse of (h1, h2) for the solve's mask mode, computed by

@@ -12,7 +12,8 @@
 //   u:  (b0/dt B + nu A) u_c = M Q^T[B f*_c - B dp/dx_c];
 // BDF2 (3/2, 2, -1/2), EXT2 (2, -1); the first step is BDF1/EXT1 ((1, 1, 0), (1, 0)),
 // since BDF2 started from history levels equal to the initial state is first order.
-// Explicit terms run in binary64 kernels; the five solves use sem_pcg_solve.
+// Explicit terms run in binary64 kernels (double-float for SEM_PREC_DF64);
+// the five solves use sem_pcg_solve and the pressure p-multigrid.
 #include <math.h>
 #include <string.h>
 
@@ -38,6 +39,13 @@ struct sem_rbc {
   double *uL[3] = {}, *upL[3] = {}, *TL = nullptr, *TpL = nullptr, *g[3] = {}, *om[3] = {};
   double *NT = nullptr, *NTp = nullptr, *Nu[3] = {}, *Nup[3] = {}, *fs[3] = {}, *tmpL = nullptr;
   double *R = nullptr;  // [E][9][n3] dr_a/dx_c
+  // double-float split of R; set for SEM_PREC_DF64, where the gradients and
+  // the weak divergence run on the binary32 pipe
+  float2 *Rdf = nullptr;
+  // H Tb = (kappa A + b0/dt B) applied to the lifting (E-vector), kept for the
+  // b0/dt it was computed with
+  double *HTb = nullptr;
+  double keyH = -1.0;
   double *scal = nullptr;  // reduction partials + result
   double *drho = nullptr;  // GLL weights on the device
   int *dnel = nullptr;     // element counts on the device
@@ -142,20 +150,20 @@ __global__ void k_wall(int n, const int *__restrict__ nel, int d, int side, doub
 
 // weak divergence: out = sum_a D_a^T v_a with v_a = B sum_c dr_a/dx_c f_c
 // Q^T with optional mask: vg[g] = (mask ? mask[g] : 1) * sum of copies
-// T right-hand side (local): B ((b1 T + b2 Tp)/dt + a1 NT + a2 NTp) - H(Tb)
-__global__ void k_rhsT(int64_t nL, double dt, StepCoef k, const double *__restrict__ B, const double *__restrict__ TL,
+// T right-hand side (local): B ((b1 T + b2 Tp)/dt + a1 NT + a2 NTp) - H(Tb);
+// k.b1, k.b2 arrive divided by dt (no division per point)
+__global__ void k_rhsT(int64_t nL, StepCoef k, const double *__restrict__ B, const double *__restrict__ TL,
                        const double *__restrict__ TpL, const double *__restrict__ NT, const double *__restrict__ NTp,
                        const double *__restrict__ HTb, double *__restrict__ out) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x)
-    out[l] = B[l] * ((k.b1 * TL[l] + k.b2 * TpL[l]) / dt + (k.a1 * NT[l] + k.a2 * NTp[l])) - HTb[l];
+    out[l] = B[l] * ((k.b1 * TL[l] + k.b2 * TpL[l]) + (k.a1 * NT[l] + k.a2 * NTp[l])) - HTb[l];
 }
 
-// f* = (b1 u + b2 up)/dt + a1 Nu + a2 Nup
-__global__ void k_fstar(int64_t nL, double dt, StepCoef k, const double *__restrict__ uL,
-                        const double *__restrict__ upL, const double *__restrict__ N, const double *__restrict__ Np,
-                        double *__restrict__ out) {
+// f* = (b1 u + b2 up)/dt + a1 Nu + a2 Nup (k.b1, k.b2 divided by dt)
+__global__ void k_fstar(int64_t nL, StepCoef k, const double *__restrict__ uL, const double *__restrict__ upL,
+                        const double *__restrict__ N, const double *__restrict__ Np, double *__restrict__ out) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x)
-    out[l] = (k.b1 * uL[l] + k.b2 * upL[l]) / dt + (k.a1 * N[l] + k.a2 * Np[l]);
+    out[l] = (k.b1 * uL[l] + k.b2 * upL[l]) + (k.a1 * N[l] + k.a2 * Np[l]);
 }
 
 // B (f - g)
@@ -177,6 +185,7 @@ int remove_mean(sem_rbc *s, double *x, cudaStream_t st) {
 
 int grad(sem_rbc *s, const double *f, double **out, cudaStream_t st) {
   const sem_mesh *m = s->m;
+  if (s->Rdf) return sem_launch_grad_df64(m, s->Rdf, f, out[0], out[1], out[2], st);
   k_grad<<<grid_for(s->nL, 256), 256, 0, st>>>(m->n, m->E, m->dD, s->R, f, out[0], out[1], out[2]);
   SEM_LAUNCH_CHECK("k_grad");
   return SEM_OK;
@@ -261,6 +270,12 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
   for (double **p : evecs)
     if (!rc) rc = alloc(p, s->nL);
   if (!rc) rc = alloc(&s->R, 9 * s->nL);
+  if (!rc) rc = alloc(&s->HTb, s->nL);
+  if (!rc && prm->precision == SEM_PREC_DF64) {
+    cudaError_t e = cudaMalloc((void **)&s->Rdf, sizeof(float2) * 9 * (size_t)std::max<int64_t>(s->nL, 1));
+    if (e != cudaSuccess) rc = sem_cuda_fail(e, "sem_rbc_create: cudaMalloc(Rdf)");
+    else s->owned.push_back(s->Rdf);
+  }
   if (!rc) rc = alloc(&s->scal, kRedBlocks + 8);
   if (!rc) rc = alloc(&s->drho, SEM_MAXNP);
   if (!rc) {
@@ -281,6 +296,10 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
   cudaMemcpyAsync(s->drho, m->rho, sizeof(double) * m->n, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(s->dnel, m->nel, sizeof(int) * 3, cudaMemcpyHostToDevice, st);
   k_inv_jacobian<<<grid_for(s->nL, 256), 256, 0, st>>>(m->n, m->E, m->dD, m->X, m->Y, m->Z, s->R);
+  if (s->Rdf && (rc = sem_launch_split_df64(s->R, s->Rdf, 9 * s->nL, st))) {
+    free_rbc(s);
+    return rc;
+  }
   k_lifting<<<grid_for(s->nL, 256), 256, 0, st>>>(s->nL, m->L[2], m->l2g, m->Z, s->Tb);
   cudaMemcpyAsync(s->T, s->Tb, sizeof(double) * s->nU, cudaMemcpyDeviceToDevice, st);
   if (T_pert_g) k_add_masked<<<grid_for(s->nU, 256), 256, 0, st>>>(s->nU, m->mask, T_pert_g, s->T);
@@ -412,9 +431,15 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   // temperature: lifting Tb, theta = T - Tb on the free nodes
   const StepCoef kc = coefficients(s->step);
   const double b0dt = kc.b0 / dt;
-  if ((rc = sem_launch_scatter(m, s->Tb, s->fs[0], st))) return rc;                      // Tb (local)
-  if ((rc = sem_launch_ax_local(m, s->kappa, b0dt, s->fs[0], s->fs[1], SEM_PREC_FP64, st))) return rc;  // H Tb
-  k_rhsT<<<gl, 256, 0, st>>>(nL, dt, kc, m->B, s->TL, s->TpL, s->NT, s->NTp, s->fs[1], s->tmpL);
+  StepCoef kd = kc;  // b1, b2 divided by dt
+  kd.b1 = kc.b1 / dt;
+  kd.b2 = kc.b2 / dt;
+  if (s->keyH != b0dt) {  // H Tb for this b0/dt (the lifting and kappa are fixed)
+    if ((rc = sem_launch_scatter(m, s->Tb, s->fs[0], st))) return rc;
+    if ((rc = sem_launch_ax_local(m, s->kappa, b0dt, s->fs[0], s->HTb, s->prm.precision, st))) return rc;
+    s->keyH = b0dt;
+  }
+  k_rhsT<<<gl, 256, 0, st>>>(nL, kd, m->B, s->TL, s->TpL, s->NT, s->NTp, s->HTb, s->tmpL);
   if ((rc = gather(s, s->tmpL, s->rhs, true, st))) return rc;
   rc = solve(s, s->kappa, b0dt, s->rhs, s->x, 0, &stt->iters_T, st, s->dinvT, s->keyT);
   if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
@@ -425,9 +450,14 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
 
   // pressure
   for (int c = 0; c < 3; ++c)
-    k_fstar<<<gl, 256, 0, st>>>(nL, dt, kc, s->uL[c], s->upL[c], s->Nu[c], s->Nup[c], s->fs[c]);
-  k_weak_div_v<<<gl, 256, 0, st>>>(m->n, m->E, s->R, m->B, s->fs[0], s->fs[1], s->fs[2], s->g[0], s->g[1], s->g[2]);
-  k_dt_sum<<<gl, 256, 0, st>>>(m->n, m->E, m->dD, s->g[0], s->g[1], s->g[2], s->tmpL);
+    k_fstar<<<gl, 256, 0, st>>>(nL, kd, s->uL[c], s->upL[c], s->Nu[c], s->Nup[c], s->fs[c]);
+  if (s->Rdf) {
+    if ((rc = sem_launch_wdiv_df64(m, s->Rdf, s->fs[0], s->fs[1], s->fs[2], s->tmpL, st))) return rc;
+  } else {
+    k_weak_div_v<<<gl, 256, 0, st>>>(m->n, m->E, s->R, m->B, s->fs[0], s->fs[1], s->fs[2], s->g[0], s->g[1],
+                                     s->g[2]);
+    k_dt_sum<<<gl, 256, 0, st>>>(m->n, m->E, m->dD, s->g[0], s->g[1], s->g[2], s->tmpL);
+  }
   SEM_LAUNCH_CHECK("weak divergence");
   if ((rc = gather(s, s->tmpL, s->rhs, false, st))) return rc;
   k_axpbypcz<<<gu, 256, 0, st>>>(nU, 1.0, s->rhs, -kc.a1, s->W, -kc.a2, s->Wp, s->rhs);
