@@ -163,7 +163,7 @@ int solve(sem_tadv *t, double h2, const double *b, double *x, int *iters, cudaSt
     if (int rc = sem_jacobi_inv_mode(t->m, t->prm.kappa, h2, 1, t->dinv[slot], st)) return rc;
     t->key[slot] = h2;
   }
-  int rc = sem_pcg_solve_ex(t->m, t->prm.kappa, h2, b, x, &o, t->ws, &stt, (void *)st, 1, t->dinv[slot]);
+  int rc = sem_pcg_solve_ex(t->m, t->prm.kappa, h2, b, x, &o, t->ws, &stt, (void *)st, 8, t->dinv[slot]);
   if (iters) *iters = stt.iterations;
   return rc;
 }

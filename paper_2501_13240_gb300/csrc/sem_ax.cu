@@ -29,8 +29,10 @@ template <int NP, bool ASSEMBLED>
 __global__ void __launch_bounds__(AxCfg<NP>::THREADS)
     k_ax_fp64(int64_t E, const double *__restrict__ Dg, const double *__restrict__ G, const double *__restrict__ B,
               double h1, double h2, const double *__restrict__ u, double *__restrict__ w,
-              const int32_t *__restrict__ l2gm, double *__restrict__ pw_partial, double *__restrict__ wloc) {
+              const int32_t *__restrict__ l2gm, double *__restrict__ pw_partial, double *__restrict__ wloc,
+              const int *__restrict__ skip) {
   using C = AxCfg<NP>;
+  if (skip != nullptr && *skip != 0) return;
   extern __shared__ double smem[];
   double *sD = smem;  // [NP][NP+1]
   const int tid = threadIdx.x;
@@ -129,12 +131,12 @@ __global__ void __launch_bounds__(AxCfg<NP>::THREADS)
 
 template <int NP, bool ASSEMBLED>
 int launch_fp64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
-                unsigned grid, cudaStream_t st, const int32_t *map) {
+                unsigned grid, cudaStream_t st, const int32_t *map, const int *skip) {
   using C = AxCfg<NP>;
   auto kern = k_ax_fp64<NP, ASSEMBLED>;
   if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   double *wloc = ASSEMBLED ? (double *)m->det_w : nullptr;
-  kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->dD, m->G, m->B, h1, h2, u, w, map, pw_partial, wloc);
+  kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->dD, m->G, m->B, h1, h2, u, w, map, pw_partial, wloc, skip);
   SEM_LAUNCH_CHECK("k_ax_fp64");
   if (wloc) return sem_launch_gather_add(m, wloc, w, st);
   return SEM_OK;
@@ -152,19 +154,19 @@ unsigned ax_grid(const sem_mesh *m, bool assembled) {
 
 template <int NP>
 int dispatch_np(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
-                bool assembled, int precision, cudaStream_t st, const int32_t *map) {
-  if (precision == SEM_PREC_DF64) return sem_launch_ax_df64(m, h1, h2, u, w, pw_partial, assembled, st, map);
+                bool assembled, int precision, cudaStream_t st, const int32_t *map, const int *skip) {
+  if (precision == SEM_PREC_DF64) return sem_launch_ax_df64(m, h1, h2, u, w, pw_partial, assembled, st, map, skip);
   unsigned grid = ax_grid<NP>(m, assembled);
-  if (assembled) return launch_fp64<NP, true>(m, h1, h2, u, w, pw_partial, grid, st, map);
-  return launch_fp64<NP, false>(m, h1, h2, u, w, nullptr, grid, st, map);
+  if (assembled) return launch_fp64<NP, true>(m, h1, h2, u, w, pw_partial, grid, st, map, skip);
+  return launch_fp64<NP, false>(m, h1, h2, u, w, nullptr, grid, st, map, skip);
 }
 
 int dispatch(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial, bool assembled,
-             int precision, cudaStream_t st, const int32_t *map) {
+             int precision, cudaStream_t st, const int32_t *map, const int *skip = nullptr) {
   switch (m->n) {
 #define CASE(NPV) \
   case NPV:       \
-    return dispatch_np<NPV>(m, h1, h2, u, w, pw_partial, assembled, precision, st, map);
+    return dispatch_np<NPV>(m, h1, h2, u, w, pw_partial, assembled, precision, st, map, skip);
     CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
 #undef CASE
     default:
@@ -205,9 +207,10 @@ int sem_launch_ax_local(const sem_mesh *m, double h1, double h2, const double *u
 }
 
 int sem_launch_ax_assembled(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
-                            double *pw_partial, int precision, cudaStream_t st, const int32_t *map) {
-  if (m->N == 1 && m->K1) return sem_launch_ax_n1(m, h1, h2, u_g, w_g, pw_partial, precision, st, map ? map : m->l2gm);
-  return dispatch(m, h1, h2, u_g, w_g, pw_partial, true, precision, st, map ? map : m->l2gm);
+                            double *pw_partial, int precision, cudaStream_t st, const int32_t *map, const int *skip) {
+  if (m->N == 1 && m->K1)
+    return sem_launch_ax_n1(m, h1, h2, u_g, w_g, pw_partial, precision, st, map ? map : m->l2gm, skip);
+  return dispatch(m, h1, h2, u_g, w_g, pw_partial, true, precision, st, map ? map : m->l2gm, skip);
 }
 
 int sem_ax_assembled_blocks(const sem_mesh *m, int precision) {

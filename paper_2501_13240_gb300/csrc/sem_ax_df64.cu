@@ -156,8 +156,9 @@ template <int NP, bool ASSEMBLED, bool HELM>
 __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
     k_ax_df64(int64_t E, const float2 *__restrict__ Gdf, const float2 *__restrict__ Bdf, float2 h1, float2 h2,
               const double *__restrict__ u, double *__restrict__ w, const int32_t *__restrict__ l2gm,
-              double *__restrict__ pw_partial, double *__restrict__ wloc) {
+              double *__restrict__ pw_partial, double *__restrict__ wloc, const int *__restrict__ skip) {
   using C = DfCfg<NP>;
+  if (skip != nullptr && *skip != 0) return;
   extern __shared__ float2 sm2[];
   const int tid = threadIdx.x;
   const int le = tid / C::N2;
@@ -510,7 +511,7 @@ int df_grid(const sem_mesh *m, bool assembled, unsigned *grid) {
 
 template <int NP>
 int launch_np(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial, bool assembled,
-              cudaStream_t st, const int32_t *map) {
+              cudaStream_t st, const int32_t *map, const int *skip) {
   using C = DfCfg<NP>;
   unsigned grid;
   if (int rc = df_grid<NP>(m, assembled, &grid)) return rc;
@@ -522,7 +523,7 @@ int launch_np(const sem_mesh *m, double h1, double h2, const double *u, double *
     auto kern = k_ax_df64<NP, ASM, HLM>;                                                                    \
     if (C::SMEM > 48 * 1024)                                                                                \
       SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));          \
-    kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->Gdf, m->Bdf, h1d, h2d, u, w, map, pw_partial, wloc);    \
+    kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->Gdf, m->Bdf, h1d, h2d, u, w, map, pw_partial, wloc, skip); \
   } while (0)
   if (assembled) {
     if (helm) LAUNCH(true, true);
@@ -556,12 +557,12 @@ int sem_df64_grid(const sem_mesh *m) {
 }
 
 int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
-                       bool assembled, cudaStream_t st, const int32_t *map) {
+                       bool assembled, cudaStream_t st, const int32_t *map, const int *skip) {
   if (int rc = ensure_tables(m->device)) return rc;
   switch (m->n) {
 #define CASE(NPV) \
   case NPV:       \
-    return launch_np<NPV>(m, h1, h2, u, w, pw_partial, assembled, st, map);
+    return launch_np<NPV>(m, h1, h2, u, w, pw_partial, assembled, st, map, skip);
     CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
 #undef CASE
     default:

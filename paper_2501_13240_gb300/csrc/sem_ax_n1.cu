@@ -71,7 +71,9 @@ __device__ __forceinline__ double block_pw_sum(double v, double *red) {
 __global__ void __launch_bounds__(128)
     k_ax_n1_fp64(int64_t E, const double *__restrict__ K, const double *__restrict__ B, double h1, double h2,
                  const double *__restrict__ u, double *__restrict__ w, const int32_t *__restrict__ map,
-                 double *__restrict__ pw_partial, double *__restrict__ wloc) {
+                 double *__restrict__ pw_partial, double *__restrict__ wloc,
+                 const int *__restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
   __shared__ double red[32];
   double pw = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
@@ -108,7 +110,9 @@ template <bool HELM>
 __global__ void __launch_bounds__(128)
     k_ax_n1_df64(int64_t E, const float2 *__restrict__ Kdf, const float2 *__restrict__ Bdf, float2 h1, float2 h2,
                  const double *__restrict__ u, double *__restrict__ w, const int32_t *__restrict__ map,
-                 double *__restrict__ pw_partial, double *__restrict__ wloc) {
+                 double *__restrict__ pw_partial, double *__restrict__ wloc,
+                 const int *__restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
   __shared__ double red[32];
   df::Acc pw = {0.0f, 0.0f};
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
@@ -167,18 +171,18 @@ int sem_n1_prepare(sem_mesh *m, cudaStream_t st) {
 }
 
 int sem_launch_ax_n1(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g, double *pw_partial,
-                     int precision, cudaStream_t st, const int32_t *map) {
+                     int precision, cudaStream_t st, const int32_t *map, const int *skip) {
   // the grids are those sem_ax_assembled_blocks reports (one p.w partial per CTA)
   const int grid = std::max(sem_ax_assembled_blocks(m, precision), 1);
   double *wloc = (double *)m->det_w;
   if (precision == SEM_PREC_DF64) {
     const float2 h1d = split(h1), h2d = split(h2);
     if (h1 == 1.0 && h2 == 0.0)
-      k_ax_n1_df64<false><<<grid, 128, 0, st>>>(m->E, m->K1df, m->Bdf, h1d, h2d, u_g, w_g, map, pw_partial, wloc);
+      k_ax_n1_df64<false><<<grid, 128, 0, st>>>(m->E, m->K1df, m->Bdf, h1d, h2d, u_g, w_g, map, pw_partial, wloc, skip);
     else
-      k_ax_n1_df64<true><<<grid, 128, 0, st>>>(m->E, m->K1df, m->Bdf, h1d, h2d, u_g, w_g, map, pw_partial, wloc);
+      k_ax_n1_df64<true><<<grid, 128, 0, st>>>(m->E, m->K1df, m->Bdf, h1d, h2d, u_g, w_g, map, pw_partial, wloc, skip);
   } else {
-    k_ax_n1_fp64<<<grid, 128, 0, st>>>(m->E, m->K1, m->B, h1, h2, u_g, w_g, map, pw_partial, wloc);
+    k_ax_n1_fp64<<<grid, 128, 0, st>>>(m->E, m->K1, m->B, h1, h2, u_g, w_g, map, pw_partial, wloc, skip);
   }
   SEM_LAUNCH_CHECK("k_ax_n1");
   if (wloc) return sem_launch_gather_add(m, wloc, w_g, st);

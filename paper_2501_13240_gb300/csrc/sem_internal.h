@@ -83,13 +83,16 @@ int sem_gll_host(int N, double *xi, double *rho, double *D);
 int sem_launch_ax_local(const sem_mesh *m, double h1, double h2, const double *u, double *w,
                         int precision, cudaStream_t st);
 // map: local-to-unique map to gather/scatter through (nullptr: the masked
-// map l2gm; m->l2g for the unmasked operator)
+// map l2gm; m->l2g for the unmasked operator). skip: a device flag read by the
+// kernel when it starts; non-zero makes the launch a no-op (w and the p.w
+// partials untouched) so a solve can queue iterations past its stopping point
 int sem_launch_ax_assembled(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
-                            double *pw_partial, int precision, cudaStream_t st, const int32_t *map = nullptr);
+                            double *pw_partial, int precision, cudaStream_t st, const int32_t *map = nullptr,
+                            const int *skip = nullptr);
 int sem_ax_assembled_blocks(const sem_mesh *m, int precision);
 int sem_df64_grid(const sem_mesh *m);
 int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
-                       bool assembled, cudaStream_t st, const int32_t *map);
+                       bool assembled, cudaStream_t st, const int32_t *map, const int *skip = nullptr);
 int sem_launch_gs(const sem_mesh *m, double *v, int apply_mask, cudaStream_t st);
 int sem_launch_gather(const sem_mesh *m, const double *vL, double *vg, cudaStream_t st);
 int sem_launch_scatter(const sem_mesh *m, const double *vg, double *vL, cudaStream_t st);
@@ -99,7 +102,7 @@ int sem_launch_gather_add(const sem_mesh *m, const double *wL, double *w, cudaSt
 // N = 1 meshes: element matrices (set-up) and the assembled operator from them
 int sem_n1_prepare(sem_mesh *m, cudaStream_t st);
 int sem_launch_ax_n1(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g, double *pw_partial,
-                     int precision, cudaStream_t st, const int32_t *map);
+                     int precision, cudaStream_t st, const int32_t *map, const int *skip = nullptr);
 // Jacobi-PCG on an N = 1 mesh in one cooperative launch (the p-multigrid
 // coarsest level); synchronises the stream
 size_t sem_pcg_n1_workspace_bytes(const sem_mesh *m);

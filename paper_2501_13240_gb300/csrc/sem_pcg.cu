@@ -3,11 +3,17 @@
 // Poisson solve is the stiffest substep and is preconditioned).
 //
 // Vectors are U-vectors (one value per unique node). Each iteration runs
-//   w = 0; w = M Q^T A_L Q p  (fused operator, also the p.w partial sums)
+//   w = M Q^T A_L Q p  (fused operator into w = 0, also the p.w partial sums)
 //   update1: alpha = rho / p.w;  x += alpha p;  r -= alpha w;  partial r.z, r.r
-//   update2: beta = r.z / rho;   p = z + beta p   (z = dinv * r, not stored)
+//   update2: beta = r.z / rho;   p = z + beta p   (z = dinv * r, not stored);
+//            w = 0 for the next operator; the stopping test on the device
 // All reductions are two-level and in a fixed order, so for a given mesh and
 // input every scalar is reproducible except through the operator's atomics.
+// The stopping test (||r|| <= tol ||b||, or a breakdown) is taken by update2
+// itself, which records the iteration in the scalars; the kernels of later
+// iterations then return at once. The host can therefore queue several
+// iterations between reads of the scalars and still stop exactly where a
+// check after every iteration would.
 #include <math.h>
 
 #include <algorithm>
@@ -21,6 +27,7 @@
 namespace {
 
 constexpr int kUpdThreads = 256;
+constexpr int kCheckEvery = 8;  // iterations queued between host reads of the scalars
 constexpr int kUpdBlocks = 152 * 4;
 
 struct PcgScalars {
@@ -30,7 +37,8 @@ struct PcgScalars {
   double beta;
   double rr;      // r.r after the last update
   double bb;      // b.b
-  double pad;
+  int stop_it;    // 0 while running; else the iteration at which the solve stopped
+  int stop_status;  // 1: converged, 2: breakdown (written before stop_it)
 };
 
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -61,8 +69,8 @@ __device__ __forceinline__ double sum_partials(const double *__restrict__ part, 
 
 __global__ void __launch_bounds__(kUpdThreads)
     k_pcg_init(int64_t nU, const double *__restrict__ b, double inv_scale, double *__restrict__ x,
-               double *__restrict__ r, double *__restrict__ p, const double *__restrict__ dinv,
-               double *__restrict__ part_a, double *__restrict__ part_b) {
+               double *__restrict__ r, double *__restrict__ p, double *__restrict__ w,
+               const double *__restrict__ dinv, double *__restrict__ part_a, double *__restrict__ part_b) {
   __shared__ double red[32];
   double rz = 0.0, bb = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
@@ -71,6 +79,7 @@ __global__ void __launch_bounds__(kUpdThreads)
     x[g] = 0.0;
     r[g] = bv;
     p[g] = z;
+    w[g] = 0.0;
     rz = fma(bv, z, rz);
     bb = fma(bv, bv, bb);
   }
@@ -91,6 +100,8 @@ __global__ void __launch_bounds__(kUpdThreads)
     s->rho[0] = rz;
     s->bb = bb;
     s->rr = bb;
+    s->stop_it = 0;
+    s->stop_status = 0;
   }
 }
 
@@ -99,6 +110,7 @@ __global__ void __launch_bounds__(kUpdThreads)
                   const double *__restrict__ w, const double *__restrict__ dinv, const double *__restrict__ pw_part,
                   int n_pw, PcgScalars *s, int par, double *__restrict__ rz_part, double *__restrict__ rr_part) {
   __shared__ double red[32];
+  if (*(volatile const int *)&s->stop_it != 0) return;  // stopped at an earlier iteration
   const double pw = sum_partials(pw_part, n_pw, red);
   // an exactly converged iterate (p = 0) gives p.w = 0: take no step; the host
   // reports a breakdown only if the residual has not met the tolerance
@@ -126,10 +138,14 @@ __global__ void __launch_bounds__(kUpdThreads)
 }
 
 __global__ void __launch_bounds__(kUpdThreads)
-    k_pcg_update2(int64_t nU, const double *__restrict__ r, double *__restrict__ p, const double *__restrict__ dinv,
-                  const double *__restrict__ rz_part, const double *__restrict__ rr_part, int n_part, PcgScalars *s,
-                  int par) {
+    k_pcg_update2(int64_t nU, const double *__restrict__ r, double *__restrict__ p, double *__restrict__ w,
+                  const double *__restrict__ dinv, const double *__restrict__ rz_part,
+                  const double *__restrict__ rr_part, int n_part, PcgScalars *s, int par, int it, double thresh) {
   __shared__ double red[32];
+  // block 0 of this launch may record a stop at this iteration while the other
+  // blocks read the flag; only a stop at an earlier iteration skips the work
+  const int sit = *(volatile const int *)&s->stop_it;
+  if (sit != 0 && sit < it) return;
   const double rz = sum_partials(rz_part, n_part, red);
   const double rho_old = s->rho[par];
   const double beta = (rho_old != 0.0) ? rz / rho_old : 0.0;
@@ -139,10 +155,21 @@ __global__ void __launch_bounds__(kUpdThreads)
       s->rr = rr;
       s->beta = beta;
       s->rho[par ^ 1] = rz;
+      const double pw = s->pw;
+      int status = 0;
+      if (isfinite(rr) && sqrt(rr) <= thresh) status = 1;
+      else if (!(pw > 0.0) || !isfinite(pw) || !isfinite(rr)) status = 2;
+      if (status != 0) {
+        s->stop_status = status;
+        __threadfence();
+        *(volatile int *)&s->stop_it = it;
+      }
     }
   }
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
     p[g] = fma(beta, p[g], dinv[g] * r[g]);
+    w[g] = 0.0;
+  }
 }
 
 // partial sums of b.b (for the scale of the system)
@@ -317,13 +344,13 @@ extern "C" int sem_pcg_workspace_bytes(const sem_mesh *m, size_t *bytes) {
 
 extern "C" int sem_pcg_solve(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
                              const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats, void *stream) {
-  return sem_pcg_solve_ex(m, h1, h2, b_g, x_g, opts, workspace, stats, stream, 1);
+  return sem_pcg_solve_ex(m, h1, h2, b_g, x_g, opts, workspace, stats, stream, kCheckEvery);
 }
 
-// check_every: the host reads the scalars (stopping test, breakdown) only every
-// check_every iterations; the step lengths are computed on the device, so the
-// iteration itself is unchanged. A solve may then run up to check_every - 1
-// iterations past the first one that meets the tolerance.
+// check_every: the host reads the scalars (stop flag, timeout) only every
+// check_every iterations; the step lengths and the stopping test are computed
+// on the device, so the result does not depend on it (iterations queued past
+// the stop return at once).
 int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g, double *x_g,
                      const sem_solver_opts *opts, void *workspace, sem_solve_stats *stats, void *stream,
                      int check_every, const double *dinv_given) {
@@ -374,7 +401,7 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
   SEM_CUDA(cudaStreamSynchronize(st));
   double scale = 1.0;
   if (hs.bb > 0.0 && std::isfinite(hs.bb)) scale = std::ldexp(1.0, std::ilogb(sqrt(hs.bb)));
-  k_pcg_init<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, 1.0 / scale, x_g, wk.r, wk.p, dinv, wk.part_a,
+  k_pcg_init<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, 1.0 / scale, x_g, wk.r, wk.p, wk.w, dinv, wk.part_a,
                                                  wk.part_b);
   k_pcg_init_finish<<<1, kUpdThreads, 0, st>>>(wk.part_a, wk.part_b, kUpdBlocks, wk.s);
   SEM_LAUNCH_CHECK("k_pcg_init");
@@ -401,20 +428,20 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
     return finish(SEM_OK, 0, 0.0);  // b = 0: x = 0 (already written)
   }
   const double thresh = opts->tol * bnorm;
+  const int *stop = &wk.s->stop_it;
   for (int it = 1; it <= opts->maxit; ++it) {
     const int par = (it - 1) & 1;
-    SEM_CUDA(cudaMemsetAsync(wk.w, 0, sizeof(double) * nU, st));
-    if ((rc = sem_launch_ax_assembled(m, h1, h2, wk.p, wk.w, wk.pw_part, opts->precision, st, map)) != SEM_OK)
+    if ((rc = sem_launch_ax_assembled(m, h1, h2, wk.p, wk.w, wk.pw_part, opts->precision, st, map, stop)) != SEM_OK)
       return rc;
     k_pcg_update1<<<nblk, kUpdThreads, 0, st>>>(nU, x_g, wk.r, wk.p, wk.w, dinv, wk.pw_part, n_pw, wk.s, par,
                                                 wk.part_a, wk.part_b);
-    k_pcg_update2<<<nblk, kUpdThreads, 0, st>>>(nU, wk.r, wk.p, dinv, wk.part_a, wk.part_b, nblk, wk.s, par);
+    k_pcg_update2<<<nblk, kUpdThreads, 0, st>>>(nU, wk.r, wk.p, wk.w, dinv, wk.part_a, wk.part_b, nblk, wk.s, par, it,
+                                                thresh);
     SEM_LAUNCH_CHECK("pcg iteration");
     if (it % check_every != 0 && it != opts->maxit) continue;
     SEM_CUDA(cudaMemcpyAsync(&hs, wk.s, sizeof(hs), cudaMemcpyDeviceToHost, st));
     SEM_CUDA(cudaStreamSynchronize(st));
-    if (std::isfinite(hs.rr) && sqrt(hs.rr) <= thresh) return finish(SEM_OK, it, hs.rr);
-    if (!(hs.pw > 0.0) || !std::isfinite(hs.pw) || !std::isfinite(hs.rr)) return finish(SEM_ERR_BREAKDOWN, it, hs.rr);
+    if (hs.stop_it != 0) return finish(hs.stop_status == 1 ? SEM_OK : SEM_ERR_BREAKDOWN, hs.stop_it, hs.rr);
     if (opts->timeout_s > 0.0) {
       double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (el > opts->timeout_s) return finish(SEM_ERR_TIMEOUT, it, hs.rr);

@@ -212,7 +212,7 @@ int solve(sem_rbc *s, double h1, double h2, const double *b, double *x, int mask
     key[0] = h1;
     key[1] = h2;
   }
-  int rc = sem_pcg_solve_ex(s->m, h1, h2, b, x, &o, s->ws, &stt, (void *)st, 1, dinv);
+  int rc = sem_pcg_solve_ex(s->m, h1, h2, b, x, &o, s->ws, &stt, (void *)st, 8, dinv);
   *iters = stt.iterations;
   return rc;
 }
