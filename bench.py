@@ -203,12 +203,12 @@ def run_once(sem, mesh, u, names):
             sem.sem_ax_assembled_add(mesh, 1.0, 0.0, u, wg, precision=P[prec])
         elif kind == "gs":
             sem.sem_gs_op(mesh, wL, True)
-        elif kind == "rbc":  # two Rayleigh-Benard steps on the 32^3-element workload (the second timed)
+        elif kind == "rbc":  # three Rayleigh-Benard steps on the 32^3-element workload
             rw = workloads.RBC_32
             rm = sem.mesh_from_workload(rw)
             pert = torch.from_numpy(workloads.perturbation(rm.n_unique, 1e-3)).cuda()
             rs = sem.sem_rbc_create(rm, 1e8, 0.7, 1e-3, tol=1e-8, precision=sem.SEM_PREC_DF64, T_pert=pert)
-            for _ in range(2):
+            for _ in range(3):
                 print(json.dumps(sem.sem_bdf_ext_step(rs)))
             rs.destroy()
             rm.destroy()
