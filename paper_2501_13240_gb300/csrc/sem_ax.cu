@@ -117,13 +117,13 @@ __global__ void __launch_bounds__(AxCfg<NP>::THREADS)
     __syncthreads();
   }
   if (ASSEMBLED && pw_partial != nullptr) {
-    __shared__ double red[32];
-    for (int off = 16; off > 0; off >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, off);
-    if ((tid & 31) == 0) red[tid >> 5] = pw;
+    // fixed-order CTA sum (the CTA may end in a partial warp, so no full-mask shuffles)
+    double *red = smem;  // the tiles are free after the last barrier
+    red[tid] = pw;
     __syncthreads();
     if (tid == 0) {
       double s = 0.0;
-      for (int t = 0; t < (C::THREADS + 31) / 32; ++t) s += red[t];
+      for (int t = 0; t < C::THREADS; ++t) s += red[t];
       pw_partial[blockIdx.x] = s;
     }
   }

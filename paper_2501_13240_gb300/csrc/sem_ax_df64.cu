@@ -17,12 +17,15 @@
 //       the t-line in registers
 //   P4  w(a,b,:) = t-part + R + S, then h1 w + h2 B u, back to binary64
 // The 1-D contractions use the even-odd split of the centro-antisymmetric
-// D (D[N-i][N-j] = -D[i][j]), which halves the multiply-adds.
+// D (D[N-i][N-j] = -D[i][j]), which halves the multiply-adds; in this kernel
+// the even and the odd dot product of each output pair run as the two lanes
+// of packed f32x2 instructions (bit-identical to the scalar sequence).
 #include <algorithm>
 #include <mutex>
 #include <vector>
 
 #include "sem_df64.cuh"
+#include "sem_df64x2.cuh"
 #include "sem_internal.h"
 
 namespace {
@@ -78,6 +81,28 @@ int ensure_tables(int device) {
   return SEM_OK;
 }
 
+// Shared coefficient table of the even-odd split (even NP): entry [i H + m]
+// = (A.hi, Bq.hi, A.lo, Bq.lo) for D, then the same for D^T at H^2, so one
+// 128-bit load feeds both packed lanes of a multiply-add.
+template <int NP>
+struct KqSize {
+  static constexpr int value = (NP % 2 == 0) ? NP * NP / 2 : 1;
+};
+
+
+template <int NP>
+__device__ __forceinline__ void load_kq(float4 *kq) {
+  if constexpr (NP % 2 == 0) {
+    constexpr int H = NP / 2;
+    for (int q = threadIdx.x; q < 2 * H * H; q += blockDim.x) {
+      const int tr = q / (H * H), im = q - tr * H * H;
+      const float2 *A = c_tab + tab_off(NP) + tr * 2 * H * H;
+      const float2 a = A[im], b = A[H * H + im];
+      kq[q] = make_float4(a.x, b.x, a.y, b.y);
+    }
+  }
+}
+
 // y = M x along one line (M = D, or D^T when TR), df64 in, normalised df64
 // out. Compensated dot products (exact products, TwoSum accumulation).
 template <int NP, bool TR>
@@ -127,6 +152,53 @@ __device__ __forceinline__ void line_apply(const float2 (&x)[NP], float2 (&y)[NP
   }
 }
 
+// The same contraction for even NP, writing its outputs straight to the
+// shared tile O at base + str m. The even and the odd dot product of each
+// output pair run as the two lanes of packed f32x2 instructions (each lane
+// does exactly the operation sequence of line_apply, so the results are
+// bit-identical to it) with coefficients (A.hi, Bq.hi, A.lo, Bq.lo) from kq;
+// the output loop is rolled pairwise to bound the live registers.
+template <int NP, bool TR>
+__device__ __forceinline__ void line_apply_store(const float2 (&x)[NP], float2 *O, int base, int str,
+                                                 const float4 *__restrict__ kq) {
+  static_assert(NP % 2 == 0, "even-odd form");
+  constexpr int N = NP - 1, H = NP / 2;
+  const float4 *K = kq + (TR ? H * H : 0);
+  float2 eh[H], el[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    float s, e;
+    df::two_sum(x[m].x, x[N - m].x, s, e);
+    eh[m].x = s;
+    el[m].x = df::add(e, df::add(x[m].y, x[N - m].y));
+    df::two_sum(x[m].x, -x[N - m].x, s, e);
+    eh[m].y = s;
+    el[m].y = df::add(e, df::sub(x[m].y, x[N - m].y));
+  }
+#pragma unroll 2
+  for (int i = 0; i < H; ++i) {
+    float4 k = K[i * H];
+    dfx::Acc PQ = dfx::mul_first(make_float2(k.x, k.y), make_float2(k.z, k.w), eh[0], el[0]);
+#pragma unroll
+    for (int m = 1; m < H; ++m) {
+      k = K[i * H + m];
+      dfx::mac(PQ, make_float2(k.x, k.y), make_float2(k.z, k.w), eh[m], el[m]);
+    }
+    float s, e, h, l;
+    df::two_sum(PQ.s.x, PQ.s.y, s, e);
+    df::fast_two_sum(s, df::add(df::add(PQ.c.x, PQ.c.y), e), h, l);
+    O[base + str * i] = make_float2(h, l);
+    df::two_sum(PQ.s.y, -PQ.s.x, s, e);
+    df::fast_two_sum(s, df::add(df::sub(PQ.c.y, PQ.c.x), e), h, l);
+    O[base + str * (N - i)] = make_float2(h, l);
+  }
+}
+
+// L2 prefetch of a contiguous block (bytes a multiple of 16, 16-byte aligned)
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // one output of the metric step: g0 u0 + g1 u1 + g2 u2
 __device__ __forceinline__ float2 metric_row(float2 g0, float2 g1, float2 g2, float2 u0, float2 u1, float2 u2) {
   df::Acc a = df::mul_first(g0.x, g0.y, u0.x, u0.y);
@@ -147,19 +219,24 @@ struct DfCfg {
   // at least 128 threads per CTA, shared tiles within 48 KB
   static constexpr int ELB_T = (N2 >= 128) ? 1 : 128 / N2;
   static constexpr int ELB_S = (48 * 1024) / (4 * NP * NP * (NP + 1) * (int)sizeof(float2));
-  static constexpr int ELB = ELB_T < ELB_S ? ELB_T : (ELB_S > 0 ? ELB_S : 1);
+  // NP = 8: one element (64 threads) per CTA, so barriers wait on two warps only
+  static constexpr int ELB = (NP == 8) ? 1 : (ELB_T < ELB_S ? ELB_T : (ELB_S > 0 ? ELB_S : 1));
   static constexpr int THREADS = N2 * ELB;
   static constexpr int SMEM = 4 * TILE * ELB * (int)sizeof(float2);
+  // NP = 8: ten 64-thread CTAs per SM (at most 102 registers per thread)
+  static constexpr int MINB = (NP == 8) ? 10 : 1;
 };
 
 template <int NP, bool ASSEMBLED, bool HELM>
-__global__ void __launch_bounds__(DfCfg<NP>::THREADS)
+__global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
     k_ax_df64(int64_t E, const float2 *__restrict__ Gdf, const float2 *__restrict__ Bdf, float2 h1, float2 h2,
               const double *__restrict__ u, double *__restrict__ w, const int32_t *__restrict__ l2gm,
               double *__restrict__ pw_partial, double *__restrict__ wloc, const int *__restrict__ skip) {
   using C = DfCfg<NP>;
   if (skip != nullptr && *skip != 0) return;
   extern __shared__ float2 sm2[];
+  __shared__ float4 kq[KqSize<NP>::value];  // read after the first barrier of the element loop
+  load_kq<NP>(kq);
   const int tid = threadIdx.x;
   const int le = tid / C::N2;
   const int t = tid - le * C::N2;
@@ -183,7 +260,9 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
   for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += estride) {
     e = e0 + le;
     const bool act = e < E;
-    // P0: gather and split the t-column
+    // P0: gather and split the t-column; one thread per element starts the
+    // L2 prefetch of the element's geometric factors (read in P2)
+    if (act && t == 0) prefetch_l2(Gdf + e * 6 * C::N3, 48u * C::N3);
     float2 x[NP];
     {
       double v[NP];
@@ -214,23 +293,35 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
       const int base = d == 0 ? C::PJ * a + C::PK * b : (d == 1 ? a + C::PK * b : col);
       const int str = d == 0 ? 1 : (d == 1 ? C::PJ : C::PK);
       float2 *O = d == 0 ? R : (d == 1 ? S : T);
-      float2 y[NP], z[NP];
+      float2 y[NP];
 #pragma unroll
       for (int m = 0; m < NP; ++m) y[m] = U[base + str * m];
-      line_apply<NP, false>(y, z);
+      if constexpr (NP % 2 == 0) {
+        line_apply_store<NP, false>(y, O, base, str, kq);
+      } else {
+        float2 z[NP];
+        line_apply<NP, false>(y, z);
 #pragma unroll
-      for (int m = 0; m < NP; ++m) O[base + str * m] = z[m];
+        for (int m = 0; m < NP; ++m) O[base + str * m] = z[m];
+      }
     }
     __syncthreads();
     // P2: metric on the t-column (a, b, :), in place
     const float2 *Ge = Gdf + (act ? e : 0) * 6 * C::N3 + a + NP * b;
+    float2 gn[6];  // level k + 1's factors, loaded while level k is computed
+#pragma unroll
+    for (int f = 0; f < 6; ++f) gn[f] = act ? Ge[f * C::N3] : make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       const int q = col + C::PK * k;
       const float2 ur = R[q], us = S[q], uu = T[q];
       float2 g[6];
 #pragma unroll
-      for (int f = 0; f < 6; ++f) g[f] = act ? Ge[f * C::N3 + C::N2 * k] : make_float2(0.0f, 0.0f);
+      for (int f = 0; f < 6; ++f) g[f] = gn[f];
+      if (k + 1 < NP) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f) gn[f] = act ? Ge[f * C::N3 + C::N2 * (k + 1)] : make_float2(0.0f, 0.0f);
+      }
       R[q] = metric_row(g[0], g[1], g[2], ur, us, uu);
       S[q] = metric_row(g[1], g[3], g[4], ur, us, uu);
       T[q] = metric_row(g[2], g[4], g[5], ur, us, uu);
@@ -242,12 +333,17 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
       const int base = d == 0 ? C::PJ * a + C::PK * b : (d == 1 ? a + C::PK * b : col);
       const int str = d == 0 ? 1 : (d == 1 ? C::PJ : C::PK);
       float2 *O = d == 0 ? R : (d == 1 ? S : T);
-      float2 y[NP], z[NP];
+      float2 y[NP];
 #pragma unroll
       for (int m = 0; m < NP; ++m) y[m] = O[base + str * m];
-      line_apply<NP, true>(y, z);
+      if constexpr (NP % 2 == 0) {
+        line_apply_store<NP, true>(y, O, base, str, kq);
+      } else {
+        float2 z[NP];
+        line_apply<NP, true>(y, z);
 #pragma unroll
-      for (int m = 0; m < NP; ++m) O[base + str * m] = z[m];
+        for (int m = 0; m < NP; ++m) O[base + str * m] = z[m];
+      }
     }
     __syncthreads();
     // P4: sum the three directions, scale, convert, write
@@ -283,15 +379,14 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS)
     __syncthreads();
   }
   if (ASSEMBLED && pw_partial != nullptr) {
-    __shared__ double red[32];
+    // fixed-order CTA sum (the CTA may end in a partial warp, so no full-mask shuffles)
+    double *red = reinterpret_cast<double *>(sm2);  // the tiles are free after the last barrier
     const float2 pn = df::norm(pw);
-    double v = (double)pn.x + (double)pn.y;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if ((tid & 31) == 0) red[tid >> 5] = v;
+    red[tid] = (double)pn.x + (double)pn.y;
     __syncthreads();
     if (tid == 0) {
       double s = 0.0;
-      for (int q = 0; q < (C::THREADS + 31) / 32; ++q) s += red[q];
+      for (int q = 0; q < C::THREADS; ++q) s += red[q];
       pw_partial[blockIdx.x] = s;
     }
   }

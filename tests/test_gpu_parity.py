@@ -47,6 +47,10 @@ MESHES = [
     dict(nel=(9, 7, 5), N=1, deform=0.05, periodic=(1, 0, 0), dirichlet=(0, 0, 1, 1, 1, 1)),  # element matrices
     dict(nel=(2, 2, 2), N=10, deform=0.05),
     dict(nel=(3, 3, 2), N=2, deform=0.05, periodic=(1, 0, 1), dirichlet=(0, 0, 1, 1, 0, 0)),
+    # even point counts NP = 4, 6: the packed double-float operator with two and
+    # eight elements per CTA (idle padding threads at NP = 6)
+    dict(nel=(3, 4, 3), N=3, deform=0.06, periodic=(0, 1, 0), dirichlet=(1, 1, 0, 0, 1, 1)),
+    dict(nel=(4, 2, 3), N=5, deform=0.05, L=(2.0, 1.0, 1.5)),
 ]
 
 
