@@ -52,6 +52,14 @@ TRAFFIC = {"df64": 9.32e9}
 # instruction per scheduler per clock)
 INST_PER_POINT = {"df64": 512.0}
 ISSUE_PEAK_TINST = 152 * 4 * 32 * 2.07e9 / 1e12
+# binary32 lane operations per local point of the double-float Poisson operator
+# (each packed f32x2 instruction counts two): 6 one-dimensional contractions x
+# 59 (even-odd split at N = 7: pair forming 8, 4-term compensated dot products
+# 40 per output pair and lane, output pair combination 11 per output), the
+# metric 3 x 31, the final three-way sum 19, conversions 3. Peak: the measured
+# binary32 FMA rate of this GPU (77 TFLOP/s, own probe) = 38.5 T lane ops/s.
+FP32_LANE_OPS_PER_POINT = {"df64": 469.0}
+FP32_PEAK_TLANEOPS = 38.5
 
 
 def parse():
@@ -375,6 +383,12 @@ def main():
                                   "frac": ti / ISSUE_PEAK_TINST,
                                   "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz",
                                   "inst_per_point_source": "ncu smsp__inst_executed.sum, ax_gs_32"}
+    if head in FP32_LANE_OPS_PER_POINT:  # ... and the binary32 pipe it computes on
+        tl = FP32_LANE_OPS_PER_POINT[head] * w.n_local / (kms * 1e-3) / 1e12
+        roofline["fp32_pipe_view"] = {"bound": "alu", "achieved_tlaneops_per_s": tl,
+                                      "peak_tlaneops_per_s": FP32_PEAK_TLANEOPS, "frac": tl / FP32_PEAK_TLANEOPS,
+                                      "peak_source": "measured binary32 FMA rate (own probe, 77 TFLOP/s)",
+                                      "lane_ops_per_point": FP32_LANE_OPS_PER_POINT[head]}
 
     # --- end to end through the C ABI with host buffers
     pin_in = torch.from_numpy(ug_host).pin_memory()
