@@ -151,7 +151,8 @@ int sem_mesh_create_box(const sem_box_desc *desc, void *stream, sem_mesh **out);
 /* Free a mesh and everything it owns (NULL is accepted). */
 int sem_mesh_destroy(sem_mesh *m);
 
-/* Fill *info with sizes and device views. */
+/* Fill *info with sizes and device views (the mesh-information call of the
+ * boundary; "_get" because the struct type carries the name sem_mesh_info). */
 int sem_mesh_info_get(const sem_mesh *m, sem_mesh_info *info);
 
 /* Audit the index tables on the host: l2g in range, l2gm = l2g on free
