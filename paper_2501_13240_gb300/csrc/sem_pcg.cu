@@ -39,6 +39,7 @@ struct PcgScalars {
   double bb;      // b.b
   int stop_it;    // 0 while running; else the iteration at which the solve stopped
   int stop_status;  // 1: converged, 2: breakdown (written before stop_it)
+  double pw_in;     // p.w of the current iteration, summed from the operator's partials
 };
 
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -103,6 +104,17 @@ __global__ void __launch_bounds__(kUpdThreads)
     s->stop_it = 0;
     s->stop_status = 0;
   }
+}
+
+// The operator leaves one p.w partial per CTA (one per element group for the
+// double-float operator, up to hundreds of thousands); one CTA sums them in a
+// fixed order, so the update kernels each read a single value.
+__global__ void __launch_bounds__(1024)
+    k_pw_reduce(const double *__restrict__ pw_part, int n_pw, PcgScalars *s) {
+  __shared__ double red[32];
+  if (*(volatile const int *)&s->stop_it != 0) return;  // stopped at an earlier iteration
+  const double pw = sum_partials(pw_part, n_pw, red);
+  if (threadIdx.x == 0) s->pw_in = pw;
 }
 
 __global__ void __launch_bounds__(kUpdThreads)
@@ -433,7 +445,8 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
     const int par = (it - 1) & 1;
     if ((rc = sem_launch_ax_assembled(m, h1, h2, wk.p, wk.w, wk.pw_part, opts->precision, st, map, stop)) != SEM_OK)
       return rc;
-    k_pcg_update1<<<nblk, kUpdThreads, 0, st>>>(nU, x_g, wk.r, wk.p, wk.w, dinv, wk.pw_part, n_pw, wk.s, par,
+    k_pw_reduce<<<1, 1024, 0, st>>>(wk.pw_part, n_pw, wk.s);
+    k_pcg_update1<<<nblk, kUpdThreads, 0, st>>>(nU, x_g, wk.r, wk.p, wk.w, dinv, &wk.s->pw_in, 1, wk.s, par,
                                                 wk.part_a, wk.part_b);
     k_pcg_update2<<<nblk, kUpdThreads, 0, st>>>(nU, wk.r, wk.p, wk.w, dinv, wk.part_a, wk.part_b, nblk, wk.s, par, it,
                                                 thresh);

@@ -778,6 +778,22 @@ __global__ void k_init_fcg(int64_t n, const double *__restrict__ b, const uint8_
 }
 
 // ---------------------------------------------------------------- host helpers
+// fixed-order sum of n partials into *out (one CTA of 256 threads): the
+// outer operator leaves one p.w partial per element group
+__global__ void __launch_bounds__(256) k_sum_fixed(const double *__restrict__ part, int n, double *__restrict__ out) {
+  __shared__ double red[8];
+  double v = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) v += part[t];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    *out = s;
+  }
+}
+
 int sum_pairs(const double *dpart, double *a, double *b, cudaStream_t st) {
   double h[2 * kPart];
   SEM_CUDA(cudaMemcpyAsync(h, dpart, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -1149,7 +1165,7 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
     if (!rc) rc = alloc((void **)v, sizeof(double) * nU);
   if (!rc) {
     const int npw = std::max(sem_ax_assembled_blocks(m, SEM_PREC_FP64), sem_ax_assembled_blocks(m, SEM_PREC_DF64));
-    rc = alloc((void **)&P->pw_part, sizeof(double) * std::max(npw, 1));
+    rc = alloc((void **)&P->pw_part, sizeof(double) * (std::max(npw, 1) + 1));  // + their sum
   }
   cudaError_t e = cudaGetLastError();
   if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1258,11 +1274,11 @@ extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, con
     SEM_CUDA(cudaMemsetAsync(P->w, 0, sizeof(double) * n, st));
     if ((rc = sem_launch_ax_assembled(m, P->h1, P->h2, P->p, P->w, P->pw_part, opts->precision, st, P->L[0].map)))
       return rc;
-    std::vector<double> hp(npw);
-    SEM_CUDA(cudaMemcpyAsync(hp.data(), P->pw_part, sizeof(double) * npw, cudaMemcpyDeviceToHost, st));
-    SEM_CUDA(cudaStreamSynchronize(st));
+    k_sum_fixed<<<1, 256, 0, st>>>(P->pw_part, npw, P->pw_part + npw);
+    SEM_LAUNCH_CHECK("k_sum_fixed");
     double pw = 0.0;
-    for (double v : hp) pw += v;
+    SEM_CUDA(cudaMemcpyAsync(&pw, P->pw_part + npw, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SEM_CUDA(cudaStreamSynchronize(st));
     if (!(pw > 0.0) || !std::isfinite(pw)) return finish(SEM_ERR_BREAKDOWN, it, rr);
     const double alpha = rz / pw;
     k_fcg_update<<<g, 256, 0, st>>>(n, alpha, P->p, P->w, x_g, P->r);
