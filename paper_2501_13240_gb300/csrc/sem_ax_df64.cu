@@ -223,8 +223,11 @@ struct DfCfg {
   static constexpr int ELB = (NP == 8) ? 1 : (ELB_T < ELB_S ? ELB_T : (ELB_S > 0 ? ELB_S : 1));
   static constexpr int THREADS = N2 * ELB;
   static constexpr int SMEM = 4 * TILE * ELB * (int)sizeof(float2);
-  // NP = 8: ten 64-thread CTAs per SM (at most 102 registers per thread)
-  static constexpr int MINB = (NP == 8) ? 10 : 1;
+  // the operator: tiles U, R, S, and T (the t-derivative) in a fourth tile
+  // only when the Helmholtz term needs u at the end; otherwise T replaces U
+  static constexpr int smem_ax(bool helm) { return (helm ? 4 : 3) * TILE * ELB * (int)sizeof(float2); }
+  // NP = 8: twelve 64-thread CTAs per SM (at most 85 registers per thread)
+  static constexpr int MINB = (NP == 8) ? 12 : 1;
 };
 
 template <int NP, bool ASSEMBLED, bool HELM>
@@ -241,55 +244,42 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
   const int le = tid / C::N2;
   const int t = tid - le * C::N2;
   const int a = t % NP, b = t / NP;
-  float2 *U = sm2 + le * 4 * C::TILE;
+  constexpr int NT = HELM ? 4 : 3;  // tiles per element
+  float2 *U = sm2 + le * NT * C::TILE;
   float2 *R = U + C::TILE;
   float2 *S = R + C::TILE;
-  float2 *T = S + C::TILE;
+  float2 *T = HELM ? S + C::TILE : U;  // without the Helmholtz term T replaces U after the r/s passes
   const int col = a + C::PJ * b;  // padded offset of the t-column (a, b, 0)
   df::Acc pw = {0.0f, 0.0f};
   const int64_t estride = (int64_t)gridDim.x * C::ELB;
 
-  // gather indices of this thread's column, prefetched one element ahead;
-  // go keeps the current element's for the scatter at the end
-  int32_t gi[NP], go[NP];
-  int64_t e = (int64_t)blockIdx.x * C::ELB + le;
-  if (ASSEMBLED) {
-#pragma unroll
-    for (int k = 0; k < NP; ++k) gi[k] = (e < E) ? l2gm[e * C::N3 + a + NP * b + C::N2 * k] : -1;
-  }
+  int32_t go[NP];  // gather indices of this thread's column, kept for the scatter
   for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += estride) {
-    e = e0 + le;
+    const int64_t e = e0 + le;
     const bool act = e < E;
     // P0: gather and split the t-column; one thread per element starts the
     // L2 prefetch of the element's geometric factors (read in P2)
     if (act && t == 0) prefetch_l2(Gdf + e * 6 * C::N3, 48u * C::N3);
-    float2 x[NP];
     {
       double v[NP];
+      if (ASSEMBLED) {  // all indices, then all values: one round trip each
 #pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        const int p = a + NP * b + C::N2 * k;
-        if (ASSEMBLED) {
-          go[k] = gi[k];
-          v[k] = (gi[k] >= 0) ? u[gi[k]] : 0.0;
-        }
-        else v[k] = act ? u[e * C::N3 + p] : 0.0;
-      }
-      if (ASSEMBLED) {
-        const int64_t en = e + estride;
+        for (int k = 0; k < NP; ++k) go[k] = act ? l2gm[e * C::N3 + a + NP * b + C::N2 * k] : -1;
 #pragma unroll
-        for (int k = 0; k < NP; ++k) gi[k] = (en < E) ? l2gm[en * C::N3 + a + NP * b + C::N2 * k] : -1;
+        for (int k = 0; k < NP; ++k) v[k] = (go[k] >= 0) ? u[go[k]] : 0.0;
+      } else {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) v[k] = act ? u[e * C::N3 + a + NP * b + C::N2 * k] : 0.0;
       }
 #pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        x[k] = df::from_f64(v[k]);
-        U[col + C::PK * k] = x[k];
-      }
+      for (int k = 0; k < NP; ++k) U[col + C::PK * k] = df::from_f64(v[k]);
     }
     __syncthreads();
-    // P1: forward contractions, r-, s- and t-lines, one loop body
+    // P1: forward contractions, r-, s- and t-lines, one loop body (when T
+    // replaces U, the t-lines wait until every thread has read its r/s lines)
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
+      if (!HELM && d == 2) __syncthreads();
       const int base = d == 0 ? C::PJ * a + C::PK * b : (d == 1 ? a + C::PK * b : col);
       const int str = d == 0 ? 1 : (d == 1 ? C::PJ : C::PK);
       float2 *O = d == 0 ? R : (d == 1 ? S : T);
@@ -358,8 +348,9 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
       float2 v;
       df::fast_two_sum(acc.s, acc.c, v.x, v.y);
       if (HELM) {
+        const float2 xk = U[q];
         const float2 Bv = act ? Bdf[e * C::N3 + p] : make_float2(0.0f, 0.0f);
-        const float2 buv = df::norm(df::mul_first(Bv.x, Bv.y, x[k].x, x[k].y));
+        const float2 buv = df::norm(df::mul_first(Bv.x, Bv.y, xk.x, xk.y));
         df::Acc o = df::mul_first(h1.x, h1.y, v.x, v.y);
         df::mac(o, h2.x, h2.y, buv.x, buv.y);
         v = df::norm(o);
@@ -370,7 +361,10 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
           const int32_t g = go[k];
           if (wloc) wloc[e * C::N3 + p] = (g >= 0) ? vd : 0.0;
           else if (g >= 0) atomicAdd(&w[g], vd);
-          if (pw_partial) df::mac(pw, x[k].x, x[k].y, v.x, v.y);
+          if (pw_partial) {  // u at the point: from U, or gathered again (L2) when T replaced U
+            const float2 xk = HELM ? U[q] : df::from_f64((g >= 0) ? u[g] : 0.0);
+            df::mac(pw, xk.x, xk.y, v.x, v.y);
+          }
         } else {
           w[e * C::N3 + p] = vd;
         }
@@ -594,26 +588,12 @@ int launch_field(const sem_mesh *m, const float2 *Rdf, const double *f0, const d
   }
 }
 
-int num_sms(int device) {
-  int n = 0;
-  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n < 1) n = 152;
-  return n;
-}
-
-// Fixed grid of the assembled form: every CTA resident at once (one wave),
-// so the p.w partial sums come from a mesh-determined number of CTAs.
+// Grid of the operator: one CTA per element group (with p.w accumulation,
+// one partial sum per CTA, so their number is a property of the mesh)
 template <int NP>
-int df_grid(const sem_mesh *m, bool assembled, unsigned *grid) {
+int df_grid(const sem_mesh *m, unsigned *grid) {
   using C = DfCfg<NP>;
-  int64_t blocks = (m->E + C::ELB - 1) / C::ELB;
-  if (assembled) {
-    auto kern = k_ax_df64<NP, true, false>;
-    if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    int per_sm = 0;
-    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS, C::SMEM));
-    blocks = std::min<int64_t>(blocks, (int64_t)std::max(per_sm, 1) * num_sms(m->device));
-  }
-  *grid = (unsigned)std::max<int64_t>(blocks, 1);
+  *grid = (unsigned)std::max<int64_t>((m->E + C::ELB - 1) / C::ELB, 1);
   return SEM_OK;
 }
 
@@ -623,18 +603,18 @@ int launch_np(const sem_mesh *m, double h1, double h2, const double *u, double *
   using C = DfCfg<NP>;
   unsigned grid;
   // one CTA per element group (the hardware scheduler balances the SMs; a
-  // single resident wave of persistent CTAs measured 11 % slower); with p.w
-  // accumulation that is also the number of partial sums
-  if (int rc = df_grid<NP>(m, false, &grid)) return rc;
+  // single resident wave of persistent CTAs measured 11 % slower)
+  if (int rc = df_grid<NP>(m, &grid)) return rc;
   const float2 h1d = split_host(h1), h2d = split_host(h2);
   const bool helm = !(h1 == 1.0 && h2 == 0.0);
   double *wloc = assembled ? (double *)m->det_w : nullptr;
 #define LAUNCH(ASM, HLM)                                                                                    \
   do {                                                                                                      \
     auto kern = k_ax_df64<NP, ASM, HLM>;                                                                    \
-    if (C::SMEM > 48 * 1024)                                                                                \
-      SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));          \
-    kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->Gdf, m->Bdf, h1d, h2d, u, w, map, pw_partial, wloc, skip); \
+    constexpr int smem = C::smem_ax(HLM);                                                                   \
+    if (smem > 48 * 1024)                                                                                   \
+      SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));             \
+    kern<<<grid, C::THREADS, smem, st>>>(m->E, m->Gdf, m->Bdf, h1d, h2d, u, w, map, pw_partial, wloc, skip); \
   } while (0)
   if (assembled) {
     if (helm) LAUNCH(true, true);
@@ -657,7 +637,7 @@ int sem_df64_grid(const sem_mesh *m) {
   switch (m->n) {
 #define CASE(NPV)                              \
   case NPV:                                    \
-    rc = df_grid<NPV>(m, false, &grid);        \
+    rc = df_grid<NPV>(m, &grid);               \
     break;
     CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
 #undef CASE
