@@ -7,17 +7,20 @@
 // error-free transformations costs ~10 binary32 operations per binary64
 // multiply-add and keeps ~2^-46 relative accuracy.
 //
-// Structure per element (NP = N+1 points per direction, NP^2 threads):
-//   P0  gather u (binary64), split to df64; thread (a,b) keeps the t-line
-//       u(a,b,:) in registers and stores it to the shared tile U
-//   P1  each thread contracts three lines with D: its t-line (registers),
-//       the r-line u(:,a,b) and the s-line u(a,:,b) (shared tile) -> R, S
-//   P2  pointwise metric on its t-column: (wr, ws, wt) = G (ur, us, ut)
-//   P3  transposed contractions: r-lines of R and s-lines of S in place,
-//       the t-line in registers
-//   P4  w(a,b,:) = t-part + R + S, then h1 w + h2 B u, back to binary64
+// Structure per element (NP = N+1 points per direction, NP^2 threads; one
+// element per CTA at N = 7, one CTA per element group in every launch):
+//   P0  gather the t-column u(a,b,:) (binary64; all indices, then all
+//       values), split to df64 into the shared tile U; thread 0 starts the
+//       L2 prefetch of the element's geometric factors
+//   P1  each thread contracts three lines with D, one loop body: the r-line
+//       u(:,a,b) -> R, the s-line u(a,:,b) -> S, its t-line -> T (without the
+//       Helmholtz term T is the U tile, written after a barrier)
+//   P2  pointwise metric on its t-column: (wr, ws, wt) = G (ur, us, ut), the
+//       factors of level k + 1 loaded while level k is computed
+//   P3  transposed contractions of the same lines, in place
+//   P4  w(a,b,:) = T + R + S, then h1 w + h2 B u, back to binary64, scatter
 // The 1-D contractions use the even-odd split of the centro-antisymmetric
-// D (D[N-i][N-j] = -D[i][j]), which halves the multiply-adds; in this kernel
+// D (D[N-i][N-j] = -D[i][j]), which halves the multiply-adds; for even NP
 // the even and the odd dot product of each output pair run as the two lanes
 // of packed f32x2 instructions (bit-identical to the scalar sequence).
 #include <algorithm>
