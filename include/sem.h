@@ -240,6 +240,24 @@ int sem_ax_assembled_add(const sem_mesh *m, double h1, double h2, const double *
 int sem_ax_assembled_host(const sem_mesh *m, double h1, double h2, const double *u_host, double *w_host,
                           int precision, double *u_dev, double *w_dev, int nchunks, void *stream);
 
+/* nsteps independent applications of the same assembled operator (Sec. 2.2)
+ * on host vectors: w_host[k] = M Q^T (h1 A_L + h2 B_L) Q M u_host[k],
+ * k = 0 .. nsteps - 1, pipelined across the applications: the copy-in of
+ * application k + 1, the operator of application k (on `stream`) and the
+ * copy-out of application k - 1 overlap, each copy moving a whole vector
+ * (a copy-in and a copy-out stream are created and destroyed by the call).
+ * u_host, w_host: arrays of nsteps pointers to n_unique doubles each (pinned
+ * host memory lets the copies overlap); the w_host vectors must not overlap
+ * any u_host vector still to be read. u_dev2, w_dev2: caller-owned device
+ * scratch of 2 n_unique doubles each (double buffers). The call waits for
+ * work already queued on `stream`, returns after the last copy-out, and
+ * rejects NULL pointers, a negative count, misaligned or identical device
+ * buffers, an unknown precision or a mesh on another device
+ * (SEM_ERR_INVALID_ARG). nsteps = 0 does nothing. */
+int sem_ax_assembled_host_batch(const sem_mesh *m, double h1, double h2, int nsteps,
+                                const double *const *u_host, double *const *w_host, int precision,
+                                double *u_dev2, double *w_dev2, void *stream);
+
 /* Masked inverse of the assembled diagonal of h1 A + h2 B (the Jacobi
  * preconditioner, including the D_ii D_jj G_rs cross terms at element
  * boundaries): dinv_g[g] = mask[g] / (Q^T diag_L)[g]. Device U-vector out. */

@@ -35,7 +35,7 @@ SEM_PREC_BF16 = 3
 EXPORTS = (
     "sem_last_error", "sem_version", "sem_gll", "sem_mesh_create_box", "sem_mesh_destroy",
     "sem_mesh_info_get", "sem_mesh_set_deterministic", "sem_mesh_validate", "sem_mesh_copy_maps", "sem_mesh_copy_gs_tables", "sem_ax_apply", "sem_gs_op",
-    "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_ax_assembled_add", "sem_ax_assembled_host", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
+    "sem_gather", "sem_scatter", "sem_ax_assembled", "sem_ax_assembled_add", "sem_ax_assembled_host", "sem_ax_assembled_host_batch", "sem_jacobi_inv", "sem_weak_rhs", "sem_pcg_workspace_bytes",
     "sem_pcg_solve", "sem_pcg_solve_noalloc", "sem_pcg_noalloc_capacity",
     "sem_rbc_create", "sem_bdf_ext_step", "sem_rbc_fields", "sem_rbc_destroy",
     "sem_rbc_state_bytes", "sem_rbc_save_state", "sem_rbc_load_state", "sem_rbc_save", "sem_rbc_load",
@@ -151,6 +151,7 @@ def lib() -> ctypes.CDLL:
             "sem_ax_assembled": ([_vp, _d, _d, _vp, _vp, _i, _vp], _i),
             "sem_ax_assembled_add": ([_vp, _d, _d, _vp, _vp, _i, _vp], _i),
             "sem_ax_assembled_host": ([_vp, _d, _d, _vp, _vp, _i, _vp, _vp, _i, _vp], _i),
+            "sem_ax_assembled_host_batch": ([_vp, _d, _d, _i, _vp, _vp, _i, _vp, _vp, _vp], _i),
             "sem_jacobi_inv": ([_vp, _d, _d, _vp, _vp], _i),
             "sem_weak_rhs": ([_vp, _vp, _vp, _vp], _i),
             "sem_pcg_workspace_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], _i),
@@ -427,6 +428,29 @@ def sem_ax_assembled_host(mesh: Mesh, h1: float, h2: float, u_host, w_host, u_de
                                        _ptr(w_dev, torch.float64, mesh.n_unique, "w_dev"), int(nchunks),
                                        _stream(stream)))
     return w_host
+
+
+def sem_ax_assembled_host_batch(mesh: Mesh, h1: float, h2: float, u_hosts, w_hosts, u_dev2, w_dev2,
+                                precision: int = SEM_PREC_DF64, stream=None):
+    """len(u_hosts) independent applications on host vectors (CPU torch
+    tensors, ideally pinned), pipelined across the applications; u_dev2 and
+    w_dev2 are device scratch of 2 n_unique doubles each."""
+    import torch
+    if len(u_hosts) != len(w_hosts):
+        raise ValueError("u_hosts and w_hosts must have the same length")
+    for lst, nm in ((u_hosts, "u_hosts"), (w_hosts, "w_hosts")):
+        for t in lst:
+            if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() \
+                    or t.numel() != mesh.n_unique:
+                raise TypeError(f"{nm} entries must be contiguous float64 CPU tensors of n_unique elements")
+    n = len(u_hosts)
+    up = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in u_hosts])
+    wp = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in w_hosts])
+    _check(lib().sem_ax_assembled_host_batch(mesh.handle, float(h1), float(h2), n, up, wp, int(precision),
+                                             _ptr(u_dev2, torch.float64, 2 * mesh.n_unique, "u_dev2"),
+                                             _ptr(w_dev2, torch.float64, 2 * mesh.n_unique, "w_dev2"),
+                                             _stream(stream)))
+    return w_hosts
 
 
 def sem_jacobi_inv(mesh: Mesh, h1: float, h2: float, dinv_g, stream=None):

@@ -128,3 +128,69 @@ extern "C" int sem_ax_assembled_host(const sem_mesh *m, double h1, double h2, co
   SEM_CUDA(cudaStreamSynchronize(st));
   return SEM_OK;
 }
+
+// Several independent applications on host vectors, pipelined across the
+// applications instead of within one: the copy-in of application k + 1, the
+// operator of application k and the copy-out of application k - 1 run at the
+// same time, each copy moving one whole vector (cutting a vector into chunks
+// costs link throughput). Device vectors are double-buffered: application k
+// uses u_dev2 + (k & 1) n_unique and w_dev2 + (k & 1) n_unique.
+extern "C" int sem_ax_assembled_host_batch(const sem_mesh *m, double h1, double h2, int nsteps,
+                                           const double *const *u_host, double *const *w_host, int precision,
+                                           double *u_dev2, double *w_dev2, void *stream) {
+  SemRange nvtx_range("sem_ax_assembled_host_batch");
+  if (!m || !u_host || !w_host || !u_dev2 || !w_dev2 || nsteps < 0)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_host_batch: NULL argument or negative count");
+  for (int k = 0; k < nsteps; ++k)
+    if (!u_host[k] || !w_host[k]) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_host_batch: NULL host vector");
+  if ((((uintptr_t)u_dev2) | ((uintptr_t)w_dev2)) & 7 || u_dev2 == w_dev2)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_host_batch: misaligned or overlapping device vectors");
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_DF64)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_host_batch: unknown precision");
+  int dev = -1;
+  SEM_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_host_batch: the mesh's device must be current");
+  if (nsteps == 0) return SEM_OK;
+  cudaStream_t st = as_stream(stream);
+  const int64_t nU = m->n_unique;
+  const size_t bytes = sizeof(double) * (size_t)nU;
+
+  IoStreams io;
+  SEM_CUDA(cudaStreamCreateWithFlags(&io.in, cudaStreamNonBlocking));
+  SEM_CUDA(cudaStreamCreateWithFlags(&io.out, cudaStreamNonBlocking));
+  cudaEvent_t start = io.make();
+  if (!start) return sem_fail(SEM_ERR_CUDA, "sem_ax_assembled_host_batch: cudaEventCreate");
+  SEM_CUDA(cudaEventRecord(start, st));
+  SEM_CUDA(cudaStreamWaitEvent(io.in, start, 0));
+  SEM_CUDA(cudaStreamWaitEvent(io.out, start, 0));
+  // per application: copy-in done, operator done, copy-out done
+  std::vector<cudaEvent_t> ev_in(nsteps), ev_op(nsteps), ev_out(nsteps);
+  for (int k = 0; k < nsteps; ++k) {
+    ev_in[k] = io.make();
+    ev_op[k] = io.make();
+    ev_out[k] = io.make();
+    if (!ev_in[k] || !ev_op[k] || !ev_out[k]) return sem_fail(SEM_ERR_CUDA, "sem_ax_assembled_host_batch: cudaEventCreate");
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    double *ub = u_dev2 + (size_t)(k & 1) * nU;
+    double *wb = w_dev2 + (size_t)(k & 1) * nU;
+    // copy-in: u buffer free once application k - 2's operator has read it
+    if (k >= 2) SEM_CUDA(cudaStreamWaitEvent(io.in, ev_op[k - 2], 0));
+    SEM_CUDA(cudaMemcpyAsync(ub, u_host[k], bytes, cudaMemcpyHostToDevice, io.in));
+    SEM_CUDA(cudaEventRecord(ev_in[k], io.in));
+    // operator: after its copy-in, and after application k - 2's result left w buffer
+    SEM_CUDA(cudaStreamWaitEvent(st, ev_in[k], 0));
+    if (k >= 2) SEM_CUDA(cudaStreamWaitEvent(st, ev_out[k - 2], 0));
+    SEM_CUDA(cudaMemsetAsync(wb, 0, bytes, st));
+    if (int rc = sem_launch_ax_assembled(m, h1, h2, ub, wb, nullptr, precision, st)) return rc;
+    SEM_CUDA(cudaEventRecord(ev_op[k], st));
+    // copy-out
+    SEM_CUDA(cudaStreamWaitEvent(io.out, ev_op[k], 0));
+    SEM_CUDA(cudaMemcpyAsync(w_host[k], wb, bytes, cudaMemcpyDeviceToHost, io.out));
+    SEM_CUDA(cudaEventRecord(ev_out[k], io.out));
+  }
+  SEM_CUDA(cudaStreamWaitEvent(st, ev_out[nsteps - 1], 0));
+  SEM_CUDA(cudaStreamSynchronize(st));
+  return SEM_OK;
+}
