@@ -778,18 +778,20 @@ __global__ void k_init_fcg(int64_t n, const double *__restrict__ b, const uint8_
 }
 
 // ---------------------------------------------------------------- host helpers
-// fixed-order sum of n partials into *out (one CTA of 256 threads): the
+// fixed-order sum of n partials into *out (one CTA of 1024 threads): the
 // outer operator leaves one p.w partial per element group
-__global__ void __launch_bounds__(256) k_sum_fixed(const double *__restrict__ part, int n, double *__restrict__ out) {
-  __shared__ double red[8];
+constexpr int kSumThreads = 1024;
+__global__ void __launch_bounds__(kSumThreads) k_sum_fixed(const double *__restrict__ part, int n,
+                                                           double *__restrict__ out) {
+  __shared__ double red[kSumThreads / 32];
   double v = 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) v += part[t];
+  for (int t = threadIdx.x; t < n; t += kSumThreads) v += part[t];
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += red[w];
+    for (int w = 0; w < kSumThreads / 32; ++w) s += red[w];
     *out = s;
   }
 }
@@ -1274,7 +1276,7 @@ extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, con
     SEM_CUDA(cudaMemsetAsync(P->w, 0, sizeof(double) * n, st));
     if ((rc = sem_launch_ax_assembled(m, P->h1, P->h2, P->p, P->w, P->pw_part, opts->precision, st, P->L[0].map)))
       return rc;
-    k_sum_fixed<<<1, 256, 0, st>>>(P->pw_part, npw, P->pw_part + npw);
+    k_sum_fixed<<<1, kSumThreads, 0, st>>>(P->pw_part, npw, P->pw_part + npw);
     SEM_LAUNCH_CHECK("k_sum_fixed");
     double pw = 0.0;
     SEM_CUDA(cudaMemcpyAsync(&pw, P->pw_part + npw, sizeof(double), cudaMemcpyDeviceToHost, st));
