@@ -225,7 +225,6 @@ struct DfCfg {
   // NP = 8: one element (64 threads) per CTA, so barriers wait on two warps only
   static constexpr int ELB = (NP == 8) ? 1 : (ELB_T < ELB_S ? ELB_T : (ELB_S > 0 ? ELB_S : 1));
   static constexpr int THREADS = N2 * ELB;
-  static constexpr int SMEM = 4 * TILE * ELB * (int)sizeof(float2);
   // the operator: tiles U, R, S, and T (the t-derivative) in a fourth tile
   // only when the Helmholtz term needs u at the end; otherwise T replaces U
   static constexpr int smem_ax(bool helm) { return (helm ? 4 : 3) * TILE * ELB * (int)sizeof(float2); }
