@@ -1,7 +1,8 @@
 """Pins of the oracle's p-multigrid preconditioner (Sec. 2.2: p-multigrid with
 4th-kind Chebyshev-accelerated smoothing): interpolation exactness, R = P^T,
 the 4th-kind Chebyshev error bound 1/(2k+1) (Lottes 2022), V-cycle symmetry,
-and the preconditioned flexible CG against a dense direct solve. CPU only."""
+and the preconditioned flexible CG against a dense direct solve, for the
+Poisson and the Helmholtz operator. CPU only."""
 import numpy as np
 import numpy.polynomial.legendre as npl
 import pytest
@@ -78,8 +79,9 @@ def test_chebyshev_fourth_kind_error_bound(k):
     assert worst >= 0.9 / (2 * k + 1)
 
 
-def test_vcycle_is_symmetric_with_exact_coarse_solve():
-    pm = pmg.PMG(box((2, 2, 2), 0.05), orders=(5, 2, 1), coarse_tol=1e-14)
+@pytest.mark.parametrize("h1,h2", [(1.0, 0.0), (0.3, 25.0)])
+def test_vcycle_is_symmetric_with_exact_coarse_solve(h1, h2):
+    pm = pmg.PMG(box((2, 2, 2), 0.05), orders=(5, 2, 1), h1=h1, h2=h2, coarse_tol=1e-14)
     rng = np.random.default_rng(5)
     mk = pm.levels[0].mk
     a, b = rng.standard_normal(len(mk)) * mk, rng.standard_normal(len(mk)) * mk
@@ -101,3 +103,23 @@ def test_fcg_matches_direct_solve_and_beats_jacobi():
     np.testing.assert_allclose(res.x, x_ref, rtol=0, atol=1e-10 * np.abs(x_ref).max())
     jac = oracle.pcg(m, b, tol=1e-12, maxit=2000)
     assert res.iterations * 4 < jac.iterations, (res.iterations, jac.iterations)
+
+
+def test_fcg_helmholtz_matches_direct_solve():
+    """h1 A + h2 B (the implicit diffusion operators of the time step): the
+    hierarchy re-discretises both terms on every level, and the flexible CG
+    reaches the dense direct solution of the masked Helmholtz system."""
+    bx = box((3, 2, 2), 0.05)
+    h1, h2 = 0.02, 400.0  # diffusion-to-mass ratio of the order of a time step's
+    pm = pmg.PMG(bx, orders=(6, 3, 1), h1=h1, h2=h2)
+    m = pm.levels[0].m
+    Hg, _, _ = dense_global(m, h1, h2)
+    free = m.mask == 1
+    b = np.random.default_rng(9).standard_normal(m.n_unique) * m.mask
+    x_ref = np.zeros(m.n_unique)
+    x_ref[free] = np.linalg.solve(Hg[np.ix_(free, free)], b[free])
+    res = pmg.fcg(pm, b, tol=1e-12, maxit=100)
+    assert res.converged
+    np.testing.assert_allclose(res.x, x_ref, rtol=0, atol=1e-10 * np.abs(x_ref).max())
+    jac = oracle.pcg(m, b, h1, h2, tol=1e-12, maxit=2000)
+    assert res.iterations <= jac.iterations, (res.iterations, jac.iterations)
