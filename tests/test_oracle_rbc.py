@@ -1,7 +1,8 @@
 """Pins of the oracle's Rayleigh-Benard BDF2/EXT2 step (Sec. 4.1, Eqs. (1)-(3);
 plates and periodicity of Sec. 4.4): exact steady states, second-order
 temporal accuracy on an exact solution, the wall term on an analytic field,
-and the weak divergence against dense brute force. CPU only."""
+the weak divergence against dense brute force, and the pressure step leaving
+a weakly divergence-free velocity (spectrally small in N). CPU only."""
 import numpy as np
 import pytest
 
@@ -117,3 +118,43 @@ def test_gradient_exact_for_polynomials():
     np.testing.assert_allclose(gr[0], 2 * m.X * m.Y - 2 * m.Z, atol=1e-11)
     np.testing.assert_allclose(gr[1], m.X ** 2, atol=1e-11)
     np.testing.assert_allclose(gr[2], 3 * m.Z ** 2 - 2 * m.X, atol=1e-11)
+
+
+def test_pressure_step_makes_velocity_weakly_divergence_free():
+    """After steps from a smooth perturbation, the weak divergence of the new
+    velocity, relative to its size, decays spectrally with the order N and is
+    far below that of the same steps with the pressure solve removed (a
+    mistake planted in the oracle: the Neumann solve returns zero)."""
+    ratios, ablated = [], []
+    for N in (3, 5, 7):
+        m = rbc_mesh((3, 3, 3), N)
+        xg, yg, zgv = np.zeros(m.n_unique), np.zeros(m.n_unique), np.zeros(m.n_unique)
+        xg[m.l2g], yg[m.l2g], zgv[m.l2g] = m.X, m.Y, m.Z
+        pert = 0.1 * np.sin(np.pi * zgv) * np.cos(2 * np.pi * xg) * np.cos(2 * np.pi * yg)
+
+        def run(no_pressure):
+            R = rbc.RBC(m, 1e5, 0.7, 2e-2, tol=1e-13)
+            orig = rbc._pcg_neumann
+            if no_pressure:
+                def zero(m_, b, tol, maxit):
+                    r = orig(m_, b, tol, maxit)
+                    r.x = np.zeros_like(r.x)
+                    return r
+                rbc._pcg_neumann = zero
+            try:
+                s = R.initial_state(pert)
+                for _ in range(3):
+                    s = R.step(s)
+            finally:
+                rbc._pcg_neumann = orig
+            uL = [oracle.scatter(m, c) for c in s.u]
+            wd = oracle.gather_sum(m, rbc.weak_div(m, R.geo, uL))
+            unorm = np.sqrt(sum(oracle.gather_sum(m, m.B * uL[c] * uL[c]).sum() for c in range(3)))
+            return np.linalg.norm(wd) / unorm
+
+        ratios.append(run(False))
+        ablated.append(run(True))
+    assert ratios[0] > ratios[1] > ratios[2], ratios
+    assert ratios[2] < ratios[0] / 10, ratios
+    for r, a in zip(ratios, ablated):
+        assert r < a / 10, (ratios, ablated)
