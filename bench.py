@@ -168,6 +168,21 @@ def time_oracle_axgs(w, budget_s: float, max_reps: int = 50):
     return gdofs, oracle.num_threads(), sample, el / reps
 
 
+def time_oracle_one_core(w):
+    """The same oracle sample on one host core (OpenMP limited to one thread
+    in a child process), a few applications."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, workloads; "
+            "g, c, s, _ = bench.time_oracle_axgs(workloads.WORKLOADS[%r], 2.0, max_reps=4); "
+            "print(json.dumps({'value': g, 'cores': c, 'sample': s}))") % (ROOT, w.name)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": d["value"], "unit": "GDOF/s", "cores": d["cores"], "sample": d["sample"]}
+    except (subprocess.SubprocessError, ValueError, IndexError, KeyError) as e:
+        return {"value": None, "note": f"one-core run failed: {type(e).__name__}"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -188,7 +203,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w.name, "N": w.N, "nel": list(w.nel),
                                             "sample": "24^3 elements per step"},
-            "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "one_core": time_oracle_one_core(w)},
             "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -566,7 +582,8 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         g, cores, sample, _ = time_oracle_axgs(w, 12.0)
-        cpu = {"value": g, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": g, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "one_core": time_oracle_one_core(w)}
 
     if rank == 0:
         line = {
