@@ -70,24 +70,6 @@ __device__ __forceinline__ void acc_add(Acc &acc, float bh, float bl) {
   acc.c = add(acc.c, add(err, bl));
 }
 
-// a + b of two accumulators (unnormalised result)
-__device__ __forceinline__ Acc sum(const Acc &a, const Acc &b) {
-  Acc r;
-  float err;
-  two_sum(a.s, b.s, r.s, err);
-  r.c = add(add(a.c, b.c), err);
-  return r;
-}
-
-// a - b
-__device__ __forceinline__ Acc diff(const Acc &a, const Acc &b) {
-  Acc r;
-  float err;
-  two_sum(a.s, -b.s, r.s, err);
-  r.c = add(sub(a.c, b.c), err);
-  return r;
-}
-
 // normalised (hi, lo) of an accumulator: TwoSum, valid for any magnitudes
 __device__ __forceinline__ float2 norm(const Acc &a) {
   float h, l;
