@@ -65,3 +65,28 @@ def test_adjoint_against_central_differences():
         d = rng.standard_normal(m.n_unique) * ta.mk
         fd = (J(T0 + eps * d) - J(T0 - eps * d)) / (2 * eps)
         assert abs(fd - np.dot(grad, d)) <= 1e-6 * (abs(fd) + 1e-12), (fd, np.dot(grad, d))
+
+
+@pytest.mark.parametrize("stretch", [0.0, 1.5])
+def test_nusselt_reads_the_bottom_plate_flux(stretch):
+    """T = 1 - z + c z (Lz - z)(1 + b x (Lx - x)) lies in the discrete space
+    (each element is affine in z with or without the tanh clustering of its
+    interfaces), so the GLL quadrature is exact: the bottom plate's mean flux
+    gives Nu_b = 1 - c Lz (1 + b Lx^2/6), the top plate's would give
+    1 + c Lz (1 + b Lx^2/6). Pins the plate (k = 0 of the bottom elements),
+    the sign and the area normalisation."""
+    m = rbc_mesh((3, 2, 3), 4, stretch)
+    g = rbc.geometry(m)
+    x = np.zeros(m.n_unique)
+    z = np.zeros(m.n_unique)
+    x[m.l2g] = m.X
+    z[m.l2g] = m.Z
+    Lx, Lz = m.L[0], m.L[2]
+    x = np.where(np.isclose(x, Lx), 0.0, x)  # the periodic seam holds one node for x = 0 and x = Lx
+    c, b = 0.3, 0.8
+    T = 1.0 - z + c * z * (Lz - z) * (1.0 + b * x * (Lx - x))
+    expect = 1.0 - c * Lz * (1.0 + b * Lx ** 2 / 6.0)
+    assert abs(adjoint.nusselt_bottom(m, g, T) - expect) < 1e-12
+    w = adjoint.bottom_weights(m, g)
+    assert abs(w.sum() - m.L[0] * m.L[1]) < 1e-12
+    assert np.all(w[np.repeat(np.arange(m.E) // (m.nel[0] * m.nel[1]) > 0, (m.N + 1) ** 3)] == 0.0)
