@@ -158,3 +158,26 @@ def test_pressure_step_makes_velocity_weakly_divergence_free():
     assert ratios[2] < ratios[0] / 10, ratios
     for r, a in zip(ratios, ablated):
         assert r < a / 10, (ratios, ablated)
+
+
+def test_bdf_ext_coefficients_are_exact_on_polynomials():
+    """The time-stepping coefficients (b0, b1, b2, a1, a2) of the step from
+    level n: (b0 f^{n+1} - b1 f^n - b2 f^{n-1}) / dt is exact for f' at
+    t^{n+1} on polynomials of the scheme's order (quadratics for BDF2, lines
+    for the BDF1 first step) and a1 f^n + a2 f^{n-1} extrapolates f^{n+1}
+    exactly on lines (EXT2) and constants (EXT1). Taylor tables of the
+    textbook schemes, checked on every monomial."""
+    dt = 0.37
+    for step, order in ((0, 1), (1, 2), (5, 2)):
+        b0, b1, b2, a1, a2 = rbc.coefficients(step)
+        for p in range(order + 1):
+            f = lambda t: (t / dt) ** p  # noqa: E731
+            df = p * (1.0 / dt) ** p * dt ** (p - 1) if p else 0.0  # f'(dt) for f = (t/dt)^p
+            bdf = (b0 * f(dt) - b1 * f(0.0) - b2 * f(-dt)) / dt
+            assert abs(bdf - df) < 1e-14 * max(1.0, abs(df)), (step, p)
+        for p in range(order):
+            f = lambda t: (t / dt) ** p  # noqa: E731
+            assert abs(a1 * f(0.0) + a2 * f(-dt) - f(dt)) < 1e-14, (step, p)
+        # and they are not exact one order higher (the scheme is of that order, no more)
+        f = lambda t: (t / dt) ** (order + 1)  # noqa: E731
+        assert abs((b0 * f(dt) - b1 * f(0.0) - b2 * f(-dt)) / dt - (order + 1) / dt) > 1e-3
