@@ -2,6 +2,8 @@
 summation (Sec. 2.2: matrix-free tensor contractions carried to deformed
 elements by the chain rule) against closed forms, invariants and dense brute
 force. CPU only."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -209,3 +211,18 @@ def test_element_matrices_affine_1d_limit():
     assert abs(A[0, 0] - 3 * h / 4) < 1e-15
     d = oracle.diag_assembled(m)
     np.testing.assert_allclose(d, np.diag(A), rtol=1e-14)
+
+
+def test_element_subset_equals_slices_of_the_whole_mesh():
+    """The per-element builder used for spot checks of meshes too large to
+    build whole gives, for any list of elements in any order, exactly the
+    elements of the whole mesh (same coordinates, G_ab and mass)."""
+    import workloads
+    w = dataclasses.replace(workloads.AX_GS_64.with_nel((3, 4, 2), name="subset"), N=4)
+    m = oracle.mesh_from_workload(w)
+    n3 = (w.N + 1) ** 3
+    elems = np.array([23, 0, 7, 7, 12, 5], dtype=np.int64)
+    X, Y, Z, G, B, D = oracle.element_subset(w, elems)
+    idx = (elems[:, None] * n3 + np.arange(n3)[None, :]).ravel()
+    assert np.array_equal(X, m.X[idx]) and np.array_equal(Y, m.Y[idx]) and np.array_equal(Z, m.Z[idx])
+    assert np.array_equal(G, m.G[:, idx]) and np.array_equal(B, m.B[idx]) and np.array_equal(D, m.D)
