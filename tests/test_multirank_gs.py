@@ -1,7 +1,8 @@
 """Multi-rank direct stiffness summation on CPU ranks (gloo): the element-slab
 partition's interface maps against brute force (bit-exact), and the summed
 result against the single-partition Q Q^T (Sec. 2.2: one rank per GPU,
-shared surface values summed across ranks)."""
+shared surface values summed across ranks), and a whole Jacobi-PCG over the
+partition against the single-partition solve."""
 import os
 import socket
 
@@ -148,3 +149,108 @@ def test_failed_rank_is_detected_on_the_host():
     msg, elapsed = res[0]
     assert msg == "heartbeat_missing=True exchange_failed=True", msg
     assert elapsed < 30.0
+
+
+def _worker_pcg(rank, world, port, case, h2, queue):
+    """Jacobi-PCG over the element-slab partition: each rank applies the local
+    operator to its own elements, sums the shared surface values with one
+    exchange per operator application (and one for the diagonal), and forms
+    inner products over its unique nodes with each shared node weighted by
+    1 / (ranks holding it), reduced across ranks."""
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        import paper_2501_13240_gb300 as sem
+        N = case["N"]
+        om = oracle.box_mesh(case["nel"], N, periodic=case["periodic"], dirichlet=case["dirichlet"],
+                             deform_amp=0.1, kappa=np.full(9, 1.0), phi=np.array([0.3, 0.7, 1.1]))
+        desc = sem.box_desc(case["nel"], N, periodic=case["periodic"], dirichlet=case["dirichlet"])
+        n3 = (N + 1) ** 3
+        e0, e1, _ = sem.sem_partition_info(desc, world, rank)
+        gids, nshare = sem.sem_partition_interface(desc, world, rank)
+        allg = np.unique(np.concatenate([sem.sem_partition_interface(desc, world, q)[0] for q in range(world)]))
+        mine = slice(e0 * n3, e1 * n3)
+        own = np.unique(om.l2g[mine])
+        loc = np.searchsorted(own, om.l2g[mine])  # local node -> this rank's unique node
+        at, slot = np.searchsorted(own, gids), np.searchsorted(allg, gids)
+        wdot = np.ones(len(own))
+        wdot[at] = 1.0 / nshare
+        mk = om.mask[own].astype(np.float64)
+        G = np.ascontiguousarray(om.G[:, mine])
+        B = np.ascontiguousarray(om.B[mine])
+
+        def exchange(part):
+            buf = torch.zeros(len(allg), dtype=torch.float64)
+            buf[slot] = torch.from_numpy(part[at])
+            dist.all_reduce(buf)
+            part[at] = buf.numpy()[slot]
+            return part
+
+        def assemble(vL):
+            part = np.zeros(len(own))
+            np.add.at(part, loc, vL)
+            return exchange(part)
+
+        def A(v):
+            return mk * assemble(oracle.ax_local_raw(N, om.D, G, B, (mk * v)[loc], 1.0, h2))
+
+        def dot(a, b):
+            t = torch.tensor([float(np.sum(wdot * a * b))], dtype=torch.float64)
+            dist.all_reduce(t)
+            return float(t[0])
+
+        dL = np.zeros(e1 * n3 - e0 * n3)
+        oracle.lib().or_diag_local(e1 - e0, N, np.ascontiguousarray(om.D.ravel()), np.ascontiguousarray(G.ravel()),
+                                   B, 1.0, float(h2), dL)
+        d = assemble(dL)
+        dinv = np.where(mk != 0, 1.0 / np.where(mk != 0, d, 1.0), 0.0)
+        b_all = om.mask * np.random.default_rng(23).standard_normal(om.n_unique)
+        ref = oracle.pcg(om, b_all, 1.0, h2, tol=1e-10, maxit=500)
+        b = b_all[own]
+        x = np.zeros_like(b)
+        r = b.copy()
+        bn = np.sqrt(dot(b, b))
+        z = dinv * r
+        p = z.copy()
+        rho = dot(r, z)
+        its = 0
+        for its in range(1, 501):
+            w = A(p)
+            alpha = rho / dot(p, w)
+            x += alpha * p
+            r -= alpha * w
+            if np.sqrt(dot(r, r)) <= 1e-10 * bn:
+                break
+            z = dinv * r
+            rho1 = dot(r, z)
+            p = z + (rho1 / rho) * p
+            rho = rho1
+        err = float(np.abs(x - ref.x[own]).max() / np.abs(ref.x).max())
+        dd = float(np.abs(d - oracle.diag_assembled(om, 1.0, h2)[own]).max())
+        queue.put((rank, its, ref.iterations, err, dd))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("case,h2", [(0, 0.0), (1, 0.5), (2, 0.0)])
+def test_partitioned_jacobi_pcg_matches_single_partition(world, case, h2):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_pcg, args=(r, world, port, CASES[case], h2, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, its, ref_its, err, dd in sorted(res):
+        assert abs(its - ref_its) <= 1, (rank, its, ref_its)
+        assert err < 1e-9, (rank, err)
+        assert dd < 1e-12, (rank, dd)
+    assert len({r[1] for r in res}) == 1  # every rank stops at the same iteration
