@@ -64,3 +64,36 @@ def test_write_ppm_host_only(tmp_path):
     assert (body[0, :, 2] == 255).all() and (body[1, :, 0] == 255).all()  # top row first in the file
     with pytest.raises(sem.SemError):
         sem.sem_write_ppm(str(tmp_path / "missing_dir" / "y.ppm"), img)
+
+
+def test_every_entry_point_rejects_null_arguments():
+    """Each C entry point, given NULL handles and pointers and zero sizes,
+    returns SEM_ERR_INVALID_ARG with text naming the call, before touching a
+    device; the destroy calls accept NULL as a no-op (like free)."""
+    import ctypes
+    L = sem.lib()
+    destroys = {"sem_mesh_destroy", "sem_rbc_destroy", "sem_tadv_destroy", "sem_pmg_destroy"}
+    for name in sem.EXPORTS:
+        if name in ("sem_last_error", "sem_version", "sem_pcg_noalloc_capacity"):
+            continue
+        f = getattr(L, name)
+        args = [0 if t is ctypes.c_int else 0.0 if t is ctypes.c_double else None for t in f.argtypes]
+        rc = f(*args)
+        if name in destroys:
+            assert rc == 0, name
+        else:
+            assert rc == -1, (name, rc)
+            msg = L.sem_last_error().decode()
+            assert msg.split(":")[0] in (name, "sem_partition"), (name, msg)
+
+
+@pytest.mark.skipif(__import__("torch").cuda.is_available(), reason="checks the behaviour without a GPU")
+def test_device_work_fails_loudly_without_a_gpu():
+    """No CPU fallback: with no GPU the first call that needs one (building a
+    mesh) returns SEM_ERR_CUDA with CUDA's message and hands out no mesh."""
+    import ctypes
+    d = sem.box_desc((2, 2, 2), 3)
+    h = ctypes.c_void_p()
+    rc = sem.lib().sem_mesh_create_box(ctypes.byref(d), None, ctypes.byref(h))
+    assert rc == -2 and h.value is None
+    assert "cuda" in sem.lib().sem_last_error().decode().lower()
