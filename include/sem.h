@@ -561,6 +561,24 @@ int sem_partition_info(const sem_box_desc *desc, int nranks, int rank, int64_t *
  * and, if nshare is not NULL, the number of ranks holding each. */
 int sem_partition_interface(const sem_box_desc *desc, int nranks, int rank, int64_t *gids, int32_t *nshare);
 
+/* The rank's exchange partners, for summing interface partial sums pairwise
+ * instead of over all ranks: the other ranks q that share interface nodes
+ * with it, ascending, into peers[i] = q and counts[i] = the number of nodes
+ * shared with q (both arrays hold at least nranks - 1 entries, or are NULL
+ * to count only), and their number into *npeers. Every node of an element-
+ * slab partition is held by at most two ranks, so a node's full sum is the
+ * rank's own partial sum plus the one partner's. Same argument checks as
+ * sem_partition_info; NULL npeers is SEM_ERR_INVALID_ARG. */
+int sem_partition_peers(const sem_box_desc *desc, int nranks, int rank, int32_t *peers, int64_t *counts,
+                        int32_t *npeers);
+
+/* The unique ids (ascending) that rank shares with peer, into
+ * gids[counts[i]] from sem_partition_peers. Both ranks of a pair get the same
+ * list in the same order, so their buffers of partial sums line up with no
+ * exchange of indices. A peer that shares nothing writes nothing.
+ * SEM_ERR_INVALID_ARG if peer is out of range or equals rank, or gids is NULL. */
+int sem_partition_peer_nodes(const sem_box_desc *desc, int nranks, int rank, int peer, int64_t *gids);
+
 /* Jacobi-PCG like sem_pcg_solve, for callers that cannot allocate device
  * memory themselves -- for example a host program or plug-in whose device
  * memory is owned entirely by another framework's allocator, or a loop that

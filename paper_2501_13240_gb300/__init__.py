@@ -43,6 +43,7 @@ EXPORTS = (
     "sem_tadv_nusselt", "sem_tadv_nusselt_grad", "sem_render_slice", "sem_render_scene", "sem_write_ppm",
     "sem_pmg_create", "sem_pmg_lambda", "sem_pmg_vcycle", "sem_pmg_prolong", "sem_pmg_restrict",
     "sem_pmg_pcg_solve", "sem_pmg_destroy", "sem_partition_info", "sem_partition_interface",
+    "sem_partition_peers", "sem_partition_peer_nodes",
 )
 
 
@@ -192,6 +193,9 @@ def lib() -> ctypes.CDLL:
         sig["sem_partition_info"] = ([ctypes.POINTER(sem_box_desc), _i, _i, ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], _i)
         sig["sem_partition_interface"] = ([ctypes.POINTER(sem_box_desc), _i, _i, _vp, _vp], _i)
+        sig["sem_partition_peers"] = ([ctypes.POINTER(sem_box_desc), _i, _i, _vp, _vp, ctypes.POINTER(ctypes.c_int32)],
+                                      _i)
+        sig["sem_partition_peer_nodes"] = ([ctypes.POINTER(sem_box_desc), _i, _i, _i, _vp], _i)
         for name, (args, res) in sig.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -360,6 +364,24 @@ def sem_partition_interface(desc: sem_box_desc, nranks: int, rank: int):
     c = np.zeros(max(n, 1), dtype=np.int32)
     _check(lib().sem_partition_interface(ctypes.byref(desc), int(nranks), int(rank), g.ctypes.data, c.ctypes.data))
     return g[:n], c[:n]
+
+
+def sem_partition_peers(desc: sem_box_desc, nranks: int, rank: int):
+    """[(peer, count)] of the ranks sharing interface nodes with `rank`, ascending."""
+    peers = np.zeros(max(nranks, 1), dtype=np.int32)
+    counts = np.zeros(max(nranks, 1), dtype=np.int64)
+    n = ctypes.c_int32()
+    _check(lib().sem_partition_peers(ctypes.byref(desc), int(nranks), int(rank), peers.ctypes.data,
+                                     counts.ctypes.data, ctypes.byref(n)))
+    return [(int(peers[i]), int(counts[i])) for i in range(n.value)]
+
+
+def sem_partition_peer_nodes(desc: sem_box_desc, nranks: int, rank: int, peer: int) -> np.ndarray:
+    """Unique ids (int64, ascending) that `rank` shares with `peer`."""
+    n = dict(sem_partition_peers(desc, nranks, rank)).get(int(peer), 0)
+    g = np.zeros(max(n, 1), dtype=np.int64)
+    _check(lib().sem_partition_peer_nodes(ctypes.byref(desc), int(nranks), int(rank), int(peer), g.ctypes.data))
+    return g[:n]
 
 
 def mesh_from_workload(w, stream=None, deterministic: bool = False) -> Mesh:

@@ -112,3 +112,38 @@ extern "C" int sem_partition_interface(const sem_box_desc *d, int nranks, int ra
   }
   return SEM_OK;
 }
+
+extern "C" int sem_partition_peers(const sem_box_desc *d, int nranks, int rank, int32_t *peers, int64_t *counts,
+                                   int32_t *npeers) {
+  if (int rc = check(d, nranks, rank)) return rc;
+  if (!npeers) return sem_fail(SEM_ERR_INVALID_ARG, "sem_partition_peers: NULL npeers");
+  const Lattice L = lattice(d);
+  std::vector<int64_t> per(nranks, 0);
+  for (int64_t Kw : iface_planes(d, nranks, rank))
+    for (int q : sharers(d, nranks, L, Kw, rank)) per[q] += L.nx * L.ny;
+  int32_t n = 0;
+  for (int q = 0; q < nranks; ++q) {
+    if (per[q] == 0) continue;
+    if (peers) peers[n] = q;
+    if (counts) counts[n] = per[q];
+    ++n;
+  }
+  *npeers = n;
+  return SEM_OK;
+}
+
+extern "C" int sem_partition_peer_nodes(const sem_box_desc *d, int nranks, int rank, int peer, int64_t *gids) {
+  if (int rc = check(d, nranks, rank)) return rc;
+  if (peer < 0 || peer >= nranks || peer == rank)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_partition_peer_nodes: need 0 <= peer < nranks, peer != rank");
+  if (!gids) return sem_fail(SEM_ERR_INVALID_ARG, "sem_partition_peer_nodes: NULL output");
+  const Lattice L = lattice(d);
+  int64_t t = 0;
+  for (int64_t Kw : iface_planes(d, nranks, rank)) {
+    const std::vector<int> s = sharers(d, nranks, L, Kw, rank);
+    if (std::find(s.begin(), s.end(), peer) == s.end()) continue;
+    for (int64_t J = 0; J < L.ny; ++J)
+      for (int64_t I = 0; I < L.nx; ++I) gids[t++] = I + L.nx * (J + L.ny * Kw);
+  }
+  return SEM_OK;
+}

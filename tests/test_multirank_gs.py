@@ -1,7 +1,8 @@
 """Multi-rank direct stiffness summation on CPU ranks (gloo): the element-slab
 partition's interface maps against brute force (bit-exact), and the summed
 result against the single-partition Q Q^T (Sec. 2.2: one rank per GPU,
-shared surface values summed across ranks), and a whole Jacobi-PCG over the
+shared surface values summed across ranks) both by an all-reduce and by
+pairwise exchanges over the neighbour plan, and a whole Jacobi-PCG over the
 partition against the single-partition solve."""
 import os
 import socket
@@ -254,3 +255,103 @@ def test_partitioned_jacobi_pcg_matches_single_partition(world, case, h2):
         assert err < 1e-9, (rank, err)
         assert dd < 1e-12, (rank, dd)
     assert len({r[1] for r in res}) == 1  # every rank stops at the same iteration
+
+
+def _worker_peers(rank, world, port, case, queue):
+    """Pairwise exchange over the neighbour plan: each rank trades its
+    partial sums at the nodes it shares with each partner (point to point,
+    no collective over all ranks) and adds them in ascending rank order, so
+    both ranks of a pair hold the same bits."""
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        import paper_2501_13240_gb300 as sem
+        om = oracle.box_mesh(case["nel"], case["N"], periodic=case["periodic"], dirichlet=case["dirichlet"])
+        desc = sem.box_desc(case["nel"], case["N"], periodic=case["periodic"], dirichlet=case["dirichlet"])
+        n3 = (case["N"] + 1) ** 3
+        e0, e1, ni = sem.sem_partition_info(desc, world, rank)
+        gids, _ = sem.sem_partition_interface(desc, world, rank)
+        mine = slice(e0 * n3, e1 * n3)
+        own = np.unique(om.l2g[mine])
+        peers = sem.sem_partition_peers(desc, world, rank)
+        brute = []
+        for q in range(world):
+            a, b, _ = sem.sem_partition_info(desc, world, q)
+            shared = np.intersect1d(own, om.l2g[a * n3:b * n3]) if q != rank else np.zeros(0)
+            if len(shared):
+                brute.append((q, shared))
+        plan_ok = [p for p, _ in peers] == [q for q, _ in brute]
+        nodes = {p: sem.sem_partition_peer_nodes(desc, world, rank, p) for p, _ in peers}
+        plan_ok &= all(np.array_equal(nodes[q], s) and c == len(s) for (q, s), (_, c) in zip(brute, peers))
+        plan_ok &= np.array_equal(np.unique(np.concatenate(list(nodes.values()) or [np.zeros(0, np.int64)])), gids)
+        plan_ok &= sum(c for _, c in peers) == ni
+        v = np.random.default_rng(29).standard_normal(om.n_local)
+        part = np.zeros(om.n_unique)
+        np.add.at(part, om.l2g[mine], v[mine])
+        recv = {}
+        reqs = []
+        for p, _ in peers:
+            recv[p] = torch.zeros(len(nodes[p]), dtype=torch.float64)
+            reqs.append(dist.isend(torch.from_numpy(part[nodes[p]].copy()), p))
+            reqs.append(dist.irecv(recv[p], p))
+        for r in reqs:
+            r.wait()
+        total = part.copy()
+        for p, _ in peers:
+            mine_p, theirs = part[nodes[p]], recv[p].numpy()
+            total[nodes[p]] = (mine_p + theirs) if rank < p else (theirs + mine_p)
+        ref = oracle.qqt(om, v)[mine]
+        err = float(np.abs(total[om.l2g[mine]] - ref).max() / np.abs(ref).max())
+        # both ranks of each pair hold the same bits on the shared nodes
+        back = {}
+        reqs = []
+        for p, _ in peers:
+            back[p] = torch.zeros(len(nodes[p]), dtype=torch.float64)
+            reqs.append(dist.isend(torch.from_numpy(total[nodes[p]].copy()), p))
+            reqs.append(dist.irecv(back[p], p))
+        for r in reqs:
+            r.wait()
+        same = all(np.array_equal(back[p].numpy(), total[nodes[p]]) for p, _ in peers)
+        queue.put((rank, bool(plan_ok), err, bool(same), len(peers)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3, 4])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_pairwise_exchange_over_the_neighbour_plan(world, case):
+    if world > CASES[case]["nel"][2]:
+        pytest.skip("more ranks than element planes")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_peers, args=(r, world, port, CASES[case], q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    periodic_z = CASES[case]["periodic"][2]
+    for rank, plan_ok, err, same, npeers in sorted(res):
+        assert plan_ok, rank
+        assert err < 1e-14, (rank, err)
+        assert same, rank
+        interior = 0 < rank < world - 1
+        assert npeers == (1 if world == 2 else 2 if (interior or periodic_z) else 1), (rank, npeers)
+
+
+def test_neighbour_plan_arguments():
+    import paper_2501_13240_gb300 as sem
+    d = sem.box_desc((2, 2, 4), 3, periodic=(0, 0, 1), dirichlet=(1, 1, 1, 1, 0, 0))
+    assert sem.sem_partition_peers(d, 1, 0) == []  # one rank: the periodic wrap is its own
+    assert sem.sem_partition_peers(d, 2, 0) == [(1, 2 * 7 * 7)]  # the middle plane and the wrapped one
+    with pytest.raises(sem.SemError):
+        sem.sem_partition_peer_nodes(d, 2, 0, 0)
+    with pytest.raises(sem.SemError):
+        sem.sem_partition_peer_nodes(d, 2, 0, 2)
+    assert len(sem.sem_partition_peer_nodes(d, 4, 0, 2)) == 0  # not a partner: nothing shared
