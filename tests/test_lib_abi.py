@@ -97,3 +97,14 @@ def test_device_work_fails_loudly_without_a_gpu():
     rc = sem.lib().sem_mesh_create_box(ctypes.byref(d), None, ctypes.byref(h))
     assert rc == -2 and h.value is None
     assert "cuda" in sem.lib().sem_last_error().decode().lower()
+
+
+def test_binding_refuses_host_tensors_for_device_arguments():
+    """Device arguments must be contiguous CUDA tensors of the stated dtype
+    and size: a host tensor is refused before any call into the library (the
+    binding never computes on the CPU)."""
+    import torch
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        sem._ptr(torch.zeros(8, dtype=torch.float64), torch.float64, 8, "u")
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        sem._ptr(np.zeros(8), torch.float64, 8, "u")
