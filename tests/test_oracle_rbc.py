@@ -2,7 +2,9 @@
 plates and periodicity of Sec. 4.4): exact steady states, second-order
 temporal accuracy on an exact solution, the wall term on an analytic field,
 the weak divergence against dense brute force, and the pressure step leaving
-a weakly divergence-free velocity (spectrally small in N). CPU only."""
+a weakly divergence-free velocity (spectrally small in N), the BDF/EXT
+coefficients on polynomials, and the onset of convection at the critical
+Rayleigh number of linear theory. CPU only."""
 import numpy as np
 import pytest
 
@@ -181,3 +183,36 @@ def test_bdf_ext_coefficients_are_exact_on_polynomials():
         # and they are not exact one order higher (the scheme is of that order, no more)
         f = lambda t: (t / dt) ** (order + 1)  # noqa: E731
         assert abs((b0 * f(dt) - b1 * f(0.0) - b2 * f(-dt)) / dt - (order + 1) / dt) > 1e-3
+
+
+def _onset_growth_rate(Ra, kc=3.117, dt=0.1, steps=160):
+    """Exponential growth rate of |w| for a perturbation T' = 1e-4 sin(pi z)
+    cos(kc x) in a box holding one wavelength, rigid isothermal plates,
+    Pr = 1 (fit over the second half of the run)."""
+    Lx = 2.0 * np.pi / kc
+    m = oracle.box_mesh((4, 1, 4), 5, L=(Lx, 0.5, 1.0), periodic=(1, 1, 0), dirichlet=(0, 0, 0, 0, 1, 1))
+    R = rbc.RBC(m, Ra, 1.0, dt, tol=1e-11)
+    x, z = np.zeros(m.n_unique), np.zeros(m.n_unique)
+    x[m.l2g], z[m.l2g] = m.X, m.Z
+    s = R.initial_state(1e-4 * np.sin(np.pi * z) * np.cos(kc * x))
+    amp = []
+    for _ in range(steps):
+        s = R.step(s)
+        amp.append(np.linalg.norm(s.u[2]))
+    t = dt * np.arange(1, steps + 1)
+    h = steps // 2
+    return np.polyfit(t[h:], np.log(np.array(amp[h:])), 1)[0]
+
+
+def test_onset_of_convection_at_the_critical_rayleigh_number():
+    """Linear stability of the Boussinesq equations (Sec. 4.1, Eqs. (1)-(3))
+    between rigid isothermal plates (Sec. 4.4): the conduction state loses
+    stability at Ra_c = 1707.76 with critical wavenumber k_c = 3.117
+    (Chandrasekhar 1961). The critical mode decays at Ra = 1650 and grows at
+    1770, and the zero of the growth rate (secant) lies within 1 % of Ra_c.
+    A wrong sign or scale of buoyancy, viscosity or diffusivity, or slip
+    walls, moves or removes the onset."""
+    s_lo, s_hi = _onset_growth_rate(1650.0), _onset_growth_rate(1770.0)
+    assert s_lo < 0.0 < s_hi, (s_lo, s_hi)
+    ra0 = 1650.0 + 120.0 * (-s_lo) / (s_hi - s_lo)
+    assert abs(ra0 / 1707.76 - 1.0) < 0.01, ra0
