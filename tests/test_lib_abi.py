@@ -108,3 +108,25 @@ def test_binding_refuses_host_tensors_for_device_arguments():
         sem._ptr(torch.zeros(8, dtype=torch.float64), torch.float64, 8, "u")
     with pytest.raises(TypeError, match="CUDA tensor"):
         sem._ptr(np.zeros(8), torch.float64, 8, "u")
+
+
+def test_readme_example_uses_existing_calls_and_keywords():
+    """The README's Python example names only functions and keyword
+    arguments the binding has (guards the documentation against drift)."""
+    import ast
+    import inspect
+    txt = open(os.path.join(ROOT, "README.md")).read()
+    code = txt.split("```python\n", 1)[1].split("```", 1)[0]
+    tree = ast.parse(code)
+    seen = 0
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Attribute) and isinstance(node.value, ast.Name) and node.value.id == "sem":
+            assert hasattr(sem, node.attr), node.attr
+            seen += 1
+        if isinstance(node, ast.Call) and isinstance(node.func, ast.Attribute) and \
+                isinstance(node.func.value, ast.Name) and node.func.value.id == "sem":
+            params = inspect.signature(getattr(sem, node.func.attr)).parameters
+            for kw in node.keywords:
+                assert kw.arg in params, (node.func.attr, kw.arg)
+            assert len(node.args) <= len(params), node.func.attr
+    assert seen >= 10
