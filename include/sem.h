@@ -579,6 +579,17 @@ int sem_partition_peers(const sem_box_desc *desc, int nranks, int rank, int32_t 
  * SEM_ERR_INVALID_ARG if peer is out of range or equals rank, or gids is NULL. */
 int sem_partition_peer_nodes(const sem_box_desc *desc, int nranks, int rank, int peer, int64_t *gids);
 
+/* The rank's surface elements, for overlapping the exchange with interior
+ * work (Sec. 2.2: update the elements on the subdomain surface, start the
+ * exchange of their shared values, update the interior elements, then finish
+ * the sums with what arrived). Writes the ids (ascending) of the elements
+ * that touch an interface node into elems (if not NULL; at most
+ * 2 nelx nely entries) and their number into *n_surface. Every
+ * contribution to an interface node comes from these elements, so the
+ * interface partial sums are complete after the surface pass. Same argument
+ * checks as sem_partition_info; NULL n_surface is SEM_ERR_INVALID_ARG. */
+int sem_partition_surface(const sem_box_desc *desc, int nranks, int rank, int64_t *elems, int64_t *n_surface);
+
 /* Jacobi-PCG like sem_pcg_solve, for callers that cannot allocate device
  * memory themselves -- for example a host program or plug-in whose device
  * memory is owned entirely by another framework's allocator, or a loop that

@@ -43,7 +43,7 @@ EXPORTS = (
     "sem_tadv_nusselt", "sem_tadv_nusselt_grad", "sem_render_slice", "sem_render_scene", "sem_write_ppm",
     "sem_pmg_create", "sem_pmg_lambda", "sem_pmg_vcycle", "sem_pmg_prolong", "sem_pmg_restrict",
     "sem_pmg_pcg_solve", "sem_pmg_destroy", "sem_partition_info", "sem_partition_interface",
-    "sem_partition_peers", "sem_partition_peer_nodes",
+    "sem_partition_peers", "sem_partition_peer_nodes", "sem_partition_surface",
 )
 
 
@@ -196,6 +196,8 @@ def lib() -> ctypes.CDLL:
         sig["sem_partition_peers"] = ([ctypes.POINTER(sem_box_desc), _i, _i, _vp, _vp, ctypes.POINTER(ctypes.c_int32)],
                                       _i)
         sig["sem_partition_peer_nodes"] = ([ctypes.POINTER(sem_box_desc), _i, _i, _i, _vp], _i)
+        sig["sem_partition_surface"] = ([ctypes.POINTER(sem_box_desc), _i, _i, _vp, ctypes.POINTER(ctypes.c_int64)],
+                                        _i)
         for name, (args, res) in sig.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -382,6 +384,15 @@ def sem_partition_peer_nodes(desc: sem_box_desc, nranks: int, rank: int, peer: i
     g = np.zeros(max(n, 1), dtype=np.int64)
     _check(lib().sem_partition_peer_nodes(ctypes.byref(desc), int(nranks), int(rank), int(peer), g.ctypes.data))
     return g[:n]
+
+
+def sem_partition_surface(desc: sem_box_desc, nranks: int, rank: int) -> np.ndarray:
+    """Element ids (int64, ascending) of the rank's elements touching an interface node."""
+    n = ctypes.c_int64()
+    _check(lib().sem_partition_surface(ctypes.byref(desc), int(nranks), int(rank), None, ctypes.byref(n)))
+    e = np.zeros(max(n.value, 1), dtype=np.int64)
+    _check(lib().sem_partition_surface(ctypes.byref(desc), int(nranks), int(rank), e.ctypes.data, ctypes.byref(n)))
+    return e[:n.value]
 
 
 def mesh_from_workload(w, stream=None, deterministic: bool = False) -> Mesh:

@@ -147,3 +147,24 @@ extern "C" int sem_partition_peer_nodes(const sem_box_desc *d, int nranks, int r
   }
   return SEM_OK;
 }
+
+extern "C" int sem_partition_surface(const sem_box_desc *d, int nranks, int rank, int64_t *elems,
+                                     int64_t *n_surface) {
+  if (int rc = check(d, nranks, rank)) return rc;
+  if (!n_surface) return sem_fail(SEM_ERR_INVALID_ARG, "sem_partition_surface: NULL n_surface");
+  const Lattice L = lattice(d);
+  const int ez0 = ez_begin(d, nranks, rank), ez1 = ez_begin(d, nranks, rank + 1);
+  // element planes next to a shared lattice plane: the first one (plane ez0 N) and the last (ez1 N)
+  std::vector<int> eplanes;
+  if (!sharers(d, nranks, L, wrapK(d, L, (int64_t)ez0 * d->N), rank).empty()) eplanes.push_back(ez0);
+  if (!sharers(d, nranks, L, wrapK(d, L, (int64_t)ez1 * d->N), rank).empty() &&
+      (eplanes.empty() || eplanes.back() != ez1 - 1))
+    eplanes.push_back(ez1 - 1);
+  const int64_t plane = (int64_t)d->nelx * d->nely;
+  int64_t t = 0;
+  for (int ez : eplanes)
+    for (int64_t i = 0; i < plane; ++i, ++t)
+      if (elems) elems[t] = (int64_t)ez * plane + i;
+  *n_surface = t;
+  return SEM_OK;
+}

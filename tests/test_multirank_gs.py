@@ -2,8 +2,9 @@
 partition's interface maps against brute force (bit-exact), and the summed
 result against the single-partition Q Q^T (Sec. 2.2: one rank per GPU,
 shared surface values summed across ranks) both by an all-reduce and by
-pairwise exchanges over the neighbour plan, and a whole Jacobi-PCG over the
-partition against the single-partition solve."""
+pairwise exchanges over the neighbour plan, the surface-first overlapped
+schedule, and a whole Jacobi-PCG over the partition against the
+single-partition solve."""
 import os
 import socket
 
@@ -355,3 +356,84 @@ def test_neighbour_plan_arguments():
     with pytest.raises(sem.SemError):
         sem.sem_partition_peer_nodes(d, 2, 0, 2)
     assert len(sem.sem_partition_peer_nodes(d, 4, 0, 2)) == 0  # not a partner: nothing shared
+
+
+def _worker_overlap(rank, world, port, case, queue):
+    """The overlapped schedule of Sec. 2.2 over the surface-element plan:
+    surface elements first, then the pairwise exchange of the interface
+    partial sums started (non-blocking) while the interior elements are
+    summed, then the received partial sums added."""
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        import paper_2501_13240_gb300 as sem
+        om = oracle.box_mesh(case["nel"], case["N"], periodic=case["periodic"], dirichlet=case["dirichlet"])
+        desc = sem.box_desc(case["nel"], case["N"], periodic=case["periodic"], dirichlet=case["dirichlet"])
+        n3 = (case["N"] + 1) ** 3
+        e0, e1, _ = sem.sem_partition_info(desc, world, rank)
+        gids, _ = sem.sem_partition_interface(desc, world, rank)
+        surf = sem.sem_partition_surface(desc, world, rank)
+        l2g = om.l2g.reshape(om.E, n3)
+        brute = np.array([e for e in range(e0, e1) if np.intersect1d(l2g[e], gids).size], dtype=np.int64)
+        plan_ok = np.array_equal(surf, brute)
+        inner = np.setdiff1d(np.arange(e0, e1), surf)
+        v = np.random.default_rng(31).standard_normal(om.n_local).reshape(om.E, n3)
+        part = np.zeros(om.n_unique)
+        np.add.at(part, l2g[surf].ravel(), v[surf].ravel())  # surface pass
+        full = np.zeros(om.n_unique)
+        np.add.at(full, l2g[e0:e1].ravel(), v[e0:e1].ravel())
+        plan_ok &= np.array_equal(part[gids], full[gids])  # interface sums complete after the surface pass
+        peers = [p for p, _ in sem.sem_partition_peers(desc, world, rank)]
+        nodes = {p: sem.sem_partition_peer_nodes(desc, world, rank, p) for p in peers}
+        recv = {p: torch.zeros(len(nodes[p]), dtype=torch.float64) for p in peers}
+        reqs = []
+        for p in peers:
+            reqs.append(dist.isend(torch.from_numpy(part[nodes[p]].copy()), p))
+            reqs.append(dist.irecv(recv[p], p))
+        np.add.at(part, l2g[inner].ravel(), v[inner].ravel())  # interior pass while the exchange is in flight
+        for r in reqs:
+            r.wait()
+        for p in peers:
+            mine_p, theirs = part[nodes[p]], recv[p].numpy()
+            part[nodes[p]] = (mine_p + theirs) if rank < p else (theirs + mine_p)
+        ref = oracle.qqt(om, v.ravel())[e0 * n3:e1 * n3]
+        err = float(np.abs(part[l2g[e0:e1].ravel()] - ref).max() / np.abs(ref).max())
+        queue.put((rank, bool(plan_ok), err, len(surf) // (case["nel"][0] * case["nel"][1]), e1 - e0))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_overlapped_exchange_over_the_surface_plan(world, case):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_overlap, args=(r, world, port, CASES[case], q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    periodic_z = CASES[case]["periodic"][2]
+    plane = CASES[case]["nel"][0] * CASES[case]["nel"][1]
+    for rank, plan_ok, err, nplanes, nelem in sorted(res):
+        assert plan_ok, rank
+        assert err < 1e-14, (rank, err)
+        shared_sides = int(rank > 0 or bool(periodic_z)) + int(rank < world - 1 or bool(periodic_z))
+        assert nplanes == min(shared_sides, nelem // plane), (rank, nplanes)
+
+
+def test_surface_plan_single_rank_and_arguments():
+    import paper_2501_13240_gb300 as sem
+    d = sem.box_desc((2, 3, 4), 3, periodic=(0, 0, 1), dirichlet=(1, 1, 1, 1, 0, 0))
+    assert len(sem.sem_partition_surface(d, 1, 0)) == 0  # one rank: no interface, all elements interior
+    assert np.array_equal(sem.sem_partition_surface(d, 4, 1), np.arange(6, 12))  # one plane, both sides
+    assert np.array_equal(sem.sem_partition_surface(d, 2, 0), np.arange(0, 12))  # periodic: planes 0 and 1
+    with pytest.raises(sem.SemError):
+        sem.sem_partition_surface(d, 5, 0)
