@@ -130,3 +130,40 @@ def test_readme_example_uses_existing_calls_and_keywords():
                 assert kw.arg in params, (node.func.attr, kw.arg)
             assert len(node.args) <= len(params), node.func.attr
     assert seen >= 10
+
+
+STRUCTS = ("sem_box_desc", "sem_mesh_info", "sem_solver_opts", "sem_solve_stats", "sem_pmg_opts", "sem_rbc_params",
+           "sem_step_stats", "sem_rbc_view", "sem_tadv_params", "sem_slice_desc", "sem_scene_desc")
+
+
+def test_binding_structs_match_the_c_header(tmp_path):
+    """Every struct the binding passes by pointer has the size and field
+    offsets the C compiler gives include/sem.h (a layout mismatch would
+    corrupt arguments silently)."""
+    import ctypes
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sem.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(sem, name)
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    c = {}
+    for ln in out:
+        if ln.strip():
+            parts = ln.split()
+            c[(parts[0], parts[1])] = int(parts[2])
+    for name in STRUCTS:
+        cls = getattr(sem, name)
+        assert ctypes.sizeof(cls) == c[(name, "size")], name
+        for fname, _ in cls._fields_:
+            assert getattr(cls, fname).offset == c[(name, fname)], (name, fname)
