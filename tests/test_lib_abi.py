@@ -167,3 +167,25 @@ def test_binding_structs_match_the_c_header(tmp_path):
         assert ctypes.sizeof(cls) == c[(name, "size")], name
         for fname, _ in cls._fields_:
             assert getattr(cls, fname).offset == c[(name, fname)], (name, fname)
+
+
+def test_binding_signatures_match_the_c_prototypes():
+    """Each function's ctypes argument list has the prototype's arity, and
+    each argument the prototype's kind: pointer, int, int64, size_t or
+    double."""
+    import ctypes
+    txt = open(os.path.join(ROOT, "include", "sem.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = dict((m.group(1), m.group(2)) for m in re.finditer(r"\b(sem_\w+)\s*\(([^)]*)\)\s*;", txt))
+    L = sem.lib()
+    scalar = {"int": ctypes.c_int, "double": ctypes.c_double, "int64_t": ctypes.c_int64, "size_t": ctypes.c_size_t}
+    for name in sem.EXPORTS:
+        params = [p.strip() for p in protos[name].split(",") if p.strip() and p.strip() != "void"]
+        args = getattr(L, name).argtypes
+        assert len(args) == len(params), (name, len(args), len(params))
+        for p, a in zip(params, args):
+            if "*" in p or "[" in p:
+                assert a in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(a, ctypes._Pointer), (name, p, a)
+            else:
+                base = p.replace("const", "").split()[0]
+                assert a is scalar[base] or (a is ctypes.c_int and base == "int"), (name, p, a)
