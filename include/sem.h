@@ -606,8 +606,8 @@ int sem_partition_surface(const sem_box_desc *desc, int nranks, int rank, int64_
  * device.
  *
  * The first call on each device looks up the array's device address (once,
- * with that device current); make that first call before any CUDA stream
- * capture. All calls share the one array and every call re-initialises what
+ * with that device current, and again after a device reset gives the device
+ * a new context); make that first call before any CUDA stream capture. All calls share the one array and every call re-initialises what
  * it reads, so results do not depend on earlier calls; but calls whose work
  * overlaps on the GPU (different streams, or different host threads on one
  * device) race on the array and must be serialised by the caller.

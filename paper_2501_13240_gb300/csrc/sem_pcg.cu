@@ -22,6 +22,8 @@
 #include <mutex>
 #include <string>
 
+#include <cuda.h>
+
 #include "sem_internal.h"
 
 namespace {
@@ -422,8 +424,12 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
   const double bnorm = sqrt(hs.bb);
   auto finish = [&](int status, int it, double rr) {
     if (scale != 1.0 && it > 0) {
+      // undo the scaling of x; if that fails, x is not the solution and the
+      // call reports the CUDA error instead of the solver status
       k_scale<<<grid_for(nU, 256), 256, 0, st>>>(nU, scale, x_g);
-      cudaStreamSynchronize(st);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) status = sem_cuda_fail(e, "sem_pcg_solve: rescaling the solution");
     }
     stats->iterations = it;
     stats->rel_residual = (bnorm > 0.0) ? sqrt(rr) / bnorm : 0.0;
@@ -476,16 +482,42 @@ static __device__ __align__(256) unsigned char g_pcg_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
+// per device: the array's address and the context it was looked up in (a
+// device reset replaces the context, and the module is loaded anew at
+// another address, so the address is looked up again)
 void *g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+
+// the driver's cuCtxGetCurrent, reached through the runtime (no link to libcuda)
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  return fn;
+}
 
 int scratch_address(int device, void **out) {
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   if (device < 0 || device >= kMaxDevices) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve_noalloc: device index out of range");
-  if (!g_scratch_ptr[device]) {
+  CtxGetCurrentFn getctx = ctx_get_current();
+  CUcontext ctx = nullptr;
+  if (getctx && getctx(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+  // look up once per device and context: on the first call, after a device
+  // reset, or whenever the current context cannot be identified
+  if (!g_scratch_ptr[device] || ctx == nullptr || ctx != g_scratch_ctx[device]) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
     if (e != cudaSuccess) return sem_cuda_fail(e, "sem_pcg_solve_noalloc: cudaGetSymbolAddress");
+    if (getctx && getctx(&ctx) != CUDA_SUCCESS) ctx = nullptr;  // the lookup makes the context current
     g_scratch_ptr[device] = p;
+    g_scratch_ctx[device] = ctx;
   }
   *out = g_scratch_ptr[device];
   return SEM_OK;
