@@ -59,9 +59,15 @@ enum {
                         unevaluated sum of two binary32 (hi + lo) and combined
                         with error-free transformations (Dekker 1971; Knuth's
                         TwoSum; Joldes, Muller & Popescu 2017). About 2^-44
-                        relative accuracy per operator application; inputs,
-                        outputs and intermediate values must stay within
-                        |x| in [2^-80, 2^100] (binary32 exponent range). */
+                        relative accuracy per operator application, relative
+                        to the largest value of each element. The operators
+                        compute every element at the power-of-two scale of its
+                        largest input (set from the binary64 exponent, exact),
+                        so any finite binary64 input is accepted; input values
+                        below 2^-126 times their element's largest count as
+                        zero. The geometric factors, B and the Helmholtz
+                        coefficients h1, h2 must lie within |x| in
+                        [2^-80, 2^100] (binary32 exponent range). */
   SEM_PREC_FP32 = 2, /* binary32 (multigrid smoothing levels) */
   SEM_PREC_BF16 = 3  /* geometric factors stored as bfloat16, binary32 arithmetic
                         (multigrid smoothing levels) */
@@ -131,6 +137,19 @@ const char *sem_last_error(void);
 
 /* Library version string. */
 const char *sem_version(void);
+
+/* Bound of the grid-wide waits inside cooperative kernels (the persistent
+ * N = 1 coarse solve of the p-multigrid): a CTA waiting at a grid barrier
+ * polls at most `polls` times (about 0.1 us each) and then sets an error
+ * flag, every CTA leaves the kernel at its next barrier, and the calling
+ * entry point returns SEM_ERR_CUDA ("a grid barrier wait exceeded its
+ * limit") with the CUDA context intact. 0 restores the default, 2^24 polls
+ * (about a second). The setting is process-wide and applies to launches
+ * made after the call; *previous (if not NULL) receives the old value.
+ * Failure detection (no counterpart in the paper, whose runs relied on
+ * scheduler-level health checks, Sec. 5.2): a kernel never hangs on a CTA
+ * that does not arrive. Always returns SEM_OK. */
+int sem_set_grid_wait_limit(unsigned polls, unsigned *previous);
 
 /* GLL nodes xi[N+1] (ascending, xi_0 = -1, xi_N = 1), weights
  * rho_i = 2 / (N (N+1) P_N(xi_i)^2) and derivative matrix D[(N+1)^2],

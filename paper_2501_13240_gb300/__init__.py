@@ -162,6 +162,7 @@ def lib() -> ctypes.CDLL:
         sig["sem_pcg_solve_noalloc"] = ([_vp, _d, _d, _vp, _vp, ctypes.POINTER(sem_solver_opts),
                                           ctypes.POINTER(sem_solve_stats), _vp], _i)
         sig["sem_pcg_noalloc_capacity"] = ([], ctypes.c_size_t)
+        sig["sem_set_grid_wait_limit"] = ([ctypes.c_uint, ctypes.POINTER(ctypes.c_uint)], _i)
         sig["sem_rbc_create"] = ([_vp, ctypes.POINTER(sem_rbc_params), _vp, _vp, ctypes.POINTER(_vp)], _i)
         sig["sem_bdf_ext_step"] = ([_vp, ctypes.POINTER(sem_step_stats), _vp], _i)
         sig["sem_rbc_fields"] = ([_vp, ctypes.POINTER(sem_rbc_view)], _i)
@@ -233,6 +234,14 @@ def _ptr(t, dtype=None, n=None, name="tensor"):
 
 def sem_version() -> str:
     return lib().sem_version().decode()
+
+
+def sem_set_grid_wait_limit(polls: int) -> int:
+    """Set the poll bound of grid-barrier waits in cooperative kernels (0:
+    the default); returns the previous bound."""
+    prev = ctypes.c_uint(0)
+    _check(lib().sem_set_grid_wait_limit(int(polls), ctypes.byref(prev)))
+    return int(prev.value)
 
 
 def sem_gll(N: int):

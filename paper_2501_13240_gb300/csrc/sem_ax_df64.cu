@@ -252,10 +252,17 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
   float2 *S = R + C::TILE;
   float2 *T = HELM ? S + C::TILE : U;  // without the Helmholtz term T replaces U after the r/s passes
   const int col = a + C::PJ * b;  // padded offset of the t-column (a, b, 0)
-  df::Acc pw = {0.0f, 0.0f};
+  double pw = 0.0;  // p.w of this thread's points (binary64 across elements)
   const int64_t estride = (int64_t)gridDim.x * C::ELB;
+  // per element: the largest binary64 exponent of its input values, which
+  // sets the power-of-two scale the element is computed at (values outside
+  // the binary32 exponent range stay exact to the operator's accuracy)
+  __shared__ int s_emax[C::ELB];
+  if (tid < C::ELB) s_emax[tid] = 0;
+  __syncthreads();
 
   int32_t go[NP];  // gather indices of this thread's column, kept for the scatter
+  int sh = 0;      // the element's scale: values are carried as x 2^-sh
   for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += estride) {
     const int64_t e = e0 + le;
     const bool act = e < E;
@@ -273,10 +280,17 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
 #pragma unroll
         for (int k = 0; k < NP; ++k) v[k] = act ? u[e * C::N3 + a + NP * b + C::N2 * k] : 0.0;
       }
+      int em = 0;
 #pragma unroll
-      for (int k = 0; k < NP; ++k) U[col + C::PK * k] = df::from_f64(v[k]);
+      for (int k = 0; k < NP; ++k) em = max(em, df::exp_field(v[k]));
+      atomicMax(&s_emax[le], em);
+      __syncthreads();
+      sh = s_emax[le] - 1023;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) U[col + C::PK * k] = df::from_f64_scaled(v[k], sh);
     }
     __syncthreads();
+    if (t == 0) s_emax[le] = 0;  // every thread of the element has read it
     // P1: forward contractions, r-, s- and t-lines, one loop body (when T
     // replaces U, the t-lines wait until every thread has read its r/s lines)
 #pragma unroll 1
@@ -339,6 +353,7 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
     }
     __syncthreads();
     // P4: sum the three directions, scale, convert, write
+    df::Acc pwe = {0.0f, 0.0f};  // this element's p.w terms (scaled by 2^-2sh)
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       const int q = col + C::PK * k;
@@ -358,19 +373,23 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
         v = df::norm(o);
       }
       if (act) {
-        const double vd = df::to_f64(v.x, v.y);
+        const double vd = df::to_f64_scaled(v.x, v.y, sh);
         if (ASSEMBLED) {
           const int32_t g = go[k];
           if (wloc) wloc[e * C::N3 + p] = (g >= 0) ? vd : 0.0;
           else if (g >= 0) atomicAdd(&w[g], vd);
           if (pw_partial) {  // u at the point: from U, or gathered again (L2) when T replaced U
-            const float2 xk = HELM ? U[q] : df::from_f64((g >= 0) ? u[g] : 0.0);
-            df::mac(pw, xk.x, xk.y, v.x, v.y);
+            const float2 xk = HELM ? U[q] : df::from_f64_scaled((g >= 0) ? u[g] : 0.0, sh);
+            df::mac(pwe, xk.x, xk.y, v.x, v.y);
           }
         } else {
           w[e * C::N3 + p] = vd;
         }
       }
+    }
+    if (ASSEMBLED && pw_partial != nullptr) {
+      const float2 pn = df::norm(pwe);
+      pw += df::to_f64_scaled(pn.x, pn.y, 2 * sh);
     }
     __syncthreads();
   }
@@ -378,8 +397,7 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
     // fixed-order CTA sum: a shuffle tree per warp when the CTA is whole
     // warps, else (a partial warp) a serial sum over shared memory
     double *red = reinterpret_cast<double *>(sm2);  // the tiles are free after the last barrier
-    const float2 pn = df::norm(pw);
-    double v = (double)pn.x + (double)pn.y;
+    double v = pw;
     if constexpr (C::THREADS % 32 == 0) {
       for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
       if ((tid & 31) == 0) red[tid >> 5] = v;

@@ -114,15 +114,22 @@ __global__ void __launch_bounds__(128)
                  const int *__restrict__ skip) {
   if (skip != nullptr && *skip != 0) return;
   __shared__ double red[32];
-  df::Acc pw = {0.0f, 0.0f};
+  double pw = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
     int32_t gi[8];
     float2 x[8];
+    double uv[8];
+    int em = 0;  // the element is computed at the scale 2^-sh of its largest input
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       gi[a] = map[e * 8 + a];
-      x[a] = df::from_f64(gi[a] >= 0 ? u[gi[a]] : 0.0);
+      uv[a] = gi[a] >= 0 ? u[gi[a]] : 0.0;
+      em = max(em, df::exp_field(uv[a]));
     }
+    const int sh = em - 1023;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) x[a] = df::from_f64_scaled(uv[a], sh);
+    df::Acc pwe = {0.0f, 0.0f};
     float2 Kv[kTri];
 #pragma unroll
     for (int t = 0; t < kTri; ++t) Kv[t] = Kdf[(int64_t)t * E + e];
@@ -139,15 +146,18 @@ __global__ void __launch_bounds__(128)
         df::mac(o, h2.x, h2.y, buv.x, buv.y);
         v = df::norm(o);
       }
-      const double vd = df::to_f64(v.x, v.y);
+      const double vd = df::to_f64_scaled(v.x, v.y, sh);
       if (wloc) wloc[e * 8 + a] = gi[a] >= 0 ? vd : 0.0;
       else if (gi[a] >= 0) atomicAdd(&w[gi[a]], vd);
-      if (pw_partial) df::mac(pw, x[a].x, x[a].y, v.x, v.y);
+      if (pw_partial) df::mac(pwe, x[a].x, x[a].y, v.x, v.y);
+    }
+    if (pw_partial) {
+      const float2 pn = df::norm(pwe);
+      pw += df::to_f64_scaled(pn.x, pn.y, 2 * sh);
     }
   }
   if (pw_partial) {
-    const float2 pn = df::norm(pw);
-    const double s = block_pw_sum((double)pn.x + (double)pn.y, red);
+    const double s = block_pw_sum(pw, red);
     if (threadIdx.x == 0) pw_partial[blockIdx.x] = s;
   }
 }
@@ -207,9 +217,7 @@ struct GridBar {
   int err, pad;
 };
 
-constexpr unsigned kSpinLimit = 1u << 24;  // polls of ~0.1 us: about a second
-
-__device__ bool grid_sync(GridBar *gb, unsigned nblocks) {
+__device__ bool grid_sync(GridBar *gb, unsigned nblocks, unsigned spin_limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -223,7 +231,7 @@ __device__ bool grid_sync(GridBar *gb, unsigned nblocks) {
       atomicAdd(&gb->gen, 1u);
     } else {
       for (unsigned it = 0; *vgen == g0; ++it) {
-        if (it > kSpinLimit) {
+        if (it >= spin_limit) {
           ok = false;
           atomicExch(&gb->err, 1);
           break;
@@ -267,6 +275,7 @@ struct CoarseArgs {
   double *out_rel;
   double tol;
   int maxit;
+  unsigned spin_limit;  // polls of a grid-barrier wait before it gives up
 };
 
 // w += h1 K p (+ h2 B p) over this thread's elements; returns its p.w contribution
@@ -317,7 +326,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_n1(CoarseArgs a) {
   for (int64_t g = t0; g < a.nU; g += nt) s = fma(a.b[g], a.b[g], s);
   s = block_sum_d(s, red);
   if (threadIdx.x == 0) mine[0] = s;
-  if (!grid_sync(a.bar, nb)) return;
+  if (!grid_sync(a.bar, nb, a.spin_limit)) return;
   const double bb = sum_parts(a.part, nb, 0, red);
   const double bnorm = sqrt(bb);
   if (!(bnorm > 0.0) || !isfinite(bb)) {
@@ -342,7 +351,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_n1(CoarseArgs a) {
   }
   s = block_sum_d(s, red);
   if (threadIdx.x == 0) mine[1] = s;
-  if (!grid_sync(a.bar, nb)) return;
+  if (!grid_sync(a.bar, nb, a.spin_limit)) return;
   double rz = sum_parts(a.part, nb, 1, red), rr = bb * inv * inv;
   const double thresh = a.tol * bnorm * inv;
   int status = SEM_ERR_NOT_CONVERGED, it = 0;
@@ -351,7 +360,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_n1(CoarseArgs a) {
     s = n1_apply<HELM>(a, t0, nt);  // w = A p
     s = block_sum_d(s, red);
     if (threadIdx.x == 0) mine[2] = s;
-    if (!grid_sync(a.bar, nb)) return;
+    if (!grid_sync(a.bar, nb, a.spin_limit)) return;
     const double pw = sum_parts(a.part, nb, 2, red);
     if (!(pw > 0.0) || !isfinite(pw)) {
       status = SEM_ERR_BREAKDOWN;
@@ -373,7 +382,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_n1(CoarseArgs a) {
       mine[3] = sz;
       mine[0] = sr;
     }
-    if (!grid_sync(a.bar, nb)) return;
+    if (!grid_sync(a.bar, nb, a.spin_limit)) return;
     const double rzn = sum_parts(a.part, nb, 3, red);
     rr = sum_parts(a.part, nb, 0, red);
     if (isfinite(rr) && sqrt(rr) <= thresh) {
@@ -387,7 +396,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_n1(CoarseArgs a) {
     const double beta = rzn / rz;
     rz = rzn;
     for (int64_t g = t0; g < a.nU; g += nt) a.p[g] = fma(beta, a.p[g], a.dinv[g] * a.r[g]);
-    if (!grid_sync(a.bar, nb)) return;
+    if (!grid_sync(a.bar, nb, a.spin_limit)) return;
   }
   for (int64_t g = t0; g < a.nU; g += nt) a.x[g] *= scale;
   if (lead) {
@@ -443,6 +452,7 @@ int sem_pcg_n1_persistent(const sem_mesh *m, double h1, double h2, const double 
   a.out_rel = reinterpret_cast<double *>(ires + 2);
   a.tol = tol;
   a.maxit = maxit;
+  a.spin_limit = sem_grid_wait_limit();
   SEM_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBar), st));
   void *args[] = {&a};
   SEM_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(nb), dim3(256), args, 0, st));

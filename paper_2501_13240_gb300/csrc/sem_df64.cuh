@@ -121,4 +121,43 @@ __device__ __forceinline__ double to_f64(float h, float l) {
   return __longlong_as_double(D);
 }
 
+// Biased binary64 exponent of x (0 for zero and subnormals), or 0 for
+// infinities and NaN so that they do not set an element's scale.
+__device__ __forceinline__ int exp_field(double x) {
+  const int e = (int)((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7FFull);
+  return e == 0x7FF ? 0 : e;
+}
+
+// Power-of-two scaling for values outside the binary32 exponent range: an
+// element's values are carried as x 2^-sh with sh the unbiased exponent of
+// its largest |x|, so the largest maps to [1, 2) and everything below it by
+// up to 2^-126 stays representable (smaller values flush to zero, below the
+// accuracy the operator promises relative to the element's largest value).
+// sh comes from exp_field: sh = emax - 1023.
+//
+// (hi, lo) of x 2^-sh; infinities and NaN keep their class.
+__device__ __forceinline__ float2 from_f64_scaled(double x, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FFull);
+  if (e == 0x7FF || sh == 0) return from_f64(x);
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const int es = e - sh;  // biased exponent of the scaled value
+  if (e == 0 || es <= 896) return make_float2(__uint_as_float(sgn), 0.0f);
+  if (es >= 896 + 255) return make_float2(__uint_as_float(sgn | 0x7F800000u), 0.0f);
+  const unsigned long long bs = (b & ~(0x7FFull << 52)) | ((unsigned long long)es << 52);
+  return from_f64(__longlong_as_double((long long)bs));
+}
+
+// nearest binary64 of (h + l) 2^sh (the inverse scaling of from_f64_scaled)
+__device__ __forceinline__ double to_f64_scaled(float h, float l, int sh) {
+  const double d = to_f64(h, l);
+  if (sh == 0) return d;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7FFull);
+  if (e == 0 || e == 0x7FF) return d;  // zero (h = 0) or not finite
+  const int es = e + sh;
+  if (es >= 1 && es <= 0x7FE) return __longlong_as_double((long long)(b + ((unsigned long long)(long long)sh << 52)));
+  return ldexp(d, sh);  // result below the normal range or overflowing: rare slow path
+}
+
 }  // namespace df

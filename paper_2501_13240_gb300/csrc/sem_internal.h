@@ -109,6 +109,9 @@ size_t sem_pcg_n1_workspace_bytes(const sem_mesh *m);
 int sem_pcg_n1_persistent(const sem_mesh *m, double h1, double h2, const double *b, double *x, const double *dinv,
                           const int32_t *map, double tol, int maxit, void *work, int *iters, double *rel,
                           cudaStream_t st);
+// polls (of about 0.1 us) after which a grid-barrier wait of a cooperative
+// kernel gives up and the kernel ends with an error flag (sem_set_grid_wait_limit)
+unsigned sem_grid_wait_limit();
 int sem_launch_gather_add_f(const sem_mesh *m, const float *wL, float *w, cudaStream_t st);
 // binary64-accurate element-local field operators in double-float
 // arithmetic; Rdf = the inverse Jacobian dr_a/dx_c split to (hi, lo),

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -28,6 +29,17 @@ int sem_cuda_fail(cudaError_t e, const char *what) {
 
 extern "C" const char *sem_last_error(void) { return g_last_error.c_str(); }
 extern "C" const char *sem_version(void) { return "semgb 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------- bounded device waits
+static std::atomic<unsigned> g_grid_wait_limit{1u << 24};
+
+unsigned sem_grid_wait_limit() { return g_grid_wait_limit.load(std::memory_order_relaxed); }
+
+extern "C" int sem_set_grid_wait_limit(unsigned polls, unsigned *previous) {
+  const unsigned old = g_grid_wait_limit.exchange(polls == 0 ? (1u << 24) : polls);
+  if (previous) *previous = old;
+  return SEM_OK;
+}
 
 // ---------------------------------------------------------------- GLL
 // Interior GLL nodes are the zeros of (1 - x^2) P_N'(x) = N (P_{N-1}(x) - x P_N(x)).

@@ -198,16 +198,32 @@ def test_large_grid_stride_assembled():
     gm.destroy()
 
 
-@pytest.mark.parametrize("scale", [1.0, 1e-20, 3.7e25, 2.0 ** -60])
-def test_df64_wide_magnitudes(scale):
-    """The double-float path keeps binary64-level accuracy for inputs far
-    from 1 in magnitude (within its documented range)."""
-    spec = dict(nel=(3, 2, 2), N=7, deform=0.05)
+WIDE = [1.0, 1e-20, 3.7e25, 2.0 ** -60, 1e40, 1e-35, 1e200, 1e-200]
+
+
+@pytest.mark.parametrize("scale", WIDE)
+@pytest.mark.parametrize("N", [7, 4, 1])
+def test_df64_wide_magnitudes(scale, N):
+    """The double-float operators (local and assembled, Helmholtz and
+    Poisson) keep binary64-level accuracy for inputs far outside the binary32
+    exponent range: each element is computed at the power-of-two scale of its
+    largest input. Nothing comes back infinite or flushed to zero."""
+    spec = dict(nel=(3, 2, 2), N=N, deform=0.05)
     om, gm = make(spec)
-    u = np.random.default_rng(22).uniform(-1, 1, om.n_local) * scale
+    rng = np.random.default_rng(22)
+    u = rng.uniform(-1, 1, om.n_local) * scale
     w = torch.empty(om.n_local, dtype=torch.float64, device="cuda")
     sem.sem_ax_apply(gm, 1.0, 0.0, dev(u), w, precision=sem.SEM_PREC_DF64)
-    assert rel_err(host(w), oracle.ax_local(om, u)) < RTOL
+    ref = oracle.ax_local(om, u)
+    assert np.isfinite(host(w)).all() and rel_err(host(w), ref) < RTOL
+    ug = rng.uniform(-1, 1, om.n_unique) * scale
+    for h1, h2 in [(1.0, 0.0), (0.7, 30.0)]:
+        wg = torch.empty(om.n_unique, dtype=torch.float64, device="cuda")
+        sem.sem_ax_assembled(gm, h1, h2, dev(ug), wg, precision=sem.SEM_PREC_DF64)
+        refg = oracle.apply_assembled(om, ug, h1, h2)
+        got = host(wg)
+        assert np.isfinite(got).all() and rel_err(got, refg) < RTOL, (h1, h2)
+        assert (got[refg != 0] != 0).all()
     gm.destroy()
 
 

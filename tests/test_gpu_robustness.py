@@ -145,3 +145,55 @@ def test_truncated_checkpoint_is_rejected(tmp_path):
     sem.sem_rbc_load(st, str(path))  # the whole file still loads
     st.destroy()
     gm.destroy()
+
+
+def test_pcg_wall_clock_limit_returns_timeout():
+    """The host-side wall-clock limit of sem_pcg_solve (opts.timeout_s): a
+    solve needing thousands of iterations, given a microsecond, stops at the
+    host's next check of the scalars with SEM_ERR_TIMEOUT and the iterate
+    reached so far (already scaled back): CG lowers the energy
+    1/2 x.Ax - b.x monotonically from its value 0 at x = 0."""
+    kappa = np.array([[1.0, 2.0, 1.0], [2.0, 1.0, 1.0], [1.0, 1.0, 2.0]])
+    gm = sem.sem_mesh_create_box((12, 12, 12), 7, deform_amp=0.05, kappa=kappa, phi=np.array([0.3, 1.7, 4.1]))
+    _, mask = gm.maps()
+    rng = np.random.default_rng(11)
+    b = torch.from_numpy(rng.standard_normal(gm.n_unique) * mask).cuda()
+    x = torch.zeros_like(b)
+    st = sem.sem_pcg_solve(gm, 1.0, 0.0, b, x, tol=1e-14, maxit=100000, precision=sem.SEM_PREC_DF64,
+                           timeout_s=1e-6, raise_on_error=False)
+    assert st["status"] == sem.SEM_ERR_TIMEOUT, st
+    assert 0 < st["iterations"] < 100000 and np.isfinite(st["rel_residual"])
+    w = torch.zeros_like(b)
+    sem.sem_ax_assembled(gm, 1.0, 0.0, x, w, sem.SEM_PREC_DF64)
+    xs, ws, bs = x.cpu().numpy(), w.cpu().numpy(), b.cpu().numpy()
+    assert 0.5 * xs @ ws - bs @ xs < 0.0
+    gm.destroy()
+
+
+def test_grid_barrier_wait_limit_ends_the_coarse_solve():
+    """The grid barriers of the cooperative N = 1 coarse solve are bounded
+    waits: with the bound set to one poll, CTAs that arrive early give up, the
+    kernel ends without hanging and the V-cycle returns SEM_ERR_CUDA; with the
+    default bound restored, the same context runs the V-cycle again and gives
+    the result of an undisturbed run."""
+    gm = sem.sem_mesh_create_box((24, 24, 24), 7)  # coarse level: 25^3 nodes, dozens of CTAs
+    gp = sem.sem_pmg_create(gm, orders=(7, 3, 1))
+    _, mask = gm.maps()
+    r = torch.from_numpy(np.random.default_rng(12).standard_normal(gm.n_unique) * mask).cuda()
+    z_ref = torch.zeros_like(r)
+    sem.sem_pmg_vcycle(gp, r, z_ref)
+    prev = sem.sem_set_grid_wait_limit(1)
+    try:
+        with pytest.raises(sem.SemError) as ei:
+            sem.sem_pmg_vcycle(gp, r, torch.zeros_like(r))
+        assert ei.value.code == sem.SEM_ERR_CUDA
+        assert "grid barrier" in str(ei.value)
+    finally:
+        sem.sem_set_grid_wait_limit(0)
+    assert prev == 1 << 24
+    z = torch.zeros_like(r)
+    sem.sem_pmg_vcycle(gp, r, z)
+    zr = z_ref.cpu().numpy()
+    assert np.abs(z.cpu().numpy() - zr).max() <= 1e-5 * np.abs(zr).max()
+    gp.destroy()
+    gm.destroy()

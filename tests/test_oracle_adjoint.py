@@ -90,3 +90,32 @@ def test_nusselt_reads_the_bottom_plate_flux(stretch):
     w = adjoint.bottom_weights(m, g)
     assert abs(w.sum() - m.L[0] * m.L[1]) < 1e-12
     assert np.all(w[np.repeat(np.arange(m.E) // (m.nel[0] * m.nel[1]) > 0, (m.N + 1) ** 3)] == 0.0)
+
+
+def test_transport_replays_the_rbc_temperatures():
+    """The frozen-velocity temperature steps are the temperature update of the
+    RBC step (Sec. 4.1 Eq. (2)): fed the velocity u^n at the start of every
+    step of an oracle RBC run, TAdv.forward reproduces that run's T^1..T^K to
+    the solver tolerance. The two are written separately (the lifting enters
+    as H_L Tb in one and as (b0/dt) B Tb + kappa A Tb in the other), so a
+    dropped term, a wrong BDF/EXT coefficient or a wrong start-up step in
+    either breaks the match."""
+    m = rbc_mesh((2, 2, 3), 4, 1.5)
+    Ra, Pr, dt, K = 2e4, 1.0, 5e-3, 5
+    R = rbc.RBC(m, Ra, Pr, dt, tol=1e-13)
+    pert = 0.3 * np.random.default_rng(9).standard_normal(m.n_unique)
+    s = R.initial_state(pert)
+    T0 = s.T.copy()
+    us, Ts = [], []
+    for _ in range(K):
+        us.append([c.copy() for c in s.u])
+        s = R.step(s)
+        Ts.append(s.T.copy())
+    assert max(np.abs(c).max() for c in s.u) > 1e-4  # buoyancy has set the fluid moving
+    ta = adjoint.TAdv(m, R.kappa, dt, tol=1e-13)
+    for k in range(1, K + 1):
+        Tk = ta.forward(T0, us[:k])
+        assert np.abs(Tk - Ts[k - 1]).max() < 1e-10, k
+    # the velocity matters: replaying with the velocity of the wrong step fails
+    shifted = [us[0]] + us[:-1]
+    assert np.abs(ta.forward(T0, shifted) - Ts[-1]).max() > 1e-8
