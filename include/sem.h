@@ -196,6 +196,16 @@ int sem_mesh_validate(const sem_mesh *m);
  * serialised by the caller). Turning it off synchronises the device. */
 int sem_mesh_set_deterministic(sem_mesh *m, int on);
 
+/* Arithmetic route of the double-float operator at N = 7 (SEM_PREC_DF64):
+ * on = 1 (the default) evaluates the 1-D tensor contractions of Sec. 2.2
+ * exactly on the fp16 tensor cores (operands cut into five 10-bit digits on
+ * a fixed-point grid per element, digit products summed exactly in binary32
+ * by level, levels recombined to double-float); on = 0 uses the compensated
+ * double-float dot products on the binary32 pipe. Both meet the same
+ * binary64-level accuracy; the setting exists to compare them. Other orders
+ * always use the binary32 route. */
+int sem_mesh_set_tensor_cores(sem_mesh *m, int on);
+
 /* Copy l2g (n_local int32) and mask (n_unique uint8) to host arrays; either
  * may be NULL. Synchronous. */
 int sem_mesh_copy_maps(const sem_mesh *m, int32_t *l2g_host, uint8_t *mask_host);

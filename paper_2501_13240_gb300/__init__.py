@@ -142,6 +142,7 @@ def lib() -> ctypes.CDLL:
             "sem_mesh_destroy": ([_vp], _i),
             "sem_mesh_info_get": ([_vp, ctypes.POINTER(sem_mesh_info)], _i),
             "sem_mesh_set_deterministic": ([_vp, _i], _i),
+            "sem_mesh_set_tensor_cores": ([_vp, _i], _i),
             "sem_mesh_validate": ([_vp], _i),
             "sem_mesh_copy_maps": ([_vp, _vp, _vp], _i),
             "sem_mesh_copy_gs_tables": ([_vp, _vp, _vp], _i),
@@ -358,6 +359,12 @@ def sem_mesh_validate(mesh: Mesh):
 
 def sem_mesh_set_deterministic(mesh: Mesh, on: bool = True):
     _check(lib().sem_mesh_set_deterministic(mesh.handle, int(bool(on))))
+
+
+def sem_mesh_set_tensor_cores(mesh: Mesh, on: bool = True):
+    """N = 7 double-float operator on the tensor pipe (default) or on the
+    binary32 pipe."""
+    _check(lib().sem_mesh_set_tensor_cores(mesh.handle, int(bool(on))))
 
 
 def sem_partition_info(desc: sem_box_desc, nranks: int, rank: int):

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(AxCfg<NP>::THREADS)
     k_ax_fp64(int64_t E, const double *__restrict__ Dg, const double *__restrict__ G, const double *__restrict__ B,
               double h1, double h2, const double *__restrict__ u, double *__restrict__ w,
               const int32_t *__restrict__ l2gm, double *__restrict__ pw_partial, double *__restrict__ wloc,
-              const int *__restrict__ skip) {
+              const int *__restrict__ skip, const int32_t *__restrict__ elist) {
   using C = AxCfg<NP>;
   if (skip != nullptr && *skip != 0) return;
   extern __shared__ double smem[];
@@ -46,8 +46,9 @@ __global__ void __launch_bounds__(AxCfg<NP>::THREADS)
   double pw = 0.0;
   __syncthreads();
   for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += (int64_t)gridDim.x * C::ELB) {
-    const int64_t e = e0 + le;
-    const bool act = e < E;
+    const int64_t ei = e0 + le;  // position in the element list (or the element itself)
+    const bool act = ei < E;
+    const int64_t e = !act ? 0 : (elist ? (int64_t)elist[ei] : ei);
     double ru[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
@@ -131,12 +132,14 @@ __global__ void __launch_bounds__(AxCfg<NP>::THREADS)
 
 template <int NP, bool ASSEMBLED>
 int launch_fp64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
-                unsigned grid, cudaStream_t st, const int32_t *map, const int *skip) {
+                unsigned grid, cudaStream_t st, const int32_t *map, const int *skip, const int32_t *elist = nullptr,
+                int64_t nlist = 0) {
   using C = AxCfg<NP>;
   auto kern = k_ax_fp64<NP, ASSEMBLED>;
   if (C::SMEM > 48 * 1024) SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-  double *wloc = ASSEMBLED ? (double *)m->det_w : nullptr;
-  kern<<<grid, C::THREADS, C::SMEM, st>>>(m->E, m->dD, m->G, m->B, h1, h2, u, w, map, pw_partial, wloc, skip);
+  double *wloc = (ASSEMBLED && !elist) ? (double *)m->det_w : nullptr;
+  kern<<<grid, C::THREADS, C::SMEM, st>>>(elist ? nlist : m->E, m->dD, m->G, m->B, h1, h2, u, w, map, pw_partial,
+                                          wloc, skip, elist);
   SEM_LAUNCH_CHECK("k_ax_fp64");
   if (wloc) return sem_launch_gather_add(m, wloc, w, st);
   return SEM_OK;
@@ -159,6 +162,15 @@ int dispatch_np(const sem_mesh *m, double h1, double h2, const double *u, double
   unsigned grid = ax_grid<NP>(m, assembled);
   if (assembled) return launch_fp64<NP, true>(m, h1, h2, u, w, pw_partial, grid, st, map, skip);
   return launch_fp64<NP, false>(m, h1, h2, u, w, nullptr, grid, st, map, skip);
+}
+
+template <int NP>
+int dispatch_list_np(const sem_mesh *m, double h1, double h2, const double *u, double *w, int precision,
+                     cudaStream_t st, const int32_t *elist, int64_t nlist) {
+  if (precision == SEM_PREC_DF64) return sem_launch_ax_df64_list(m, h1, h2, u, w, st, elist, nlist);
+  using C = AxCfg<NP>;
+  const unsigned grid = (unsigned)std::max<int64_t>(std::min<int64_t>((nlist + C::ELB - 1) / C::ELB, 152 * 16), 1);
+  return launch_fp64<NP, true>(m, h1, h2, u, w, nullptr, grid, st, m->l2gm, nullptr, elist, nlist);
 }
 
 int dispatch(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial, bool assembled,
@@ -211,6 +223,20 @@ int sem_launch_ax_assembled(const sem_mesh *m, double h1, double h2, const doubl
   if (m->N == 1 && m->K1)
     return sem_launch_ax_n1(m, h1, h2, u_g, w_g, pw_partial, precision, st, map ? map : m->l2gm, skip);
   return dispatch(m, h1, h2, u_g, w_g, pw_partial, true, precision, st, map ? map : m->l2gm, skip);
+}
+
+int sem_launch_ax_assembled_list(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
+                                 int precision, cudaStream_t st, const int32_t *elist, int64_t nlist) {
+  if (nlist <= 0) return SEM_OK;
+  switch (m->n) {  // N = 1 too: the sum-factorised kernels (the element-matrix ones assume the whole mesh)
+#define CASE(NPV) \
+  case NPV:       \
+    return dispatch_list_np<NPV>(m, h1, h2, u_g, w_g, precision, st, elist, nlist);
+    CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
+#undef CASE
+    default:
+      return sem_fail(SEM_ERR_INVALID_ARG, "unsupported polynomial order");
+  }
 }
 
 int sem_ax_assembled_blocks(const sem_mesh *m, int precision) {

@@ -236,7 +236,8 @@ template <int NP, bool ASSEMBLED, bool HELM>
 __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
     k_ax_df64(int64_t E, const float2 *__restrict__ Gdf, const float2 *__restrict__ Bdf, float2 h1, float2 h2,
               const double *__restrict__ u, double *__restrict__ w, const int32_t *__restrict__ l2gm,
-              double *__restrict__ pw_partial, double *__restrict__ wloc, const int *__restrict__ skip) {
+              double *__restrict__ pw_partial, double *__restrict__ wloc, const int *__restrict__ skip,
+              const int32_t *__restrict__ elist) {
   using C = DfCfg<NP>;
   if (skip != nullptr && *skip != 0) return;
   extern __shared__ float2 sm2[];
@@ -264,8 +265,9 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
   int32_t go[NP];  // gather indices of this thread's column, kept for the scatter
   int sh = 0;      // the element's scale: values are carried as x 2^-sh
   for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += estride) {
-    const int64_t e = e0 + le;
-    const bool act = e < E;
+    const int64_t ei = e0 + le;  // position in the element list (or the element itself)
+    const bool act = ei < E;
+    const int64_t e = !act ? E : (elist ? (int64_t)elist[ei] : ei);  // inactive: never dereferenced
     // P0: gather and split the t-column; one thread per element starts the
     // L2 prefetch of the element's geometric factors (read in P2)
     if (act && t == 0) prefetch_l2(Gdf + e * 6 * C::N3, 48u * C::N3);
@@ -619,22 +621,26 @@ int df_grid(const sem_mesh *m, unsigned *grid) {
 
 template <int NP>
 int launch_np(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial, bool assembled,
-              cudaStream_t st, const int32_t *map, const int *skip) {
+              cudaStream_t st, const int32_t *map, const int *skip, const int32_t *elist = nullptr,
+              int64_t nlist = 0) {
   using C = DfCfg<NP>;
   unsigned grid;
   // one CTA per element group (the hardware scheduler balances the SMs; a
   // single resident wave of persistent CTAs measured 11 % slower)
   if (int rc = df_grid<NP>(m, &grid)) return rc;
+  const int64_t nE = elist ? nlist : m->E;
+  if (elist) grid = (unsigned)std::max<int64_t>((nlist + C::ELB - 1) / C::ELB, 1);
   const float2 h1d = split_host(h1), h2d = split_host(h2);
   const bool helm = !(h1 == 1.0 && h2 == 0.0);
-  double *wloc = assembled ? (double *)m->det_w : nullptr;
-#define LAUNCH(ASM, HLM)                                                                                    \
-  do {                                                                                                      \
-    auto kern = k_ax_df64<NP, ASM, HLM>;                                                                    \
-    constexpr int smem = C::smem_ax(HLM);                                                                   \
-    if (smem > 48 * 1024)                                                                                   \
-      SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));             \
-    kern<<<grid, C::THREADS, smem, st>>>(m->E, m->Gdf, m->Bdf, h1d, h2d, u, w, map, pw_partial, wloc, skip); \
+  double *wloc = (assembled && !elist) ? (double *)m->det_w : nullptr;
+#define LAUNCH(ASM, HLM)                                                                                  \
+  do {                                                                                                    \
+    auto kern = k_ax_df64<NP, ASM, HLM>;                                                                  \
+    constexpr int smem = C::smem_ax(HLM);                                                                 \
+    if (smem > 48 * 1024)                                                                                 \
+      SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));           \
+    kern<<<grid, C::THREADS, smem, st>>>(nE, m->Gdf, m->Bdf, h1d, h2d, u, w, map, pw_partial, wloc, skip, \
+                                         elist);                                                          \
   } while (0)
   if (assembled) {
     if (helm) LAUNCH(true, true);
@@ -669,11 +675,28 @@ int sem_df64_grid(const sem_mesh *m) {
 
 int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
                        bool assembled, cudaStream_t st, const int32_t *map, const int *skip) {
+  if (m->n == 8 && m->use_tc) return sem_launch_ax_tc(m, h1, h2, u, w, pw_partial, assembled, st, map, skip);
   if (int rc = ensure_tables(m->device)) return rc;
   switch (m->n) {
 #define CASE(NPV) \
   case NPV:       \
     return launch_np<NPV>(m, h1, h2, u, w, pw_partial, assembled, st, map, skip);
+    CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
+#undef CASE
+    default:
+      return sem_fail(SEM_ERR_INVALID_ARG, "unsupported polynomial order");
+  }
+}
+
+int sem_launch_ax_df64_list(const sem_mesh *m, double h1, double h2, const double *u, double *w, cudaStream_t st,
+                            const int32_t *elist, int64_t nlist) {
+  if (m->n == 8 && m->use_tc)
+    return sem_launch_ax_tc(m, h1, h2, u, w, nullptr, true, st, m->l2gm, nullptr, elist, nlist);
+  if (int rc = ensure_tables(m->device)) return rc;
+  switch (m->n) {
+#define CASE(NPV) \
+  case NPV:       \
+    return launch_np<NPV>(m, h1, h2, u, w, nullptr, true, st, m->l2gm, nullptr, elist, nlist);
     CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
 #undef CASE
     default:

@@ -54,6 +54,9 @@ struct sem_mesh {
   // results here (n_local doubles, or floats for binary32 levels) and sum the
   // copies of each unique node in ascending copy order instead of with atomics
   void *det_w = nullptr;
+  // N = 7 double-float operator: 1-D contractions on the tensor pipe
+  // (sem_ax_tc.cu) when set (the default), else on the binary32 pipe
+  int use_tc = 1;
   // N = 1 only: element stiffness matrices (upper triangle, [36][E]) in
   // binary64 and double-float
   double *K1 = nullptr;
@@ -90,9 +93,18 @@ int sem_launch_ax_assembled(const sem_mesh *m, double h1, double h2, const doubl
                             double *pw_partial, int precision, cudaStream_t st, const int32_t *map = nullptr,
                             const int *skip = nullptr);
 int sem_ax_assembled_blocks(const sem_mesh *m, int precision);
+// the assembled operator over a device list of elements only: w_g +=
+// M Q_e^T A_e Q_e M u_g for the listed e (atomic assembly, no p.w partials)
+int sem_launch_ax_assembled_list(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
+                                 int precision, cudaStream_t st, const int32_t *elist, int64_t nlist);
+int sem_launch_ax_df64_list(const sem_mesh *m, double h1, double h2, const double *u, double *w, cudaStream_t st,
+                            const int32_t *elist, int64_t nlist);
 int sem_df64_grid(const sem_mesh *m);
 int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
                        bool assembled, cudaStream_t st, const int32_t *map, const int *skip = nullptr);
+int sem_launch_ax_tc(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
+                     bool assembled, cudaStream_t st, const int32_t *map, const int *skip,
+                     const int32_t *elist = nullptr, int64_t nlist = 0);
 int sem_launch_gs(const sem_mesh *m, double *v, int apply_mask, cudaStream_t st);
 int sem_launch_gather(const sem_mesh *m, const double *vL, double *vg, cudaStream_t st);
 int sem_launch_scatter(const sem_mesh *m, const double *vg, double *vL, cudaStream_t st);

@@ -589,6 +589,12 @@ extern "C" int sem_mesh_set_deterministic(sem_mesh *m, int on) {
   return SEM_OK;
 }
 
+extern "C" int sem_mesh_set_tensor_cores(sem_mesh *m, int on) {
+  if (!m) return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_set_tensor_cores: NULL mesh");
+  m->use_tc = on ? 1 : 0;
+  return SEM_OK;
+}
+
 extern "C" int sem_mesh_info_get(const sem_mesh *m, sem_mesh_info *info) {
   if (!m || !info) return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_info_get: NULL argument");
   info->E = m->E;
