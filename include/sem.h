@@ -619,6 +619,88 @@ int sem_partition_peer_nodes(const sem_box_desc *desc, int nranks, int rank, int
  * checks as sem_partition_info; NULL n_surface is SEM_ERR_INVALID_ARG. */
 int sem_partition_surface(const sem_box_desc *desc, int nranks, int rank, int64_t *elems, int64_t *n_surface);
 
+/* ------------------------------------------------------------------------
+ * One rank's share of the element-slab partition on its GPU (Sec. 2.2: one
+ * MPI rank per GPU; the gather-scatter sums shared surface values across
+ * ranks, and the exchange is overlapped with the work on interior elements:
+ * surface elements first, start the exchange, interior elements, finish).
+ *
+ * The rank holds a slab mesh: its element planes of the box, in the box's
+ * element order, with the slab's own unique numbering (lattice planes
+ * p0 N .. p1 N of the box, numbered like a box of that height: no periodic
+ * wrap in z; the Dirichlet faces of the box where the slab reaches them).
+ * Its vectors are U-vectors of that slab mesh. The communication between
+ * ranks is the caller's, through two callbacks, so any transport (MPI,
+ * NCCL host staging, gloo, a test harness) can carry it; the library never
+ * blocks on another rank inside a kernel.
+ * ------------------------------------------------------------------------ */
+typedef struct sem_part sem_part; /* opaque; owns its slab mesh, lists and buffers */
+
+/* Exchange: buf (host memory) holds this rank's partial sums at its
+ * interface nodes, n of them, in the order of sem_partition_interface
+ * (ascending unique id of the box). On return buf must hold, for each node,
+ * the sum of the partial sums of every rank that holds it (the same value
+ * on every rank). Return 0 on success; anything else ends the calling entry
+ * point with SEM_ERR_IO. Called from the calling host thread only. */
+typedef int (*sem_exchange_fn)(double *buf, int64_t n, void *user);
+
+/* All-reduce: replace vals[0..n-1] by their sums over all ranks (same
+ * order of summation on every rank, so that every rank takes the same
+ * decisions). Return 0 on success, else the entry point returns SEM_ERR_IO. */
+typedef int (*sem_allreduce_fn)(double *vals, int n, void *user);
+
+typedef struct {
+  const sem_mesh *mesh;   /* the slab mesh (owned by the partition; usable with the
+                             operator, gather-scatter and solver entry points) */
+  int64_t e_begin, e_end; /* the slab's elements in the box's numbering */
+  int64_t n_surface;      /* elements touching an interface node */
+  int64_t n_interior;     /* the other elements of the slab */
+  int64_t n_interface;    /* interface nodes (exchanged values per application) */
+  int64_t n_unique;       /* unique nodes of the slab mesh (the length of its vectors) */
+} sem_part_info_t;
+
+/* Build rank `rank` of `nranks` (the plan of sem_partition_info): its slab
+ * mesh, surface and interior element lists, interface node list, inner-
+ * product weights (1 / number of ranks holding the node) and buffers (pinned
+ * host staging for the exchange, a second stream for the interior
+ * elements). Same argument checks as sem_partition_info. Synchronises. */
+int sem_part_create(const sem_box_desc *desc, int nranks, int rank, void *stream, sem_part **out);
+int sem_part_destroy(sem_part *p);
+int sem_part_info(const sem_part *p, sem_part_info_t *info);
+
+/* The box's unique id of every unique node of the slab mesh, into
+ * gids_host[n_unique] (host). */
+int sem_part_global_ids(const sem_part *p, int64_t *gids_host);
+
+/* The assembled operator over a list of elements only:
+ * w_g += M Q_e^T (h1 A_e + h2 B_e) Q_e M u_g summed over e in elems
+ * (device int32[n_elems], element ids of mesh m), atomic assembly. The
+ * building block of the overlapped schedule; u_g, w_g are U-vectors of m.
+ * SEM_ERR_INVALID_ARG for a bad list length or precision. */
+int sem_ax_assembled_elems(const sem_mesh *m, double h1, double h2, const double *u_g, double *w_g,
+                           const int32_t *elems, int64_t n_elems, int precision, void *stream);
+
+/* w = M Q^T (h1 A + h2 B) Q M u on the rank's nodes, with complete sums at
+ * the interface: surface elements on `stream`, their interface values
+ * staged to the host and passed to ex(...) while the interior elements run
+ * on the partition's second stream, the returned sums written back, the
+ * streams joined. u, w: U-vectors of the slab mesh (device). The call
+ * returns once the exchange is done; the rest is queued on `stream`. */
+int sem_part_ax(sem_part *p, double h1, double h2, const double *u, double *w, int precision,
+                sem_exchange_fn ex, void *user, void *stream);
+
+/* Jacobi-PCG over the partition: the same iteration as sem_pcg_solve (x0 =
+ * 0, stop at the first ||r|| <= tol ||b||), each operator application
+ * sem_part_ax, the Jacobi diagonal summed over the ranks like the operator,
+ * inner products over the rank's nodes with shared nodes weighted by one
+ * over the number of ranks holding them, summed by ar(...). b, x: U-vectors
+ * of the slab mesh; b must be zero on Dirichlet nodes and agree across ranks
+ * on shared nodes. opts.mask_mode must be 0. Every rank returns the same
+ * iteration count and status. Returns like sem_pcg_solve, or SEM_ERR_IO
+ * when a callback fails. */
+int sem_part_pcg_solve(sem_part *p, double h1, double h2, const double *b, double *x, const sem_solver_opts *opts,
+                       sem_solve_stats *stats, sem_exchange_fn ex, sem_allreduce_fn ar, void *user, void *stream);
+
 /* Jacobi-PCG like sem_pcg_solve, for callers that cannot allocate device
  * memory themselves -- for example a host program or plug-in whose device
  * memory is owned entirely by another framework's allocator, or a loop that

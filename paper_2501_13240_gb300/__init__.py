@@ -44,6 +44,8 @@ EXPORTS = (
     "sem_pmg_create", "sem_pmg_lambda", "sem_pmg_vcycle", "sem_pmg_prolong", "sem_pmg_restrict",
     "sem_pmg_pcg_solve", "sem_pmg_destroy", "sem_partition_info", "sem_partition_interface",
     "sem_partition_peers", "sem_partition_peer_nodes", "sem_partition_surface",
+    "sem_set_grid_wait_limit", "sem_mesh_set_tensor_cores", "sem_part_create", "sem_part_destroy", "sem_part_info",
+    "sem_part_global_ids", "sem_ax_assembled_elems", "sem_part_ax", "sem_part_pcg_solve",
 )
 
 
@@ -115,6 +117,17 @@ class sem_scene_desc(ctypes.Structure):
                 ("n_iso", ctypes.c_int), ("iso", ctypes.c_double * 4)]
 
 
+class sem_part_info_t(ctypes.Structure):
+    _fields_ = [("mesh", ctypes.c_void_p), ("e_begin", ctypes.c_int64), ("e_end", ctypes.c_int64),
+                ("n_surface", ctypes.c_int64), ("n_interior", ctypes.c_int64), ("n_interface", ctypes.c_int64),
+                ("n_unique", ctypes.c_int64)]
+
+
+# communication callbacks of the partitioned operator and solve (sem.h)
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_void_p)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p)
+
+
 class sem_tadv_params(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_double), ("dt", ctypes.c_double), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("precision", ctypes.c_int)]
@@ -164,6 +177,14 @@ def lib() -> ctypes.CDLL:
                                           ctypes.POINTER(sem_solve_stats), _vp], _i)
         sig["sem_pcg_noalloc_capacity"] = ([], ctypes.c_size_t)
         sig["sem_set_grid_wait_limit"] = ([ctypes.c_uint, ctypes.POINTER(ctypes.c_uint)], _i)
+        sig["sem_part_create"] = ([ctypes.POINTER(sem_box_desc), _i, _i, _vp, ctypes.POINTER(_vp)], _i)
+        sig["sem_part_destroy"] = ([_vp], _i)
+        sig["sem_part_info"] = ([_vp, ctypes.POINTER(sem_part_info_t)], _i)
+        sig["sem_part_global_ids"] = ([_vp, _vp], _i)
+        sig["sem_ax_assembled_elems"] = ([_vp, _d, _d, _vp, _vp, _vp, ctypes.c_int64, _i, _vp], _i)
+        sig["sem_part_ax"] = ([_vp, _d, _d, _vp, _vp, _i, EXCHANGE_FN, _vp, _vp], _i)
+        sig["sem_part_pcg_solve"] = ([_vp, _d, _d, _vp, _vp, ctypes.POINTER(sem_solver_opts),
+                                      ctypes.POINTER(sem_solve_stats), EXCHANGE_FN, ALLREDUCE_FN, _vp, _vp], _i)
         sig["sem_rbc_create"] = ([_vp, ctypes.POINTER(sem_rbc_params), _vp, _vp, ctypes.POINTER(_vp)], _i)
         sig["sem_bdf_ext_step"] = ([_vp, ctypes.POINTER(sem_step_stats), _vp], _i)
         sig["sem_rbc_fields"] = ([_vp, ctypes.POINTER(sem_rbc_view)], _i)
@@ -257,8 +278,9 @@ def sem_gll(N: int):
 class Mesh:
     """Owns a ``sem_mesh`` handle; exposes sizes and the device views."""
 
-    def __init__(self, handle: ctypes.c_void_p):
+    def __init__(self, handle: ctypes.c_void_p, owned: bool = True):
         self._h = handle
+        self._owned = owned  # False: a view of a mesh owned by another handle (a partition's slab)
         info = sem_mesh_info()
         _check(lib().sem_mesh_info_get(self._h, ctypes.byref(info)))
         self.info = info
@@ -276,7 +298,8 @@ class Mesh:
 
     def destroy(self):
         if self._h is not None:
-            lib().sem_mesh_destroy(self._h)
+            if self._owned:
+                lib().sem_mesh_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -365,6 +388,99 @@ def sem_mesh_set_tensor_cores(mesh: Mesh, on: bool = True):
     """N = 7 double-float operator on the tensor pipe (default) or on the
     binary32 pipe."""
     _check(lib().sem_mesh_set_tensor_cores(mesh.handle, int(bool(on))))
+
+
+class Partition:
+    """Owns a ``sem_part`` handle: one rank's slab of an element-slab
+    partition on its GPU. ``mesh`` is a view of the slab mesh (owned by the
+    partition). ``exchange(buf)`` and ``allreduce(vals)`` are the caller's
+    communication: numpy float64 arrays changed in place (see sem.h)."""
+
+    def __init__(self, handle, desc, nranks, rank):
+        self._h = handle
+        self.desc, self.nranks, self.rank = desc, nranks, rank
+        info = sem_part_info_t()
+        _check(lib().sem_part_info(self._h, ctypes.byref(info)))
+        self.info = info
+        self.mesh = Mesh(ctypes.c_void_p(info.mesh), owned=False)
+        self.e_begin, self.e_end = int(info.e_begin), int(info.e_end)
+        self.n_surface, self.n_interior = int(info.n_surface), int(info.n_interior)
+        self.n_interface, self.n_unique = int(info.n_interface), int(info.n_unique)
+        self._keep = []
+
+    def destroy(self):
+        if self._h is not None:
+            self.mesh._h = None
+            lib().sem_part_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def global_ids(self) -> np.ndarray:
+        g = np.zeros(self.n_unique, dtype=np.int64)
+        _check(lib().sem_part_global_ids(self._h, g.ctypes.data))
+        return g
+
+    @staticmethod
+    def _callbacks(exchange, allreduce):
+        def ex(buf, n, user):
+            try:
+                exchange(np.ctypeslib.as_array(buf, shape=(int(n),)))
+                return 0
+            except Exception:  # reported to the library as a failed exchange
+                return 1
+
+        def ar(vals, n, user):
+            try:
+                allreduce(np.ctypeslib.as_array(vals, shape=(int(n),)))
+                return 0
+            except Exception:
+                return 1
+
+        return EXCHANGE_FN(ex), ALLREDUCE_FN(ar)
+
+    def ax(self, h1, h2, u, w, exchange, precision=SEM_PREC_DF64, stream=None):
+        import torch
+        exf, _ = self._callbacks(exchange, lambda v: None)
+        _check(lib().sem_part_ax(self._h, float(h1), float(h2), _ptr(u, torch.float64, self.n_unique, "u"),
+                                 _ptr(w, torch.float64, self.n_unique, "w"), int(precision), exf, None,
+                                 _stream(stream)))
+        return w
+
+    def pcg_solve(self, h1, h2, b, x, exchange, allreduce, tol=1e-8, maxit=1000, precision=SEM_PREC_DF64,
+                  timeout_s=0.0, stream=None, raise_on_error=True) -> dict:
+        import torch
+        exf, arf = self._callbacks(exchange, allreduce)
+        o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s), 0)
+        st = sem_solve_stats()
+        rc = lib().sem_part_pcg_solve(self._h, float(h1), float(h2), _ptr(b, torch.float64, self.n_unique, "b"),
+                                      _ptr(x, torch.float64, self.n_unique, "x"), ctypes.byref(o), ctypes.byref(st),
+                                      exf, arf, None, _stream(stream))
+        out = {"iterations": st.iterations, "rel_residual": st.rel_residual, "solve_ms": st.solve_ms,
+               "status": st.status}
+        if rc != SEM_OK and (raise_on_error or rc not in (SEM_ERR_NOT_CONVERGED, SEM_ERR_TIMEOUT, SEM_ERR_BREAKDOWN)):
+            _check(rc)
+        return out
+
+
+def sem_part_create(desc: sem_box_desc, nranks: int, rank: int, stream=None) -> Partition:
+    h = ctypes.c_void_p()
+    _check(lib().sem_part_create(ctypes.byref(desc), int(nranks), int(rank), _stream(stream), ctypes.byref(h)))
+    return Partition(h, desc, nranks, rank)
+
+
+def sem_ax_assembled_elems(mesh: Mesh, h1: float, h2: float, u_g, w_g, elems, precision=SEM_PREC_DF64, stream=None):
+    """w_g += the assembled operator over the elements in ``elems`` (device int32 tensor)."""
+    import torch
+    _check(lib().sem_ax_assembled_elems(mesh.handle, float(h1), float(h2), _ptr(u_g, torch.float64, mesh.n_unique, "u_g"),
+                                        _ptr(w_g, torch.float64, mesh.n_unique, "w_g"),
+                                        _ptr(elems, torch.int32, None, "elems"), int(elems.numel()), int(precision),
+                                        _stream(stream)))
+    return w_g
 
 
 def sem_partition_info(desc: sem_box_desc, nranks: int, rank: int):

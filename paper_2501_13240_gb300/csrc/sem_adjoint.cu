@@ -210,6 +210,7 @@ bool bad(const void *p) { return !p || ((uintptr_t)p & 7); }
 extern "C" int sem_tadv_create(const sem_mesh *m, const sem_tadv_params *prm, void *stream, sem_tadv **out) {
   if (!m || !prm || !out) return sem_fail(SEM_ERR_INVALID_ARG, "sem_tadv_create: NULL argument");
   *out = nullptr;
+  if (m->slab) return sem_fail(SEM_ERR_INVALID_ARG, "sem_tadv_create: needs the whole box, not a partition's slab mesh");
   if (!(prm->kappa > 0) || !(prm->dt > 0) || !(prm->tol > 0) || prm->maxit < 1)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_tadv_create: kappa, dt, tol must be > 0 and maxit >= 1");
   if (prm->precision != SEM_PREC_FP64 && prm->precision != SEM_PREC_DF64)

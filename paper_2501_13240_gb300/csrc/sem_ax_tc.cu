@@ -63,6 +63,7 @@
 #include <vector>
 
 #include "sem_df64.cuh"
+#include "sem_df64x2.cuh"
 #include "sem_internal.h"
 
 namespace {
@@ -124,14 +125,14 @@ int ensure_digits(int device) {
 }
 
 // ---------------------------------------------------------------- tensor-core primitives
-// d += A B, m16n8k16, fp16 inputs, f32 accumulate
+// d = A B + c, m16n8k16, fp16 inputs, f32 accumulate
 __device__ __forceinline__ void mma16(float &d0, float &d1, float &d2, float &d3, uint32_t a0, uint32_t a1,
-                                      uint32_t a2, uint32_t a3, uint32_t b0, uint32_t b1) {
-  asm(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+                                      uint32_t a2, uint32_t a3, uint32_t b0, uint32_t b1, float c0, float c1,
+                                      float c2, float c3) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%10,%11,%12,%13};"
+      : "=f"(d0), "=f"(d1), "=f"(d2), "=f"(d3)
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(c0), "f"(c1), "f"(c2), "f"(c3));
 }
 
 __device__ __forceinline__ uint32_t movtrans(uint32_t a) {
@@ -152,89 +153,128 @@ __device__ __forceinline__ void ldsm1t(uint32_t addr, uint32_t &r0) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x1.trans.shared.b16 {%0}, [%1];" : "=r"(r0) : "r"(addr) : "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
-  const __half2 h = __floats2half2_rn(lo, hi);
+__device__ __forceinline__ uint32_t pack_f16(float2 v) {
+  const __half2 h = __floats2half2_rn(v.x, v.y);
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// Digits of y = (h + l) s1 2^-10 (|y| < 1): s1 = 2^10 2^-scale, c2 = s1 2^10.
-// Round to nearest integer by the 1.5 2^23 shift. The low word enters at
-// the third digit through an exact Fast2Sum (|r| >= |l c2| unless r = 0: r
-// is a multiple of ulp(h) there, and |l| < ulp(h)).
-__device__ __forceinline__ void digits5(float h, float l, float s1, float c2, float (&d)[NSL]) {
-  const float M = 12582912.0f;
-  float t = __fmaf_rn(h, s1, M);
-  d[0] = __fsub_rn(t, M);
-  float r = __fmaf_rn(h, s1, -d[0]);
-  t = __fmaf_rn(r, 1024.0f, M);
-  d[1] = __fsub_rn(t, M);
-  r = __fmaf_rn(r, 1024.0f, -d[1]);
-  const float sm = __fmaf_rn(l, c2, r);
-  const float z = __fsub_rn(sm, r);
-  const float eps = __fmaf_rn(l, c2, -z);
-  t = __fmaf_rn(sm, 1024.0f, M);
-  d[2] = __fsub_rn(t, M);
-  r = __fmaf_rn(sm, 1024.0f, -d[2]);
-  r = __fmaf_rn(eps, 1024.0f, r);
-  t = __fmaf_rn(r, 1024.0f, M);
-  d[3] = __fsub_rn(t, M);
-  r = __fmaf_rn(r, 1024.0f, -d[3]);
-  d[4] = __fmul_rn(r, 1024.0f);  // rounded to 11 bits by the fp16 conversion
+// ---------------------------------------------------------------- packed binary32 pairs
+// A thread's two points (r = 2q, 2q+1) are the two lanes of f32x2
+// instructions: one issue slot for both (each lane does the scalar
+// operation sequence).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return dfx::sub(a, b); }
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+
+// Digits of the pair y = (h + l) s1 2^-10 (|y| <= 1): s1 = 2^10 2^-scale,
+// c2 = s1 2^10; out[j] = the fp16 pair of digit j. Round to nearest integer
+// by the 1.5 2^23 shift. The low word enters at the third digit through an
+// exact Fast2Sum (|r| >= |l c2| unless r = 0: there r is a multiple of
+// ulp(h), and |l| < ulp(h)).
+__device__ __forceinline__ void digits5(float2 h, float2 l, float s1, float c2, uint32_t (&out)[NSL]) {
+  const float2 M = dup(12582912.0f), K = dup(1024.0f), S = dup(s1), C = dup(c2);
+  float2 t = fma2(h, S, M);
+  float2 d = sub2(t, M);
+  out[0] = pack_f16(d);
+  float2 r = fma2(h, S, neg2(d));
+  t = fma2(r, K, M);
+  d = sub2(t, M);
+  out[1] = pack_f16(d);
+  r = fma2(r, K, neg2(d));
+  const float2 sm = fma2(l, C, r);
+  const float2 z = sub2(sm, r);
+  const float2 eps = fma2(l, C, neg2(z));
+  t = fma2(sm, K, M);
+  d = sub2(t, M);
+  out[2] = pack_f16(d);
+  r = fma2(sm, K, neg2(d));
+  r = fma2(eps, K, r);
+  t = fma2(r, K, M);
+  d = sub2(t, M);
+  out[3] = pack_f16(d);
+  r = fma2(r, K, neg2(d));
+  out[4] = pack_f16(mul2(r, K));  // rounded to 11 bits by the fp16 conversion
 }
 
-// The five level sums L_0..L_4 (exact integers) of one output, weight
-// 2^-10(L+2) times sc, to a normalised double-float (16 binary32 operations).
-__device__ __forceinline__ float2 recombine(float L0, float L1, float L2, float L3, float L4, float sc) {
-  const float M = 12582912.0f;
-  const float v1 = __fmul_rn(L1, 0x1p-10f);
-  const float hi1 = __fsub_rn(__fadd_rn(v1, M), M);  // integer part of level 1 (|v1| < 2^22)
-  const float fr1 = __fsub_rn(v1, hi1);              // its fraction, exact
-  const float A = __fadd_rn(L0, hi1);                // integer below 2^24: exact
-  const float B = __fmaf_rn(L2, 0x1p-20f, fr1);      // on the 2^-20 grid, below 2^3: exact
-  const float C = __fmaf_rn(L4, 0x1p-10f, L3);       // levels 3, 4 in level-3 units (error < 2^-32)
-  const float h = __fadd_rn(A, B);                   // Fast2Sum: exact when |A| >= 8, else A + B is exact
-  const float e = __fsub_rn(B, __fsub_rn(h, A));
-  const float l = __fmaf_rn(C, 0x1p-30f, e);
-  const float H = __fadd_rn(h, l);
-  const float Lo = __fsub_rn(l, __fsub_rn(H, h));
-  return make_float2(__fmul_rn(H, sc), __fmul_rn(Lo, sc));
+// The five level sums L_0..L_4 (exact integers) of an output pair, weight
+// 2^-10(L+2) times sc, to normalised double-floats: (hi pair, lo pair).
+__device__ __forceinline__ void recombine(float2 L0, float2 L1, float2 L2, float2 L3, float2 L4, float sc,
+                                          float2 &H, float2 &Lo) {
+  const float2 M = dup(12582912.0f);
+  const float2 v1 = mul2(L1, dup(0x1p-10f));
+  const float2 hi1 = sub2(add2(v1, M), M);  // integer part of level 1 (|v1| < 2^22)
+  const float2 fr1 = sub2(v1, hi1);         // its fraction, exact
+  const float2 A = add2(L0, hi1);           // integer below 2^24: exact
+  const float2 B = fma2(L2, dup(0x1p-20f), fr1);  // on the 2^-20 grid, below 2^3: exact
+  const float2 C = fma2(L4, dup(0x1p-10f), L3);   // levels 3, 4 in level-3 units (error < 2^-32)
+  const float2 h = add2(A, B);              // Fast2Sum: exact when |A| >= 8, else A + B is exact
+  const float2 e = sub2(B, sub2(h, A));
+  const float2 l = fma2(C, dup(0x1p-30f), e);
+  const float2 S = add2(h, l);
+  const float2 T = sub2(l, sub2(S, h));
+  H = mul2(S, dup(sc));
+  Lo = mul2(T, dup(sc));
 }
 
-// 15 digit products of D-as-A contractions: A rows 0..7 and 8..15 are two
-// levels, B = (digits j of k 0..7 | digits j' of k 8..15); acc[L][0..1] are
-// the two outputs of level L held by this thread.
-__device__ __forceinline__ void contract_da(const uint32_t (&Dg)[NSL], const uint32_t (&b)[NSL], float (&acc)[NSL][2]) {
+// 15 digit products, D as the A operand: rows 0..7 and 8..15 of A are two
+// levels, B = (digits j of k 0..7 | digits j' of k 8..15); acc[L] = the
+// output pair of level L held by this thread. The first product into each
+// level starts from zero; the last MMA's second row block is all zero.
+__device__ __forceinline__ void contract_da(const uint32_t (&Dg)[NSL], const uint32_t (&b)[NSL], float2 (&acc)[NSL]) {
   const uint32_t Z = 0u;
   // L1 | L3
-  mma16(acc[1][0], acc[1][1], acc[3][0], acc[3][1], Dg[0], Dg[2], Dg[1], Dg[3], b[1], b[0]);
+  mma16(acc[1].x, acc[1].y, acc[3].x, acc[3].y, Dg[0], Dg[2], Dg[1], Dg[3], b[1], b[0], 0.f, 0.f, 0.f, 0.f);
   // L2 | L4
-  mma16(acc[2][0], acc[2][1], acc[4][0], acc[4][1], Dg[0], Dg[2], Dg[1], Dg[3], b[2], b[1]);
+  mma16(acc[2].x, acc[2].y, acc[4].x, acc[4].y, Dg[0], Dg[2], Dg[1], Dg[3], b[2], b[1], 0.f, 0.f, 0.f, 0.f);
   // L3: D0 u3 + D1 u2 | L4: D1 u3
-  mma16(acc[3][0], acc[3][1], acc[4][0], acc[4][1], Dg[0], Dg[1], Dg[1], Z, b[3], b[2]);
+  mma16(acc[3].x, acc[3].y, acc[4].x, acc[4].y, Dg[0], Dg[1], Dg[1], Z, b[3], b[2], acc[3].x, acc[3].y, acc[4].x,
+        acc[4].y);
   // L4: D0 u4 + D4 u0 | L2: D2 u0
-  mma16(acc[4][0], acc[4][1], acc[2][0], acc[2][1], Dg[0], Z, Dg[4], Dg[2], b[4], b[0]);
-  // L0: D0 u0 | (zero rows)
-  mma16(acc[0][0], acc[0][1], acc[1][0], acc[1][1], Dg[0], Z, Z, Z, b[0], b[0]);
+  mma16(acc[4].x, acc[4].y, acc[2].x, acc[2].y, Dg[0], Z, Dg[4], Dg[2], b[4], b[0], acc[4].x, acc[4].y, acc[2].x,
+        acc[2].y);
+  // L0: D0 u0 | (zero rows, into a scratch pair)
+  float s0, s1;
+  mma16(acc[0].x, acc[0].y, s0, s1, Dg[0], Z, Z, Z, b[0], b[0], 0.f, 0.f, 0.f, 0.f);
 }
 
-// 15 digit products of U-as-A contractions: A = digits of two t-planes
-// (rows 0..7: plane a, rows 8..15: plane b; a[j] = plane a, c[j] = plane b),
-// B = D digits; acc[L][0..1] plane a, acc[L][2..3] plane b.
-__device__ __forceinline__ void contract_ua(const uint32_t (&a)[NSL], const uint32_t (&c)[NSL],
-                                            const uint32_t (&Dg)[NSL], float (&acc)[NSL][4]) {
+// the same, accumulating into acc (no zero start)
+__device__ __forceinline__ void contract_da_acc(const uint32_t (&Dg)[NSL], const uint32_t (&b)[NSL],
+                                                float2 (&acc)[NSL]) {
   const uint32_t Z = 0u;
-#define MMA_UA(L, j, jp, i, ip) \
-  mma16(acc[L][0], acc[L][1], acc[L][2], acc[L][3], a[j], c[j], (jp) < 0 ? Z : a[(jp) < 0 ? 0 : (jp)], \
-        (jp) < 0 ? Z : c[(jp) < 0 ? 0 : (jp)], Dg[i], (ip) < 0 ? Z : Dg[(ip) < 0 ? 0 : (ip)])
-  MMA_UA(0, 0, -1, 0, -1);  // D0 u0
-  MMA_UA(1, 1, 0, 0, 1);    // D0 u1 + D1 u0
-  MMA_UA(2, 2, 1, 0, 1);    // D0 u2 + D1 u1
-  MMA_UA(2, 0, -1, 2, -1);  // D2 u0
-  MMA_UA(3, 3, 2, 0, 1);    // D0 u3 + D1 u2
-  MMA_UA(3, 1, 0, 2, 3);    // D2 u1 + D3 u0
-  MMA_UA(4, 4, 3, 0, 1);    // D0 u4 + D1 u3
-  MMA_UA(4, 2, 1, 2, 3);    // D2 u2 + D3 u1
-  MMA_UA(4, 0, -1, 4, -1);  // D4 u0
+  mma16(acc[1].x, acc[1].y, acc[3].x, acc[3].y, Dg[0], Dg[2], Dg[1], Dg[3], b[1], b[0], acc[1].x, acc[1].y, acc[3].x,
+        acc[3].y);
+  mma16(acc[2].x, acc[2].y, acc[4].x, acc[4].y, Dg[0], Dg[2], Dg[1], Dg[3], b[2], b[1], acc[2].x, acc[2].y, acc[4].x,
+        acc[4].y);
+  mma16(acc[3].x, acc[3].y, acc[4].x, acc[4].y, Dg[0], Dg[1], Dg[1], Z, b[3], b[2], acc[3].x, acc[3].y, acc[4].x,
+        acc[4].y);
+  mma16(acc[4].x, acc[4].y, acc[2].x, acc[2].y, Dg[0], Z, Dg[4], Dg[2], b[4], b[0], acc[4].x, acc[4].y, acc[2].x,
+        acc[2].y);
+  float s0, s1;
+  mma16(acc[0].x, acc[0].y, s0, s1, Dg[0], Z, Z, Z, b[0], b[0], acc[0].x, acc[0].y, 0.f, 0.f);
+}
+
+// 15 digit products, the digits as the A operand: rows 0..7 plane a, rows
+// 8..15 plane b (a[j], c[j]), B = D's digits; acc[L] / bcc[L] = the output
+// pairs of level L on planes a / b. ZERO: start each level from zero.
+template <bool ZERO>
+__device__ __forceinline__ void contract_ua(const uint32_t (&a)[NSL], const uint32_t (&c)[NSL],
+                                            const uint32_t (&Dg)[NSL], float2 (&acc)[NSL], float2 (&bcc)[NSL]) {
+  const uint32_t Z = 0u;
+#define MMA_UA(L, FIRST, A0, A1, A2, A3, B0, B1)                                                           \
+  mma16(acc[L].x, acc[L].y, bcc[L].x, bcc[L].y, A0, A1, A2, A3, B0, B1, (ZERO && FIRST) ? 0.f : acc[L].x, \
+        (ZERO && FIRST) ? 0.f : acc[L].y, (ZERO && FIRST) ? 0.f : bcc[L].x, (ZERO && FIRST) ? 0.f : bcc[L].y)
+  MMA_UA(0, true, a[0], c[0], Z, Z, Dg[0], Z);           // D0 u0
+  MMA_UA(1, true, a[1], c[1], a[0], c[0], Dg[0], Dg[1]);  // D0 u1 + D1 u0
+  MMA_UA(2, true, a[2], c[2], a[1], c[1], Dg[0], Dg[1]);  // D0 u2 + D1 u1
+  MMA_UA(2, false, a[0], c[0], Z, Z, Dg[2], Z);          // D2 u0
+  MMA_UA(3, true, a[3], c[3], a[2], c[2], Dg[0], Dg[1]);  // D0 u3 + D1 u2
+  MMA_UA(3, false, a[1], c[1], a[0], c[0], Dg[2], Dg[3]); // D2 u1 + D3 u0
+  MMA_UA(4, true, a[4], c[4], a[3], c[3], Dg[0], Dg[1]);  // D0 u4 + D1 u3
+  MMA_UA(4, false, a[2], c[2], a[1], c[1], Dg[2], Dg[3]); // D2 u2 + D3 u1
+  MMA_UA(4, false, a[0], c[0], Z, Z, Dg[4], Z);          // D4 u0
 #undef MMA_UA
 }
 
@@ -247,34 +287,47 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ float2 metric_row(float2 g0, float2 g1, float2 g2, float2 u0, float2 u1, float2 u2) {
-  df::Acc a = df::mul_first(g0.x, g0.y, u0.x, u0.y);
-  df::mac(a, g1.x, g1.y, u1.x, u1.y);
-  df::mac(a, g2.x, g2.y, u2.x, u2.y);
-  float h, l;
-  df::fast_two_sum(a.s, a.c, h, l);
-  return make_float2(h, l);
+// one output pair of the metric step, g0 u0 + g1 u1 + g2 u2, in double-float
+// (hi pair, lo pair) for the two points
+__device__ __forceinline__ void metric_row2(const float2 (&gh)[6], const float2 (&gl)[6], int i0, int i1, int i2,
+                                            const float2 (&uh)[3], const float2 (&ul)[3], float2 &oh, float2 &ol) {
+  dfx::Acc a = dfx::mul_first(gh[i0], gl[i0], uh[0], ul[0]);
+  dfx::mac(a, gh[i1], gl[i1], uh[1], ul[1]);
+  dfx::mac(a, gh[i2], gl[i2], uh[2], ul[2]);
+  oh = add2(a.s, a.c);  // Fast2Sum (|s| >= |c|)
+  ol = sub2(a.c, sub2(oh, a.s));
 }
 
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(k + 127) << 23); }
 
-// largest biased binary32 exponent of the hi parts (NaN/inf excluded)
-__device__ __forceinline__ int fexp(float h) {
-  const int e = (int)((__float_as_uint(h) >> 23) & 0xFFu);
-  return e == 0xFF ? 0 : e;
+// biased binary32 exponent of the larger of a pair (NaN/inf excluded)
+__device__ __forceinline__ int fexp2(float2 h) {
+  const unsigned a = __float_as_uint(h.x) & 0x7F800000u, b = __float_as_uint(h.y) & 0x7F800000u;
+  const unsigned m = max(a == 0x7F800000u ? 0u : a, b == 0x7F800000u ? 0u : b);
+  return (int)(m >> 23);
 }
 
 // the two inputs of a point pair: gathered through the map (assembled), or
 // from the caller's E-vector (only 8-byte alignment is promised there)
 template <bool ASSEMBLED>
-__device__ __forceinline__ void load_u(const double *__restrict__ u, const int32_t (&gi)[2], int64_t l, double (&v)[2]) {
+__device__ __forceinline__ void load_u(const double *__restrict__ u, int2 gi, int64_t l, double (&v)[2]) {
   if (ASSEMBLED) {
-    v[0] = gi[0] >= 0 ? u[gi[0]] : 0.0;
-    v[1] = gi[1] >= 0 ? u[gi[1]] : 0.0;
+    v[0] = gi.x >= 0 ? u[gi.x] : 0.0;
+    v[1] = gi.y >= 0 ? u[gi.y] : 0.0;
   } else {
     v[0] = u[l];
     v[1] = u[l + 1];
   }
+}
+
+// a point pair's double-float values in shared memory: (hi pair, lo pair)
+__device__ __forceinline__ void st_pair(float2 *base, int p, float2 h, float2 l) {
+  *reinterpret_cast<float4 *>(base + p) = make_float4(h.x, h.y, l.x, l.y);
+}
+__device__ __forceinline__ void ld_pair(const float2 *base, int p, float2 &h, float2 &l) {
+  const float4 v = *reinterpret_cast<const float4 *>(base + p);
+  h = make_float2(v.x, v.y);
+  l = make_float2(v.z, v.w);
 }
 
 template <bool ASSEMBLED, bool HELM>
@@ -284,6 +337,7 @@ __global__ void __launch_bounds__(64, kMinBlocks)
             double *__restrict__ pw_partial, double *__restrict__ wloc, const int *__restrict__ skip,
             const int32_t *__restrict__ elist) {
   if (skip != nullptr && *skip != 0) return;
+  // double-float values of point pairs, (hi pair, lo pair) at even p
   __shared__ __align__(16) float2 sR[N3];
   __shared__ __align__(16) float2 sS[N3];
   __shared__ __align__(16) float2 sT[N3];
@@ -300,29 +354,21 @@ __global__ void __launch_bounds__(64, kMinBlocks)
   const uint32_t sdig_base = (uint32_t)__cvta_generic_to_shared(sDig);
   // ldmatrix row addresses: lane L reads row t = L & 7 of matrix L >> 3
   const int lrow = lane & 7, lmat = lane >> 3;
+  const int pbase = 2 * q + 8 * g + 256 * wp;  // the thread's point pair on its first plane (+64 per plane)
   double pw = 0.0;
-  const float scD = (float)kDScale * 0x1p-20f;  // weight of level 0
+  constexpr float scD = (float)kDScale * 0x1p-20f;  // weight of level 0
 
   for (int64_t ei = blockIdx.x; ei < E; ei += gridDim.x) {
     const int64_t e = elist ? (int64_t)elist[ei] : ei;  // the element (E: the list's length with a list)
     // ---------------------------------------------------------------- P0
     if (tid == 0) prefetch_l2(Gdf + e * 6 * N3, 48u * N3);
-    int32_t gi[4][2];
+    int2 gi[4];
+    double uv0[4][2];
 #pragma unroll
-    for (int tt = 0; tt < 4; ++tt) {
-      const int p = 2 * q + 8 * g + 64 * (4 * wp + tt);
-      if (ASSEMBLED) {
-        const int2 ii = *reinterpret_cast<const int2 *>(l2gm + e * N3 + p);
-        gi[tt][0] = ii.x;
-        gi[tt][1] = ii.y;
-      }
-    }
-    double uv0[4][2];  // the thread's inputs (read again from L2 in P4)
+    for (int tt = 0; tt < 4; ++tt)
+      if (ASSEMBLED) gi[tt] = *reinterpret_cast<const int2 *>(l2gm + e * N3 + pbase + 64 * tt);
 #pragma unroll
-    for (int tt = 0; tt < 4; ++tt) {
-      const int p = 2 * q + 8 * g + 64 * (4 * wp + tt);
-      load_u<ASSEMBLED>(u, gi[tt], e * N3 + p, uv0[tt]);
-    }
+    for (int tt = 0; tt < 4; ++tt) load_u<ASSEMBLED>(u, gi[tt], e * N3 + pbase + 64 * tt, uv0[tt]);
     int em = 0;
 #pragma unroll
     for (int tt = 0; tt < 4; ++tt) em = max(em, max(df::exp_field(uv0[tt][0]), df::exp_field(uv0[tt][1])));
@@ -334,23 +380,20 @@ __global__ void __launch_bounds__(64, kMinBlocks)
     // kept in shared memory: the owner reads its own words back per plane
 #pragma unroll
     for (int tt = 0; tt < 4; ++tt) {
-      float d0[NSL], d1[NSL];
       const float2 x0 = df::from_f64_scaled(uv0[tt][0], su), x1 = df::from_f64_scaled(uv0[tt][1], su);
-      digits5(x0.x, x0.y, 1024.0f, 1048576.0f, d0);
-      digits5(x1.x, x1.y, 1024.0f, 1048576.0f, d1);
+      uint32_t d[NSL];
+      digits5(make_float2(x0.x, x1.x), make_float2(x0.y, x1.y), 1024.0f, 1048576.0f, d);
       const int t = 4 * wp + tt;
 #pragma unroll
-      for (int j = 0; j < NSL; ++j) sDig[dig_word(j, t, g, q)] = pack_f16(d0[j], d1[j]);
+      for (int j = 0; j < NSL; ++j) sDig[dig_word(j, t, g, q)] = d[j];
     }
     __syncthreads();
     // ---------------------------------------------------------------- P1
-    // r: U-as-A over the plane pairs (4w, 4w+1), (4w+2, 4w+3); ur -> sR, us -> sS
-    // (own points), ut -> sT (points of other threads)
+    // r: digits as A over the plane pairs (4w, 4w+1), (4w+2, 4w+3); ur -> sR,
+    // us -> sS (own points), ut -> sT (points of other threads)
 #pragma unroll 1
     for (int pp = 0; pp < 2; ++pp) {
-      float acc[NSL][4];
-#pragma unroll
-      for (int L = 0; L < NSL; ++L) acc[L][0] = acc[L][1] = acc[L][2] = acc[L][3] = 0.0f;
+      float2 acc[NSL], bcc[NSL];
       uint32_t a[NSL], c[NSL];
       const int ta = 4 * wp + 2 * pp;
 #pragma unroll
@@ -358,46 +401,37 @@ __global__ void __launch_bounds__(64, kMinBlocks)
         a[j] = sDig[dig_word(j, ta, g, q)];
         c[j] = sDig[dig_word(j, ta + 1, g, q)];
       }
-      contract_ua(a, c, Fd, acc);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int p = 2 * q + 8 * g + 64 * (4 * wp + 2 * pp + h);
-        const float2 o0 = recombine(acc[0][2 * h], acc[1][2 * h], acc[2][2 * h], acc[3][2 * h], acc[4][2 * h], scD);
-        const float2 o1 =
-            recombine(acc[0][2 * h + 1], acc[1][2 * h + 1], acc[2][2 * h + 1], acc[3][2 * h + 1], acc[4][2 * h + 1], scD);
-        *reinterpret_cast<float4 *>(&sR[p]) = make_float4(o0.x, o0.y, o1.x, o1.y);
-      }
+      contract_ua<true>(a, c, Fd, acc, bcc);
+      float2 H, L;
+      recombine(acc[0], acc[1], acc[2], acc[3], acc[4], scD, H, L);
+      st_pair(sR, pbase + 128 * pp, H, L);
+      recombine(bcc[0], bcc[1], bcc[2], bcc[3], bcc[4], scD, H, L);
+      st_pair(sR, pbase + 128 * pp + 64, H, L);
     }
-    // s: D-as-A per plane, B = the transposed digit matrices
+    // s: D as A per plane, B = the transposed digit matrices
 #pragma unroll 1
     for (int tt = 0; tt < 4; ++tt) {
-      float acc[NSL][2];
-#pragma unroll
-      for (int L = 0; L < NSL; ++L) acc[L][0] = acc[L][1] = 0.0f;
+      float2 acc[NSL];
       uint32_t b[NSL];
 #pragma unroll
       for (int j = 0; j < NSL; ++j) b[j] = movtrans(sDig[dig_word(j, 4 * wp + tt, g, q)]);
       contract_da(Fd, b, acc);
-      const int p = 2 * q + 8 * g + 64 * (4 * wp + tt);
-      const float2 o0 = recombine(acc[0][0], acc[1][0], acc[2][0], acc[3][0], acc[4][0], scD);
-      const float2 o1 = recombine(acc[0][1], acc[1][1], acc[2][1], acc[3][1], acc[4][1], scD);
-      *reinterpret_cast<float4 *>(&sS[p]) = make_float4(o0.x, o0.y, o1.x, o1.y);
+      float2 H, L;
+      recombine(acc[0], acc[1], acc[2], acc[3], acc[4], scD, H, L);
+      st_pair(sS, pbase + 64 * tt, H, L);
     }
-    // t: D-as-A per s (this warp: s = 4w..4w+3), B from shared memory
+    // t: D as A per s (this warp: s = 4w..4w+3), B from shared memory
 #pragma unroll 1
     for (int ss = 0; ss < 4; ++ss) {
       const int s = 4 * wp + ss;
       uint32_t b[NSL];
       ldsm4t(sdig_base + 4u * (uint32_t)dig_word(lmat, lrow, s, 0), b[0], b[1], b[2], b[3]);
       ldsm1t(sdig_base + 4u * (uint32_t)dig_word(4, lrow, s, 0), b[4]);
-      float acc[NSL][2];
-#pragma unroll
-      for (int L = 0; L < NSL; ++L) acc[L][0] = acc[L][1] = 0.0f;
+      float2 acc[NSL];
       contract_da(Fd, b, acc);
-      // outputs (t_out = g, r = 2q, 2q+1) at this s
-      const float2 o0 = recombine(acc[0][0], acc[1][0], acc[2][0], acc[3][0], acc[4][0], scD);
-      const float2 o1 = recombine(acc[0][1], acc[1][1], acc[2][1], acc[3][1], acc[4][1], scD);
-      *reinterpret_cast<float4 *>(&sT[2 * q + 8 * s + 64 * g]) = make_float4(o0.x, o0.y, o1.x, o1.y);
+      float2 H, L;  // outputs (t_out = g, r = 2q, 2q+1) at this s
+      recombine(acc[0], acc[1], acc[2], acc[3], acc[4], scD, H, L);
+      st_pair(sT, 2 * q + 8 * s + 64 * g, H, L);
     }
     __syncthreads();
     // ---------------------------------------------------------------- P2
@@ -405,30 +439,28 @@ __global__ void __launch_bounds__(64, kMinBlocks)
     int evm = 0;
 #pragma unroll 1
     for (int tt = 0; tt < 4; ++tt) {
-      const int p = 2 * q + 8 * g + 64 * (4 * wp + tt);
-      const float4 ur4 = *reinterpret_cast<const float4 *>(&sR[p]);
-      const float4 us4 = *reinterpret_cast<const float4 *>(&sS[p]);
-      const float4 ut4 = *reinterpret_cast<const float4 *>(&sT[p]);
-      const float2 ur[2] = {make_float2(ur4.x, ur4.y), make_float2(ur4.z, ur4.w)};
-      const float2 us[2] = {make_float2(us4.x, us4.y), make_float2(us4.z, us4.w)};
-      const float2 ut[2] = {make_float2(ut4.x, ut4.y), make_float2(ut4.z, ut4.w)};
-      float4 G4[6];
+      const int p = pbase + 64 * tt;
+      float2 uh[3], ul[3];
+      ld_pair(sR, p, uh[0], ul[0]);
+      ld_pair(sS, p, uh[1], ul[1]);
+      ld_pair(sT, p, uh[2], ul[2]);
+      float2 gh[6], gl[6];
 #pragma unroll
-      for (int f = 0; f < 6; ++f) G4[f] = *reinterpret_cast<const float4 *>(Ge + f * N3 + p);
-      float2 vr[2], vs[2], vt[2];
-#pragma unroll
-      for (int o = 0; o < 2; ++o) {
-        float2 gg[6];
-#pragma unroll
-        for (int f = 0; f < 6; ++f) gg[f] = o == 0 ? make_float2(G4[f].x, G4[f].y) : make_float2(G4[f].z, G4[f].w);
-        vr[o] = metric_row(gg[0], gg[1], gg[2], ur[o], us[o], ut[o]);
-        vs[o] = metric_row(gg[1], gg[3], gg[4], ur[o], us[o], ut[o]);
-        vt[o] = metric_row(gg[2], gg[4], gg[5], ur[o], us[o], ut[o]);
-        evm = max(evm, max(fexp(vr[o].x), max(fexp(vs[o].x), fexp(vt[o].x))));
+      for (int f = 0; f < 6; ++f) {
+        const float4 G4 = *reinterpret_cast<const float4 *>(Ge + f * N3 + p);
+        gh[f] = make_float2(G4.x, G4.z);
+        gl[f] = make_float2(G4.y, G4.w);
       }
-      *reinterpret_cast<float4 *>(&sR[p]) = make_float4(vr[0].x, vr[0].y, vr[1].x, vr[1].y);
-      *reinterpret_cast<float4 *>(&sS[p]) = make_float4(vs[0].x, vs[0].y, vs[1].x, vs[1].y);
-      *reinterpret_cast<float4 *>(&sT[p]) = make_float4(vt[0].x, vt[0].y, vt[1].x, vt[1].y);
+      float2 oh, ol;
+      metric_row2(gh, gl, 0, 1, 2, uh, ul, oh, ol);
+      evm = max(evm, fexp2(oh));
+      st_pair(sR, p, oh, ol);
+      metric_row2(gh, gl, 1, 3, 4, uh, ul, oh, ol);
+      evm = max(evm, fexp2(oh));
+      st_pair(sS, p, oh, ol);
+      metric_row2(gh, gl, 2, 4, 5, uh, ul, oh, ol);
+      evm = max(evm, fexp2(oh));
+      st_pair(sT, p, oh, ol);
     }
     evm = __reduce_max_sync(0xffffffffu, evm);
     if (lane == 0) s_red[2 + wp] = evm;
@@ -444,59 +476,42 @@ __global__ void __launch_bounds__(64, kMinBlocks)
     // t first: digits of wt to shared memory (the forward digits are no longer needed)
 #pragma unroll
     for (int tt = 0; tt < 4; ++tt) {
-      const int t = 4 * wp + tt, p = 2 * q + 8 * g + 64 * t;
-      const float4 v4 = *reinterpret_cast<const float4 *>(&sT[p]);
-      float d0[NSL], d1[NSL];
-      digits5(v4.x, v4.y, s1, c2, d0);
-      digits5(v4.z, v4.w, s1, c2, d1);
+      const int t = 4 * wp + tt;
+      float2 vh, vl;
+      ld_pair(sT, pbase + 64 * tt, vh, vl);
+      uint32_t d[NSL];
+      digits5(vh, vl, s1, c2, d);
 #pragma unroll
-      for (int j = 0; j < NSL; ++j) sDig[dig_word(j, t, g, q)] = pack_f16(d0[j], d1[j]);
+      for (int j = 0; j < NSL; ++j) sDig[dig_word(j, t, g, q)] = d[j];
     }
     // r and s into one level set, per plane pair
 #pragma unroll 1
     for (int pp = 0; pp < 2; ++pp) {
-      float acc[NSL][4];
+      float2 acc[NSL], bcc[NSL];
+      uint32_t a[NSL], c[NSL], bs[NSL];
+      float2 vh, vl;
+      const int p0 = pbase + 128 * pp;
+      ld_pair(sR, p0, vh, vl);
+      digits5(vh, vl, s1, c2, a);
+      ld_pair(sR, p0 + 64, vh, vl);
+      digits5(vh, vl, s1, c2, c);
+      contract_ua<true>(a, c, Td, acc, bcc);
+      // s: D^T as A, one plane at a time, into the same level pairs
+      ld_pair(sS, p0, vh, vl);
+      digits5(vh, vl, s1, c2, bs);
 #pragma unroll
-      for (int L = 0; L < NSL; ++L) acc[L][0] = acc[L][1] = acc[L][2] = acc[L][3] = 0.0f;
-      uint32_t a[NSL], c[NSL];
+      for (int j = 0; j < NSL; ++j) bs[j] = movtrans(bs[j]);
+      contract_da_acc(Td, bs, acc);
+      ld_pair(sS, p0 + 64, vh, vl);
+      digits5(vh, vl, s1, c2, bs);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int t = 4 * wp + 2 * pp + h, p = 2 * q + 8 * g + 64 * t;
-        const float4 r4 = *reinterpret_cast<const float4 *>(&sR[p]);
-        const float4 s4 = *reinterpret_cast<const float4 *>(&sS[p]);
-        float d0[NSL], d1[NSL];
-        digits5(r4.x, r4.y, s1, c2, d0);
-        digits5(r4.z, r4.w, s1, c2, d1);
-#pragma unroll
-        for (int j = 0; j < NSL; ++j) (h == 0 ? a[j] : c[j]) = pack_f16(d0[j], d1[j]);
-        digits5(s4.x, s4.y, s1, c2, d0);
-        digits5(s4.z, s4.w, s1, c2, d1);
-        uint32_t b[NSL];
-#pragma unroll
-        for (int j = 0; j < NSL; ++j) b[j] = movtrans(pack_f16(d0[j], d1[j]));
-        // s: D^T as A, the two outputs of plane t land in acc[.][2h], acc[.][2h+1]
-        float sacc[NSL][2];
-#pragma unroll
-        for (int L = 0; L < NSL; ++L) {
-          sacc[L][0] = acc[L][2 * h];
-          sacc[L][1] = acc[L][2 * h + 1];
-        }
-        contract_da(Td, b, sacc);
-#pragma unroll
-        for (int L = 0; L < NSL; ++L) {
-          acc[L][2 * h] = sacc[L][0];
-          acc[L][2 * h + 1] = sacc[L][1];
-        }
-      }
-      contract_ua(a, c, Td, acc);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int t = 4 * wp + 2 * pp + h, p = 2 * q + 8 * g + 64 * t;
-        const float2 o0 = recombine(acc[0][2 * h], acc[1][2 * h], acc[2][2 * h], acc[3][2 * h], acc[4][2 * h], scV);
-        const float2 o1 =
-            recombine(acc[0][2 * h + 1], acc[1][2 * h + 1], acc[2][2 * h + 1], acc[3][2 * h + 1], acc[4][2 * h + 1], scV);
-        *reinterpret_cast<float4 *>(&sR[p]) = make_float4(o0.x, o0.y, o1.x, o1.y);
-      }
+      for (int j = 0; j < NSL; ++j) bs[j] = movtrans(bs[j]);
+      contract_da_acc(Td, bs, bcc);
+      float2 H, L;
+      recombine(acc[0], acc[1], acc[2], acc[3], acc[4], scV, H, L);
+      st_pair(sR, p0, H, L);
+      recombine(bcc[0], bcc[1], bcc[2], bcc[3], bcc[4], scV, H, L);
+      st_pair(sR, p0 + 64, H, L);
     }
     __syncthreads();  // the digits of wt are in shared memory; sT is free
 #pragma unroll 1
@@ -505,63 +520,64 @@ __global__ void __launch_bounds__(64, kMinBlocks)
       uint32_t b[NSL];
       ldsm4t(sdig_base + 4u * (uint32_t)dig_word(lmat, lrow, s, 0), b[0], b[1], b[2], b[3]);
       ldsm1t(sdig_base + 4u * (uint32_t)dig_word(4, lrow, s, 0), b[4]);
-      float acc[NSL][2];
-#pragma unroll
-      for (int L = 0; L < NSL; ++L) acc[L][0] = acc[L][1] = 0.0f;
+      float2 acc[NSL];
       contract_da(Td, b, acc);
-      const float2 o0 = recombine(acc[0][0], acc[1][0], acc[2][0], acc[3][0], acc[4][0], scV);
-      const float2 o1 = recombine(acc[0][1], acc[1][1], acc[2][1], acc[3][1], acc[4][1], scV);
-      *reinterpret_cast<float4 *>(&sT[2 * q + 8 * s + 64 * g]) = make_float4(o0.x, o0.y, o1.x, o1.y);
+      float2 H, L;
+      recombine(acc[0], acc[1], acc[2], acc[3], acc[4], scV, H, L);
+      st_pair(sT, 2 * q + 8 * s + 64 * g, H, L);
     }
     __syncthreads();
     // ---------------------------------------------------------------- P4
-    df::Acc pwe = {0.0f, 0.0f};
+    dfx::Acc pwe = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
 #pragma unroll 1
     for (int tt = 0; tt < 4; ++tt) {
-      const int p = 2 * q + 8 * g + 64 * (4 * wp + tt);
-      const float4 a4 = *reinterpret_cast<const float4 *>(&sR[p]);
-      const float4 b4 = *reinterpret_cast<const float4 *>(&sT[p]);
-      float2 Bv2[2];
+      const int p = pbase + 64 * tt;
+      float2 ah, al, bh, bl;
+      ld_pair(sR, p, ah, al);
+      ld_pair(sT, p, bh, bl);
+      // (ah, al) + (bh, bl): TwoSum of the highs, lows added, normalised
+      float2 s, er;
+      dfx::two_sum(ah, bh, s, er);
+      float2 vh, vl;
+      dfx::two_sum(s, add2(add2(al, bl), er), vh, vl);
+      int2 gp = make_int2(0, 0);  // the point pair's gather indices, read again (L1/L2)
+      if (ASSEMBLED) gp = *reinterpret_cast<const int2 *>(l2gm + e * N3 + p);
+      float2 xh = make_float2(0.0f, 0.0f), xl = xh;
+      if (HELM || (ASSEMBLED && pw_partial != nullptr)) {
+        double uv[2];
+        load_u<ASSEMBLED>(u, gp, e * N3 + p, uv);
+        const float2 x0 = df::from_f64_scaled(uv[0], su), x1 = df::from_f64_scaled(uv[1], su);
+        xh = make_float2(x0.x, x1.x);
+        xl = make_float2(x0.y, x1.y);
+      }
       if (HELM) {
         const float4 B4 = *reinterpret_cast<const float4 *>(Bdf + e * N3 + p);
-        Bv2[0] = make_float2(B4.x, B4.y);
-        Bv2[1] = make_float2(B4.z, B4.w);
+        const float2 Bh = make_float2(B4.x, B4.z), Bl = make_float2(B4.y, B4.w);
+        dfx::Acc bu = dfx::mul_first(Bh, Bl, xh, xl);
+        float2 buh, bul;
+        dfx::two_sum(bu.s, bu.c, buh, bul);
+        dfx::Acc o = dfx::mul_first(dup(h1.x), dup(h1.y), vh, vl);
+        dfx::mac(o, dup(h2.x), dup(h2.y), buh, bul);
+        dfx::two_sum(o.s, o.c, vh, vl);
       }
-      int32_t gp[2] = {0, 0};  // the point pair's gather indices, read again (L1/L2)
+      const double v0 = df::to_f64_scaled(vh.x, vl.x, su), v1 = df::to_f64_scaled(vh.y, vl.y, su);
       if (ASSEMBLED) {
-        const int2 ii = *reinterpret_cast<const int2 *>(l2gm + e * N3 + p);
-        gp[0] = ii.x;
-        gp[1] = ii.y;
-      }
-      double uv[2];
-      if (HELM || (ASSEMBLED && pw_partial != nullptr)) load_u<ASSEMBLED>(u, gp, e * N3 + p, uv);
-#pragma unroll
-      for (int o = 0; o < 2; ++o) {
-        df::Acc acc = {o == 0 ? a4.x : a4.z, o == 0 ? a4.y : a4.w};
-        df::acc_add(acc, o == 0 ? b4.x : b4.z, o == 0 ? b4.y : b4.w);
-        float2 v = df::norm(acc);
-        float2 xk = make_float2(0.0f, 0.0f);
-        if (HELM || (ASSEMBLED && pw_partial != nullptr)) xk = df::from_f64_scaled(uv[o], su);
-        if (HELM) {
-          const float2 buv = df::norm(df::mul_first(Bv2[o].x, Bv2[o].y, xk.x, xk.y));
-          df::Acc oo = df::mul_first(h1.x, h1.y, v.x, v.y);
-          df::mac(oo, h2.x, h2.y, buv.x, buv.y);
-          v = df::norm(oo);
-        }
-        const double vd = df::to_f64_scaled(v.x, v.y, su);
-        if (ASSEMBLED) {
-          const int32_t gg = gp[o];
-          if (wloc) wloc[e * N3 + p + o] = (gg >= 0) ? vd : 0.0;
-          else if (gg >= 0) atomicAdd(&w[gg], vd);
-          if (pw_partial != nullptr) df::mac(pwe, xk.x, xk.y, v.x, v.y);
+        if (wloc) {
+          wloc[e * N3 + p] = (gp.x >= 0) ? v0 : 0.0;
+          wloc[e * N3 + p + 1] = (gp.y >= 0) ? v1 : 0.0;
         } else {
-          w[e * N3 + p + o] = vd;
+          if (gp.x >= 0) atomicAdd(&w[gp.x], v0);
+          if (gp.y >= 0) atomicAdd(&w[gp.y], v1);
         }
+        if (pw_partial != nullptr) dfx::mac(pwe, xh, xl, vh, vl);
+      } else {
+        w[e * N3 + p] = v0;
+        w[e * N3 + p + 1] = v1;
       }
     }
     if (ASSEMBLED && pw_partial != nullptr) {
-      const float2 pn = df::norm(pwe);
-      pw += df::to_f64_scaled(pn.x, pn.y, 2 * su);
+      const float2 p0 = df::norm(df::Acc{pwe.s.x, pwe.c.x}), p1 = df::norm(df::Acc{pwe.s.y, pwe.c.y});
+      pw += df::to_f64_scaled(p0.x, p0.y, 2 * su) + df::to_f64_scaled(p1.x, p1.y, 2 * su);
     }
     __syncthreads();  // shared tiles and digit planes are reused by the next element
   }

@@ -105,11 +105,16 @@ __device__ __forceinline__ float2 from_f64(double x) {
 __device__ __forceinline__ double to_f64(float h, float l) {
   const unsigned hb = __float_as_uint(h);
   const unsigned ef = (hb >> 23) & 0xFFu;
-  if (ef < 54u || ef == 255u) return (double)h + (double)l;  // tiny, zero, inf, nan: rare slow path
   const unsigned sgn = hb & 0x80000000u;
   const unsigned m = hb & 0x7FFFFFu;
+  // the binary64 bits of hi (exact)
   long long D = (long long)(((unsigned long long)(sgn | ((ef + 896u) << 20) | (m >> 3)) << 32) |
                             ((unsigned long long)(m & 7u) << 29));
+  if (ef < 54u || ef == 255u) {  // rare: integer bit work only, no binary64 arithmetic
+    if (ef == 255u) return __longlong_as_double((long long)((unsigned long long)(sgn | 0x7FF00000u | (m ? 0x80000u : 0u)) << 32));
+    if (ef == 0u) return __longlong_as_double((long long)((unsigned long long)sgn << 32));  // zero (binary32 subnormals too)
+    return __longlong_as_double(D);  // |hi| < 2^-73: hi alone (|lo| < 2^-24 |hi|)
+  }
   // lo in ulps of hi (2^(E-52), E = ef - 127): scale 2^(179 - ef); when hi is
   // a power of two and lo points toward zero the sum lies in the binade
   // below, whose ulp is half as large: scale by 2^(180 - ef)
@@ -157,7 +162,9 @@ __device__ __forceinline__ double to_f64_scaled(float h, float l, int sh) {
   if (e == 0 || e == 0x7FF) return d;  // zero (h = 0) or not finite
   const int es = e + sh;
   if (es >= 1 && es <= 0x7FE) return __longlong_as_double((long long)(b + ((unsigned long long)(long long)sh << 52)));
-  return ldexp(d, sh);  // result below the normal range or overflowing: rare slow path
+  // rare: below the normal range (flushed to a signed zero) or overflowing (infinity)
+  const unsigned long long sg = b & 0x8000000000000000ull;
+  return __longlong_as_double((long long)(es < 1 ? sg : (sg | 0x7FF0000000000000ull)));
 }
 
 }  // namespace df

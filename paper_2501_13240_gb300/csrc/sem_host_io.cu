@@ -59,6 +59,7 @@ sem_mesh sub_range(const sem_mesh *m, int64_t e0, int64_t e1) {
 extern "C" int sem_ax_assembled_host(const sem_mesh *m, double h1, double h2, const double *u_host, double *w_host,
                                      int precision, double *u_dev, double *w_dev, int nchunks, void *stream) {
   SemRange nvtx_range("sem_ax_assembled_host");
+  if (m && m->slab) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_host: needs the whole box, not a partition's slab mesh");
   if (!m || !u_host || !w_host || !u_dev || !w_dev)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_host: NULL argument");
   if ((((uintptr_t)u_dev) | ((uintptr_t)w_dev)) & 7 || u_dev == w_dev)
@@ -139,6 +140,7 @@ extern "C" int sem_ax_assembled_host_batch(const sem_mesh *m, double h1, double 
                                            const double *const *u_host, double *const *w_host, int precision,
                                            double *u_dev2, double *w_dev2, void *stream) {
   SemRange nvtx_range("sem_ax_assembled_host_batch");
+  if (m && m->slab) return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_host_batch: needs the whole box, not a partition's slab mesh");
   if (!m || !u_host || !w_host || !u_dev2 || !w_dev2 || nsteps < 0)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_ax_assembled_host_batch: NULL argument or negative count");
   for (int k = 0; k < nsteps; ++k)

@@ -57,11 +57,17 @@ struct sem_mesh {
   // N = 7 double-float operator: 1-D contractions on the tensor pipe
   // (sem_ax_tc.cu) when set (the default), else on the binary32 pipe
   int use_tc = 1;
+  // a slab of element planes of a box (a partition's share, sem_part): its
+  // own unique numbering, no periodic wrap in z; first plane slab_p0
+  int slab = 0;
+  int slab_p0 = 0;
   // N = 1 only: element stiffness matrices (upper triangle, [36][E]) in
   // binary64 and double-float
   double *K1 = nullptr;
   float2 *K1df = nullptr;
 };
+
+int sem_mesh_create_slab(const sem_box_desc *d, int p0, int p1, void *stream, sem_mesh **out);
 
 // thread-local error reporting
 int sem_fail(int code, const std::string &msg);

@@ -1060,6 +1060,7 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
                               sem_pmg **out) {
   if (!m || !o || !out) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: NULL argument");
   *out = nullptr;
+  if (m->slab) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: needs the whole box, not a partition's slab mesh");
   if (o->nlevels < 2 || o->nlevels > 4 || o->orders[0] != m->N)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: need 2..4 levels with orders[0] = the mesh's N");
   for (int l = 1; l < o->nlevels; ++l)

@@ -230,6 +230,7 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
                               sem_rbc **out) {
   if (!m || !prm || !out) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: NULL argument");
   *out = nullptr;
+  if (m->slab) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: needs the whole box, not a partition's slab mesh");
   if (!(prm->Ra > 0) || !(prm->Pr > 0) || !(prm->dt > 0) || !(prm->tol > 0) || prm->maxit < 1)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: Ra, Pr, dt, tol must be > 0 and maxit >= 1");
   if (prm->precision != SEM_PREC_FP64 && prm->precision != SEM_PREC_DF64)

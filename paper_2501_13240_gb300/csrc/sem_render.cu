@@ -136,6 +136,7 @@ extern "C" int sem_render_slice(const sem_mesh *m, const double *u_g, const sem_
                                 uint8_t *rgba, void *stream) {
   SemRange nvtx_range("sem_render_slice");
   if (!m || !u_g || !d || !values || !rgba) return sem_fail(SEM_ERR_INVALID_ARG, "sem_render_slice: NULL argument");
+  if (m->slab) return sem_fail(SEM_ERR_INVALID_ARG, "sem_render_slice: needs the whole box, not a partition's slab mesh");
   if (d->axis < 0 || d->axis > 2 || !(d->coord >= 0.0) || !(d->coord <= m->L[d->axis]))
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_render_slice: axis must be 0..2 and 0 <= coord <= L[axis]");
   if (d->width < 1 || d->height < 1 || d->width > 32768 || d->height > 32768)
@@ -384,6 +385,7 @@ extern "C" int sem_render_scene(const sem_mesh *m, const double *u_g, const sem_
                                 float *depth, uint8_t *rgba, void *stream) {
   SemRange nvtx_range("sem_render_scene");
   if (!m || !u_g || !d || !volume || !depth || !rgba) return sem_fail(SEM_ERR_INVALID_ARG, "sem_render_scene: NULL argument");
+  if (m->slab) return sem_fail(SEM_ERR_INVALID_ARG, "sem_render_scene: needs the whole box, not a partition's slab mesh");
   if (d->width < 1 || d->height < 1 || d->width > 16384 || d->height > 16384)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_render_scene: width and height must be in [1, 16384]");
   for (int q = 0; q < 3; ++q)

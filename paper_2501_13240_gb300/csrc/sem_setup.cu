@@ -118,7 +118,11 @@ struct BoxParams {
   double xi[SEM_MAXNP];
   int periodic[3];
   int dirichlet[6];
-  int64_t nd[3];  // unique lattice extent per direction
+  int64_t nd[3];  // unique lattice extent per direction (z: of the slab)
+  // a slab of whole element planes: elements e_off.. of the box, lattice
+  // planes from k_off; wrapz: z is periodic and the slab is the whole box
+  int64_t e_off, k_off;
+  int wrapz;
 };
 
 __device__ __forceinline__ double iface(const BoxParams &p, int d, int k) {
@@ -129,8 +133,9 @@ __device__ __forceinline__ double iface(const BoxParams &p, int d, int k) {
 __global__ void k_coords(BoxParams p, int64_t nL, double *X, double *Y, double *Z) {
   const int n = p.n, n3 = n * n * n;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
-    int64_t e = l / n3;
-    int q = (int)(l - e * n3);
+    const int64_t el = l / n3;
+    int q = (int)(l - el * n3);
+    const int64_t e = el + p.e_off;  // element of the whole box
     int loc[3] = {q % n, (q / n) % n, q / (n * n)};
     int64_t ex = e % p.nel[0];
     int64_t ey = (e / p.nel[0]) % p.nel[1];
@@ -242,24 +247,27 @@ __global__ void k_l2g(BoxParams p, int64_t nL, int32_t *l2g) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL; l += (int64_t)gridDim.x * blockDim.x) {
     int64_t e = l / n3;
     int q = (int)(l - e * n3);
+    e += p.e_off;
     int64_t ex = e % p.nel[0], ey = (e / p.nel[0]) % p.nel[1], ez = e / ((int64_t)p.nel[0] * p.nel[1]);
     int64_t I = ex * N + q % n, J = ey * N + (q / n) % n, K = ez * N + q / (n * n);
     if (p.periodic[0] && I == (int64_t)p.nel[0] * N) I = 0;
     if (p.periodic[1] && J == (int64_t)p.nel[1] * N) J = 0;
-    if (p.periodic[2] && K == (int64_t)p.nel[2] * N) K = 0;
-    l2g[l] = (int32_t)(I + p.nd[0] * (J + p.nd[1] * K));
+    if (p.wrapz && K == (int64_t)p.nel[2] * N) K = 0;
+    l2g[l] = (int32_t)(I + p.nd[0] * (J + p.nd[1] * (K - p.k_off)));
   }
 }
 
 __global__ void k_mask(BoxParams p, int64_t nU, uint8_t *mask) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
-    int64_t idx[3] = {g % p.nd[0], (g / p.nd[0]) % p.nd[1], g / (p.nd[0] * p.nd[1])};
+    // lattice indices in the whole box (z offset by the slab's first plane)
+    int64_t idx[3] = {g % p.nd[0], (g / p.nd[0]) % p.nd[1], g / (p.nd[0] * p.nd[1]) + p.k_off};
+    const int64_t top[3] = {p.nd[0] - 1, p.nd[1] - 1, (int64_t)p.nel[2] * p.N};
     uint8_t m = 1;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (p.periodic[d]) continue;
       if (p.dirichlet[2 * d] && idx[d] == 0) m = 0;
-      if (p.dirichlet[2 * d + 1] && idx[d] == p.nd[d] - 1) m = 0;
+      if (p.dirichlet[2 * d + 1] && idx[d] == top[d]) m = 0;
     }
     mask[g] = m;
   }
@@ -420,6 +428,13 @@ static int build_gs_tables(sem_mesh *m, cudaStream_t st) {
 }
 
 extern "C" int sem_mesh_create_box(const sem_box_desc *d, void *stream, sem_mesh **out) {
+  return sem_mesh_create_slab(d, 0, -1, stream, out);
+}
+
+// The box, or the slab of its element planes [p0, p1) (p1 < 0: the whole box):
+// the slab's elements in box order, its own unique numbering of lattice
+// planes p0 N .. p1 N (no periodic wrap in z unless it is the whole box).
+int sem_mesh_create_slab(const sem_box_desc *d, int p0, int p1, void *stream, sem_mesh **out) {
   SemRange nvtx_range("sem_mesh_create_box");
   if (!d || !out) return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_create_box: NULL argument");
   *out = nullptr;
@@ -433,7 +448,14 @@ extern "C" int sem_mesh_create_box(const sem_box_desc *d, void *stream, sem_mesh
     if (d->periodic[c] && (c == 0 ? d->nelx : c == 1 ? d->nely : d->nelz) < 2)
       return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_create_box: a periodic direction needs >= 2 elements");
   const int n = d->N + 1;
-  const int64_t E = (int64_t)d->nelx * d->nely * d->nelz;
+  if (p1 < 0) {
+    p0 = 0;
+    p1 = d->nelz;
+  }
+  if (p0 < 0 || p1 > d->nelz || p0 >= p1) return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_create_box: bad slab");
+  const bool whole = (p0 == 0 && p1 == d->nelz);
+  const int64_t plane = (int64_t)d->nelx * d->nely;
+  const int64_t E = plane * (p1 - p0);
   const int64_t nL = E * n * n * n;
   if (nL > 2147483647LL) return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_create_box: more than 2^31-1 local nodes");
   cudaStream_t st = as_stream(stream);
@@ -441,7 +463,9 @@ extern "C" int sem_mesh_create_box(const sem_box_desc *d, void *stream, sem_mesh
   sem_mesh *m = new sem_mesh();
   m->nel[0] = d->nelx;
   m->nel[1] = d->nely;
-  m->nel[2] = d->nelz;
+  m->nel[2] = p1 - p0;
+  m->slab = whole ? 0 : 1;
+  m->slab_p0 = p0;
   m->N = d->N;
   m->n = n;
   m->n3 = n * n * n;
@@ -458,12 +482,17 @@ extern "C" int sem_mesh_create_box(const sem_box_desc *d, void *stream, sem_mesh
 
   BoxParams p;
   memset(&p, 0, sizeof(p));
+  const int nel_box[3] = {d->nelx, d->nely, d->nelz};
   for (int c = 0; c < 3; ++c) {
-    p.nel[c] = m->nel[c];
+    p.nel[c] = nel_box[c];
     p.L[c] = m->L[c];
     p.periodic[c] = m->periodic[c];
-    p.nd[c] = (int64_t)m->nel[c] * d->N + (m->periodic[c] ? 0 : 1);
+    p.nd[c] = (int64_t)nel_box[c] * d->N + (m->periodic[c] ? 0 : 1);
   }
+  p.e_off = plane * p0;
+  p.k_off = (int64_t)p0 * d->N;
+  p.wrapz = (m->periodic[2] && whole) ? 1 : 0;
+  if (!whole) p.nd[2] = (int64_t)(p1 - p0) * d->N + 1;
   for (int f = 0; f < 6; ++f) p.dirichlet[f] = m->dirichlet[f];
   p.N = d->N;
   p.n = n;

@@ -72,12 +72,15 @@ def test_every_entry_point_rejects_null_arguments():
     device; the destroy calls accept NULL as a no-op (like free)."""
     import ctypes
     L = sem.lib()
-    destroys = {"sem_mesh_destroy", "sem_rbc_destroy", "sem_tadv_destroy", "sem_pmg_destroy"}
+    destroys = {"sem_mesh_destroy", "sem_rbc_destroy", "sem_tadv_destroy", "sem_pmg_destroy", "sem_part_destroy"}
+    ints = (ctypes.c_int, ctypes.c_uint, ctypes.c_int64)
     for name in sem.EXPORTS:
-        if name in ("sem_last_error", "sem_version", "sem_pcg_noalloc_capacity"):
+        if name in ("sem_last_error", "sem_version", "sem_pcg_noalloc_capacity", "sem_set_grid_wait_limit"):
             continue
         f = getattr(L, name)
-        args = [0 if t is ctypes.c_int else 0.0 if t is ctypes.c_double else None for t in f.argtypes]
+        args = [0 if t in ints else 0.0 if t is ctypes.c_double else
+                t() if isinstance(t, type) and issubclass(t, ctypes._CFuncPtr) else None  # NULL callback
+                for t in f.argtypes]
         rc = f(*args)
         if name in destroys:
             assert rc == 0, name
@@ -171,14 +174,15 @@ def test_binding_structs_match_the_c_header(tmp_path):
 
 def test_binding_signatures_match_the_c_prototypes():
     """Each function's ctypes argument list has the prototype's arity, and
-    each argument the prototype's kind: pointer, int, int64, size_t or
-    double."""
+    each argument the prototype's kind: pointer, int, unsigned, int64,
+    size_t, double or one of the two callback types."""
     import ctypes
     txt = open(os.path.join(ROOT, "include", "sem.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     protos = dict((m.group(1), m.group(2)) for m in re.finditer(r"\b(sem_\w+)\s*\(([^)]*)\)\s*;", txt))
     L = sem.lib()
-    scalar = {"int": ctypes.c_int, "double": ctypes.c_double, "int64_t": ctypes.c_int64, "size_t": ctypes.c_size_t}
+    scalar = {"int": ctypes.c_int, "double": ctypes.c_double, "int64_t": ctypes.c_int64, "size_t": ctypes.c_size_t,
+              "unsigned": ctypes.c_uint, "sem_exchange_fn": sem.EXCHANGE_FN, "sem_allreduce_fn": sem.ALLREDUCE_FN}
     for name in sem.EXPORTS:
         params = [p.strip() for p in protos[name].split(",") if p.strip() and p.strip() != "void"]
         args = getattr(L, name).argtypes
