@@ -324,7 +324,12 @@ typedef struct sem_pmg sem_pmg; /* opaque; owns its level meshes and scratch */
 typedef struct {
   int nlevels;            /* 2..4 */
   int orders[4];          /* orders[0] = the fine mesh's N, strictly decreasing, >= 1 */
-  int smoother_precision; /* SEM_PREC_FP32 or SEM_PREC_BF16 */
+  int smoother_precision; /* SEM_PREC_FP32 or SEM_PREC_BF16 (the mixed-precision
+                             preconditioner of Sec. 2.2), or SEM_PREC_DF64: every
+                             smoothing level in binary64 vectors with the
+                             binary64-accurate double-float operator (the same
+                             V-cycle at full precision, to measure what the lower
+                             precision saves) */
   int cheb_degree;        /* Chebyshev degree (operator applications per smoothing), >= 1 */
   double lambda_safety;   /* factor on the power-iteration estimate of lambda_max (e.g. 1.1) */
   int power_its;          /* power iterations (e.g. 20) */

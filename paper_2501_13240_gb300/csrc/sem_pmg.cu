@@ -41,6 +41,11 @@ struct PmgLevel {
   float *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *t = nullptr;
   int *err = nullptr;  // set by a kernel whose shared-memory copies did not land (then the persistent
                        // TMA operator is used; NULL selects the plain operator)
+  // binary64-accurate smoothing (SEM_PREC_DF64): the level's vectors in
+  // binary64 and the double-float operator
+  double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *d64 = nullptr, *t64 = nullptr, *dinv64 = nullptr;
+  double *minv64 = nullptr;
+  double lam64 = 0.0;
 };
 
 constexpr int kPart = 152 * 2;
@@ -50,6 +55,7 @@ constexpr int kPart = 152 * 2;
 struct sem_pmg {
   std::vector<PmgLevel> L;
   float *J[3] = {};  // device interpolation matrices, level l+1 -> l, [n_f][n_c]
+  double *J64[3] = {};  // the same in binary64 (binary64-accurate smoothing)
   sem_pmg_opts o;
   double h1 = 1.0, h2 = 0.0;
   double *cb = nullptr, *cx = nullptr;  // coarsest level (binary64)
@@ -468,11 +474,12 @@ int launch_ax32(const PmgLevel &lv, int gprec, float h1, float h2, const float *
 struct Owner {
   int nel[3], per[3];
 };
-__global__ void k_prolong(int nf, int nc, int64_t E, const float *__restrict__ J, const int32_t *__restrict__ mapc,
-                          const float *__restrict__ uc, const int32_t *__restrict__ mapf, float *__restrict__ uf,
-                          int accumulate, Owner ow, const float *__restrict__ bf, float *__restrict__ rf) {
-  __shared__ float tile[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];
-  __shared__ float Js[SEM_MAXNP * SEM_MAXNP];
+template <typename T>
+__global__ void k_prolong(int nf, int nc, int64_t E, const T *__restrict__ J, const int32_t *__restrict__ mapc,
+                          const T *__restrict__ uc, const int32_t *__restrict__ mapf, T *__restrict__ uf,
+                          int accumulate, Owner ow, const T *__restrict__ bf, T *__restrict__ rf) {
+  __shared__ T tile[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];
+  __shared__ T Js[SEM_MAXNP * SEM_MAXNP];
   const int nc3 = nc * nc * nc, nf3 = nf * nf * nf;
   const int tid = threadIdx.x, i = tid % nf, j = tid / nf;
   for (int t = tid; t < nf * nc; t += blockDim.x) Js[t] = J[t];
@@ -481,22 +488,22 @@ __global__ void k_prolong(int nf, int nc, int64_t E, const float *__restrict__ J
     __syncthreads();
     for (int t = tid; t < nc3; t += blockDim.x) {
       const int32_t g = mapc[e * nc3 + t];
-      tile[t] = g >= 0 ? uc[g] : 0.0f;
+      tile[t] = g >= 0 ? uc[g] : T(0);
     }
     __syncthreads();
-    float t2[SEM_MAXNP];
+    T t2[SEM_MAXNP];
     for (int c = 0; c < nc; ++c) {
-      float sb = 0.0f;
+      T sb = T(0);
       for (int b = 0; b < nc; ++b) {
-        float sa = 0.0f;
-        for (int a = 0; a < nc; ++a) sa = fmaf(Js[i * nc + a], tile[a + nc * (b + nc * c)], sa);
-        sb = fmaf(Js[j * nc + b], sa, sb);
+        T sa = T(0);
+        for (int a = 0; a < nc; ++a) sa = fma(Js[i * nc + a], tile[a + nc * (b + nc * c)], sa);
+        sb = fma(Js[j * nc + b], sa, sb);
       }
       t2[c] = sb;
     }
     for (int k = 0; k < nf; ++k) {
-      float s = 0.0f;
-      for (int c = 0; c < nc; ++c) s = fmaf(Js[k * nc + c], t2[c], s);
+      T s = T(0);
+      for (int c = 0; c < nc; ++c) s = fma(Js[k * nc + c], t2[c], s);
       const int32_t g = mapf[e * nf3 + i + nf * (j + nf * k)];
       if (g < 0) continue;
       if (!accumulate) {
@@ -513,26 +520,27 @@ __global__ void k_prolong(int nf, int nc, int64_t E, const float *__restrict__ J
 
 // coarse level rc += R rf = P^T rf: J^T (x) J^T (x) J^T of the fine element's
 // rf / multiplicity, summed into the coarse vector
-__global__ void k_restrict(int nf, int nc, int64_t E, const float *__restrict__ J, const int32_t *__restrict__ mapf,
-                           const float *__restrict__ minvf, const float *__restrict__ rf,
-                           const int32_t *__restrict__ mapc, float *__restrict__ rc, float *__restrict__ wloc) {
-  __shared__ float u1[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];  // [i][j][c]
-  __shared__ float u2[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];  // [i][b][c]
-  __shared__ float Js[SEM_MAXNP * SEM_MAXNP];
+template <typename T>
+__global__ void k_restrict(int nf, int nc, int64_t E, const T *__restrict__ J, const int32_t *__restrict__ mapf,
+                           const T *__restrict__ minvf, const T *__restrict__ rf,
+                           const int32_t *__restrict__ mapc, T *__restrict__ rc, T *__restrict__ wloc) {
+  __shared__ T u1[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];  // [i][j][c]
+  __shared__ T u2[SEM_MAXNP * SEM_MAXNP * SEM_MAXNP];  // [i][b][c]
+  __shared__ T Js[SEM_MAXNP * SEM_MAXNP];
   const int nc3 = nc * nc * nc, nf3 = nf * nf * nf;
   const int tid = threadIdx.x, i = tid % nf, j = tid / nf;
   for (int t = tid; t < nf * nc; t += blockDim.x) Js[t] = J[t];
   for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
     __syncthreads();
     {
-      float v[SEM_MAXNP];
+      T v[SEM_MAXNP];
       for (int k = 0; k < nf; ++k) {
         const int32_t g = mapf[e * nf3 + i + nf * (j + nf * k)];
-        v[k] = g >= 0 ? rf[g] * minvf[g] : 0.0f;
+        v[k] = g >= 0 ? rf[g] * minvf[g] : T(0);
       }
       for (int c = 0; c < nc; ++c) {
-        float s = 0.0f;
-        for (int k = 0; k < nf; ++k) s = fmaf(Js[k * nc + c], v[k], s);
+        T s = T(0);
+        for (int k = 0; k < nf; ++k) s = fma(Js[k * nc + c], v[k], s);
         u1[(i * nf + j) * nc + c] = s;
       }
     }
@@ -540,8 +548,8 @@ __global__ void k_restrict(int nf, int nc, int64_t E, const float *__restrict__ 
     if (tid < nf * nc) {  // thread (i, b)
       const int ii = tid % nf, b = tid / nf;
       for (int c = 0; c < nc; ++c) {
-        float s = 0.0f;
-        for (int jj = 0; jj < nf; ++jj) s = fmaf(Js[jj * nc + b], u1[(ii * nf + jj) * nc + c], s);
+        T s = T(0);
+        for (int jj = 0; jj < nf; ++jj) s = fma(Js[jj * nc + b], u1[(ii * nf + jj) * nc + c], s);
         u2[(ii * nc + b) * nc + c] = s;
       }
     }
@@ -549,11 +557,11 @@ __global__ void k_restrict(int nf, int nc, int64_t E, const float *__restrict__ 
     if (tid < nc * nc) {  // thread (a, b)
       const int a = tid % nc, b = tid / nc;
       for (int c = 0; c < nc; ++c) {
-        float s = 0.0f;
-        for (int ii = 0; ii < nf; ++ii) s = fmaf(Js[ii * nc + a], u2[(ii * nc + b) * nc + c], s);
+        T s = T(0);
+        for (int ii = 0; ii < nf; ++ii) s = fma(Js[ii * nc + a], u2[(ii * nc + b) * nc + c], s);
         const int64_t lc = e * nc3 + a + nc * (b + nc * c);
         const int32_t g = mapc[lc];
-        if (wloc) wloc[lc] = (g >= 0) ? s : 0.0f;
+        if (wloc) wloc[lc] = (g >= 0) ? s : T(0);
         else if (g >= 0) atomicAdd(&rc[g], s);
       }
     }
@@ -561,38 +569,42 @@ __global__ void k_restrict(int nf, int nc, int64_t E, const float *__restrict__ 
 }
 
 // ---------------------------------------------------------------- vector kernels
-__global__ void k_cheb_start(int64_t n, const float *__restrict__ b, const float *__restrict__ dinv, float c0,
-                             float *__restrict__ x, float *__restrict__ r, float *__restrict__ d) {
+template <typename T>
+__global__ void k_cheb_start(int64_t n, const T *__restrict__ b, const T *__restrict__ dinv, T c0,
+                             T *__restrict__ x, T *__restrict__ r, T *__restrict__ d) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    const float bv = b[g];
-    x[g] = 0.0f;
+    const T bv = b[g];
+    x[g] = T(0);
     r[g] = bv;
     d[g] = c0 * dinv[g] * bv;
   }
 }
 
-__global__ void k_scaled(int64_t n, const float *__restrict__ r, const float *__restrict__ dinv, float c0,
-                         float *__restrict__ d) {
+template <typename T>
+__global__ void k_scaled(int64_t n, const T *__restrict__ r, const T *__restrict__ dinv, T c0, T *__restrict__ d) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     d[g] = c0 * dinv[g] * r[g];
 }
 
 // x += d;  d = c1 d + c2 dinv r
-__global__ void k_cheb_xd(int64_t n, float c1, float c2, const float *__restrict__ dinv, const float *__restrict__ r,
-                          float *__restrict__ x, float *__restrict__ d) {
+template <typename T>
+__global__ void k_cheb_xd(int64_t n, T c1, T c2, const T *__restrict__ dinv, const T *__restrict__ r, T *__restrict__ x,
+                          T *__restrict__ d) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    const float dv = d[g];
+    const T dv = d[g];
     x[g] += dv;
     d[g] = c1 * dv + c2 * dinv[g] * r[g];
   }
 }
 
-__global__ void k_axpy_f(int64_t n, float a, const float *__restrict__ x, float *__restrict__ y) {
+template <typename T>
+__global__ void k_axpy_f(int64_t n, T a, const T *__restrict__ x, T *__restrict__ y) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     y[g] += a * x[g];
 }
 
-__global__ void k_copy_f(int64_t n, const float *__restrict__ x, float *__restrict__ y) {
+template <typename T>
+__global__ void k_copy_f(int64_t n, const T *__restrict__ x, T *__restrict__ y) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     y[g] = x[g];
 }
@@ -631,16 +643,18 @@ __global__ void k_d2f_plain(int64_t n, const double *__restrict__ a, float *__re
     b[g] = (float)a[g];  // set-up only
 }
 
-__global__ void k_minv(int64_t n, const double *__restrict__ mult, float *__restrict__ minv) {
+template <typename T>
+__global__ void k_minv(int64_t n, const double *__restrict__ mult, T *__restrict__ minv) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    minv[g] = (float)(1.0 / mult[g]);
+    minv[g] = (T)(1.0 / mult[g]);
 }
 
 // alternating lattice vector (-1)^(I+J+K) on free nodes
-__global__ void k_alt(int64_t n, int64_t nx, int64_t ny, const uint8_t *__restrict__ mask, float *__restrict__ v) {
+template <typename T>
+__global__ void k_alt(int64_t n, int64_t nx, int64_t ny, const uint8_t *__restrict__ mask, T *__restrict__ v) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t I = g % nx, J = (g / nx) % ny, K = g / (nx * ny);
-    v[g] = (!mask || mask[g]) ? (((I + J + K) & 1) ? -1.0f : 1.0f) : 0.0f;
+    v[g] = (!mask || mask[g]) ? (((I + J + K) & 1) ? T(-1) : T(1)) : T(0);
   }
 }
 
@@ -686,22 +700,24 @@ __global__ void k_post2(int64_t n, float c1, float c2, const float *__restrict__
 }
 
 // y = a x
-__global__ void k_copy_scale_f(int64_t n, float a, const float *__restrict__ x, float *__restrict__ y) {
+template <typename T>
+__global__ void k_copy_scale_f(int64_t n, T a, const T *__restrict__ x, T *__restrict__ y) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     y[g] = a * x[g];
 }
 
 // w = dinv * w (in place), partial sums of w.w and v.v (binary32 per thread,
 // binary64 across threads: an eigenvalue estimate needs no more)
-__global__ void k_power_step(int64_t n, const float *__restrict__ dinv, float *__restrict__ w,
-                             const float *__restrict__ v, double *__restrict__ part) {
+template <typename T>
+__global__ void k_power_step(int64_t n, const T *__restrict__ dinv, T *__restrict__ w, const T *__restrict__ v,
+                             double *__restrict__ part) {
   __shared__ double red[2][32];
-  float wwf = 0.0f, vvf = 0.0f;
+  T wwf = T(0), vvf = T(0);
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    const float x = dinv[g] * w[g];
+    const T x = dinv[g] * w[g];
     w[g] = x;
-    wwf = fmaf(x, x, wwf);
-    vvf = fmaf(v[g], v[g], vvf);
+    wwf = fma(x, x, wwf);
+    vvf = fma(v[g], v[g], vvf);
   }
   double ww = wwf, vv = vvf;
   for (int off = 16; off > 0; off >>= 1) {
@@ -810,17 +826,18 @@ int sum_pairs(const double *dpart, double *a, double *b, cudaStream_t st) {
   return SEM_OK;
 }
 
-int interp_matrix(const sem_mesh *mf, const sem_mesh *mc, float *dJ, cudaStream_t st) {
+template <typename T>
+int interp_matrix(const sem_mesh *mf, const sem_mesh *mc, T *dJ, cudaStream_t st) {
   const int nf = mf->n, nc = mc->n;
-  std::vector<float> J(nf * nc);
+  std::vector<T> J(nf * nc);
   for (int i = 0; i < nf; ++i)
     for (int m = 0; m < nc; ++m) {
       long double v = 1.0L;
       for (int j = 0; j < nc; ++j)
         if (j != m) v *= ((long double)mf->xi[i] - mc->xi[j]) / ((long double)mc->xi[m] - mc->xi[j]);
-      J[i * nc + m] = (float)v;
+      J[i * nc + m] = (T)v;
     }
-  SEM_CUDA(cudaMemcpyAsync(dJ, J.data(), sizeof(float) * nf * nc, cudaMemcpyHostToDevice, st));
+  SEM_CUDA(cudaMemcpyAsync(dJ, J.data(), sizeof(T) * nf * nc, cudaMemcpyHostToDevice, st));
   SEM_CUDA(cudaStreamSynchronize(st));  // J lives on the host stack frame until copied
   return SEM_OK;
 }
@@ -833,7 +850,7 @@ int ax32(sem_pmg *P, int l, float h1s, const float *u, float *w, cudaStream_t st
 int residual(sem_pmg *P, int l, cudaStream_t st) {
   PmgLevel &lv = P->L[l];
   const int64_t n = lv.m->n_unique;
-  k_copy_f<<<grid_for(n, 256), 256, 0, st>>>(n, lv.b, lv.r);
+  k_copy_f<float><<<grid_for(n, 256), 256, 0, st>>>(n, lv.b, lv.r);
   return ax32(P, l, -1.0f, lv.x, lv.r, st);
 }
 
@@ -846,18 +863,18 @@ int smooth(sem_pmg *P, int l, bool zero, cudaStream_t st) {
   const float c0 = 4.0f / (3.0f * lam);
   int rc;
   if (zero) {
-    k_cheb_start<<<g, 256, 0, st>>>(n, lv.b, lv.dinv, c0, lv.x, lv.r, lv.d);
+    k_cheb_start<float><<<g, 256, 0, st>>>(n, lv.b, lv.dinv, c0, lv.x, lv.r, lv.d);
   } else {
     if ((rc = residual(P, l, st))) return rc;
-    k_scaled<<<g, 256, 0, st>>>(n, lv.r, lv.dinv, c0, lv.d);
+    k_scaled<float><<<g, 256, 0, st>>>(n, lv.r, lv.dinv, c0, lv.d);
   }
   for (int i = 1; i < P->o.cheb_degree; ++i) {
     if ((rc = ax32(P, l, -1.0f, lv.d, lv.r, st))) return rc;  // r -= A d
     const float c1 = (float)(2 * i - 1) / (float)(2 * i + 3);
     const float c2 = (float)(8 * i + 4) / ((float)(2 * i + 3) * lam);
-    k_cheb_xd<<<g, 256, 0, st>>>(n, c1, c2, lv.dinv, lv.r, lv.x, lv.d);
+    k_cheb_xd<float><<<g, 256, 0, st>>>(n, c1, c2, lv.dinv, lv.r, lv.x, lv.d);
   }
-  k_axpy_f<<<g, 256, 0, st>>>(n, 1.0f, lv.d, lv.x);
+  k_axpy_f<float><<<g, 256, 0, st>>>(n, 1.0f, lv.d, lv.x);
   SEM_LAUNCH_CHECK("chebyshev");
   return SEM_OK;
 }
@@ -867,7 +884,7 @@ int restrict_to(sem_pmg *P, int l, const float *rf, float *rc, cudaStream_t st) 
   SEM_CUDA(cudaMemsetAsync(rc, 0, sizeof(float) * c.m->n_unique, st));
   const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
   float *wloc = (float *)c.m->det_w;
-  k_restrict<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], f.map, f.minv, rf, c.map, rc,
+  k_restrict<float><<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], f.map, f.minv, rf, c.map, rc,
                                                 wloc);
   SEM_LAUNCH_CHECK("k_restrict");
   if (wloc) return sem_launch_gather_add_f(c.m, wloc, rc, st);
@@ -887,7 +904,7 @@ int prolong_to(sem_pmg *P, int l, const float *uc, float *uf, cudaStream_t st) {
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   SEM_CUDA(cudaMemsetAsync(uf, 0, sizeof(float) * f.m->n_unique, st));
   const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
-  k_prolong<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, uf, 0,
+  k_prolong<float><<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, uf, 0,
                                               owner_of(f.m), nullptr, nullptr);
   SEM_LAUNCH_CHECK("k_prolong");
   return SEM_OK;
@@ -897,7 +914,7 @@ int prolong_to(sem_pmg *P, int l, const float *uc, float *uf, cudaStream_t st) {
 int prolong_add(sem_pmg *P, int l, const float *uc, float *x, const float *b, float *r, cudaStream_t st) {
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
-  k_prolong<<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, x, 1,
+  k_prolong<float><<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, x, 1,
                                               owner_of(f.m), b, r);
   SEM_LAUNCH_CHECK("k_prolong (accumulate)");
   return SEM_OK;
@@ -976,7 +993,7 @@ int vcycle(sem_pmg *P, int l, cudaStream_t st) {
   if ((rc = restrict_to(P, l, lv.r, P->L[l + 1].b, st))) return rc;
   if ((rc = vcycle(P, l + 1, st))) return rc;
   if ((rc = prolong_to(P, l, P->L[l + 1].x, lv.t, st))) return rc;
-  k_axpy_f<<<grid_for(n, 256), 256, 0, st>>>(n, 1.0f, lv.t, lv.x);
+  k_axpy_f<float><<<grid_for(n, 256), 256, 0, st>>>(n, 1.0f, lv.t, lv.x);
   return smooth(P, l, false, st);
 }
 
@@ -1002,10 +1019,134 @@ int vcycle2(sem_pmg *P, int l, cudaStream_t st, const double *in64, double *out6
   if ((rc = vcycle2(P, l + 1, st, nullptr, nullptr))) return rc;
   if ((rc = prolong_add(P, l, P->L[l + 1].x, lv.x, lv.b, lv.r, st))) return rc;  // x += P xc, r = b
   if ((rc = ax32(P, l, -1.0f, lv.x, lv.r, st))) return rc;                       // r = b - A x
-  k_scaled<<<g, 256, 0, st>>>(n, lv.r, lv.dinv, c0, lv.d);
+  k_scaled<float><<<g, 256, 0, st>>>(n, lv.r, lv.dinv, c0, lv.d);
   if ((rc = ax32(P, l, -1.0f, lv.d, lv.r, st))) return rc;  // r -= A d
   k_post2<<<g, 256, 0, st>>>(n, c1, c2, lv.dinv, lv.r, lv.d, lv.x, out64);
   SEM_LAUNCH_CHECK("post-smoothing");
+  return SEM_OK;
+}
+
+// ---------------------------------------------------------------- binary64-accurate smoothing
+// The same V-cycle with every smoothing level in binary64 vectors and the
+// double-float operator (SEM_PREC_DF64): the reference against which the
+// binary32 / bfloat16 smoothing shows what the lower precision costs.
+// w += h1s (h1 A + h2 B) u on level l
+int ax64(sem_pmg *P, int l, double h1s, const double *u, double *w, cudaStream_t st) {
+  PmgLevel &lv = P->L[l];
+  return sem_launch_ax_assembled(lv.m, h1s * P->h1, h1s * P->h2, u, w, nullptr, SEM_PREC_DF64, st, lv.map);
+}
+
+int residual64(sem_pmg *P, int l, cudaStream_t st) {
+  PmgLevel &lv = P->L[l];
+  const int64_t n = lv.m->n_unique;
+  k_copy_f<double><<<grid_for(n, 256), 256, 0, st>>>(n, lv.b64, lv.r64);
+  return ax64(P, l, -1.0, lv.x64, lv.r64, st);
+}
+
+int smooth64(sem_pmg *P, int l, bool zero, cudaStream_t st) {
+  PmgLevel &lv = P->L[l];
+  const int64_t n = lv.m->n_unique;
+  const unsigned g = grid_for(n, 256);
+  const double lam = lv.lam64;
+  const double c0 = 4.0 / (3.0 * lam);
+  int rc;
+  if (zero) {
+    k_cheb_start<double><<<g, 256, 0, st>>>(n, lv.b64, lv.dinv64, c0, lv.x64, lv.r64, lv.d64);
+  } else {
+    if ((rc = residual64(P, l, st))) return rc;
+    k_scaled<double><<<g, 256, 0, st>>>(n, lv.r64, lv.dinv64, c0, lv.d64);
+  }
+  for (int i = 1; i < P->o.cheb_degree; ++i) {
+    if ((rc = ax64(P, l, -1.0, lv.d64, lv.r64, st))) return rc;  // r -= A d
+    const double c1 = (double)(2 * i - 1) / (double)(2 * i + 3);
+    const double c2 = (double)(8 * i + 4) / ((double)(2 * i + 3) * lam);
+    k_cheb_xd<double><<<g, 256, 0, st>>>(n, c1, c2, lv.dinv64, lv.r64, lv.x64, lv.d64);
+  }
+  k_axpy_f<double><<<g, 256, 0, st>>>(n, 1.0, lv.d64, lv.x64);
+  SEM_LAUNCH_CHECK("chebyshev (binary64)");
+  return SEM_OK;
+}
+
+int restrict64(sem_pmg *P, int l, const double *rf, double *rc, cudaStream_t st) {
+  PmgLevel &f = P->L[l], &c = P->L[l + 1];
+  SEM_CUDA(cudaMemsetAsync(rc, 0, sizeof(double) * c.m->n_unique, st));
+  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
+  double *wloc = (double *)c.m->det_w;
+  k_restrict<double><<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J64[l], f.map, f.minv64, rf,
+                                                        c.map, rc, wloc);
+  SEM_LAUNCH_CHECK("k_restrict (binary64)");
+  if (wloc) return sem_launch_gather_add(c.m, wloc, rc, st);
+  return SEM_OK;
+}
+
+int prolong64(sem_pmg *P, int l, const double *uc, double *uf, cudaStream_t st) {
+  PmgLevel &f = P->L[l], &c = P->L[l + 1];
+  SEM_CUDA(cudaMemsetAsync(uf, 0, sizeof(double) * f.m->n_unique, st));
+  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
+  k_prolong<double><<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J64[l], c.map, uc, f.map, uf, 0,
+                                                       owner_of(f.m), nullptr, nullptr);
+  SEM_LAUNCH_CHECK("k_prolong (binary64)");
+  return SEM_OK;
+}
+
+// the coarsest level reads P->cb and writes P->cx directly (its b64 / x64)
+int coarse_solve64(sem_pmg *P, cudaStream_t st) {
+  PmgLevel &lv = P->L.back();
+  const int64_t n = lv.m->n_unique;
+  if (P->o.mask_mode)
+    if (int rc = remove_mean_d(P, P->cb, n, st)) return rc;
+  int rc;
+  if (P->cdinv) {
+    rc = sem_pcg_n1_persistent(lv.m, P->h1, P->h2, P->cb, P->cx, P->cdinv, lv.map, P->o.coarse_tol,
+                               P->o.coarse_maxit, P->cws, nullptr, nullptr, st);
+  } else {
+    sem_solver_opts o;
+    o.tol = P->o.coarse_tol;
+    o.maxit = P->o.coarse_maxit;
+    o.precision = SEM_PREC_DF64;
+    o.timeout_s = 0.0;
+    o.mask_mode = P->o.mask_mode;
+    sem_solve_stats stt;
+    rc = sem_pcg_solve_ex(lv.m, P->h1, P->h2, P->cb, P->cx, &o, P->cws, &stt, (void *)st, 8);
+  }
+  return (rc && rc != SEM_ERR_NOT_CONVERGED) ? rc : SEM_OK;
+}
+
+int vcycle64(sem_pmg *P, int l, cudaStream_t st) {
+  if (l == (int)P->L.size() - 1) return coarse_solve64(P, st);
+  int rc;
+  PmgLevel &lv = P->L[l];
+  const int64_t n = lv.m->n_unique;
+  if ((rc = smooth64(P, l, true, st))) return rc;
+  if ((rc = residual64(P, l, st))) return rc;
+  if ((rc = restrict64(P, l, lv.r64, P->L[l + 1].b64, st))) return rc;
+  if ((rc = vcycle64(P, l + 1, st))) return rc;
+  if ((rc = prolong64(P, l, P->L[l + 1].x64, lv.t64, st))) return rc;
+  k_axpy_f<double><<<grid_for(n, 256), 256, 0, st>>>(n, 1.0, lv.t64, lv.x64);
+  return smooth64(P, l, false, st);
+}
+
+int power_lambda64(sem_pmg *P, int l, cudaStream_t st) {
+  PmgLevel &lv = P->L[l];
+  const sem_mesh *m = lv.m;
+  const int64_t n = m->n_unique;
+  const int64_t nx = (int64_t)m->nel[0] * m->N + (m->periodic[0] ? 0 : 1);
+  const int64_t ny = (int64_t)m->nel[1] * m->N + (m->periodic[1] ? 0 : 1);
+  k_alt<double><<<grid_for(n, 256), 256, 0, st>>>(n, nx, ny, P->o.mask_mode ? nullptr : m->mask, lv.x64);
+  double lam = 0.0;
+  for (int it = 0; it < P->o.power_its; ++it) {
+    SEM_CUDA(cudaMemsetAsync(lv.t64, 0, sizeof(double) * n, st));
+    if (int rc = ax64(P, l, 1.0, lv.x64, lv.t64, st)) return rc;
+    k_power_step<double><<<kPart, 256, 0, st>>>(n, lv.dinv64, lv.t64, lv.x64, P->part);
+    SEM_LAUNCH_CHECK("power iteration (binary64)");
+    double ww, vv;
+    if (int rc = sum_pairs(P->part, &ww, &vv, st)) return rc;
+    if (!(ww > 0.0) || !(vv > 0.0)) return sem_fail(SEM_ERR_BREAKDOWN, "pmg: power iteration degenerated");
+    lam = sqrt(ww / vv);
+    k_copy_scale_f<double><<<grid_for(n, 256), 256, 0, st>>>(n, 1.0 / sqrt(ww), lv.t64, lv.x64);
+  }
+  lv.lam64 = P->o.lambda_safety * lam;
+  lv.lam = (float)lv.lam64;
   return SEM_OK;
 }
 
@@ -1015,18 +1156,18 @@ int power_lambda(sem_pmg *P, int l, cudaStream_t st) {
   const int64_t n = m->n_unique;
   const int64_t nx = (int64_t)m->nel[0] * m->N + (m->periodic[0] ? 0 : 1);
   const int64_t ny = (int64_t)m->nel[1] * m->N + (m->periodic[1] ? 0 : 1);
-  k_alt<<<grid_for(n, 256), 256, 0, st>>>(n, nx, ny, P->o.mask_mode ? nullptr : m->mask, lv.x);
+  k_alt<float><<<grid_for(n, 256), 256, 0, st>>>(n, nx, ny, P->o.mask_mode ? nullptr : m->mask, lv.x);
   double lam = 0.0;
   for (int it = 0; it < P->o.power_its; ++it) {
     SEM_CUDA(cudaMemsetAsync(lv.t, 0, sizeof(float) * n, st));
     if (int rc = ax32(P, l, 1.0f, lv.x, lv.t, st)) return rc;
-    k_power_step<<<kPart, 256, 0, st>>>(n, lv.dinv, lv.t, lv.x, P->part);
+    k_power_step<float><<<kPart, 256, 0, st>>>(n, lv.dinv, lv.t, lv.x, P->part);
     SEM_LAUNCH_CHECK("power iteration");
     double ww, vv;
     if (int rc = sum_pairs(P->part, &ww, &vv, st)) return rc;
     if (!(ww > 0.0) || !(vv > 0.0)) return sem_fail(SEM_ERR_BREAKDOWN, "pmg: power iteration degenerated");
     lam = sqrt(ww / vv);
-    k_copy_scale_f<<<grid_for(n, 256), 256, 0, st>>>(n, (float)(1.0 / sqrt(ww)), lv.t, lv.x);
+    k_copy_scale_f<float><<<grid_for(n, 256), 256, 0, st>>>(n, (float)(1.0 / sqrt(ww)), lv.t, lv.x);
   }
   lv.lam = (float)(P->o.lambda_safety * lam);
   return SEM_OK;
@@ -1066,8 +1207,10 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
   for (int l = 1; l < o->nlevels; ++l)
     if (o->orders[l] < 1 || o->orders[l] >= o->orders[l - 1])
       return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: orders must decrease strictly and stay >= 1");
-  if (o->smoother_precision != SEM_PREC_FP32 && o->smoother_precision != SEM_PREC_BF16)
-    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: smoother precision must be FP32 or BF16");
+  if (o->smoother_precision != SEM_PREC_FP32 && o->smoother_precision != SEM_PREC_BF16 &&
+      o->smoother_precision != SEM_PREC_DF64)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: smoother precision must be FP32, BF16 or DF64");
+  const bool p64 = o->smoother_precision == SEM_PREC_DF64;
   if (o->mask_mode != 0 && o->mask_mode != 1) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_create: bad mask_mode");
   if (o->cheb_degree < 1 || !(o->lambda_safety >= 1.0) || o->power_its < 1 || !(o->coarse_tol > 0) ||
       o->coarse_maxit < 1 || !(h1 > 0) || !(h2 >= 0))
@@ -1102,6 +1245,13 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
     lv.map = o->mask_mode ? lv.m->l2g : lv.m->l2gm;
     const int64_t nL = lv.m->n_local, nU = lv.m->n_unique;
     const bool coarsest = l == o->nlevels - 1;
+    if (p64) {  // binary64 level vectors; the coarsest level's are the coarse solve's (set below)
+      if (!coarsest) {
+        double **v64[] = {&lv.b64, &lv.x64, &lv.r64, &lv.d64, &lv.t64, &lv.dinv64, &lv.minv64};
+        for (double **v : v64) rc = rc ? rc : alloc((void **)v, sizeof(double) * nU);
+      }
+      continue;
+    }
     if (!coarsest) {
       if (o->smoother_precision == SEM_PREC_BF16) rc = rc ? rc : alloc((void **)&lv.Gb, sizeof(__nv_bfloat16) * 6 * nL);
       else rc = rc ? rc : alloc((void **)&lv.Gf, sizeof(float) * 6 * nL);
@@ -1124,14 +1274,22 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
   }
   cudaMemsetAsync(P->err, 0, sizeof(int), st);
   for (int l = 0; l + 1 < o->nlevels; ++l) P->L[l].err = P->err;
+  // per-level binary64 data (binary64-accurate smoothing)
+  for (int l = 0; p64 && l + 1 < o->nlevels && !rc; ++l) {
+    PmgLevel &lv = P->L[l];
+    const sem_mesh *lm = lv.m;
+    k_minv<double><<<grid_for(lm->n_unique, 256), 256, 0, st>>>(lm->n_unique, lm->mult, lv.minv64);
+    rc = sem_jacobi_inv_mode(lm, h1, h2, o->mask_mode ? 0 : 1, lv.dinv64, st);
+    if (!rc) rc = power_lambda64(P, l, st);
+  }
   // per-level binary32 data
-  for (int l = 0; l + 1 < o->nlevels && !rc; ++l) {
+  for (int l = 0; !p64 && l + 1 < o->nlevels && !rc; ++l) {
     PmgLevel &lv = P->L[l];
     const sem_mesh *lm = lv.m;
     k_g_to_f32<<<grid_for(6 * lm->n_local, 256), 256, 0, st>>>(6 * lm->n_local, lm->G, lv.Gf, lv.Gb);
     k_d2f_plain<<<grid_for(lm->n_local, 256), 256, 0, st>>>(lm->n_local, lm->B, lv.Bf);
     k_d2f_plain<<<1, 128, 0, st>>>(lm->n * lm->n, lm->dD, lv.Df);
-    k_minv<<<grid_for(lm->n_unique, 256), 256, 0, st>>>(lm->n_unique, lm->mult, lv.minv);
+    k_minv<float><<<grid_for(lm->n_unique, 256), 256, 0, st>>>(lm->n_unique, lm->mult, lv.minv);
     // Jacobi diagonal (binary64) -> binary32
     double *dd = nullptr;
     if (cudaMalloc(&dd, sizeof(double) * lm->n_unique) != cudaSuccess) {
@@ -1146,7 +1304,9 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
   }
   for (int l = 0; l + 1 < o->nlevels && !rc; ++l) {
     rc = alloc((void **)&P->J[l], sizeof(float) * P->L[l].m->n * P->L[l + 1].m->n);
-    if (!rc) rc = interp_matrix(P->L[l].m, P->L[l + 1].m, P->J[l], st);
+    if (!rc) rc = interp_matrix<float>(P->L[l].m, P->L[l + 1].m, P->J[l], st);
+    if (!rc) rc = alloc((void **)&P->J64[l], sizeof(double) * P->L[l].m->n * P->L[l + 1].m->n);
+    if (!rc) rc = interp_matrix<double>(P->L[l].m, P->L[l + 1].m, P->J64[l], st);
   }
   // coarsest level binary64 vectors and solver workspace
   const sem_mesh *cm = P->L.back().m;
@@ -1154,6 +1314,10 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
   if (!rc) rc = sem_pcg_workspace_bytes(cm, &cwb);
   if (!rc) rc = alloc((void **)&P->cb, sizeof(double) * cm->n_unique);
   if (!rc) rc = alloc((void **)&P->cx, sizeof(double) * cm->n_unique);
+  if (!rc && p64) {
+    P->L.back().b64 = P->cb;
+    P->L.back().x64 = P->cx;
+  }
   const bool persistent = cm->K1 && !cm->det_w;  // atomic assembly only: deterministic mode keeps its order
   if (persistent) cwb = std::max(cwb, sem_pcg_n1_workspace_bytes(cm));
   if (!rc) rc = alloc(&P->cws, cwb);
@@ -1190,7 +1354,7 @@ extern "C" int sem_pmg_destroy(sem_pmg *P) {
 extern "C" int sem_pmg_lambda(const sem_pmg *P, int level, double *lambda) {
   if (!P || !lambda || level < 0 || level + 1 >= (int)P->L.size())
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_lambda: bad argument (smoothing levels only)");
-  *lambda = P->L[level].lam;
+  *lambda = P->o.smoother_precision == SEM_PREC_DF64 ? P->L[level].lam64 : (double)P->L[level].lam;
   return SEM_OK;
 }
 
@@ -1200,6 +1364,16 @@ extern "C" int sem_pmg_vcycle(sem_pmg *P, const double *r_g, double *z_g, void *
   cudaStream_t st = as_stream(stream);
   PmgLevel &lv = P->L[0];
   const int64_t n = lv.m->n_unique;
+  if (P->o.smoother_precision == SEM_PREC_DF64) {  // binary64 levels: the fine level reads r_g, writes z_g
+    double *sb = lv.b64, *sx = lv.x64;
+    lv.b64 = const_cast<double *>(r_g);
+    lv.x64 = z_g;
+    const int rc = vcycle64(P, 0, st);
+    lv.b64 = sb;
+    lv.x64 = sx;
+    if (rc) return rc;
+    return check_err(P, st);
+  }
   if (P->o.cheb_degree == 2) {
     if (int rc = vcycle2(P, 0, st, r_g, z_g)) return rc;
     return check_err(P, st);
@@ -1215,6 +1389,7 @@ extern "C" int sem_pmg_prolong(sem_pmg *P, int level, const double *uc_g, double
   if (!P || !uc_g || !uf_g || level < 0 || level + 1 >= (int)P->L.size())
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_prolong: bad argument");
   cudaStream_t st = as_stream(stream);
+  if (P->o.smoother_precision == SEM_PREC_DF64) return prolong64(P, level, uc_g, uf_g, st);
   PmgLevel &f = P->L[level], &c = P->L[level + 1];
   k_d2f<<<grid_for(c.m->n_unique, 256), 256, 0, st>>>(c.m->n_unique, uc_g, c.b);
   if (int rc = prolong_to(P, level, c.b, f.b, st)) return rc;
@@ -1227,6 +1402,7 @@ extern "C" int sem_pmg_restrict(sem_pmg *P, int level, const double *rf_g, doubl
   if (!P || !rf_g || !rc_g || level < 0 || level + 1 >= (int)P->L.size())
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_restrict: bad argument");
   cudaStream_t st = as_stream(stream);
+  if (P->o.smoother_precision == SEM_PREC_DF64) return restrict64(P, level, rf_g, rc_g, st);
   PmgLevel &f = P->L[level], &c = P->L[level + 1];
   k_d2f<<<grid_for(f.m->n_unique, 256), 256, 0, st>>>(f.m->n_unique, rf_g, f.b);
   if (int rc = restrict_to(P, level, f.b, c.b, st)) return rc;
