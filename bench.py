@@ -471,6 +471,7 @@ def main():
                 ("jacobi_df64", "jacobi", sem.SEM_PREC_DF64, None),
                 ("pmg_fp32_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_FP32),
                 ("pmg_bf16_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_BF16),
+                ("pmg_df64_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_DF64),
                 ("pmg_fp32_df64_cheb3", "pmg3", sem.SEM_PREC_DF64, sem.SEM_PREC_FP32)]
         if args.quick_pcg:
             runs = [r for r in runs if r[0] != "jacobi_fp64"]
@@ -484,6 +485,7 @@ def main():
         pcg48 = run_solves(sem, m48, w48, [("jacobi_df64", "jacobi", sem.SEM_PREC_DF64, None),
                                            ("pmg_fp32_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_FP32),
                                            ("pmg_bf16_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_BF16),
+                                           ("pmg_df64_df64", "pmg", sem.SEM_PREC_DF64, sem.SEM_PREC_DF64),
                                            ("pmg_fp32_df64_cheb3", "pmg3", sem.SEM_PREC_DF64, sem.SEM_PREC_FP32)],
                            args.pcg_tol)
         pcg48["workload"] = w48.name

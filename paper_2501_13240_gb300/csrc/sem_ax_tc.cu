@@ -135,23 +135,8 @@ __device__ __forceinline__ void mma16(float &d0, float &d1, float &d2, float &d3
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(c0), "f"(c1), "f"(c2), "f"(c3));
 }
 
-__device__ __forceinline__ uint32_t movtrans(uint32_t a) {
-  uint32_t d;
-  asm("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(d) : "r"(a));
-  return d;
-}
 
-// four 8x8 b16 matrices, transposed; row addresses from lanes 8i..8i+7
-__device__ __forceinline__ void ldsm4t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr)
-               : "memory");
-}
 
-__device__ __forceinline__ void ldsm1t(uint32_t addr, uint32_t &r0) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x1.trans.shared.b16 {%0}, [%1];" : "=r"(r0) : "r"(addr) : "memory");
-}
 
 __device__ __forceinline__ uint32_t pack_f16(float2 v) {
   const __half2 h = __floats2half2_rn(v.x, v.y);
@@ -219,69 +204,78 @@ __device__ __forceinline__ void recombine(float2 L0, float2 L1, float2 L2, float
   Lo = mul2(T, dup(sc));
 }
 
-// 15 digit products, D as the A operand: rows 0..7 and 8..15 of A are two
-// levels, B = (digits j of k 0..7 | digits j' of k 8..15); acc[L] = the
-// output pair of level L held by this thread. The first product into each
-// level starts from zero; the last MMA's second row block is all zero.
-__device__ __forceinline__ void contract_da(const uint32_t (&Dg)[NSL], const uint32_t (&b)[NSL], float2 (&acc)[NSL]) {
-  const uint32_t Z = 0u;
-  // L1 | L3
-  mma16(acc[1].x, acc[1].y, acc[3].x, acc[3].y, Dg[0], Dg[2], Dg[1], Dg[3], b[1], b[0], 0.f, 0.f, 0.f, 0.f);
-  // L2 | L4
-  mma16(acc[2].x, acc[2].y, acc[4].x, acc[4].y, Dg[0], Dg[2], Dg[1], Dg[3], b[2], b[1], 0.f, 0.f, 0.f, 0.f);
-  // L3: D0 u3 + D1 u2 | L4: D1 u3
-  mma16(acc[3].x, acc[3].y, acc[4].x, acc[4].y, Dg[0], Dg[1], Dg[1], Z, b[3], b[2], acc[3].x, acc[3].y, acc[4].x,
-        acc[4].y);
-  // L4: D0 u4 + D4 u0 | L2: D2 u0
-  mma16(acc[4].x, acc[4].y, acc[2].x, acc[2].y, Dg[0], Z, Dg[4], Dg[2], b[4], b[0], acc[4].x, acc[4].y, acc[2].x,
-        acc[2].y);
-  // L0: D0 u0 | (zero rows, into a scratch pair)
-  float s0, s1;
-  mma16(acc[0].x, acc[0].y, s0, s1, Dg[0], Z, Z, Z, b[0], b[0], 0.f, 0.f, 0.f, 0.f);
+// ---------------------------------------------------------------- one 1-D contraction group
+// D (or D^T) digits as the A operand in two fixed register quads:
+//   QA = (D0 | D1 over k; D2 | D3 over k)  rows 0..7 / 8..15 = levels i, i + 2
+//   QB = (D0 | D4;        D2 | 0)
+// and the digits of 8 lines as B from shared memory, in three quads loaded
+// by ldmatrix straight into the registers the MMAs read:
+//   E = (u1, u0, u3, u2), O = (u2, u1, u4, u3), Zq = (u0, 0, 0, u0)
+// Six MMAs, each into its own accumulator quad (no operand is ever moved):
+//   QA x (u1;u0) -> (L1 | L3)   QA x (u2;u1) -> (L2 | L4)   QA x (u3;u2) -> (L3 | -)
+//   QA x (u4;u3) -> (L4 | -)    QB x (u0;0)  -> (L0 | L2)   QB x (0;u0)  -> (L4 | -)
+// ("-": products of levels 5, 6, not used). The level pairs are summed with
+// exact binary32 additions (every partial sum is part of a level sum below
+// 2^23.4). Returns the output pair (output index g, lines 2q, 2q+1).
+__device__ __forceinline__ void contract(const uint4 &QA, const uint4 &QB, const uint4 &E, const uint4 &O,
+                                         const uint4 &Zq, float sc, float2 &H, float2 &Lo) {
+  float4 q1, q2, q3, q4, q5, q6;
+  mma16(q1.x, q1.y, q1.z, q1.w, QA.x, QA.y, QA.z, QA.w, E.x, E.y, 0.f, 0.f, 0.f, 0.f);
+  mma16(q2.x, q2.y, q2.z, q2.w, QA.x, QA.y, QA.z, QA.w, O.x, O.y, 0.f, 0.f, 0.f, 0.f);
+  mma16(q3.x, q3.y, q3.z, q3.w, QA.x, QA.y, QA.z, QA.w, E.z, E.w, 0.f, 0.f, 0.f, 0.f);
+  mma16(q4.x, q4.y, q4.z, q4.w, QA.x, QA.y, QA.z, QA.w, O.z, O.w, 0.f, 0.f, 0.f, 0.f);
+  mma16(q5.x, q5.y, q5.z, q5.w, QB.x, QB.y, QB.z, QB.w, Zq.x, Zq.y, 0.f, 0.f, 0.f, 0.f);
+  mma16(q6.x, q6.y, q6.z, q6.w, QB.x, QB.y, QB.z, QB.w, Zq.z, Zq.w, 0.f, 0.f, 0.f, 0.f);
+  const float2 L0 = make_float2(q5.x, q5.y), L1 = make_float2(q1.x, q1.y);
+  const float2 L2 = add2(make_float2(q2.x, q2.y), make_float2(q5.z, q5.w));
+  const float2 L3 = add2(make_float2(q1.z, q1.w), make_float2(q3.x, q3.y));
+  const float2 L4 = add2(add2(make_float2(q2.z, q2.w), make_float2(q4.x, q4.y)), make_float2(q6.x, q6.y));
+  recombine(L0, L1, L2, L3, L4, sc, H, Lo);
 }
 
-// the same, accumulating into acc (no zero start)
-__device__ __forceinline__ void contract_da_acc(const uint32_t (&Dg)[NSL], const uint32_t (&b)[NSL],
-                                                float2 (&acc)[NSL]) {
-  const uint32_t Z = 0u;
-  mma16(acc[1].x, acc[1].y, acc[3].x, acc[3].y, Dg[0], Dg[2], Dg[1], Dg[3], b[1], b[0], acc[1].x, acc[1].y, acc[3].x,
-        acc[3].y);
-  mma16(acc[2].x, acc[2].y, acc[4].x, acc[4].y, Dg[0], Dg[2], Dg[1], Dg[3], b[2], b[1], acc[2].x, acc[2].y, acc[4].x,
-        acc[4].y);
-  mma16(acc[3].x, acc[3].y, acc[4].x, acc[4].y, Dg[0], Dg[1], Dg[1], Z, b[3], b[2], acc[3].x, acc[3].y, acc[4].x,
-        acc[4].y);
-  mma16(acc[4].x, acc[4].y, acc[2].x, acc[2].y, Dg[0], Z, Dg[4], Dg[2], b[4], b[0], acc[4].x, acc[4].y, acc[2].x,
-        acc[2].y);
-  float s0, s1;
-  mma16(acc[0].x, acc[0].y, s0, s1, Dg[0], Z, Z, Z, b[0], b[0], acc[0].x, acc[0].y, 0.f, 0.f);
-}
-
-// 15 digit products, the digits as the A operand: rows 0..7 plane a, rows
-// 8..15 plane b (a[j], c[j]), B = D's digits; acc[L] / bcc[L] = the output
-// pairs of level L on planes a / b. ZERO: start each level from zero.
-template <bool ZERO>
-__device__ __forceinline__ void contract_ua(const uint32_t (&a)[NSL], const uint32_t (&c)[NSL],
-                                            const uint32_t (&Dg)[NSL], float2 (&acc)[NSL], float2 (&bcc)[NSL]) {
-  const uint32_t Z = 0u;
-#define MMA_UA(L, FIRST, A0, A1, A2, A3, B0, B1)                                                           \
-  mma16(acc[L].x, acc[L].y, bcc[L].x, bcc[L].y, A0, A1, A2, A3, B0, B1, (ZERO && FIRST) ? 0.f : acc[L].x, \
-        (ZERO && FIRST) ? 0.f : acc[L].y, (ZERO && FIRST) ? 0.f : bcc[L].x, (ZERO && FIRST) ? 0.f : bcc[L].y)
-  MMA_UA(0, true, a[0], c[0], Z, Z, Dg[0], Z);           // D0 u0
-  MMA_UA(1, true, a[1], c[1], a[0], c[0], Dg[0], Dg[1]);  // D0 u1 + D1 u0
-  MMA_UA(2, true, a[2], c[2], a[1], c[1], Dg[0], Dg[1]);  // D0 u2 + D1 u1
-  MMA_UA(2, false, a[0], c[0], Z, Z, Dg[2], Z);          // D2 u0
-  MMA_UA(3, true, a[3], c[3], a[2], c[2], Dg[0], Dg[1]);  // D0 u3 + D1 u2
-  MMA_UA(3, false, a[1], c[1], a[0], c[0], Dg[2], Dg[3]); // D2 u1 + D3 u0
-  MMA_UA(4, true, a[4], c[4], a[3], c[3], Dg[0], Dg[1]);  // D0 u4 + D1 u3
-  MMA_UA(4, false, a[2], c[2], a[1], c[1], Dg[2], Dg[3]); // D2 u2 + D3 u1
-  MMA_UA(4, false, a[0], c[0], Z, Z, Dg[4], Z);          // D4 u0
-#undef MMA_UA
-}
-
-// shared-memory digit planes: slice j, plane t, row s holds the 8 r-values
-// (16 bytes) at chunk (j 8 + t) 8 + (s ^ t) (the xor spreads the rows of a
-// fixed-s matrix over all bank groups)
+// shared-memory digit planes of one field: slice j, plane t, row s holds the
+// 8 r-values (16 bytes) at chunk (j 8 + t) 8 + (s ^ t) (the xor spreads the
+// rows of every matrix an ldmatrix reads over all bank groups)
 __device__ __forceinline__ int dig_word(int j, int t, int s, int q) { return (((j * 8 + t) * 8 + (s ^ t)) << 2) + q; }
+constexpr int kDigWords = NSL * 256;  // one field's digit planes (5 KB)
+
+__device__ __forceinline__ void ldsm4(uint32_t addr, uint4 &r) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "r"(addr)
+               : "memory");
+}
+__device__ __forceinline__ void ldsm4t(uint32_t addr, uint4 &r) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "r"(addr)
+               : "memory");
+}
+
+// B quads of one group. dir 0 (r): lines s, k = r at plane c (plain
+// ldmatrix: the stored rows are the lines); dir 1 (s): k = s, lines r at
+// plane c (transposed); dir 2 (t): k = t, lines r at row s = c (transposed).
+// Lane L gives the address of row L & 7 of matrix L >> 3; the slice of each
+// matrix is (1, 0, 3, 2), (2, 1, 4, 3), (0, Z, Z, 0) for E, O, Zq.
+__device__ __forceinline__ void load_group(uint32_t dig, uint32_t zero, int dir, int c, int lane, uint4 &E, uint4 &O,
+                                           uint4 &Zq) {
+  const int row = lane & 7, mat = lane >> 3;
+  const int t = dir == 2 ? row : c, s = dir == 2 ? c : row;
+  const int je = mat ^ 1;                    // 1, 0, 3, 2
+  const int jo = (mat & 1) ? mat : mat + 2;  // 2, 1, 4, 3
+  const uint32_t ae = dig + 4u * (uint32_t)dig_word(je, t, s, 0);
+  const uint32_t ao = dig + 4u * (uint32_t)dig_word(jo, t, s, 0);
+  const uint32_t az = (mat == 0 || mat == 3) ? dig + 4u * (uint32_t)dig_word(0, t, s, 0) : zero + 16u * (uint32_t)row;
+  if (dir == 0) {
+    ldsm4(ae, E);
+    ldsm4(ao, O);
+    ldsm4(az, Zq);
+  } else {
+    ldsm4t(ae, E);
+    ldsm4t(ao, O);
+    ldsm4t(az, Zq);
+  }
+}
 
 __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -320,7 +314,8 @@ __device__ __forceinline__ void load_u(const double *__restrict__ u, int2 gi, in
   }
 }
 
-// a point pair's double-float values in shared memory: (hi pair, lo pair)
+// double-float values in shared memory: a point pair (p even, p + 1) is
+// (h_p, h_p+1, l_p, l_p+1); single points are written into their slots
 __device__ __forceinline__ void st_pair(float2 *base, int p, float2 h, float2 l) {
   *reinterpret_cast<float4 *>(base + p) = make_float4(h.x, h.y, l.x, l.y);
 }
@@ -328,6 +323,39 @@ __device__ __forceinline__ void ld_pair(const float2 *base, int p, float2 &h, fl
   const float4 v = *reinterpret_cast<const float4 *>(base + p);
   h = make_float2(v.x, v.y);
   l = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void st_one(float2 *base, int p, float h, float l) {
+  float *f = reinterpret_cast<float *>(base + (p & ~1));
+  f[p & 1] = h;
+  f[2 + (p & 1)] = l;
+}
+
+// The 24 line groups of one pass (3 directions x 8), 12 per warp: warp 0
+// takes r at planes 0..7 and s at planes 0..3, warp 1 s at planes 4..7 and
+// t at rows 0..7. The outputs go to the direction's tile: r as single points
+// (its pair runs along s), s and t as point pairs along r.
+__device__ __forceinline__ void contract_pass(uint32_t dig0, uint32_t zero, bool per_dir_fields, const uint4 &QA,
+                                              const uint4 &QB, float sc, int wp, int lane, float2 *oR, float2 *oS,
+                                              float2 *oT) {
+  const int g = lane >> 2, q = lane & 3;
+#pragma unroll 1
+  for (int k = 0; k < 12; ++k) {
+    const int grp = 12 * wp + k;
+    const int dir = grp >> 3, c = grp & 7;
+    const uint32_t dig = per_dir_fields ? dig0 + 4u * (uint32_t)(dir * kDigWords) : dig0;
+    uint4 E, O, Zq;
+    load_group(dig, zero, dir, c, lane, E, O, Zq);
+    float2 H, L;
+    contract(QA, QB, E, O, Zq, sc, H, L);
+    if (dir == 0) {  // (r_out = g, s = 2q, 2q + 1) at plane c
+      st_one(oR, g + 8 * (2 * q) + 64 * c, H.x, L.x);
+      st_one(oR, g + 8 * (2 * q + 1) + 64 * c, H.y, L.y);
+    } else if (dir == 1) {  // (s_out = g, r = 2q, 2q + 1) at plane c
+      st_pair(oS, 2 * q + 8 * g + 64 * c, H, L);
+    } else {  // (t_out = g, r = 2q, 2q + 1) at row s = c
+      st_pair(oT, 2 * q + 8 * c + 64 * g, H, L);
+    }
+  }
 }
 
 template <bool ASSEMBLED, bool HELM>
@@ -337,30 +365,29 @@ __global__ void __launch_bounds__(64, kMinBlocks)
             double *__restrict__ pw_partial, double *__restrict__ wloc, const int *__restrict__ skip,
             const int32_t *__restrict__ elist) {
   if (skip != nullptr && *skip != 0) return;
-  // double-float values of point pairs, (hi pair, lo pair) at even p
   __shared__ __align__(16) float2 sR[N3];
   __shared__ __align__(16) float2 sS[N3];
   __shared__ __align__(16) float2 sT[N3];
-  __shared__ __align__(16) uint32_t sDig[NSL * 256];
+  __shared__ __align__(16) uint32_t sDig[3 * kDigWords];  // digits of u, then of (wr, ws, wt)
+  __shared__ __align__(16) uint32_t sZero[32];             // an 8x8 zero matrix for ldmatrix
   __shared__ int s_red[4];
   __shared__ double s_pw[2];
   const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
-  uint32_t Fd[NSL], Td[NSL];
-#pragma unroll
-  for (int j = 0; j < NSL; ++j) {
-    Fd[j] = g_dig[0][j][lane];
-    Td[j] = g_dig[1][j][lane];
-  }
-  const uint32_t sdig_base = (uint32_t)__cvta_generic_to_shared(sDig);
-  // ldmatrix row addresses: lane L reads row t = L & 7 of matrix L >> 3
-  const int lrow = lane & 7, lmat = lane >> 3;
+  if (tid < 32) sZero[tid] = 0u;
+  // D's digits as the two A quads, forward (D) and transposed (D^T)
+  const uint4 FA = make_uint4(g_dig[0][0][lane], g_dig[0][2][lane], g_dig[0][1][lane], g_dig[0][3][lane]);
+  const uint4 FB = make_uint4(g_dig[0][0][lane], g_dig[0][2][lane], g_dig[0][4][lane], 0u);
+  const uint4 TA = make_uint4(g_dig[1][0][lane], g_dig[1][2][lane], g_dig[1][1][lane], g_dig[1][3][lane]);
+  const uint4 TB = make_uint4(g_dig[1][0][lane], g_dig[1][2][lane], g_dig[1][4][lane], 0u);
+  const uint32_t sdig = (uint32_t)__cvta_generic_to_shared(sDig);
+  const uint32_t szero = (uint32_t)__cvta_generic_to_shared(sZero);
   const int pbase = 2 * q + 8 * g + 256 * wp;  // the thread's point pair on its first plane (+64 per plane)
   double pw = 0.0;
   constexpr float scD = (float)kDScale * 0x1p-20f;  // weight of level 0
 
   for (int64_t ei = blockIdx.x; ei < E; ei += gridDim.x) {
     const int64_t e = elist ? (int64_t)elist[ei] : ei;  // the element (E: the list's length with a list)
-    // ---------------------------------------------------------------- P0
+    // ---------------------------------------------------------------- P0: gather, scale, digits of x
     if (tid == 0) prefetch_l2(Gdf + e * 6 * N3, 48u * N3);
     int2 gi[4];
     double uv0[4][2];
@@ -376,65 +403,19 @@ __global__ void __launch_bounds__(64, kMinBlocks)
     if (lane == 0) s_red[wp] = em;
     __syncthreads();
     const int su = max(s_red[0], s_red[1]) - 1022;  // |u| 2^-su < 1
-    // digits of the thread's point pairs, one f16x2 word per (slice, plane),
-    // kept in shared memory: the owner reads its own words back per plane
 #pragma unroll
     for (int tt = 0; tt < 4; ++tt) {
       const float2 x0 = df::from_f64_scaled(uv0[tt][0], su), x1 = df::from_f64_scaled(uv0[tt][1], su);
       uint32_t d[NSL];
       digits5(make_float2(x0.x, x1.x), make_float2(x0.y, x1.y), 1024.0f, 1048576.0f, d);
-      const int t = 4 * wp + tt;
 #pragma unroll
-      for (int j = 0; j < NSL; ++j) sDig[dig_word(j, t, g, q)] = d[j];
+      for (int j = 0; j < NSL; ++j) sDig[dig_word(j, 4 * wp + tt, g, q)] = d[j];
     }
     __syncthreads();
-    // ---------------------------------------------------------------- P1
-    // r: digits as A over the plane pairs (4w, 4w+1), (4w+2, 4w+3); ur -> sR,
-    // us -> sS (own points), ut -> sT (points of other threads)
-#pragma unroll 1
-    for (int pp = 0; pp < 2; ++pp) {
-      float2 acc[NSL], bcc[NSL];
-      uint32_t a[NSL], c[NSL];
-      const int ta = 4 * wp + 2 * pp;
-#pragma unroll
-      for (int j = 0; j < NSL; ++j) {
-        a[j] = sDig[dig_word(j, ta, g, q)];
-        c[j] = sDig[dig_word(j, ta + 1, g, q)];
-      }
-      contract_ua<true>(a, c, Fd, acc, bcc);
-      float2 H, L;
-      recombine(acc[0], acc[1], acc[2], acc[3], acc[4], scD, H, L);
-      st_pair(sR, pbase + 128 * pp, H, L);
-      recombine(bcc[0], bcc[1], bcc[2], bcc[3], bcc[4], scD, H, L);
-      st_pair(sR, pbase + 128 * pp + 64, H, L);
-    }
-    // s: D as A per plane, B = the transposed digit matrices
-#pragma unroll 1
-    for (int tt = 0; tt < 4; ++tt) {
-      float2 acc[NSL];
-      uint32_t b[NSL];
-#pragma unroll
-      for (int j = 0; j < NSL; ++j) b[j] = movtrans(sDig[dig_word(j, 4 * wp + tt, g, q)]);
-      contract_da(Fd, b, acc);
-      float2 H, L;
-      recombine(acc[0], acc[1], acc[2], acc[3], acc[4], scD, H, L);
-      st_pair(sS, pbase + 64 * tt, H, L);
-    }
-    // t: D as A per s (this warp: s = 4w..4w+3), B from shared memory
-#pragma unroll 1
-    for (int ss = 0; ss < 4; ++ss) {
-      const int s = 4 * wp + ss;
-      uint32_t b[NSL];
-      ldsm4t(sdig_base + 4u * (uint32_t)dig_word(lmat, lrow, s, 0), b[0], b[1], b[2], b[3]);
-      ldsm1t(sdig_base + 4u * (uint32_t)dig_word(4, lrow, s, 0), b[4]);
-      float2 acc[NSL];
-      contract_da(Fd, b, acc);
-      float2 H, L;  // outputs (t_out = g, r = 2q, 2q+1) at this s
-      recombine(acc[0], acc[1], acc[2], acc[3], acc[4], scD, H, L);
-      st_pair(sT, 2 * q + 8 * s + 64 * g, H, L);
-    }
+    // ---------------------------------------------------------------- P1: ur, us, ut
+    contract_pass(sdig, szero, false, FA, FB, scD, wp, lane, sR, sS, sT);
     __syncthreads();
-    // ---------------------------------------------------------------- P2
+    // ---------------------------------------------------------------- P2: metric
     const float2 *Ge = Gdf + e * 6 * N3;
     int evm = 0;
 #pragma unroll 1
@@ -472,74 +453,42 @@ __global__ void __launch_bounds__(64, kMinBlocks)
     const int sv = max(ev - 126, -100);
     const float s1 = pow2f(10 - sv), c2 = pow2f(20 - sv);
     const float scV = pow2f(sv - 15);  // scD 2^sv
-    // ---------------------------------------------------------------- P3
-    // t first: digits of wt to shared memory (the forward digits are no longer needed)
-#pragma unroll
+    // ---------------------------------------------------------------- P3: transposed contractions
+#pragma unroll 1
     for (int tt = 0; tt < 4; ++tt) {
-      const int t = 4 * wp + tt;
+      const int t = 4 * wp + tt, p = pbase + 64 * tt;
       float2 vh, vl;
-      ld_pair(sT, pbase + 64 * tt, vh, vl);
       uint32_t d[NSL];
+      ld_pair(sR, p, vh, vl);
       digits5(vh, vl, s1, c2, d);
 #pragma unroll
       for (int j = 0; j < NSL; ++j) sDig[dig_word(j, t, g, q)] = d[j];
-    }
-    // r and s into one level set, per plane pair
-#pragma unroll 1
-    for (int pp = 0; pp < 2; ++pp) {
-      float2 acc[NSL], bcc[NSL];
-      uint32_t a[NSL], c[NSL], bs[NSL];
-      float2 vh, vl;
-      const int p0 = pbase + 128 * pp;
-      ld_pair(sR, p0, vh, vl);
-      digits5(vh, vl, s1, c2, a);
-      ld_pair(sR, p0 + 64, vh, vl);
-      digits5(vh, vl, s1, c2, c);
-      contract_ua<true>(a, c, Td, acc, bcc);
-      // s: D^T as A, one plane at a time, into the same level pairs
-      ld_pair(sS, p0, vh, vl);
-      digits5(vh, vl, s1, c2, bs);
+      ld_pair(sS, p, vh, vl);
+      digits5(vh, vl, s1, c2, d);
 #pragma unroll
-      for (int j = 0; j < NSL; ++j) bs[j] = movtrans(bs[j]);
-      contract_da_acc(Td, bs, acc);
-      ld_pair(sS, p0 + 64, vh, vl);
-      digits5(vh, vl, s1, c2, bs);
+      for (int j = 0; j < NSL; ++j) sDig[kDigWords + dig_word(j, t, g, q)] = d[j];
+      ld_pair(sT, p, vh, vl);
+      digits5(vh, vl, s1, c2, d);
 #pragma unroll
-      for (int j = 0; j < NSL; ++j) bs[j] = movtrans(bs[j]);
-      contract_da_acc(Td, bs, bcc);
-      float2 H, L;
-      recombine(acc[0], acc[1], acc[2], acc[3], acc[4], scV, H, L);
-      st_pair(sR, p0, H, L);
-      recombine(bcc[0], bcc[1], bcc[2], bcc[3], bcc[4], scV, H, L);
-      st_pair(sR, p0 + 64, H, L);
-    }
-    __syncthreads();  // the digits of wt are in shared memory; sT is free
-#pragma unroll 1
-    for (int ss = 0; ss < 4; ++ss) {
-      const int s = 4 * wp + ss;
-      uint32_t b[NSL];
-      ldsm4t(sdig_base + 4u * (uint32_t)dig_word(lmat, lrow, s, 0), b[0], b[1], b[2], b[3]);
-      ldsm1t(sdig_base + 4u * (uint32_t)dig_word(4, lrow, s, 0), b[4]);
-      float2 acc[NSL];
-      contract_da(Td, b, acc);
-      float2 H, L;
-      recombine(acc[0], acc[1], acc[2], acc[3], acc[4], scV, H, L);
-      st_pair(sT, 2 * q + 8 * s + 64 * g, H, L);
+      for (int j = 0; j < NSL; ++j) sDig[2 * kDigWords + dig_word(j, t, g, q)] = d[j];
     }
     __syncthreads();
-    // ---------------------------------------------------------------- P4
+    contract_pass(sdig, szero, true, TA, TB, scV, wp, lane, sR, sS, sT);
+    __syncthreads();
+    // ---------------------------------------------------------------- P4: sum, Helmholtz term, scatter
     dfx::Acc pwe = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
 #pragma unroll 1
     for (int tt = 0; tt < 4; ++tt) {
       const int p = pbase + 64 * tt;
-      float2 ah, al, bh, bl;
+      float2 ah, al, bh, bl, ch, cl;
       ld_pair(sR, p, ah, al);
-      ld_pair(sT, p, bh, bl);
-      // (ah, al) + (bh, bl): TwoSum of the highs, lows added, normalised
-      float2 s, er;
-      dfx::two_sum(ah, bh, s, er);
-      float2 vh, vl;
-      dfx::two_sum(s, add2(add2(al, bl), er), vh, vl);
+      ld_pair(sS, p, bh, bl);
+      ld_pair(sT, p, ch, cl);
+      // three double-floats summed: TwoSums of the highs, lows added, normalised
+      float2 s, e1, s2, e2, vh, vl;
+      dfx::two_sum(ah, bh, s, e1);
+      dfx::two_sum(s, ch, s2, e2);
+      dfx::two_sum(s2, add2(add2(add2(al, bl), cl), add2(e1, e2)), vh, vl);
       int2 gp = make_int2(0, 0);  // the point pair's gather indices, read again (L1/L2)
       if (ASSEMBLED) gp = *reinterpret_cast<const int2 *>(l2gm + e * N3 + p);
       float2 xh = make_float2(0.0f, 0.0f), xl = xh;

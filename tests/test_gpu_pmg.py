@@ -117,6 +117,7 @@ def test_bf16_smoother_converges():
 def test_pmg_invalid_options():
     gm = sem.sem_mesh_create_box((2, 2, 2), 5)
     for kw in (dict(orders=(7, 3)), dict(orders=(5, 5, 1)), dict(orders=(5, 2), smoother_precision=sem.SEM_PREC_FP64),
+               dict(orders=(5, 2), smoother_precision=7),
                dict(orders=(5, 2), cheb_degree=0)):
         with pytest.raises(sem.SemError):
             sem.sem_pmg_create(gm, **kw)
@@ -167,4 +168,47 @@ def test_pmg_48_full_size_solve():
         assert float(torch.linalg.norm(b - r) / torch.linalg.norm(b)) < 1.2e-8
         assert float((x - u).abs().max() / u.abs().max()) < 1e-3  # error <= condition number x residual
         P.destroy()
+    gm.destroy()
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_df64_smoothing_matches_the_binary64_oracle(case):
+    """The V-cycle with binary64-accurate smoothing (SEM_PREC_DF64: binary64
+    level vectors and transfers, double-float operator) against the oracle's
+    binary64 V-cycle, both with a tight coarse solve: the eigenvalue bounds,
+    the transfers and the whole V-cycle agree to binary64 level."""
+    (nel, deform), orders = CASES[case]
+    box = dict(nel=nel, deform_amp=deform, kappa=KAPPA, phi=PHI)
+    pm = pmg.PMG(box, orders=orders, coarse_tol=1e-13, coarse_maxit=4000)
+    gm = sem.sem_mesh_create_box(nel, orders[0], deform_amp=deform, kappa=KAPPA, phi=PHI)
+    gp = sem.sem_pmg_create(gm, orders=orders, smoother_precision=sem.SEM_PREC_DF64, coarse_tol=1e-13,
+                            coarse_maxit=4000)
+    for l in range(len(pm.levels) - 1):
+        assert abs(gp.lam(l) - pm.levels[l].lam) <= 1e-10 * pm.levels[l].lam
+    rng = np.random.default_rng(8)
+    for l in range(len(pm.levels) - 1):
+        mf, mc = pm.levels[l].m, pm.levels[l + 1].m
+        uc = rng.standard_normal(mc.n_unique) * mc.mask
+        uf = torch.empty(mf.n_unique, dtype=torch.float64, device="cuda")
+        sem.sem_pmg_prolong(gp, l, dev(uc), uf)
+        assert rel_err(host(uf), pm.prolong(l, uc)) < 1e-13
+        rf = rng.standard_normal(mf.n_unique) * mf.mask
+        rc = torch.empty(mc.n_unique, dtype=torch.float64, device="cuda")
+        sem.sem_pmg_restrict(gp, l, dev(rf), rc)
+        assert rel_err(host(rc), pm.restrict(l, rf) * mc.mask) < 1e-13
+    m = pm.levels[0].m
+    r = rng.standard_normal(m.n_unique) * m.mask
+    z = torch.empty(m.n_unique, dtype=torch.float64, device="cuda")
+    sem.sem_pmg_vcycle(gp, dev(r), z)
+    err = rel_err(host(z), pm.vcycle(r))
+    assert err < 1e-11, err
+    # and as the preconditioner: binary64 residual 1e-8, iterations as the oracle's
+    b = oracle.poisson_rhs(m)
+    x = torch.zeros(m.n_unique, dtype=torch.float64, device="cuda")
+    st = sem.sem_pmg_pcg_solve(gp, dev(b), x, tol=1e-8, maxit=200)
+    assert st["status"] == 0
+    assert np.linalg.norm(b - oracle.apply_assembled(m, host(x))) / np.linalg.norm(b) < 1.05e-8
+    ref = pmg.fcg(pm, b, tol=1e-8)
+    assert abs(st["iterations"] - ref.iterations) <= 1, (st, ref.iterations)
+    gp.destroy()
     gm.destroy()
