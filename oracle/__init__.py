@@ -319,13 +319,14 @@ class SolveResult:
 
 
 def pcg(m: Mesh, b: np.ndarray, h1: float = 1.0, h2: float = 0.0, tol: float = 1e-10,
-        maxit: int = 1000, precond: str = "jacobi", apply=None) -> SolveResult:
+        maxit: int = 1000, precond: str = "jacobi", apply=None, x0: np.ndarray = None) -> SolveResult:
     """Textbook preconditioned conjugate gradients (Hestenes-Stiefel) on the
-    unique-node vectors, x0 = 0.
+    unique-node vectors, from x0 (zero when not given): r_0 = b - A x0.
 
     Reading of the stopping rule (the paper gives none): stop after the first
     iteration k with ||r_k||_2 <= tol ||b||_2, Euclidean norms over the unique
-    nodes; the iteration count is the number of operator applications."""
+    nodes (||b||, not ||r_0||, so that an initial guess does not change what
+    is solved); the iteration count is the number of operator applications."""
     A = apply or (lambda v: apply_assembled(m, v, h1, h2))
     if precond == "jacobi":
         dinv = jacobi_inv(m, h1, h2)
@@ -340,6 +341,12 @@ def pcg(m: Mesh, b: np.ndarray, h1: float = 1.0, h2: float = 0.0, tol: float = 1
     hist = []
     if bn == 0.0:
         return SolveResult(x, 0, 0.0, True, hist)
+    if x0 is not None:
+        x = np.array(x0, dtype=np.float64)
+        r = b - A(x)
+        rn0 = float(np.sqrt(np.dot(r, r)))
+        if rn0 <= tol * bn:  # the guess already meets the tolerance
+            return SolveResult(x, 0, rn0 / bn, True, hist)
     z = dinv * r
     p = z.copy()
     rho = float(np.dot(r, z))

@@ -71,7 +71,7 @@ namespace {
 constexpr int NP = 8, N3 = 512;
 constexpr int NSL = 5;             // digit slices per operand
 constexpr double kDScale = 32.0;   // D is sliced as D / 32
-constexpr int kMinBlocks = 8;      // resident 64-thread CTAs per SM the register budget aims at
+constexpr int kMinBlocks = 5;      // resident 128-thread CTAs per SM the register budget aims at
 
 // D's digits as mma fragment registers, per lane: [0][j][lane] = (D_j[g][2q],
 // D_j[g][2q+1]) (forward: B of the r-contraction, A of s and t),
@@ -252,27 +252,42 @@ __device__ __forceinline__ void ldsm4t(uint32_t addr, uint4 &r) {
                : "memory");
 }
 
-// B quads of one group. dir 0 (r): lines s, k = r at plane c (plain
-// ldmatrix: the stored rows are the lines); dir 1 (s): k = s, lines r at
-// plane c (transposed); dir 2 (t): k = t, lines r at row s = c (transposed).
-// Lane L gives the address of row L & 7 of matrix L >> 3; the slice of each
-// matrix is (1, 0, 3, 2), (2, 1, 4, 3), (0, Z, Z, 0) for E, O, Zq.
-__device__ __forceinline__ void load_group(uint32_t dig, uint32_t zero, int dir, int c, int lane, uint4 &E, uint4 &O,
+// B quads of one group. DIR 0 (r): lines s, k = r at plane c (plain
+// ldmatrix: the stored rows are the lines); DIR 1 (s): k = s, lines r at
+// plane c (transposed); DIR 2 (t): k = t, lines r at row s = c (transposed).
+// Lane L gives the address of row L & 7 of matrix L >> 3; the slices of the
+// four matrices are (1, 0, 3, 2), (2, 1, 4, 3), (0, Z, Z, 0) for E, O, Zq.
+struct LaneRows {
+  uint32_t je, jo, j0;  // byte offsets of this lane's matrix slices in a field's digit planes
+  bool zmat;            // this lane's Zq matrix is the zero matrix
+  int row;
+};
+
+__device__ __forceinline__ LaneRows lane_rows(int lane) {
+  LaneRows L;
+  const int mat = lane >> 3;
+  L.row = lane & 7;
+  L.je = 1024u * (uint32_t)(mat ^ 1);                    // slices 1, 0, 3, 2
+  L.jo = 1024u * (uint32_t)((mat & 1) ? mat : mat + 2);  // slices 2, 1, 4, 3
+  L.j0 = 0u;
+  L.zmat = (mat == 1 || mat == 2);
+  return L;
+}
+
+template <int DIR>
+__device__ __forceinline__ void load_group(uint32_t dig, uint32_t zrow, const LaneRows &L, int c, uint4 &E, uint4 &O,
                                            uint4 &Zq) {
-  const int row = lane & 7, mat = lane >> 3;
-  const int t = dir == 2 ? row : c, s = dir == 2 ? c : row;
-  const int je = mat ^ 1;                    // 1, 0, 3, 2
-  const int jo = (mat & 1) ? mat : mat + 2;  // 2, 1, 4, 3
-  const uint32_t ae = dig + 4u * (uint32_t)dig_word(je, t, s, 0);
-  const uint32_t ao = dig + 4u * (uint32_t)dig_word(jo, t, s, 0);
-  const uint32_t az = (mat == 0 || mat == 3) ? dig + 4u * (uint32_t)dig_word(0, t, s, 0) : zero + 16u * (uint32_t)row;
-  if (dir == 0) {
-    ldsm4(ae, E);
-    ldsm4(ao, O);
+  // row address of (plane t, row s): chunk (j 8 + t) 8 + (s ^ t), 16 bytes each
+  const int t = DIR == 2 ? L.row : c, s = DIR == 2 ? c : L.row;
+  const uint32_t rowoff = dig + 128u * (uint32_t)t + 16u * (uint32_t)(s ^ t);
+  const uint32_t az = L.zmat ? zrow : rowoff + L.j0;
+  if (DIR == 0) {
+    ldsm4(rowoff + L.je, E);
+    ldsm4(rowoff + L.jo, O);
     ldsm4(az, Zq);
   } else {
-    ldsm4t(ae, E);
-    ldsm4t(ao, O);
+    ldsm4t(rowoff + L.je, E);
+    ldsm4t(rowoff + L.jo, O);
     ldsm4t(az, Zq);
   }
 }
@@ -330,36 +345,64 @@ __device__ __forceinline__ void st_one(float2 *base, int p, float h, float l) {
   f[2 + (p & 1)] = l;
 }
 
-// The 24 line groups of one pass (3 directions x 8), 12 per warp: warp 0
-// takes r at planes 0..7 and s at planes 0..3, warp 1 s at planes 4..7 and
-// t at rows 0..7. The outputs go to the direction's tile: r as single points
-// (its pair runs along s), s and t as point pairs along r.
-__device__ __forceinline__ void contract_pass(uint32_t dig0, uint32_t zero, bool per_dir_fields, const uint4 &QA,
-                                              const uint4 &QB, float sc, int wp, int lane, float2 *oR, float2 *oS,
-                                              float2 *oT) {
+// Groups [c0, c1) of one direction, one per iteration (the four warps of
+// an element give the overlap). The outputs go to the direction's tile: r as
+// single points (its pair runs along s), s and t as point pairs along r.
+template <int DIR>
+__device__ __forceinline__ void contract_dir(uint32_t dig, uint32_t zrow, const LaneRows &L, int c0, int c1,
+                                             const uint4 &QA, const uint4 &QB, float sc, int lane, float2 *o) {
   const int g = lane >> 2, q = lane & 3;
 #pragma unroll 1
-  for (int k = 0; k < 12; ++k) {
-    const int grp = 12 * wp + k;
-    const int dir = grp >> 3, c = grp & 7;
-    const uint32_t dig = per_dir_fields ? dig0 + 4u * (uint32_t)(dir * kDigWords) : dig0;
+  for (int c = c0; c < c1; ++c) {
     uint4 E, O, Zq;
-    load_group(dig, zero, dir, c, lane, E, O, Zq);
-    float2 H, L;
-    contract(QA, QB, E, O, Zq, sc, H, L);
-    if (dir == 0) {  // (r_out = g, s = 2q, 2q + 1) at plane c
-      st_one(oR, g + 8 * (2 * q) + 64 * c, H.x, L.x);
-      st_one(oR, g + 8 * (2 * q + 1) + 64 * c, H.y, L.y);
-    } else if (dir == 1) {  // (s_out = g, r = 2q, 2q + 1) at plane c
-      st_pair(oS, 2 * q + 8 * g + 64 * c, H, L);
+    load_group<DIR>(dig, zrow, L, c, E, O, Zq);
+    float2 H, Lo;
+    contract(QA, QB, E, O, Zq, sc, H, Lo);
+    if (DIR == 0) {  // (r_out = g, s = 2q, 2q + 1) at plane c
+      const int p = g + 16 * q + 64 * c;
+      st_one(o, p, H.x, Lo.x);
+      st_one(o, p + 8, H.y, Lo.y);
+    } else if (DIR == 1) {  // (s_out = g, r = 2q, 2q + 1) at plane c
+      st_pair(o, 2 * q + 8 * g + 64 * c, H, Lo);
     } else {  // (t_out = g, r = 2q, 2q + 1) at row s = c
-      st_pair(oT, 2 * q + 8 * c + 64 * g, H, L);
+      st_pair(o, 2 * q + 8 * c + 64 * g, H, Lo);
     }
   }
 }
 
+// The 24 line groups of one pass (3 directions x 8), 6 per warp:
+// warp 0: r 0..5 | warp 1: r 6..7, s 0..3 | warp 2: s 4..7, t 0..1 | warp 3: t 2..7.
+// per_dir: the transposed pass, whose three fields have their own digit
+// planes (kDigWords apart).
+__device__ __forceinline__ void contract_pass(uint32_t dig0, uint32_t zrow, bool per_dir, const uint4 &QA,
+                                              const uint4 &QB, float sc, int wp, int lane, float2 *oR, float2 *oS,
+                                              float2 *oT) {
+  const LaneRows L = lane_rows(lane);
+  const uint32_t fs = per_dir ? 4u * kDigWords : 0u;
+  switch (wp) {
+    case 0:
+      contract_dir<0>(dig0, zrow, L, 0, 6, QA, QB, sc, lane, oR);
+      break;
+    case 1:
+      contract_dir<0>(dig0, zrow, L, 6, 8, QA, QB, sc, lane, oR);
+      contract_dir<1>(dig0 + fs, zrow, L, 0, 4, QA, QB, sc, lane, oS);
+      break;
+    case 2:
+      contract_dir<1>(dig0 + fs, zrow, L, 4, 8, QA, QB, sc, lane, oS);
+      contract_dir<2>(dig0 + 2 * fs, zrow, L, 0, 2, QA, QB, sc, lane, oT);
+      break;
+    default:
+      contract_dir<2>(dig0 + 2 * fs, zrow, L, 2, 8, QA, QB, sc, lane, oT);
+      break;
+  }
+}
+
+// Threads: one element per 128-thread CTA, four warps; warp w owns planes
+// t = 2w, 2w + 1, lane (g, q) the point pair r = 2q, 2q + 1 at s = g of each.
+constexpr int kThreads = 128;
+
 template <bool ASSEMBLED, bool HELM>
-__global__ void __launch_bounds__(64, kMinBlocks)
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
     k_ax_tc(int64_t E, const float2 *__restrict__ Gdf, const float2 *__restrict__ Bdf, float2 h1, float2 h2,
             const double *__restrict__ u, double *__restrict__ w, const int32_t *__restrict__ l2gm,
             double *__restrict__ pw_partial, double *__restrict__ wloc, const int *__restrict__ skip,
@@ -370,8 +413,8 @@ __global__ void __launch_bounds__(64, kMinBlocks)
   __shared__ __align__(16) float2 sT[N3];
   __shared__ __align__(16) uint32_t sDig[3 * kDigWords];  // digits of u, then of (wr, ws, wt)
   __shared__ __align__(16) uint32_t sZero[32];             // an 8x8 zero matrix for ldmatrix
-  __shared__ int s_red[4];
-  __shared__ double s_pw[2];
+  __shared__ int s_red[8];
+  __shared__ double s_pw[4];
   const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
   if (tid < 32) sZero[tid] = 0u;
   // D's digits as the two A quads, forward (D) and transposed (D^T)
@@ -380,8 +423,9 @@ __global__ void __launch_bounds__(64, kMinBlocks)
   const uint4 TA = make_uint4(g_dig[1][0][lane], g_dig[1][2][lane], g_dig[1][1][lane], g_dig[1][3][lane]);
   const uint4 TB = make_uint4(g_dig[1][0][lane], g_dig[1][2][lane], g_dig[1][4][lane], 0u);
   const uint32_t sdig = (uint32_t)__cvta_generic_to_shared(sDig);
-  const uint32_t szero = (uint32_t)__cvta_generic_to_shared(sZero);
-  const int pbase = 2 * q + 8 * g + 256 * wp;  // the thread's point pair on its first plane (+64 per plane)
+  const uint32_t szero = (uint32_t)__cvta_generic_to_shared(sZero) + 16u * (uint32_t)(lane & 7);
+  const int t0 = 2 * wp;                      // the thread's first plane
+  const int pbase = 2 * q + 8 * g + 64 * t0;  // its point pair there (+64 on the second plane)
   double pw = 0.0;
   constexpr float scD = (float)kDScale * 0x1p-20f;  // weight of level 0
 
@@ -389,27 +433,29 @@ __global__ void __launch_bounds__(64, kMinBlocks)
     const int64_t e = elist ? (int64_t)elist[ei] : ei;  // the element (E: the list's length with a list)
     // ---------------------------------------------------------------- P0: gather, scale, digits of x
     if (tid == 0) prefetch_l2(Gdf + e * 6 * N3, 48u * N3);
-    int2 gi[4];
-    double uv0[4][2];
+    int2 gi[2] = {make_int2(0, 0), make_int2(0, 0)};
+    double uv[2][2];  // the thread's inputs, kept for the Helmholtz term and p.w
 #pragma unroll
-    for (int tt = 0; tt < 4; ++tt)
-      if (ASSEMBLED) gi[tt] = *reinterpret_cast<const int2 *>(l2gm + e * N3 + pbase + 64 * tt);
+    for (int h = 0; h < 2; ++h)
+      if (ASSEMBLED) gi[h] = *reinterpret_cast<const int2 *>(l2gm + e * N3 + pbase + 64 * h);
 #pragma unroll
-    for (int tt = 0; tt < 4; ++tt) load_u<ASSEMBLED>(u, gi[tt], e * N3 + pbase + 64 * tt, uv0[tt]);
-    int em = 0;
-#pragma unroll
-    for (int tt = 0; tt < 4; ++tt) em = max(em, max(df::exp_field(uv0[tt][0]), df::exp_field(uv0[tt][1])));
+    for (int h = 0; h < 2; ++h) load_u<ASSEMBLED>(u, gi[h], e * N3 + pbase + 64 * h, uv[h]);
+    int em = max(max(df::exp_field(uv[0][0]), df::exp_field(uv[0][1])),
+                 max(df::exp_field(uv[1][0]), df::exp_field(uv[1][1])));
     em = __reduce_max_sync(0xffffffffu, em);
     if (lane == 0) s_red[wp] = em;
     __syncthreads();
-    const int su = max(s_red[0], s_red[1]) - 1022;  // |u| 2^-su < 1
+    const int su = max(max(s_red[0], s_red[1]), max(s_red[2], s_red[3])) - 1022;  // |u| 2^-su < 1
+    float2 xh[2], xl[2];  // x = u 2^-su in double-float
 #pragma unroll
-    for (int tt = 0; tt < 4; ++tt) {
-      const float2 x0 = df::from_f64_scaled(uv0[tt][0], su), x1 = df::from_f64_scaled(uv0[tt][1], su);
+    for (int h = 0; h < 2; ++h) {
+      const float2 x0 = df::from_f64_scaled(uv[h][0], su), x1 = df::from_f64_scaled(uv[h][1], su);
+      xh[h] = make_float2(x0.x, x1.x);
+      xl[h] = make_float2(x0.y, x1.y);
       uint32_t d[NSL];
-      digits5(make_float2(x0.x, x1.x), make_float2(x0.y, x1.y), 1024.0f, 1048576.0f, d);
+      digits5(xh[h], xl[h], 1024.0f, 1048576.0f, d);
 #pragma unroll
-      for (int j = 0; j < NSL; ++j) sDig[dig_word(j, 4 * wp + tt, g, q)] = d[j];
+      for (int j = 0; j < NSL; ++j) sDig[dig_word(j, t0 + h, g, q)] = d[j];
     }
     __syncthreads();
     // ---------------------------------------------------------------- P1: ur, us, ut
@@ -419,8 +465,8 @@ __global__ void __launch_bounds__(64, kMinBlocks)
     const float2 *Ge = Gdf + e * 6 * N3;
     int evm = 0;
 #pragma unroll 1
-    for (int tt = 0; tt < 4; ++tt) {
-      const int p = pbase + 64 * tt;
+    for (int h = 0; h < 2; ++h) {
+      const int p = pbase + 64 * h;
       float2 uh[3], ul[3];
       ld_pair(sR, p, uh[0], ul[0]);
       ld_pair(sS, p, uh[1], ul[1]);
@@ -444,19 +490,19 @@ __global__ void __launch_bounds__(64, kMinBlocks)
       st_pair(sT, p, oh, ol);
     }
     evm = __reduce_max_sync(0xffffffffu, evm);
-    if (lane == 0) s_red[2 + wp] = evm;
+    if (lane == 0) s_red[4 + wp] = evm;
     __syncthreads();
     // digits of v 2^-sv, |v 2^-sv| <= 1: sv = (largest biased exponent) - 126,
     // at least -100 so that the digit scales stay normal binary32 numbers
     // (an element whose v is all zero, or below 2^-100, gives digits of 0)
-    const int ev = max(s_red[2], s_red[3]);
+    const int ev = max(max(s_red[4], s_red[5]), max(s_red[6], s_red[7]));
     const int sv = max(ev - 126, -100);
     const float s1 = pow2f(10 - sv), c2 = pow2f(20 - sv);
     const float scV = pow2f(sv - 15);  // scD 2^sv
     // ---------------------------------------------------------------- P3: transposed contractions
 #pragma unroll 1
-    for (int tt = 0; tt < 4; ++tt) {
-      const int t = 4 * wp + tt, p = pbase + 64 * tt;
+    for (int h = 0; h < 2; ++h) {
+      const int t = t0 + h, p = pbase + 64 * h;
       float2 vh, vl;
       uint32_t d[NSL];
       ld_pair(sR, p, vh, vl);
@@ -477,32 +523,22 @@ __global__ void __launch_bounds__(64, kMinBlocks)
     __syncthreads();
     // ---------------------------------------------------------------- P4: sum, Helmholtz term, scatter
     dfx::Acc pwe = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
-#pragma unroll 1
-    for (int tt = 0; tt < 4; ++tt) {
-      const int p = pbase + 64 * tt;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int p = pbase + 64 * h;
       float2 ah, al, bh, bl, ch, cl;
       ld_pair(sR, p, ah, al);
       ld_pair(sS, p, bh, bl);
       ld_pair(sT, p, ch, cl);
       // three double-floats summed: TwoSums of the highs, lows added, normalised
-      float2 s, e1, s2, e2, vh, vl;
-      dfx::two_sum(ah, bh, s, e1);
-      dfx::two_sum(s, ch, s2, e2);
+      float2 s_, e1, s2, e2, vh, vl;
+      dfx::two_sum(ah, bh, s_, e1);
+      dfx::two_sum(s_, ch, s2, e2);
       dfx::two_sum(s2, add2(add2(add2(al, bl), cl), add2(e1, e2)), vh, vl);
-      int2 gp = make_int2(0, 0);  // the point pair's gather indices, read again (L1/L2)
-      if (ASSEMBLED) gp = *reinterpret_cast<const int2 *>(l2gm + e * N3 + p);
-      float2 xh = make_float2(0.0f, 0.0f), xl = xh;
-      if (HELM || (ASSEMBLED && pw_partial != nullptr)) {
-        double uv[2];
-        load_u<ASSEMBLED>(u, gp, e * N3 + p, uv);
-        const float2 x0 = df::from_f64_scaled(uv[0], su), x1 = df::from_f64_scaled(uv[1], su);
-        xh = make_float2(x0.x, x1.x);
-        xl = make_float2(x0.y, x1.y);
-      }
       if (HELM) {
         const float4 B4 = *reinterpret_cast<const float4 *>(Bdf + e * N3 + p);
         const float2 Bh = make_float2(B4.x, B4.z), Bl = make_float2(B4.y, B4.w);
-        dfx::Acc bu = dfx::mul_first(Bh, Bl, xh, xl);
+        dfx::Acc bu = dfx::mul_first(Bh, Bl, xh[h], xl[h]);
         float2 buh, bul;
         dfx::two_sum(bu.s, bu.c, buh, bul);
         dfx::Acc o = dfx::mul_first(dup(h1.x), dup(h1.y), vh, vl);
@@ -512,13 +548,13 @@ __global__ void __launch_bounds__(64, kMinBlocks)
       const double v0 = df::to_f64_scaled(vh.x, vl.x, su), v1 = df::to_f64_scaled(vh.y, vl.y, su);
       if (ASSEMBLED) {
         if (wloc) {
-          wloc[e * N3 + p] = (gp.x >= 0) ? v0 : 0.0;
-          wloc[e * N3 + p + 1] = (gp.y >= 0) ? v1 : 0.0;
+          wloc[e * N3 + p] = (gi[h].x >= 0) ? v0 : 0.0;
+          wloc[e * N3 + p + 1] = (gi[h].y >= 0) ? v1 : 0.0;
         } else {
-          if (gp.x >= 0) atomicAdd(&w[gp.x], v0);
-          if (gp.y >= 0) atomicAdd(&w[gp.y], v1);
+          if (gi[h].x >= 0) atomicAdd(&w[gi[h].x], v0);
+          if (gi[h].y >= 0) atomicAdd(&w[gi[h].y], v1);
         }
-        if (pw_partial != nullptr) dfx::mac(pwe, xh, xl, vh, vl);
+        if (pw_partial != nullptr) dfx::mac(pwe, xh[h], xl[h], vh, vl);
       } else {
         w[e * N3 + p] = v0;
         w[e * N3 + p + 1] = v1;
@@ -535,7 +571,7 @@ __global__ void __launch_bounds__(64, kMinBlocks)
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (lane == 0) s_pw[wp] = v;
     __syncthreads();
-    if (tid == 0) pw_partial[blockIdx.x] = s_pw[0] + s_pw[1];
+    if (tid == 0) pw_partial[blockIdx.x] = (s_pw[0] + s_pw[1]) + (s_pw[2] + s_pw[3]);
   }
 }
 
@@ -558,7 +594,7 @@ int sem_launch_ax_tc(const sem_mesh *m, double h1, double h2, const double *u, d
   const bool helm = !(h1 == 1.0 && h2 == 0.0);
   double *wloc = (assembled && !elist) ? (double *)m->det_w : nullptr;
 #define LAUNCH(ASM, HLM) \
-  k_ax_tc<ASM, HLM><<<grid, 64, 0, st>>>(nE, m->Gdf, m->Bdf, h1d, h2d, u, w, map, pw_partial, wloc, skip, elist)
+  k_ax_tc<ASM, HLM><<<grid, kThreads, 0, st>>>(nE, m->Gdf, m->Bdf, h1d, h2d, u, w, map, pw_partial, wloc, skip, elist)
   if (assembled) {
     if (helm) LAUNCH(true, true);
     else LAUNCH(true, false);

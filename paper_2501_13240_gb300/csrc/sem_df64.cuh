@@ -140,31 +140,56 @@ __device__ __forceinline__ int exp_field(double x) {
 // accuracy the operator promises relative to the element's largest value).
 // sh comes from exp_field: sh = emax - 1023.
 //
-// (hi, lo) of x 2^-sh; infinities and NaN keep their class.
+// (hi, lo) of x 2^-sh; infinities and NaN keep their class. The binary32
+// exponent of the scaled value is computed once from the binary64 exponent
+// field; the common path is the bit work of from_f64.
 __device__ __forceinline__ float2 from_f64_scaled(double x, int sh) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FFull);
-  if (e == 0x7FF || sh == 0) return from_f64(x);
-  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
-  const int es = e - sh;  // biased exponent of the scaled value
-  if (e == 0 || es <= 896) return make_float2(__uint_as_float(sgn), 0.0f);
-  if (es >= 896 + 255) return make_float2(__uint_as_float(sgn | 0x7F800000u), 0.0f);
-  const unsigned long long bs = (b & ~(0x7FFull << 52)) | ((unsigned long long)es << 52);
-  return from_f64(__longlong_as_double((long long)bs));
+  const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+  const int e = (int)((bh >> 20) & 0x7FFu);
+  const unsigned sgn = bh & 0x80000000u;
+  const int ef = e - 896 - sh;  // binary32 biased exponent of x 2^-sh
+  if (e == 0x7FF || e == 0 || ef <= 0 || ef >= 255) {  // rare: not finite, zero, or out of range once scaled
+    if (e == 0x7FF) return from_f64(x);
+    if (e == 0 || ef <= 0) return make_float2(__uint_as_float(sgn), 0.0f);
+    return make_float2(__uint_as_float(sgn | 0x7F800000u), 0.0f);
+  }
+  const unsigned mh = ((bh & 0xFFFFFu) << 3) | (bl >> 29);
+  const float hi = __uint_as_float(sgn | ((unsigned)ef << 23) | mh);
+  const float scale = __uint_as_float((unsigned)ef << 23);  // 2^(unbiased exponent of hi)
+  float lo = mul(mul(__uint2float_rn(bl & 0x1FFFFFFFu), 0x1p-52f), scale);
+  lo = __uint_as_float(__float_as_uint(lo) ^ sgn);
+  return make_float2(hi, lo);
 }
 
-// nearest binary64 of (h + l) 2^sh (the inverse scaling of from_f64_scaled)
+// nearest binary64 of (h + l) 2^sh (the inverse scaling of from_f64_scaled):
+// to_f64 with the exponent of the result raised by sh
 __device__ __forceinline__ double to_f64_scaled(float h, float l, int sh) {
-  const double d = to_f64(h, l);
-  if (sh == 0) return d;
-  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const int e = (int)((b >> 52) & 0x7FFull);
-  if (e == 0 || e == 0x7FF) return d;  // zero (h = 0) or not finite
-  const int es = e + sh;
-  if (es >= 1 && es <= 0x7FE) return __longlong_as_double((long long)(b + ((unsigned long long)(long long)sh << 52)));
-  // rare: below the normal range (flushed to a signed zero) or overflowing (infinity)
-  const unsigned long long sg = b & 0x8000000000000000ull;
-  return __longlong_as_double((long long)(es < 1 ? sg : (sg | 0x7FF0000000000000ull)));
+  const unsigned hb = __float_as_uint(h);
+  const unsigned ef = (hb >> 23) & 0xFFu;
+  const int e64 = (int)ef + 896 + sh;  // binary64 biased exponent of hi 2^sh
+  if (ef < 54u || ef == 255u || e64 < 2 || e64 > 0x7FE) {  // rare: tiny, zero, not finite, or out of range
+    const double d = to_f64(h, l);
+    if (sh == 0) return d;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7FFull);
+    if (e == 0 || e == 0x7FF) return d;
+    const int es = e + sh;
+    if (es >= 1 && es <= 0x7FE) return __longlong_as_double((long long)(b + ((unsigned long long)(long long)sh << 52)));
+    const unsigned long long sg = b & 0x8000000000000000ull;  // flushed to a signed zero, or infinity
+    return __longlong_as_double((long long)(es < 1 ? sg : (sg | 0x7FF0000000000000ull)));
+  }
+  const unsigned sgn = hb & 0x80000000u;
+  const unsigned m = hb & 0x7FFFFFu;
+  long long D = (long long)(((unsigned long long)(sgn | ((unsigned)e64 << 20) | (m >> 3)) << 32) |
+                            ((unsigned long long)(m & 7u) << 29));
+  // lo in binary64 ulps of hi (as in to_f64; independent of the scaling)
+  const bool down = (m == 0u) && (l != 0.0f) && (((__float_as_uint(l) ^ hb) & 0x80000000u) != 0u);
+  const unsigned sexp = (down ? 307u : 306u) - ef;
+  const float kf = mul(l, __uint_as_float(sexp << 23));
+  const long long k = (long long)__float2int_rn(kf);
+  D += sgn ? -k : k;
+  return __longlong_as_double(D);
 }
 
 }  // namespace df

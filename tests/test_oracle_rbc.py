@@ -216,3 +216,35 @@ def test_onset_of_convection_at_the_critical_rayleigh_number():
     assert s_lo < 0.0 < s_hi, (s_lo, s_hi)
     ra0 = 1650.0 + 120.0 * (-s_lo) / (s_hi - s_lo)
     assert abs(ra0 / 1707.76 - 1.0) < 0.01, ra0
+
+
+def test_extrapolated_initial_guesses_change_only_the_iterations():
+    """Starting every solve of a step from 2 x^n - x^{n-1} (the option for the
+    RBC solves) leaves the fields of the step the same up to the solver
+    tolerance, steps from the conduction state stay at it, and from the
+    second step on the Helmholtz solves need fewer iterations."""
+    m = rbc_mesh((2, 2, 3), 4, 1.5)
+    pert = 0.2 * np.random.default_rng(5).standard_normal(m.n_unique)
+    runs = {}
+    for ex in (False, True):
+        R = rbc.RBC(m, 2e4, 1.0, 5e-3, tol=1e-11, extrapolate=ex)
+        s = R.initial_state(pert)
+        hist = []
+        for _ in range(5):
+            s = R.step(s)
+            hist.append(s.iters)
+        runs[ex] = (s, hist)
+    (s0, h0), (s1, h1) = runs[False], runs[True]
+    assert np.abs(s1.T - s0.T).max() < 1e-9
+    assert max(np.abs(a - b).max() for a, b in zip(s1.u, s0.u)) < 1e-9
+    assert np.abs(s1.p - s0.p).max() < 1e-7 * max(1.0, np.abs(s0.p).max())
+    assert h1[0] == h0[0]  # the first step has no history to extrapolate from
+    later0 = sum(h["T"] + sum(h["u"]) for h in h0[2:])
+    later1 = sum(h["T"] + sum(h["u"]) for h in h1[2:])
+    assert later1 < later0, (h0, h1)
+    R = rbc.RBC(m, 1e8, 0.7, 1e-3, tol=1e-13, extrapolate=True)  # conduction stays a fixed point
+    s = R.initial_state()
+    z = zg(m)
+    for _ in range(3):
+        s = R.step(s)
+        assert np.abs(s.T - (1.0 - z)).max() < 1e-13

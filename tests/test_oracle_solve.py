@@ -78,3 +78,23 @@ def test_pcg_zero_rhs_returns_zero():
     m = oracle.box_mesh((1, 1, 1), 3)
     res = oracle.pcg(m, np.zeros(m.n_unique))
     assert res.iterations == 0 and res.converged and not res.x.any()
+
+
+def test_pcg_initial_guess_solves_the_same_system():
+    """From an initial guess x0 the oracle's PCG starts at r0 = b - A x0 and
+    keeps the stopping test ||r|| <= tol ||b||: it reaches the solution of the
+    zero-start solve (a sign error in r0 would converge elsewhere), in fewer
+    iterations from a nearby guess, and returns the guess itself, with no
+    iteration, when the guess already meets the tolerance."""
+    m = oracle.box_mesh((2, 2, 2), 4, deform_amp=0.05, kappa=np.full(9, 1.0), phi=np.array([0.1, 0.2, 0.3]))
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(m.n_unique) * m.mask
+    ref = oracle.pcg(m, b, 1.0, 0.3, tol=1e-13, maxit=2000)
+    far = oracle.pcg(m, b, 1.0, 0.3, tol=1e-13, maxit=2000, x0=rng.standard_normal(m.n_unique) * m.mask)
+    assert far.converged and np.abs(far.x - ref.x).max() < 1e-11 * np.abs(ref.x).max()
+    near_guess = ref.x + 1e-6 * rng.standard_normal(m.n_unique) * m.mask
+    near = oracle.pcg(m, b, 1.0, 0.3, tol=1e-10, maxit=2000, x0=near_guess)
+    zero = oracle.pcg(m, b, 1.0, 0.3, tol=1e-10, maxit=2000)
+    assert near.converged and near.iterations < zero.iterations
+    done = oracle.pcg(m, b, 1.0, 0.3, tol=1e-10, maxit=2000, x0=ref.x)
+    assert done.iterations == 0 and np.array_equal(done.x, ref.x)
