@@ -60,6 +60,70 @@ ISSUE_PEAK_TINST = 152 * 4 * 32 * 2.07e9 / 1e12
 # binary32 FMA rate of this GPU (77 TFLOP/s, own probe) = 38.5 T lane ops/s.
 FP32_LANE_OPS_PER_POINT = {"df64": 469.0}
 FP32_PEAK_TLANEOPS = 38.5
+# Algorithmic bytes of the Rayleigh-Benard step's solves, per unit. Operators
+# per local point (E NP^3) plus the gathered/scattered vectors per unique node;
+# vector kernels per unique node. Levels of the pressure hierarchy: N = 7, 3, 1.
+RBC_UNIT_BYTES = {
+    # double-float Helmholtz operator: G 6 x 8 + B 8 + l2g 4 per local point
+    "helm_op_local": 60.0,
+    # double-float Poisson operator (pressure outer iteration): G 48 + l2g 4
+    "poisson_op_local": 52.0,
+    # binary32 smoothing operator with bfloat16 geometry: G 6 x 2 + l2g 4
+    "smooth_op_local": 16.0,
+    # binary64 operand gather and result scatter of an operator, per unique node
+    "op_vec64_unique": 16.0,
+    "op_vec32_unique": 8.0,
+    # Jacobi-PCG iteration vectors: update1 reads x r p w dinv, writes x r;
+    # update2 reads r p dinv, writes p w (12 binary64 words)
+    "pcg_vec_unique": 96.0,
+    # flexible-CG iteration vectors: memset w, update (p w x r read, x r
+    # written), r.r, binary64<->binary32 at the V-cycle ends (r read, b
+    # written; x read, z written), r.zn and r.z, p = zn + beta p
+    "fcg_vec_unique": 8 + 48 + 8 + 12 + 12 + 24 + 24,
+    # one V-cycle's smoothing vectors on a level at Chebyshev degree 16, in
+    # binary32 words: start 5, 15 x (x, d, r, dinv -> x, d) 6, final x += d 3,
+    # two residual copies 2 + 2, scaled start 3, 15 x 6, x += d 3, prolongation
+    # clear and add 1 + 3
+    "cheb_vec_unique_words": 5 + 90 + 3 + 2 + 2 + 3 + 90 + 3 + 1 + 3,
+}
+
+
+def box_counts(w, N):
+    """local points and unique nodes of the box workload's mesh at order N"""
+    nL = int(np.prod(w.nel)) * (N + 1) ** 3
+    nU = int(np.prod([w.nel[d] * N + (0 if w.periodic[d] else 1) for d in range(3)]))
+    return nL, nU
+
+
+def rbc_phase_roofline(w, st, guessed, hbm_gbs):
+    """Algorithmic bytes of one Rayleigh-Benard step's three solve phases
+    (the per-iteration kernels of each solve; the N = 1 coarse solve of the
+    V-cycle is latency-bound and not counted), their rate over the phase's
+    measured time and the fraction of the HBM copy rate."""
+    b = RBC_UNIT_BYTES
+    nL, nU = box_counts(w, w.N)
+    helm = nL * b["helm_op_local"] + nU * b["op_vec64_unique"]
+    poisson = nL * b["poisson_op_local"] + nU * b["op_vec64_unique"]
+    its_u = sum(st["iters_u"])
+    g = 1 if guessed else 0  # the operator application that forms r_0 = b - A x0
+    out = {}
+    out["T"] = (st["iters_T"] + g) * helm + st["iters_T"] * nU * b["pcg_vec_unique"]
+    out["u"] = (its_u + 3 * g) * helm + its_u * nU * b["pcg_vec_unique"]
+    vc = 0.0
+    for N in (w.N, max(1, w.N // 2)):  # smoothing levels 7 and 3
+        lL, lU = box_counts(w, N)
+        vc += 32 * (lL * b["smooth_op_local"] + lU * b["op_vec32_unique"]) + 4 * lU * b["cheb_vec_unique_words"]
+    its_p = st["iters_p"]
+    out["p"] = (its_p + g) * poisson + its_p * (nU * b["fcg_vec_unique"] + vc)
+    res = {}
+    for ph, key in (("T", "ms_T"), ("p", "ms_p"), ("u", "ms_u")):
+        gbs = out[ph] / (st[key] * 1e-3) / 1e9 if st[key] > 0 else 0.0
+        res[ph] = {"algorithmic_gb": out[ph] / 1e9, "ms": st[key], "achieved_gbs": gbs, "frac": gbs / hbm_gbs}
+    tot = sum(out.values())
+    ms = st["ms_T"] + st["ms_p"] + st["ms_u"]
+    res["solves"] = {"algorithmic_gb": tot / 1e9, "ms": ms, "achieved_gbs": tot / (ms * 1e-3) / 1e9,
+                     "frac": tot / (ms * 1e-3) / 1e9 / hbm_gbs}
+    return res
 
 
 def parse():
@@ -78,7 +142,7 @@ def parse():
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"])
     ap.add_argument("--once", default="",
                     help="profiling mode: comma list of kernels to launch once each on the workload "
-                         "(local_df64, asm_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16, rbc), then exit")
+                         "(local_df64, asm_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16, rbc, rbcx), then exit")
     return ap.parse_args()
 
 
@@ -227,12 +291,14 @@ def run_once(sem, mesh, u, names):
             sem.sem_ax_assembled_add(mesh, 1.0, 0.0, u, wg, precision=P[prec])
         elif kind == "gs":
             sem.sem_gs_op(mesh, wL, True)
-        elif kind == "rbc":  # three Rayleigh-Benard steps on the 32^3-element workload
+        elif kind in ("rbc", "rbcx"):  # Rayleigh-Benard steps on the 32^3-element workload
             rw = workloads.RBC_32
             rm = sem.mesh_from_workload(rw)
             pert = torch.from_numpy(workloads.perturbation(rm.n_unique, 1e-3)).cuda()
-            rs = sem.sem_rbc_create(rm, 1e8, 0.7, 1e-3, tol=1e-8, precision=sem.SEM_PREC_DF64, T_pert=pert)
-            for _ in range(3):
+            # rbcx: solves from the extrapolated guess, four steps (the fourth steady)
+            rs = sem.sem_rbc_create(rm, 1e8, 0.7, 1e-3, tol=1e-8, precision=sem.SEM_PREC_DF64, T_pert=pert,
+                                    extrapolate=kind == "rbcx")
+            for _ in range(3 if kind == "rbc" else 4):
                 print(json.dumps(sem.sem_bdf_ext_step(rs)))
             rs.destroy()
             rm.destroy()
@@ -491,19 +557,32 @@ def main():
         pcg48["workload"] = w48.name
         m48.destroy()
 
-    # --- one Rayleigh-Benard BDF2/EXT2 step (32^3 elements, Ra = 1e8, Pr = 0.7)
+    # --- Rayleigh-Benard BDF2/EXT2 steps (32^3 elements, Ra = 1e8, Pr = 0.7),
+    # solves from zero and from the extrapolated guess 2 x^n - x^{n-1}
     rbc = None
     if not args.no_rbc:
         rw = workloads.RBC_32
         rm = sem.mesh_from_workload(rw)
         pert = torch.from_numpy(workloads.perturbation(rm.n_unique, 1e-3)).cuda()
-        rs = sem.sem_rbc_create(rm, 1e8, 0.7, 1e-3, tol=1e-8, precision=sem.SEM_PREC_DF64, T_pert=pert)
-        steps = [sem.sem_bdf_ext_step(rs, raise_on_error=False) for _ in range(3)]
-        rbc = {"workload": rw.name, "steps": steps, "ms_per_step_after_first": float(
-            np.mean([s_["step_ms"] for s_ in steps[1:]]))}
+        hbm_gbs, _ = peaks()
+        rbc = {"workload": rw.name, "tol": 1e-8, "unit_bytes": RBC_UNIT_BYTES,
+               "roofline_peak_gbs": hbm_gbs}
+        for mode, ex in (("cold", False), ("extrapolated", True)):
+            rs = sem.sem_rbc_create(rm, 1e8, 0.7, 1e-3, tol=1e-8, precision=sem.SEM_PREC_DF64, T_pert=pert,
+                                    extrapolate=ex)
+            steps = [sem.sem_bdf_ext_step(rs, raise_on_error=False) for _ in range(5)]
+            for s_ in steps:
+                s_["phase_roofline"] = rbc_phase_roofline(rw, s_, ex and s_["step"] > 1, hbm_gbs)
+            rbc[mode] = {"steps": steps,
+                         "ms_per_step_after_first": float(np.mean([s_["step_ms"] for s_ in steps[1:]])),
+                         # the first two steps differ (BDF1, then new Jacobi inverses for b0 = 3/2)
+                         "ms_per_steady_step": float(np.mean([s_["step_ms"] for s_ in steps[2:]]))}
+            if mode == "extrapolated":
+                T = sem.sem_rbc_fields(rs)["T"]
+            else:
+                rs.destroy()
         # in-situ rendering of the temperature: bottom boundary-layer slice and a
         # vertical slice, 4096 x 4096 pixels each, iso-levels 0.4 and 0.6
-        T = sem.sem_rbc_fields(rs)["T"]
         render = {}
         for name, axis, coord in (("bottom_bl_z0.01", 2, 0.01), ("vertical_y0.5", 1, 0.5)):
             vals = torch.empty((4096, 4096), dtype=torch.float32, device="cuda")

@@ -123,6 +123,10 @@ typedef struct {
                       1: no mask -- the pure-Neumann (singular) operator, for
                       the pressure Poisson problem; b must be orthogonal to the
                       constant vector and x is determined up to a constant */
+  int initial_guess; /* 0: start from x = 0; 1: x on entry is the initial guess
+                        (zero on Dirichlet nodes): r_0 = b - A x, the stopping
+                        test stays ||r|| <= tol ||b||, and a guess that meets
+                        it returns at once with 0 iterations */
 } sem_solver_opts;
 
 typedef struct {
@@ -197,13 +201,13 @@ int sem_mesh_validate(const sem_mesh *m);
 int sem_mesh_set_deterministic(sem_mesh *m, int on);
 
 /* Arithmetic route of the double-float operator at N = 7 (SEM_PREC_DF64):
- * on = 1 (the default) evaluates the 1-D tensor contractions of Sec. 2.2
- * exactly on the fp16 tensor cores (operands cut into five 10-bit digits on
- * a fixed-point grid per element, digit products summed exactly in binary32
- * by level, levels recombined to double-float); on = 0 uses the compensated
- * double-float dot products on the binary32 pipe. Both meet the same
- * binary64-level accuracy; the setting exists to compare them. Other orders
- * always use the binary32 route. */
+ * on = 1 evaluates the 1-D tensor contractions of Sec. 2.2 exactly on the
+ * fp16 tensor cores (operands cut into five 10-bit digits on a fixed-point
+ * grid per element, digit products summed exactly in binary32 by level,
+ * levels recombined to double-float); on = 0 (the default, faster on this
+ * GPU) uses the compensated double-float dot products on the binary32 pipe.
+ * Both meet the same binary64-level accuracy; the setting exists to compare
+ * them. Other orders always use the binary32 route. */
 int sem_mesh_set_tensor_cores(sem_mesh *m, int on);
 
 /* Copy l2g (n_local int32) and mask (n_unique uint8) to host arrays; either
@@ -296,9 +300,12 @@ int sem_jacobi_inv(const sem_mesh *m, double h1, double h2, double *dinv_g, void
 int sem_pcg_workspace_bytes(const sem_mesh *m, size_t *bytes);
 
 /* Jacobi-preconditioned CG for (h1 A + h2 B) x = b on the free unique nodes,
- * x0 = 0, textbook Hestenes-Stiefel recurrences; stops after the first
- * iteration k with ||r_k||_2 <= tol ||b||_2. b_g, x_g: device U-vectors
- * (b must vanish on Dirichlet nodes; x is 0 there on exit). workspace: device
+ * from x0 = 0 (or from the guess in x_g when opts.initial_guess = 1), textbook
+ * Hestenes-Stiefel recurrences; stops after the first iteration k with
+ * ||r_k||_2 <= tol ||b||_2 (k = 0 when a guess already meets it). b_g, x_g:
+ * device U-vectors (b must vanish on Dirichlet nodes; x is 0 there on exit
+ * when starting from 0; a guess keeps its Dirichlet values, which the
+ * operator ignores). workspace: device
  * memory of sem_pcg_workspace_bytes() bytes, 256-byte aligned, caller-owned.
  * Returns SEM_OK, SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN or SEM_ERR_TIMEOUT
  * (stats filled in every case) or an argument/CUDA error. */
@@ -357,7 +364,8 @@ int sem_pmg_vcycle(sem_pmg *p, const double *r_g, double *z_g, void *stream);
 int sem_pmg_prolong(sem_pmg *p, int level, const double *uc_g, double *uf_g, void *stream);
 int sem_pmg_restrict(sem_pmg *p, int level, const double *rf_g, double *rc_g, void *stream);
 
-/* Flexible CG preconditioned by one V-cycle per iteration, x0 = 0; stops after
+/* Flexible CG preconditioned by one V-cycle per iteration, from x0 = 0 or, with
+ * opts.initial_guess = 1, from the guess in x_g (r_0 = M b - A x_g); stops after
  * the first iteration with ||r||_2 <= tol ||b||_2 (opts.mask_mode must equal the
  * hierarchy's mask_mode; for mask_mode 1, b must be orthogonal to constants;
  * opts.precision selects the fine operator: SEM_PREC_FP64 or SEM_PREC_DF64). */
@@ -380,7 +388,8 @@ int sem_pmg_destroy(sem_pmg *p);
  *   u:  (b0/dt B + nu A) u^{n+1} = M Q^T[B (f* - grad p)], u = 0 on the plates,
  *       nu = sqrt(Pr/Ra).
  * The first step uses history levels equal to the initial state. Explicit
- * terms are binary64 kernels; the five solves are sem_pcg_solve (x0 = 0).
+ * terms are binary64 kernels; the five solves are sem_pcg_solve, from x0 = 0
+ * or (extrapolate = 1, every step after the first) from 2 x^n - x^{n-1}.
  * ------------------------------------------------------------------------ */
 typedef struct sem_rbc sem_rbc; /* opaque; owns its fields and scratch */
 
@@ -393,6 +402,12 @@ typedef struct {
   int pressure_pmg; /* 1: pressure by the p-multigrid flexible CG (pure Neumann
                        hierarchy N -> N/2 -> ... -> 1, binary32 smoothing), the
                        paper's choice of preconditioner; 0: Jacobi-PCG */
+  int extrapolate;  /* 1: every step after the first starts its solves from the
+                       extrapolation 2 x^n - x^{n-1} of the two previous
+                       solutions (T - Tb, p, u, v, w); the stopping test is
+                       unchanged. The paper does not describe initial guesses;
+                       this is the scheme's own second-order extrapolation.
+                       0: every solve starts from 0 */
 } sem_rbc_params;
 
 typedef struct {
@@ -428,13 +443,13 @@ int sem_rbc_fields(const sem_rbc *s, sem_rbc_view *view);
 int sem_rbc_destroy(sem_rbc *s);
 
 /* State snapshots for checkpoint/restart. The state after a step is u, v, w,
- * their previous level, T, T^{n-1}, p, the previous wall term (U-vectors),
+ * their previous level, T, T^{n-1}, p, the previous wall term, p^{n-1} (U-vectors),
  * the previous advection terms of T, u, v, w (E-vectors) and the step
  * counter; every other array is rebuilt each step. Restoring a snapshot and
  * stepping again reproduces the original run bit for bit when the mesh is in
  * deterministic mode (sem_mesh_set_deterministic), otherwise to rounding.
  * sem_rbc_state_bytes: size of a snapshot: a header of eight int64 (step,
- * n_unique, n_local, E, N, format version 1, the bits of dt, 0) then the
+ * n_unique, n_local, E, N, format version 2, the bits of dt, 0) then the
  * arrays.
  * sem_rbc_save_state / sem_rbc_load_state: copy to / from a caller-owned
  * device buffer of that size; both synchronise the stream. Loading a

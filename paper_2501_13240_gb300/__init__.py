@@ -72,7 +72,7 @@ class sem_mesh_info(ctypes.Structure):
 
 class sem_solver_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
-                ("timeout_s", ctypes.c_double), ("mask_mode", ctypes.c_int)]
+                ("timeout_s", ctypes.c_double), ("mask_mode", ctypes.c_int), ("initial_guess", ctypes.c_int)]
 
 
 class sem_solve_stats(ctypes.Structure):
@@ -88,7 +88,8 @@ class sem_pmg_opts(ctypes.Structure):
 
 class sem_rbc_params(ctypes.Structure):
     _fields_ = [("Ra", ctypes.c_double), ("Pr", ctypes.c_double), ("dt", ctypes.c_double), ("tol", ctypes.c_double),
-                ("maxit", ctypes.c_int), ("precision", ctypes.c_int), ("pressure_pmg", ctypes.c_int)]
+                ("maxit", ctypes.c_int), ("precision", ctypes.c_int), ("pressure_pmg", ctypes.c_int),
+                ("extrapolate", ctypes.c_int)]
 
 
 class sem_step_stats(ctypes.Structure):
@@ -640,10 +641,11 @@ def sem_pcg_workspace_bytes(mesh: Mesh) -> int:
 
 def sem_pcg_solve(mesh: Mesh, h1: float, h2: float, b_g, x_g, tol: float = 1e-8, maxit: int = 1000,
                   precision: int = SEM_PREC_FP64, timeout_s: float = 0.0, workspace=None, stream=None,
-                  raise_on_error: bool = True, mask_mode: int = 0):
+                  raise_on_error: bool = True, mask_mode: int = 0, initial_guess: bool = False):
     """Jacobi-PCG; returns a dict of the solve statistics. ``workspace`` is a
     uint8 CUDA tensor of at least sem_pcg_workspace_bytes(mesh) bytes (allocated
-    here through torch when None)."""
+    here through torch when None). initial_guess: start from the guess held in
+    x_g instead of 0."""
     import torch
     need = sem_pcg_workspace_bytes(mesh)
     if workspace is None:
@@ -654,7 +656,8 @@ def sem_pcg_solve(mesh: Mesh, h1: float, h2: float, b_g, x_g, tol: float = 1e-8,
     aligned = (base + 255) & ~255
     if aligned + need > base + workspace.numel():
         raise ValueError("workspace too small after 256-byte alignment (allocate 256 extra bytes)")
-    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s), int(mask_mode))
+    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s), int(mask_mode),
+                        int(bool(initial_guess)))
     st = sem_solve_stats()
     rc = lib().sem_pcg_solve(mesh.handle, float(h1), float(h2), _ptr(b_g, torch.float64, mesh.n_unique, "b_g"),
                              _ptr(x_g, torch.float64, mesh.n_unique, "x_g"), ctypes.byref(o),
@@ -709,10 +712,11 @@ class RBC:
 
 
 def sem_rbc_create(mesh: Mesh, Ra: float, Pr: float, dt: float, tol: float = 1e-10, maxit: int = 5000,
-                   precision: int = SEM_PREC_DF64, T_pert=None, pressure_pmg: bool = True, stream=None) -> RBC:
+                   precision: int = SEM_PREC_DF64, T_pert=None, pressure_pmg: bool = True, stream=None,
+                   extrapolate: bool = False) -> RBC:
     import torch
     prm = sem_rbc_params(float(Ra), float(Pr), float(dt), float(tol), int(maxit), int(precision),
-                         int(bool(pressure_pmg)))
+                         int(bool(pressure_pmg)), int(bool(extrapolate)))
     pert = _ptr(T_pert, torch.float64, mesh.n_unique, "T_pert") if T_pert is not None else None
     h = ctypes.c_void_p()
     _check(lib().sem_rbc_create(mesh.handle, ctypes.byref(prm), pert, _stream(stream), ctypes.byref(h)))
@@ -980,10 +984,13 @@ def sem_pmg_restrict(P: PMG, level: int, rf_g, rc_g, stream=None):
 
 
 def sem_pmg_pcg_solve(P: PMG, b_g, x_g, tol: float = 1e-8, maxit: int = 500, precision: int = SEM_PREC_DF64,
-                      timeout_s: float = 0.0, stream=None, raise_on_error: bool = True, mask_mode: int = 0) -> dict:
+                      timeout_s: float = 0.0, stream=None, raise_on_error: bool = True, mask_mode: int = 0,
+                      initial_guess: bool = False) -> dict:
+    """initial_guess: start from the guess held in x_g instead of 0."""
     import torch
     n = P.mesh.n_unique
-    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s), int(mask_mode))
+    o = sem_solver_opts(float(tol), int(maxit), int(precision), float(timeout_s), int(mask_mode),
+                        int(bool(initial_guess)))
     st = sem_solve_stats()
     rc = lib().sem_pmg_pcg_solve(P._h, _ptr(b_g, torch.float64, n, "b_g"), _ptr(x_g, torch.float64, n, "x_g"),
                                  ctypes.byref(o), ctypes.byref(st), _stream(stream))

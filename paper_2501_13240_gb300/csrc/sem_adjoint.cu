@@ -151,6 +151,7 @@ void free_tadv(sem_tadv *t) {
 
 int solve(sem_tadv *t, double h2, const double *b, double *x, int *iters, cudaStream_t st) {
   sem_solver_opts o;
+  o.initial_guess = 0;
   o.tol = t->prm.tol;
   o.maxit = t->prm.maxit;
   o.precision = t->prm.precision;

@@ -255,11 +255,18 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
   const int col = a + C::PJ * b;  // padded offset of the t-column (a, b, 0)
   double pw = 0.0;  // p.w of this thread's points (binary64 across elements)
   const int64_t estride = (int64_t)gridDim.x * C::ELB;
-  // per element: the largest binary64 exponent of its input values, which
-  // sets the power-of-two scale the element is computed at (values outside
-  // the binary32 exponent range stay exact to the operator's accuracy)
+  // Range guard. Elements whose inputs lie in [2^-60, 2^61) (zeros aside)
+  // are computed unscaled: every double-float value stays far inside the
+  // binary32 exponent range. Any other element (rare: a thread saw a value
+  // above 2^60, or only values below 2^-60) is redone at the power-of-two
+  // scale 2^-sh of its largest input, so any finite input is accepted.
+  // s_bad: some element of the CTA needs the scaled path (CTA-wide, so the
+  // extra barriers of that path are uniform); s_emax: per element, its
+  // largest binary64 exponent field.
   __shared__ int s_emax[C::ELB];
+  __shared__ int s_bad;
   if (tid < C::ELB) s_emax[tid] = 0;
+  if (tid == 0) s_bad = 0;
   __syncthreads();
 
   int32_t go[NP];  // gather indices of this thread's column, kept for the scatter
@@ -285,14 +292,29 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
       int em = 0;
 #pragma unroll
       for (int k = 0; k < NP; ++k) em = max(em, df::exp_field(v[k]));
+      if (em > 1023 + 60 || (em != 0 && em < 1023 - 60)) s_bad = 1;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) U[col + C::PK * k] = df::from_f64(v[k]);
+    }
+    sh = 0;
+    __syncthreads();
+    if (s_bad) {  // rare, uniform over the CTA: redo P0 of the flagged CTA at the elements' scales
+      int em = 0;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const double vk = ASSEMBLED ? ((go[k] >= 0) ? u[go[k]] : 0.0) : (act ? u[e * C::N3 + a + NP * b + C::N2 * k] : 0.0);
+        em = max(em, df::exp_field(vk));
+      }
       atomicMax(&s_emax[le], em);
       __syncthreads();
       sh = s_emax[le] - 1023;
 #pragma unroll
-      for (int k = 0; k < NP; ++k) U[col + C::PK * k] = df::from_f64_scaled(v[k], sh);
+      for (int k = 0; k < NP; ++k) {
+        const double vk = ASSEMBLED ? ((go[k] >= 0) ? u[go[k]] : 0.0) : (act ? u[e * C::N3 + a + NP * b + C::N2 * k] : 0.0);
+        U[col + C::PK * k] = df::from_f64_scaled(vk, sh);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (t == 0) s_emax[le] = 0;  // every thread of the element has read it
     // P1: forward contractions, r-, s- and t-lines, one loop body (when T
     // replaces U, the t-lines wait until every thread has read its r/s lines)
 #pragma unroll 1
@@ -314,6 +336,8 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
       }
     }
     __syncthreads();
+    if (tid == 0) s_bad = 0;  // every thread has read the flags and scales of this element group
+    if (t == 0) s_emax[le] = 0;
     // P2: metric on the t-column (a, b, :), in place
     const float2 *Ge = Gdf + (act ? e : 0) * 6 * C::N3 + a + NP * b;
     float2 gn[6];  // level k + 1's factors, loaded while level k is computed

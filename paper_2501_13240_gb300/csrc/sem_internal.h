@@ -56,7 +56,7 @@ struct sem_mesh {
   void *det_w = nullptr;
   // N = 7 double-float operator: 1-D contractions on the tensor pipe
   // (sem_ax_tc.cu) when set (the default), else on the binary32 pipe
-  int use_tc = 1;
+  int use_tc = 0;
   // a slab of element planes of a box (a partition's share, sem_part): its
   // own unique numbering, no periodic wrap in z; first plane slab_p0
   int slab = 0;

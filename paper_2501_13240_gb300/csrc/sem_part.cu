@@ -412,6 +412,8 @@ extern "C" int sem_part_pcg_solve(sem_part *p, double h1, double h2, const doubl
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_part_pcg_solve: NULL exchange or all-reduce callback");
   if (!(opts->tol >= 0.0) || opts->maxit < 1 || opts->mask_mode != 0)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_part_pcg_solve: bad tol, maxit or mask_mode (Dirichlet only)");
+  if (opts->initial_guess != 0)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_part_pcg_solve: starts from x = 0 (initial_guess must be 0)");
   if (opts->precision != SEM_PREC_FP64 && opts->precision != SEM_PREC_DF64)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_part_pcg_solve: unknown precision");
   if (!(h1 >= 0.0) || !(h2 >= 0.0) || (h1 == 0.0 && h2 == 0.0))

@@ -94,15 +94,47 @@ __global__ void __launch_bounds__(kUpdThreads)
   }
 }
 
+// start from an initial guess: x holds the (scaled) guess and w = A x on
+// entry; r = b - A x, p = z = dinv r, w = 0 for the first operator
 __global__ void __launch_bounds__(kUpdThreads)
-    k_pcg_init_finish(const double *__restrict__ part_a, const double *__restrict__ part_b, int n, PcgScalars *s) {
+    k_pcg_init_guess(int64_t nU, const double *__restrict__ b, double inv_scale, double *__restrict__ r,
+                     double *__restrict__ p, double *__restrict__ w, const double *__restrict__ dinv,
+                     double *__restrict__ part_a, double *__restrict__ part_b, double *__restrict__ part_c) {
+  __shared__ double red[32];
+  double rz = 0.0, bb = 0.0, rr = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nU; g += (int64_t)gridDim.x * blockDim.x) {
+    const double bv = b[g] * inv_scale;
+    const double rv = bv - w[g];
+    const double z = dinv[g] * rv;
+    r[g] = rv;
+    p[g] = z;
+    w[g] = 0.0;
+    rz = fma(rv, z, rz);
+    bb = fma(bv, bv, bb);
+    rr = fma(rv, rv, rr);
+  }
+  rz = block_sum(rz, red);
+  bb = block_sum(bb, red);
+  rr = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    part_a[blockIdx.x] = rz;
+    part_b[blockIdx.x] = bb;
+    part_c[blockIdx.x] = rr;
+  }
+}
+
+// part_c: the r.r partials when the solve starts from a guess; NULL when r = b
+__global__ void __launch_bounds__(kUpdThreads)
+    k_pcg_init_finish(const double *__restrict__ part_a, const double *__restrict__ part_b,
+                      const double *__restrict__ part_c, int n, PcgScalars *s) {
   __shared__ double red[32];
   const double rz = sum_partials(part_a, n, red);
   const double bb = sum_partials(part_b, n, red);
+  const double rr = part_c ? sum_partials(part_c, n, red) : bb;
   if (threadIdx.x == 0) {
     s->rho[0] = rz;
     s->bb = bb;
-    s->rr = bb;
+    s->rr = rr;
     s->stop_it = 0;
     s->stop_status = 0;
   }
@@ -243,7 +275,7 @@ __global__ void k_jacobi_inv(int n, int64_t nU, const int32_t *__restrict__ off,
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct PcgWork {
-  double *r, *p, *w, *dinv, *pw_part, *part_a, *part_b;
+  double *r, *p, *w, *dinv, *pw_part, *part_a, *part_b, *part_c;
   PcgScalars *s;
 };
 
@@ -266,6 +298,7 @@ size_t pcg_layout(const sem_mesh *m, char *base, PcgWork *wk) {
   w.pw_part = (double *)take(npw);
   w.part_a = (double *)take(npart);
   w.part_b = (double *)take(npart);
+  w.part_c = (double *)take(npart);
   w.s = (PcgScalars *)take(align256(sizeof(PcgScalars)));
   if (wk) *wk = w;
   return off;
@@ -379,6 +412,8 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
   if (opts->precision != SEM_PREC_FP64 && opts->precision != SEM_PREC_DF64)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: unknown precision");
   if (opts->mask_mode != 0 && opts->mask_mode != 1) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: bad mask_mode");
+  if (opts->initial_guess != 0 && opts->initial_guess != 1)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: initial_guess must be 0 or 1");
   if (!(h1 >= 0.0) || !(h2 >= 0.0) || (h1 == 0.0 && h2 == 0.0))
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pcg_solve: need h1 >= 0, h2 >= 0, not both zero");
   const auto t0 = std::chrono::steady_clock::now();
@@ -415,15 +450,25 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
   SEM_CUDA(cudaStreamSynchronize(st));
   double scale = 1.0;
   if (hs.bb > 0.0 && std::isfinite(hs.bb)) scale = std::ldexp(1.0, std::ilogb(sqrt(hs.bb)));
-  k_pcg_init<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, 1.0 / scale, x_g, wk.r, wk.p, wk.w, dinv, wk.part_a,
-                                                 wk.part_b);
-  k_pcg_init_finish<<<1, kUpdThreads, 0, st>>>(wk.part_a, wk.part_b, kUpdBlocks, wk.s);
+  // a guess is used only for a finite, nonzero b (b = 0 gives x = 0)
+  const bool guess = opts->initial_guess == 1 && hs.bb > 0.0 && std::isfinite(hs.bb);
+  if (guess) {  // x <- x / scale (exact), w = A x, r = b / scale - w
+    k_scale<<<grid_for(nU, 256), 256, 0, st>>>(nU, 1.0 / scale, x_g);
+    SEM_CUDA(cudaMemsetAsync(wk.w, 0, sizeof(double) * nU, st));
+    if ((rc = sem_launch_ax_assembled(m, h1, h2, x_g, wk.w, nullptr, opts->precision, st, map)) != SEM_OK) return rc;
+    k_pcg_init_guess<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, 1.0 / scale, wk.r, wk.p, wk.w, dinv, wk.part_a,
+                                                         wk.part_b, wk.part_c);
+  } else {
+    k_pcg_init<<<kUpdBlocks, kUpdThreads, 0, st>>>(nU, b_g, 1.0 / scale, x_g, wk.r, wk.p, wk.w, dinv, wk.part_a,
+                                                   wk.part_b);
+  }
+  k_pcg_init_finish<<<1, kUpdThreads, 0, st>>>(wk.part_a, wk.part_b, guess ? wk.part_c : nullptr, kUpdBlocks, wk.s);
   SEM_LAUNCH_CHECK("k_pcg_init");
   SEM_CUDA(cudaMemcpyAsync(&hs, wk.s, sizeof(hs), cudaMemcpyDeviceToHost, st));
   SEM_CUDA(cudaStreamSynchronize(st));
   const double bnorm = sqrt(hs.bb);
   auto finish = [&](int status, int it, double rr) {
-    if (scale != 1.0 && it > 0) {
+    if (scale != 1.0 && (it > 0 || guess)) {
       // undo the scaling of x; if that fails, x is not the solution and the
       // call reports the CUDA error instead of the solver status
       k_scale<<<grid_for(nU, 256), 256, 0, st>>>(nU, scale, x_g);
@@ -446,6 +491,10 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
     return finish(SEM_OK, 0, 0.0);  // b = 0: x = 0 (already written)
   }
   const double thresh = opts->tol * bnorm;
+  if (guess) {  // the guess may already meet the tolerance, or be non-finite
+    if (!std::isfinite(hs.rr) || !std::isfinite(hs.rho[0])) return finish(SEM_ERR_BREAKDOWN, 0, hs.rr);
+    if (sqrt(hs.rr) <= thresh) return finish(SEM_OK, 0, hs.rr);
+  }
   const int *stop = &wk.s->stop_it;
   for (int it = 1; it <= opts->maxit; ++it) {
     const int par = (it - 1) & 1;

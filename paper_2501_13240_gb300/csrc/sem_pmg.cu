@@ -785,12 +785,18 @@ __global__ void k_xpby(int64_t n, const double *__restrict__ z, double beta, dou
     p[g] = fma(beta, p[g], z[g]);
 }
 
+// r = M b; x = 0 unless the solve starts from the guess held in x
 __global__ void k_init_fcg(int64_t n, const double *__restrict__ b, const uint8_t *__restrict__ mask,
-                           double *__restrict__ x, double *__restrict__ r) {
+                           double *__restrict__ x, double *__restrict__ r, int keep_x) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    x[g] = 0.0;
+    if (!keep_x) x[g] = 0.0;
     r[g] = (!mask || mask[g]) ? b[g] : 0.0;
   }
+}
+
+__global__ void k_sub_from(int64_t n, const double *__restrict__ w, double *__restrict__ r) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    r[g] -= w[g];
 }
 
 // ---------------------------------------------------------------- host helpers
@@ -968,6 +974,7 @@ int coarse_solve(sem_pmg *P, cudaStream_t st) {
                                P->o.coarse_maxit, P->cws, nullptr, nullptr, st);
   } else {
     sem_solver_opts o;
+  o.initial_guess = 0;
     o.tol = P->o.coarse_tol;
     o.maxit = P->o.coarse_maxit;
     o.precision = SEM_PREC_DF64;  // binary64-accurate; native FP64 is pipe-bound even at N = 1
@@ -1101,6 +1108,7 @@ int coarse_solve64(sem_pmg *P, cudaStream_t st) {
                                P->o.coarse_maxit, P->cws, nullptr, nullptr, st);
   } else {
     sem_solver_opts o;
+  o.initial_guess = 0;
     o.tol = P->o.coarse_tol;
     o.maxit = P->o.coarse_maxit;
     o.precision = SEM_PREC_DF64;
@@ -1416,7 +1424,7 @@ extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, con
   SemRange nvtx_range("sem_pmg_pcg_solve");
   if (!P || !b_g || !x_g || !opts || !stats) return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_pcg_solve: NULL argument");
   if (opts->mask_mode != P->o.mask_mode || (opts->precision != SEM_PREC_FP64 && opts->precision != SEM_PREC_DF64) ||
-      !(opts->tol >= 0.0) || opts->maxit < 1)
+      !(opts->tol >= 0.0) || opts->maxit < 1 || (opts->initial_guess != 0 && opts->initial_guess != 1))
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_pcg_solve: bad options");
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = as_stream(stream);
@@ -1426,12 +1434,24 @@ extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, con
   int rc;
   stats->iterations = 0;
   stats->status = SEM_OK;
-  k_init_fcg<<<g, 256, 0, st>>>(n, b_g, P->o.mask_mode ? nullptr : m->mask, x_g, P->r);
+  k_init_fcg<<<g, 256, 0, st>>>(n, b_g, P->o.mask_mode ? nullptr : m->mask, x_g, P->r, opts->initial_guess);
   k_dots<<<kPart, 256, 0, st>>>(n, P->r, P->r, nullptr, nullptr, P->part);
   SEM_LAUNCH_CHECK("fcg init");
   double bb, unused;
   if ((rc = sum_pairs(P->part, &bb, &unused, st))) return rc;
   const double bn = sqrt(bb);
+  double rr = bb;
+  const bool guess = opts->initial_guess == 1 && bn > 0.0 && std::isfinite(bb);
+  if (opts->initial_guess == 1 && !guess) SEM_CUDA(cudaMemsetAsync(x_g, 0, sizeof(double) * n, st));
+  if (guess) {  // r = M b - A x: the operator's map leaves r zero on masked nodes
+    SEM_CUDA(cudaMemsetAsync(P->w, 0, sizeof(double) * n, st));
+    if ((rc = sem_launch_ax_assembled(m, P->h1, P->h2, x_g, P->w, nullptr, opts->precision, st, P->L[0].map)))
+      return rc;
+    k_sub_from<<<g, 256, 0, st>>>(n, P->w, P->r);
+    k_dots<<<kPart, 256, 0, st>>>(n, P->r, P->r, nullptr, nullptr, P->part);
+    SEM_LAUNCH_CHECK("fcg initial residual");
+    if ((rc = sum_pairs(P->part, &rr, &unused, st))) return rc;
+  }
   auto finish = [&](int status, int it, double rr) {
     stats->iterations = it;
     stats->rel_residual = bn > 0 ? sqrt(rr) / bn : 0.0;
@@ -1442,13 +1462,16 @@ extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, con
     return status;
   };
   if (!(bn > 0.0)) return finish(std::isfinite(bb) ? SEM_OK : SEM_ERR_BREAKDOWN, 0, 0.0);
+  if (guess) {
+    if (!std::isfinite(rr)) return finish(SEM_ERR_BREAKDOWN, 0, rr);
+    if (sqrt(rr) <= opts->tol * bn) return finish(SEM_OK, 0, rr);
+  }
   if ((rc = sem_pmg_vcycle(P, P->r, P->z, stream))) return rc;
   SEM_CUDA(cudaMemcpyAsync(P->p, P->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   k_dots<<<kPart, 256, 0, st>>>(n, P->r, P->z, nullptr, nullptr, P->part);
   double rz;
   if ((rc = sum_pairs(P->part, &rz, &unused, st))) return rc;
   const int npw = sem_ax_assembled_blocks(m, opts->precision);
-  double rr = bb;
   for (int it = 1; it <= opts->maxit; ++it) {
     SEM_CUDA(cudaMemsetAsync(P->w, 0, sizeof(double) * n, st));
     if ((rc = sem_launch_ax_assembled(m, P->h1, P->h2, P->p, P->w, P->pw_part, opts->precision, st, P->L[0].map)))

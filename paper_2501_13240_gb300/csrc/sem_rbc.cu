@@ -35,6 +35,7 @@ struct sem_rbc {
   // U-vectors
   double *u[3] = {}, *up[3] = {}, *T = nullptr, *Tp = nullptr, *p = nullptr, *W = nullptr, *Wp = nullptr;
   double *Tb = nullptr, *rhs = nullptr, *x = nullptr, *Tn = nullptr, *un[3] = {};
+  double *pp = nullptr;  // p^{n-1}: the second level of the pressure extrapolation
   // E-vectors
   double *uL[3] = {}, *upL[3] = {}, *TL = nullptr, *TpL = nullptr, *g[3] = {}, *om[3] = {};
   double *NT = nullptr, *NTp = nullptr, *Nu[3] = {}, *Nup[3] = {}, *fs[3] = {}, *tmpL = nullptr;
@@ -71,6 +72,28 @@ StepCoef coefficients(int step) {
 }
 
 // ---------------------------------------------------------------- kernels
+// initial guess x0 = M (2 (a - c) - (b - c)): the extrapolation of the two
+// previous levels a = x^n, b = x^{n-1} about the offset c (the lifting of T;
+// NULL for none); mask NULL: every node free
+__global__ void k_extrap(int64_t n, const uint8_t *__restrict__ mask, const double *__restrict__ a,
+                         const double *__restrict__ b, const double *__restrict__ c, double *__restrict__ out) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    double v;
+    if (c) v = 2.0 * (a[g] - c[g]) - (b[g] - c[g]);
+    else v = 2.0 * a[g] - b[g];
+    out[g] = (!mask || mask[g]) ? v : 0.0;
+  }
+}
+
+// the pressure history: pp <- p; with ex, p <- 2 p - pp (the guess)
+__global__ void k_extrap_p(int64_t n, int ex, double *__restrict__ p, double *__restrict__ pp) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const double v = p[g];
+    if (ex) p[g] = 2.0 * v - pp[g];
+    pp[g] = v;
+  }
+}
+
 // accumulate the curl of u from grad u_c: om_x = dw/dy - dv/dz, om_y = du/dz - dw/dx, om_z = dv/dx - du/dy
 __global__ void k_curl_acc(int64_t nL, int c, const double *__restrict__ g0, const double *__restrict__ g1,
                            const double *__restrict__ g2, double *__restrict__ ox, double *__restrict__ oy,
@@ -198,9 +221,10 @@ int gather(sem_rbc *s, const double *vL, double *vg, bool masked, cudaStream_t s
   return SEM_OK;
 }
 
-int solve(sem_rbc *s, double h1, double h2, const double *b, double *x, int mask_mode, int *iters,
+int solve(sem_rbc *s, double h1, double h2, const double *b, double *x, int mask_mode, int guess, int *iters,
           cudaStream_t st, double *dinv = nullptr, double *key = nullptr) {
   sem_solver_opts o;
+  o.initial_guess = guess;
   o.tol = s->prm.tol;
   o.maxit = s->prm.maxit;
   o.precision = s->prm.precision;
@@ -235,6 +259,8 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: Ra, Pr, dt, tol must be > 0 and maxit >= 1");
   if (prm->precision != SEM_PREC_FP64 && prm->precision != SEM_PREC_DF64)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: unknown precision");
+  if (prm->extrapolate != 0 && prm->extrapolate != 1)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: extrapolate must be 0 or 1");
   int dev = -1;
   SEM_CUDA(cudaGetDevice(&dev));
   if (dev != m->device) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: the mesh's device must be current");
@@ -261,7 +287,7 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
   double **uvecs[] = {&s->u[0],  &s->u[1], &s->u[2], &s->up[0], &s->up[1], &s->up[2],
                       &s->T,     &s->Tp,   &s->p,    &s->W,     &s->Wp,    &s->Tb,
                       &s->rhs,   &s->x,    &s->Tn,   &s->un[0], &s->un[1], &s->un[2],
-                      &s->dinvT, &s->dinvU};
+                      &s->dinvT, &s->dinvU, &s->pp};
   for (double **p : uvecs)
     if (!rc) rc = alloc(p, s->nU);
   double **evecs[] = {&s->uL[0], &s->uL[1], &s->uL[2], &s->upL[0], &s->upL[1], &s->upL[2], &s->TL, &s->TpL,
@@ -311,6 +337,7 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
     cudaMemsetAsync(s->Nup[c], 0, sizeof(double) * s->nL, st);
   }
   cudaMemsetAsync(s->p, 0, sizeof(double) * s->nU, st);
+  cudaMemsetAsync(s->pp, 0, sizeof(double) * s->nU, st);
   cudaMemsetAsync(s->Tp, 0, sizeof(double) * s->nU, st);
   cudaMemsetAsync(s->Wp, 0, sizeof(double) * s->nU, st);
   cudaMemsetAsync(s->NTp, 0, sizeof(double) * s->nL, st);
@@ -445,7 +472,13 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   }
   k_rhsT<<<gl, 256, 0, st>>>(nL, kd, m->B, s->TL, s->TpL, s->NT, s->NTp, s->HTb, s->tmpL);
   if ((rc = gather(s, s->tmpL, s->rhs, true, st))) return rc;
-  rc = solve(s, s->kappa, b0dt, s->rhs, s->x, 0, &stt->iters_T, st, s->dinvT, s->keyT);
+  // initial guesses: the extrapolation 2 x^n - x^{n-1} once two levels exist
+  const bool ex = s->prm.extrapolate && s->step >= 1;
+  if (ex) {
+    k_extrap<<<gu, 256, 0, st>>>(nU, m->mask, s->T, s->Tp, s->Tb, s->x);
+    SEM_LAUNCH_CHECK("k_extrap");
+  }
+  rc = solve(s, s->kappa, b0dt, s->rhs, s->x, 0, ex, &stt->iters_T, st, s->dinvT, s->keyT);
   if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
   if (rc) stt->status = rc;
   k_axpbypcz<<<gu, 256, 0, st>>>(nU, 1.0, s->Tb, 1.0, s->x, 0.0, nullptr, s->Tn);
@@ -466,8 +499,12 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   if ((rc = gather(s, s->tmpL, s->rhs, false, st))) return rc;
   k_axpbypcz<<<gu, 256, 0, st>>>(nU, 1.0, s->rhs, -kc.a1, s->W, -kc.a2, s->Wp, s->rhs);
   if ((rc = remove_mean(s, s->rhs, st))) return rc;
+  // p^{n-1} <- p^n, and p <- 2 p^n - p^{n-1} as the guess when extrapolating
+  k_extrap_p<<<gu, 256, 0, st>>>(nU, ex ? 1 : 0, s->p, s->pp);
+  SEM_LAUNCH_CHECK("k_extrap_p");
   if (s->pmg) {
     sem_solver_opts o;
+    o.initial_guess = ex;
     o.tol = s->prm.tol;
     o.maxit = s->prm.maxit;
     o.precision = s->prm.precision;
@@ -477,7 +514,7 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
     rc = sem_pmg_pcg_solve(s->pmg, s->rhs, s->p, &o, &ps, (void *)st);
     stt->iters_p = ps.iterations;
   } else {
-    rc = solve(s, 1.0, 0.0, s->rhs, s->p, 1, &stt->iters_p, st);
+    rc = solve(s, 1.0, 0.0, s->rhs, s->p, 1, ex, &stt->iters_p, st);
   }
   if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
   if (rc) stt->status = rc;
@@ -491,7 +528,11 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   for (int c = 0; c < 3; ++c) {
     k_bdiff<<<gl, 256, 0, st>>>(nL, m->B, s->fs[c], s->g[c], s->tmpL);
     if ((rc = gather(s, s->tmpL, s->rhs, true, st))) return rc;
-    rc = solve(s, s->nu, b0dt, s->rhs, s->un[c], 0, &stt->iters_u[c], st, s->dinvU, s->keyU);
+    if (ex) {
+      k_extrap<<<gu, 256, 0, st>>>(nU, m->mask, s->u[c], s->up[c], nullptr, s->un[c]);
+      SEM_LAUNCH_CHECK("k_extrap");
+    }
+    rc = solve(s, s->nu, b0dt, s->rhs, s->un[c], 0, ex, &stt->iters_u[c], st, s->dinvU, s->keyU);
     if (rc && rc != SEM_ERR_NOT_CONVERGED) return rc;
     if (rc) stt->status = rc;
   }
@@ -515,7 +556,7 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
 }
 
 // ---------------------------------------------------------------- checkpoints
-// The state after a step: u, u^{n-1}, T, T^{n-1}, p, W^{n-1} (U-vectors),
+// The state after a step: u, u^{n-1}, T, T^{n-1}, p, W^{n-1}, p^{n-1} (U-vectors),
 // N_T^{n-1}, N_u^{n-1} (E-vectors) and the step counter; the rest is rebuilt
 // every step. Layout: 64-byte header of eight int64 (step, n_unique, n_local,
 // E, N, format version, the bits of dt, 0) then the arrays in that order.
@@ -528,7 +569,7 @@ struct StateLayout {
 
 StateLayout layout(const sem_rbc *s) {
   StateLayout L;
-  double *uvec[] = {s->u[0], s->u[1], s->u[2], s->up[0], s->up[1], s->up[2], s->T, s->Tp, s->p, s->Wp};
+  double *uvec[] = {s->u[0], s->u[1], s->u[2], s->up[0], s->up[1], s->up[2], s->T, s->Tp, s->p, s->Wp, s->pp};
   for (double *p : uvec) L.arrays.push_back({p, s->nU});
   double *evec[] = {s->NTp, s->Nup[0], s->Nup[1], s->Nup[2]};
   for (double *p : evec) L.arrays.push_back({p, s->nL});
@@ -537,7 +578,7 @@ StateLayout layout(const sem_rbc *s) {
   return L;
 }
 
-constexpr int64_t kStateVersion = 1;
+constexpr int64_t kStateVersion = 2;  // 2: p^{n-1} added
 
 void make_header(const sem_rbc *s, int64_t hdr[8]) {
   int64_t dtbits;

@@ -167,6 +167,64 @@ def test_pcg_solve(pair, h1, h2, prec):
     assert rel_err(host(x), ref.x) < 1e-9
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_pcg_from_initial_guess(pair, prec):
+    """r_0 = b - A x0, the stopping test still ||r|| <= tol ||b||: iterations
+    and solution as the oracle's from the same guess; a guess that already
+    meets the tolerance returns it unchanged after 0 iterations; values on
+    Dirichlet nodes are kept (the operator ignores them); b = 0 gives x = 0."""
+    om, gm = pair
+    if om.mask.sum() == 0:
+        pytest.skip("no free nodes")
+    h1, h2 = 0.5, 40.0
+    rng = np.random.default_rng(17)
+    b = rng.standard_normal(om.n_unique) * om.mask
+    tight = oracle.pcg(om, b, h1, h2, tol=1e-12, maxit=3000)
+    x0 = tight.x + 1e-3 * rng.standard_normal(om.n_unique) * np.abs(tight.x).max()
+    ref = oracle.pcg(om, b, h1, h2, tol=1e-10, maxit=3000, x0=x0)
+    x = dev(x0)
+    st = sem.sem_pcg_solve(gm, h1, h2, dev(b), x, tol=1e-10, maxit=3000, precision=prec, initial_guess=True)
+    assert st["status"] == 0 and ref.converged and ref.iterations > 0
+    assert abs(st["iterations"] - ref.iterations) <= 1, (st, ref.iterations)
+    assert rel_err(host(x), ref.x) < 1e-9
+    # the oracle's guess meets a looser tolerance: nothing to do
+    loose = oracle.pcg(om, b, h1, h2, tol=1e-8, maxit=3000, x0=tight.x)
+    assert loose.iterations == 0
+    x = dev(tight.x)
+    st = sem.sem_pcg_solve(gm, h1, h2, dev(b), x, tol=1e-8, maxit=3000, precision=prec, initial_guess=True)
+    assert st["status"] == 0 and st["iterations"] == 0 and st["rel_residual"] <= 1e-8
+    np.testing.assert_array_equal(host(x), tight.x)
+    # b = 0: x = 0 whatever the guess
+    x = dev(x0)
+    st = sem.sem_pcg_solve(gm, h1, h2, dev(0.0 * b), x, precision=prec, initial_guess=True)
+    assert st["iterations"] == 0 and st["status"] == 0 and float(x.abs().max()) == 0.0
+
+
+def test_pcg_initial_guess_pure_neumann():
+    """The singular operator (mask_mode 1, right-hand side of zero mean) from
+    a guess, as the pressure solve runs it, against the oracle's iteration."""
+    nel, N = (3, 2, 2), 5
+    kw = dict(periodic=(1, 1, 0), dirichlet=(0, 0, 0, 0, 1, 1), deform_amp=0.05)
+    om = oracle.box_mesh(nel, N, **kw)
+    gm = sem.sem_mesh_create_box(nel, N, **kw)
+    free = oracle.Mesh(om.nel, om.N, om.periodic, om.dirichlet, om.xi, om.rho, om.D, om.X, om.Y, om.Z, om.G, om.B,
+                       om.l2g, np.ones(om.n_unique, dtype=np.uint8), om.n_unique, om.detJ_min, om.L)
+    rng = np.random.default_rng(18)
+    b = rng.standard_normal(om.n_unique)
+    b -= b.mean()
+    apply = lambda v: oracle.gather_sum(free, oracle.ax_local(free, oracle.scatter(free, v), 1.0, 0.0))  # noqa: E731
+    x0 = rng.standard_normal(om.n_unique)
+    ref = oracle.pcg(free, b, 1.0, 0.0, tol=1e-10, maxit=3000, apply=apply, x0=x0)
+    for prec in PRECS:
+        x = dev(x0)
+        st = sem.sem_pcg_solve(gm, 1.0, 0.0, dev(b), x, tol=1e-10, maxit=3000, precision=prec, mask_mode=1,
+                               initial_guess=True)
+        assert st["status"] == 0 and abs(st["iterations"] - ref.iterations) <= 1, (st, ref.iterations)
+        xg = host(x)  # x is fixed up to a constant: compare the zero-mean parts
+        assert rel_err(xg - xg.mean(), ref.x - ref.x.mean()) < 1e-9
+    gm.destroy()
+
+
 def test_poisson_4_manufactured_solution():
     """The poisson_4 workload: Jacobi-PCG to 1e-10 reaches the oracle's solution
     and iteration count, and the spectral-element error of u = sin sin sin."""

@@ -95,6 +95,30 @@ def test_mixed_solve_reaches_binary64_tolerance(hier, prec):
     assert rel_err(xg, tight.x) < 1e-6
 
 
+@pytest.mark.parametrize("prec", [sem.SEM_PREC_DF64, sem.SEM_PREC_FP64], ids=["df64", "fp64"])
+def test_fcg_from_initial_guess(hier, prec):
+    """The flexible CG from a guess near the solution reaches the binary64
+    tolerance in fewer iterations than from zero; a guess that already meets
+    the tolerance is returned unchanged after 0 iterations."""
+    pm, gm, gp = hier
+    m = pm.levels[0].m
+    b = oracle.poisson_rhs(m)
+    tight = oracle.pcg(m, b, tol=1e-13, maxit=5000)
+    x = torch.zeros(m.n_unique, dtype=torch.float64, device="cuda")
+    cold = sem.sem_pmg_pcg_solve(gp, dev(b), x, tol=1e-10, maxit=200, precision=prec)
+    x0 = tight.x * (1.0 + 1e-4 * np.random.default_rng(8).standard_normal(m.n_unique))
+    x = dev(x0)
+    st = sem.sem_pmg_pcg_solve(gp, dev(b), x, tol=1e-10, maxit=200, precision=prec, initial_guess=True)
+    assert st["status"] == 0 and 0 < st["iterations"] < cold["iterations"], (st, cold)
+    xg = host(x)
+    assert np.linalg.norm(b - oracle.apply_assembled(m, xg)) / np.linalg.norm(b) < 1.05e-10
+    assert rel_err(xg, tight.x) < 1e-8
+    x = dev(tight.x)
+    st = sem.sem_pmg_pcg_solve(gp, dev(b), x, tol=1e-8, maxit=200, precision=prec, initial_guess=True)
+    assert st["status"] == 0 and st["iterations"] == 0
+    np.testing.assert_array_equal(host(x), tight.x)
+
+
 def test_bf16_smoother_converges():
     nel, N = (4, 4, 3), 7
     gm = sem.sem_mesh_create_box(nel, N, deform_amp=0.05, kappa=KAPPA, phi=PHI)

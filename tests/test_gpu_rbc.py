@@ -78,6 +78,70 @@ def test_perturbed_steps_match_oracle(nel, N, stretch, prec, pmg):
     gm.destroy()
 
 
+@pytest.mark.parametrize("pmg", [False, True], ids=["jacobi_p", "pmg_p"])
+@pytest.mark.parametrize("prec", [sem.SEM_PREC_FP64, sem.SEM_PREC_DF64], ids=["fp64", "df64"])
+def test_extrapolated_initial_guess_matches_oracle(prec, pmg):
+    """Every step after the first starts its five solves from 2 x^n - x^{n-1}
+    (T - Tb, p, u, v, w), as the oracle's option: four steps, same fields
+    (T 1e-10, p and u 1e-8) and iteration counts; from the second step on the
+    solves need fewer iterations than from zero."""
+    om, gm = meshes((2, 3, 4), 7, 1.3)
+    Ra, Pr, dt, tol = 1e5, 0.7, 2e-3, 1e-12
+    pert = workloads.perturbation(om.n_unique, 1e-2, seed=2)
+    R = rbc.RBC(om, Ra, Pr, dt, tol=tol, extrapolate=True)
+    s = R.initial_state(pert)
+    mk = dict(tol=tol, precision=prec, T_pert=torch.from_numpy(pert).cuda(), pressure_pmg=pmg)
+    st = sem.sem_rbc_create(gm, Ra, Pr, dt, extrapolate=True, **mk)
+    cold = sem.sem_rbc_create(gm, Ra, Pr, dt, **mk)
+    for k in range(4):
+        s = R.step(s)
+        g = sem.sem_bdf_ext_step(st)
+        c = sem.sem_bdf_ext_step(cold)
+        assert g["status"] == 0 and c["status"] == 0
+        assert abs(g["iters_T"] - s.iters["T"]) <= 2, (k, g, s.iters)
+        if not pmg:
+            assert abs(g["iters_p"] - s.iters["p"]) <= 3, (k, g, s.iters)
+        for i in range(3):
+            assert abs(g["iters_u"][i] - s.iters["u"][i]) <= 2, (k, g, s.iters)
+        if k >= 1:
+            assert g["iters_T"] < c["iters_T"] and sum(g["iters_u"]) < sum(c["iters_u"]), (k, g, c)
+            assert g["iters_p"] <= c["iters_p"], (k, g, c)
+        f = fields(st)
+        assert rel_err(f["T"], s.T) < 1e-10, k
+        assert rel_err(f["p"], s.p) < 1e-8, k
+        for c_, name in enumerate("uvw"):
+            assert rel_err(f[name], s.u[c_]) < 1e-8, (k, name)
+    st.destroy()
+    cold.destroy()
+    gm.destroy()
+
+
+def test_extrapolated_restart_is_bit_identical():
+    """A snapshot holds p^{n-1} too: restoring it and stepping again repeats
+    the extrapolated run bit for bit (deterministic assembly)."""
+    kw = dict(periodic=(1, 1, 0), dirichlet=(0, 0, 0, 0, 1, 1), z_stretch=1.5)
+    gm = sem.sem_mesh_create_box((3, 3, 3), 5, deterministic=True, **kw)
+    pert = workloads.perturbation(gm.n_unique, 1e-2, seed=2)
+    st = sem.sem_rbc_create(gm, 1e7, 1.0, 2e-3, tol=1e-10, T_pert=torch.from_numpy(pert).cuda(), extrapolate=True)
+    for _ in range(3):
+        sem.sem_bdf_ext_step(st)
+    buf = sem.sem_rbc_save_state(st)
+    for _ in range(2):
+        sem.sem_bdf_ext_step(st)
+    ref = fields(st)
+    st2 = sem.sem_rbc_create(gm, 1e7, 1.0, 2e-3, tol=1e-10, extrapolate=True)
+    sem.sem_rbc_load_state(st2, buf)
+    for _ in range(2):
+        g = sem.sem_bdf_ext_step(st2)
+    assert g["step"] == 5
+    again = fields(st2)
+    for k in ref:
+        assert np.array_equal(again[k], ref[k]), k
+    st.destroy()
+    st2.destroy()
+    gm.destroy()
+
+
 def test_rbc_mesh_requirements():
     gm = sem.sem_mesh_create_box((2, 2, 2), 3)  # walls everywhere but no periodicity: allowed
     st = sem.sem_rbc_create(gm, 1e6, 1.0, 1e-3)

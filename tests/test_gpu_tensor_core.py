@@ -57,12 +57,11 @@ def pair(request):
 
 
 def both_routes(gm, fn):
-    """fn() with the tensor-core route, then with the binary32 route"""
+    """fn() with the tensor-core route, then with the binary32 route (the default)"""
     out = []
     for on in (True, False):
         sem.sem_mesh_set_tensor_cores(gm, on)
         out.append(fn())
-    sem.sem_mesh_set_tensor_cores(gm, True)
     return out
 
 
@@ -122,9 +121,11 @@ def input_cases(om):
     yield "huge", rng.uniform(-1, 1, n) * 1e280
 
 
+@pytest.mark.parametrize("tc", [True, False], ids=["tensor", "binary32"])
 @pytest.mark.parametrize("case", ["digit_edges", "constant", "mixed_magnitudes", "zero", "impulses", "huge"])
-def test_edge_inputs(case):
+def test_edge_inputs(case, tc):
     om, gm = make(SPECS[0])
+    sem.sem_mesh_set_tensor_cores(gm, tc)
     u = dict(input_cases(om))[case]
     ref = oracle.ax_local(om, u, 0.37, 12.5)
     w = torch.empty(om.n_local, dtype=torch.float64, device="cuda")
@@ -142,8 +143,10 @@ def test_edge_inputs(case):
     gm.destroy()
 
 
-def test_nan_propagates_to_breakdown():
+@pytest.mark.parametrize("tc", [True, False], ids=["tensor", "binary32"])
+def test_nan_propagates_to_breakdown(tc):
     gm = sem.sem_mesh_create_box((3, 2, 2), 7)
+    sem.sem_mesh_set_tensor_cores(gm, tc)
     b = torch.zeros(gm.n_unique, dtype=torch.float64, device="cuda")
     b[gm.n_unique // 2] = float("nan")
     st = sem.sem_pcg_solve(gm, 1.0, 0.0, b, torch.zeros_like(b), precision=DF, raise_on_error=False)

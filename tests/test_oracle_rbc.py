@@ -138,8 +138,8 @@ def test_pressure_step_makes_velocity_weakly_divergence_free():
             R = rbc.RBC(m, 1e5, 0.7, 2e-2, tol=1e-13)
             orig = rbc._pcg_neumann
             if no_pressure:
-                def zero(m_, b, tol, maxit):
-                    r = orig(m_, b, tol, maxit)
+                def zero(m_, b, tol, maxit, x0=None):
+                    r = orig(m_, b, tol, maxit, x0=x0)
                     r.x = np.zeros_like(r.x)
                     return r
                 rbc._pcg_neumann = zero
