@@ -243,7 +243,7 @@ int sem_ax_assembled_blocks(const sem_mesh *m, int precision) {
   // element-matrix operator of N = 1 meshes: one element per thread, 128
   // threads per CTA, at most 2 CTAs per SM (few p.w partials to sum)
   if (m->N == 1 && m->K1) return (int)std::max<int64_t>(1, std::min<int64_t>((m->E + 127) / 128, 152 * 2));
-  if (precision == SEM_PREC_DF64) return sem_df64_grid(m);
+  if (precision == SEM_PREC_DF64) return sem_df64_pw_count(m);
   switch (m->n) {
 #define CASE(NPV) \
   case NPV:       \

@@ -230,6 +230,9 @@ struct DfCfg {
   static constexpr int smem_ax(bool helm) { return (helm ? 4 : 3) * TILE * ELB * (int)sizeof(float2); }
   // NP = 8: twelve 64-thread CTAs per SM (at most 85 registers per thread)
   static constexpr int MINB = (NP == 8) ? 12 : 1;
+  // p.w partial sums per CTA: one per warp when the CTA is whole warps (a
+  // shuffle tree each, no CTA barrier), else one per CTA
+  static constexpr int PW_PARTS = (THREADS % 32 == 0) ? THREADS / 32 : 1;
 };
 
 template <int NP, bool ASSEMBLED, bool HELM>
@@ -270,6 +273,7 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
   __syncthreads();
 
   int32_t go[NP];  // gather indices of this thread's column, kept for the scatter
+  float2 uk[NP];   // its (scaled) u values, kept for p.w when T replaces the U tile
   int sh = 0;      // the element's scale: values are carried as x 2^-sh
   for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += estride) {
     const int64_t ei = e0 + le;  // position in the element list (or the element itself)
@@ -294,7 +298,10 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
       for (int k = 0; k < NP; ++k) em = max(em, df::exp_field(v[k]));
       if (em > 1023 + 60 || (em != 0 && em < 1023 - 60)) s_bad = 1;
 #pragma unroll
-      for (int k = 0; k < NP; ++k) U[col + C::PK * k] = df::from_f64(v[k]);
+      for (int k = 0; k < NP; ++k) {
+        uk[k] = df::from_f64(v[k]);
+        U[col + C::PK * k] = uk[k];
+      }
     }
     sh = 0;
     __syncthreads();
@@ -311,7 +318,8 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
         const double vk = ASSEMBLED ? ((go[k] >= 0) ? u[go[k]] : 0.0) : (act ? u[e * C::N3 + a + NP * b + C::N2 * k] : 0.0);
-        U[col + C::PK * k] = df::from_f64_scaled(vk, sh);
+        uk[k] = df::from_f64_scaled(vk, sh);
+        U[col + C::PK * k] = uk[k];
       }
       __syncthreads();
     }
@@ -404,8 +412,8 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
           const int32_t g = go[k];
           if (wloc) wloc[e * C::N3 + p] = (g >= 0) ? vd : 0.0;
           else if (g >= 0) atomicAdd(&w[g], vd);
-          if (pw_partial) {  // u at the point: from U, or gathered again (L2) when T replaced U
-            const float2 xk = HELM ? U[q] : df::from_f64_scaled((g >= 0) ? u[g] : 0.0, sh);
+          if (pw_partial) {  // u at the point: the thread's own values from P0
+            const float2 xk = uk[k];
             df::mac(pwe, xk.x, xk.y, v.x, v.y);
           }
         } else {
@@ -420,20 +428,15 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
     __syncthreads();
   }
   if (ASSEMBLED && pw_partial != nullptr) {
-    // fixed-order CTA sum: a shuffle tree per warp when the CTA is whole
-    // warps, else (a partial warp) a serial sum over shared memory
-    double *red = reinterpret_cast<double *>(sm2);  // the tiles are free after the last barrier
+    // fixed-order sums: a shuffle tree per warp, one partial per warp, when
+    // the CTA is whole warps; else (a partial warp) a serial CTA sum over
+    // shared memory
     double v = pw;
     if constexpr (C::THREADS % 32 == 0) {
       for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if ((tid & 31) == 0) red[tid >> 5] = v;
-      __syncthreads();
-      if (tid == 0) {
-        double s = 0.0;
-        for (int q = 0; q < C::THREADS / 32; ++q) s += red[q];
-        pw_partial[blockIdx.x] = s;
-      }
+      if ((tid & 31) == 0) pw_partial[(int64_t)blockIdx.x * C::PW_PARTS + (tid >> 5)] = v;
     } else {
+      double *red = reinterpret_cast<double *>(sm2);  // the tiles are free after the last barrier
       red[tid] = v;
       __syncthreads();
       if (tid == 0) {
@@ -635,7 +638,7 @@ int launch_field(const sem_mesh *m, const float2 *Rdf, const double *f0, const d
 }
 
 // Grid of the operator: one CTA per element group (with p.w accumulation,
-// one partial sum per CTA, so their number is a property of the mesh)
+// PW_PARTS partial sums per CTA, so their number is a property of the mesh)
 template <int NP>
 int df_grid(const sem_mesh *m, unsigned *grid) {
   using C = DfCfg<NP>;
@@ -681,13 +684,14 @@ int launch_np(const sem_mesh *m, double h1, double h2, const double *u, double *
 
 }  // namespace
 
-int sem_df64_grid(const sem_mesh *m) {
+int sem_df64_pw_count(const sem_mesh *m) {
   unsigned grid = 0;
   int rc = SEM_OK;
   switch (m->n) {
 #define CASE(NPV)                              \
   case NPV:                                    \
     rc = df_grid<NPV>(m, &grid);               \
+    grid *= DfCfg<NPV>::PW_PARTS;              \
     break;
     CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
 #undef CASE

@@ -29,29 +29,24 @@
 // works); the metric outputs v are digit-sliced at a second power-of-two
 // scale 2^-sv of the element's largest |v|.
 //
-// Threads: one element per 64-thread CTA, two warps; lane = 4g + q. A thread
-// owns the 8 points r in {2q, 2q+1}, s = g, t in {4w..4w+3} (w = warp). The
-// digits of a point pair (2q, 2q+1) at one (s, t) are one f16x2 register,
-// which is exactly an mma fragment register:
-//   r-contractions: the digits are the A operand (rows = s of two t-planes,
-//     k = r), D's digits the B operand; the accumulator lands on the
-//     thread's own points;
-//   s-contractions: D's digits are A (rows = s_out, two levels stacked in
-//     the 16 rows), the digits transposed by movmatrix are B (k = s, n = r);
-//     the accumulator lands on the thread's own points;
-//   t-contractions: lines (r, s) cross the two warps, so the digits go
-//     through shared memory (ldmatrix.trans gives B with k = t, n = r); the
-//     results (t_out = g, r = 2q..) go back through shared memory.
-// In the transposed pass the r- and s-contractions accumulate into the same
-// level registers (both land on the thread's points at the same scale).
+// Threads: one element per 128-thread CTA, four warps. In P0, P2 and P4
+// warp w owns the planes t = 2w, 2w + 1 and lane (g, q) the point pair
+// r = 2q, 2q + 1 at s = g of each; the digits of a point pair are one f16x2
+// word. The digits go to shared memory, and each contraction pass works on
+// 24 line groups (three directions x eight planes or rows, six per warp):
+// D's digits are the A operand, held in two fixed register quads so that
+// each accumulator collects digit products of one level, and the group's
+// digits are the B operand, loaded by ldmatrix (.trans where the lines run
+// across the shared-memory rows). Each group's five levels are recombined
+// to double-float and stored to the direction's shared tile.
 //
 // Phases per element:
 //   P0 gather u, element scale su, digits of x (registers and shared memory)
-//   P1 forward contractions (24 mma per warp-level per direction pair) and
-//      recombination to double-float: ur, us in registers, ut via shared
-//   P2 metric (wr, ws, wt) = G (ur, us, ut) in double-float, to shared
-//      memory; element scale sv of the result
-//   P3 transposed contractions: r and s into one level set, t via shared
+//   P1 forward contractions (six mma per line group) and recombination to
+//      double-float: ur, us, ut in the shared tiles
+//   P2 metric (wr, ws, wt) = G (ur, us, ut) in double-float; element scale
+//      sv of the result; digits of the three fields to shared memory
+//   P3 transposed contractions of the three fields into the shared tiles
 //   P4 sum, Helmholtz term, scale back to binary64, scatter (atomics or the
 //      deterministic E-vector), p.w partial
 #include <math.h>
@@ -571,7 +566,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (lane == 0) s_pw[wp] = v;
     __syncthreads();
-    if (tid == 0) pw_partial[blockIdx.x] = (s_pw[0] + s_pw[1]) + (s_pw[2] + s_pw[3]);
+    // the sum-factorised kernel's count of partials: two per element (one
+    // per warp of its 64-thread CTAs); the second slot holds 0
+    if (tid == 0) {
+      pw_partial[2 * (int64_t)blockIdx.x] = (s_pw[0] + s_pw[1]) + (s_pw[2] + s_pw[3]);
+      pw_partial[2 * (int64_t)blockIdx.x + 1] = 0.0;
+    }
   }
 }
 

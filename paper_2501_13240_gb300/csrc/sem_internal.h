@@ -105,7 +105,9 @@ int sem_launch_ax_assembled_list(const sem_mesh *m, double h1, double h2, const 
                                  int precision, cudaStream_t st, const int32_t *elist, int64_t nlist);
 int sem_launch_ax_df64_list(const sem_mesh *m, double h1, double h2, const double *u, double *w, cudaStream_t st,
                             const int32_t *elist, int64_t nlist);
-int sem_df64_grid(const sem_mesh *m);
+// number of p.w partial sums the double-float assembled operator writes (both
+// routes at N = 7: one per warp of the sum-factorised kernel's CTAs)
+int sem_df64_pw_count(const sem_mesh *m);
 int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
                        bool assembled, cudaStream_t st, const int32_t *map, const int *skip = nullptr);
 int sem_launch_ax_tc(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
