@@ -142,7 +142,7 @@ def parse():
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"])
     ap.add_argument("--once", default="",
                     help="profiling mode: comma list of kernels to launch once each on the workload "
-                         "(local_df64, asm_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16, rbc, rbcx), then exit")
+                         "(local_df64, asm_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16, rbc, rbcx, pcg_df64), then exit")
     return ap.parse_args()
 
 
@@ -302,6 +302,12 @@ def run_once(sem, mesh, u, names):
                 print(json.dumps(sem.sem_bdf_ext_step(rs)))
             rs.destroy()
             rm.destroy()
+        elif kind == "pcg":  # 16 Jacobi-PCG iterations (no stopping), for launch lists
+            b = torch.ones_like(u)
+            x = torch.zeros_like(u)
+            st = sem.sem_pcg_solve(mesh, 1.0, 0.0, b, x, tol=0.0, maxit=16, precision=P[prec],
+                                   raise_on_error=False)
+            print(json.dumps(st))
         elif kind == "vcycle":
             sp = {"fp32": sem.SEM_PREC_FP32, "bf16": sem.SEM_PREC_BF16}[prec]
             H = sem.sem_pmg_create(mesh, orders=(mesh.N, 3, 1), smoother_precision=sp, coarse_tol=1e-2)
@@ -342,11 +348,26 @@ def run_solves(sem, mesh, w, runs, tol):
                                    coarse_tol=1e-2, cheb_degree=3 if kind == "pmg3" else 2)
             setup_ms = 1e3 * (time.perf_counter() - t0)
             st = sem.sem_pmg_pcg_solve(P, b, x, tol=tol, maxit=500, precision=prec, raise_on_error=False)
+            # one V-cycle on its own (CUDA events, 5 after one warm-up)
+            z = torch.empty_like(b)
+            sem.sem_pmg_vcycle(P, b, z)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record()
+            for _ in range(5):
+                sem.sem_pmg_vcycle(P, b, z)
+            ev1.record()
+            torch.cuda.synchronize()
+            vcycle_ms = ev0.elapsed_time(ev1) / 5
+            del z
             P.destroy()
         rr = torch.empty_like(b)  # true residual with the binary64 operator
         sem.sem_ax_assembled(mesh, 1.0, 0.0, x, rr, precision=sem.SEM_PREC_FP64)
         true_res = float(torch.linalg.norm(b - rr) / torch.linalg.norm(b))
+        if kind == "jacobi":
+            vcycle_ms = None
         out[name] = {"iterations": st["iterations"], "solve_ms": st["solve_ms"], "setup_ms": setup_ms,
+                     "vcycle_ms": vcycle_ms,
                      "ms_per_iteration": st["solve_ms"] / max(st["iterations"], 1),
                      "rel_residual": st["rel_residual"], "true_rel_residual_fp64": true_res, "status": st["status"]}
         sols[name] = x

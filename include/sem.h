@@ -331,12 +331,16 @@ typedef struct sem_pmg sem_pmg; /* opaque; owns its level meshes and scratch */
 typedef struct {
   int nlevels;            /* 2..4 */
   int orders[4];          /* orders[0] = the fine mesh's N, strictly decreasing, >= 1 */
-  int smoother_precision; /* SEM_PREC_FP32 or SEM_PREC_BF16 (the mixed-precision
-                             preconditioner of Sec. 2.2), or SEM_PREC_DF64: every
-                             smoothing level in binary64 vectors with the
-                             binary64-accurate double-float operator (the same
-                             V-cycle at full precision, to measure what the lower
-                             precision saves) */
+  int smoother_precision; /* the mixed-precision preconditioner of Sec. 2.2:
+                             SEM_PREC_FP32: binary32 vectors, geometry and arithmetic;
+                             SEM_PREC_BF16: binary32 vectors, bfloat16 geometry; at
+                               N = 7 the operator runs on the bfloat16 tensor cores
+                               (two-part bfloat16 operands, binary32 accumulation,
+                               about 2^-15 relative), at other orders in binary32;
+                             SEM_PREC_DF64: every smoothing level in binary64 vectors
+                               with the binary64-accurate double-float operator (the
+                               same V-cycle at full precision, to measure what the
+                               lower precision saves) */
   int cheb_degree;        /* Chebyshev degree (operator applications per smoothing), >= 1 */
   double lambda_safety;   /* factor on the power-iteration estimate of lambda_max (e.g. 1.1) */
   int power_its;          /* power iterations (e.g. 20) */
@@ -363,6 +367,15 @@ int sem_pmg_vcycle(sem_pmg *p, const double *r_g, double *z_g, void *stream);
  * device U-vectors, for tests of the transfer operators. */
 int sem_pmg_prolong(sem_pmg *p, int level, const double *uc_g, double *uf_g, void *stream);
 int sem_pmg_restrict(sem_pmg *p, int level, const double *rf_g, double *rc_g, void *stream);
+
+/* The smoothing operator of level l (l below the coarsest), as the V-cycle
+ * applies it: w_g = M Q^T (h1 A_L + h2 B_L) Q M u_g with the hierarchy's h1,
+ * h2, in the level's smoother precision (binary32 vectors for FP32 and BF16:
+ * u_g is converted to binary32 on the way in, w_g back to binary64; at
+ * N = 7 BF16 is the bfloat16 tensor-core operator). u_g, w_g: device
+ * U-vectors of level l's mesh, binary64, not overlapping. For tests of the
+ * level operators. */
+int sem_pmg_level_apply(sem_pmg *p, int level, const double *u_g, double *w_g, void *stream);
 
 /* Flexible CG preconditioned by one V-cycle per iteration, from x0 = 0 or, with
  * opts.initial_guess = 1, from the guess in x_g (r_0 = M b - A x_g); stops after

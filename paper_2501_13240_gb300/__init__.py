@@ -42,6 +42,7 @@ EXPORTS = (
     "sem_tadv_create", "sem_tadv_destroy", "sem_tadv_info", "sem_tadv_step", "sem_tadv_adjoint_step",
     "sem_tadv_nusselt", "sem_tadv_nusselt_grad", "sem_render_slice", "sem_render_scene", "sem_write_ppm",
     "sem_pmg_create", "sem_pmg_lambda", "sem_pmg_vcycle", "sem_pmg_prolong", "sem_pmg_restrict",
+    "sem_pmg_level_apply",
     "sem_pmg_pcg_solve", "sem_pmg_destroy", "sem_partition_info", "sem_partition_interface",
     "sem_partition_peers", "sem_partition_peer_nodes", "sem_partition_surface",
     "sem_set_grid_wait_limit", "sem_mesh_set_tensor_cores", "sem_part_create", "sem_part_destroy", "sem_part_info",
@@ -211,6 +212,7 @@ def lib() -> ctypes.CDLL:
         sig["sem_pmg_vcycle"] = ([_vp, _vp, _vp, _vp], _i)
         sig["sem_pmg_prolong"] = ([_vp, _i, _vp, _vp, _vp], _i)
         sig["sem_pmg_restrict"] = ([_vp, _i, _vp, _vp, _vp], _i)
+        sig["sem_pmg_level_apply"] = ([_vp, _i, _vp, _vp, _vp], _i)
         sig["sem_pmg_pcg_solve"] = ([_vp, _vp, _vp, ctypes.POINTER(sem_solver_opts), ctypes.POINTER(sem_solve_stats),
                                      _vp], _i)
         sig["sem_pmg_destroy"] = ([_vp], _i)
@@ -981,6 +983,15 @@ def sem_pmg_restrict(P: PMG, level: int, rf_g, rc_g, stream=None):
     _check(lib().sem_pmg_restrict(P._h, int(level), _ptr(rf_g, torch.float64, None, "rf_g"),
                                   _ptr(rc_g, torch.float64, None, "rc_g"), _stream(stream)))
     return rc_g
+
+
+def sem_pmg_level_apply(P: PMG, level: int, u_g, w_g, stream=None):
+    """w_g = the smoothing operator of level `level` applied to u_g (binary64
+    device vectors of that level's mesh), in the level's smoother precision."""
+    import torch
+    _check(lib().sem_pmg_level_apply(P._h, int(level), _ptr(u_g, torch.float64, None, "u_g"),
+                                     _ptr(w_g, torch.float64, None, "w_g"), _stream(stream)))
+    return w_g
 
 
 def sem_pmg_pcg_solve(P: PMG, b_g, x_g, tol: float = 1e-8, maxit: int = 500, precision: int = SEM_PREC_DF64,

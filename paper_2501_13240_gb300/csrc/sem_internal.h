@@ -105,6 +105,13 @@ int sem_launch_ax_assembled_list(const sem_mesh *m, double h1, double h2, const 
                                  int precision, cudaStream_t st, const int32_t *elist, int64_t nlist);
 int sem_launch_ax_df64_list(const sem_mesh *m, double h1, double h2, const double *u, double *w, cudaStream_t st,
                             const int32_t *elist, int64_t nlist);
+// bfloat16 tensor-core operator of the N = 7 smoothing level (sem_ax_bf16.cu):
+// sizes of its lane-major copies (which = 0: geometry; 1: map, and mass),
+// their set-up, and the launch (w += h1 A u + h2 B u, binary32 vectors)
+size_t sem_bf16_layout_bytes(const sem_mesh *m, int which);
+int sem_bf16_pack(const sem_mesh *m, const int32_t *map, void *Gl, void *Ml, void *Bl, cudaStream_t st);
+int sem_launch_ax_bf16(const sem_mesh *m, const void *Gl, const void *Ml, const void *Bl, float h1, float h2,
+                       const float *u, float *w, float *wloc, cudaStream_t st);
 // number of p.w partial sums the double-float assembled operator writes (both
 // routes at N = 7: one per warp of the sum-factorised kernel's CTAs)
 int sem_df64_pw_count(const sem_mesh *m);

@@ -41,6 +41,9 @@ struct PmgLevel {
   float *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *t = nullptr;
   int *err = nullptr;  // set by a kernel whose shared-memory copies did not land (then the persistent
                        // TMA operator is used; NULL selects the plain operator)
+  // bfloat16 smoothing at N = 7: lane-major geometry, map and (Helmholtz)
+  // mass of the tensor-core operator (sem_ax_bf16.cu); NULL otherwise
+  void *Gl = nullptr, *Ml = nullptr, *Bl = nullptr;
   // binary64-accurate smoothing (SEM_PREC_DF64): the level's vectors in
   // binary64 and the double-float operator
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *d64 = nullptr, *t64 = nullptr, *dinv64 = nullptr;
@@ -429,6 +432,12 @@ int launch_ax32_tma(const PmgLevel &lv, const GT *Gp, float h1, float h2, const 
 template <int NP>
 int launch_ax32_np(const PmgLevel &lv, int gprec, float h1, float h2, const float *u, float *w, cudaStream_t st) {
   using C = F32Cfg<NP>;
+  if (lv.Gl) {  // N = 7, bfloat16 smoothing: the tensor-core operator
+    float *wl = (float *)lv.m->det_w;
+    if (int rc = sem_launch_ax_bf16(lv.m, lv.Gl, lv.Ml, lv.Bl, h1, h2, u, w, wl, st)) return rc;
+    if (wl) return sem_launch_gather_add_f(lv.m, wl, w, st);
+    return SEM_OK;
+  }
   if constexpr (NP % 2 == 0 && NP >= 4) {
     if (lv.err) {
       if (gprec == SEM_PREC_BF16) return launch_ax32_tma<NP, __nv_bfloat16>(lv, lv.Gb, h1, h2, u, w, lv.err, st);
@@ -800,9 +809,24 @@ __global__ void k_sub_from(int64_t n, const double *__restrict__ w, double *__re
 }
 
 // ---------------------------------------------------------------- host helpers
-// fixed-order sum of n partials into *out (one CTA of 1024 threads): the
-// outer operator leaves one p.w partial per element group
+// fixed-order sum of n partials into *out (one CTA of 1024 threads); for the
+// outer operator's many p.w partials, first summed in chunks by k_sum_chunks
 constexpr int kSumThreads = 1024;
+__global__ void __launch_bounds__(256) k_sum_chunks(const double *__restrict__ part, int n, int chunk,
+                                                    double *__restrict__ out) {
+  __shared__ double red[8];
+  const int b0 = blockIdx.x * chunk, m = min(chunk, n - b0);
+  double v = 0.0;
+  for (int t = threadIdx.x; t < m; t += 256) v += part[b0 + t];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    out[blockIdx.x] = s;
+  }
+}
 __global__ void __launch_bounds__(kSumThreads) k_sum_fixed(const double *__restrict__ part, int n,
                                                            double *__restrict__ out) {
   __shared__ double red[kSumThreads / 32];
@@ -1261,8 +1285,15 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
       continue;
     }
     if (!coarsest) {
-      if (o->smoother_precision == SEM_PREC_BF16) rc = rc ? rc : alloc((void **)&lv.Gb, sizeof(__nv_bfloat16) * 6 * nL);
-      else rc = rc ? rc : alloc((void **)&lv.Gf, sizeof(float) * 6 * nL);
+      if (o->smoother_precision == SEM_PREC_BF16 && lv.m->n == 8) {  // N = 7: bfloat16 tensor-core operator
+        rc = rc ? rc : alloc(&lv.Gl, sem_bf16_layout_bytes(lv.m, 0));
+        rc = rc ? rc : alloc(&lv.Ml, sem_bf16_layout_bytes(lv.m, 1));
+        if (h2 != 0.0) rc = rc ? rc : alloc(&lv.Bl, sem_bf16_layout_bytes(lv.m, 1));
+      } else if (o->smoother_precision == SEM_PREC_BF16) {
+        rc = rc ? rc : alloc((void **)&lv.Gb, sizeof(__nv_bfloat16) * 6 * nL);
+      } else {
+        rc = rc ? rc : alloc((void **)&lv.Gf, sizeof(float) * 6 * nL);
+      }
       rc = rc ? rc : alloc((void **)&lv.Bf, sizeof(float) * nL);
       rc = rc ? rc : alloc((void **)&lv.Df, sizeof(float) * lv.m->n * lv.m->n);
       rc = rc ? rc : alloc((void **)&lv.dinv, sizeof(float) * nU);
@@ -1294,7 +1325,9 @@ extern "C" int sem_pmg_create(const sem_mesh *m, double h1, double h2, const sem
   for (int l = 0; !p64 && l + 1 < o->nlevels && !rc; ++l) {
     PmgLevel &lv = P->L[l];
     const sem_mesh *lm = lv.m;
-    k_g_to_f32<<<grid_for(6 * lm->n_local, 256), 256, 0, st>>>(6 * lm->n_local, lm->G, lv.Gf, lv.Gb);
+    if (lv.Gl) rc = sem_bf16_pack(lm, lv.map, lv.Gl, lv.Ml, lv.Bl, st);
+    else k_g_to_f32<<<grid_for(6 * lm->n_local, 256), 256, 0, st>>>(6 * lm->n_local, lm->G, lv.Gf, lv.Gb);
+    if (rc) break;
     k_d2f_plain<<<grid_for(lm->n_local, 256), 256, 0, st>>>(lm->n_local, lm->B, lv.Bf);
     k_d2f_plain<<<1, 128, 0, st>>>(lm->n * lm->n, lm->dD, lv.Df);
     k_minv<float><<<grid_for(lm->n_unique, 256), 256, 0, st>>>(lm->n_unique, lm->mult, lv.minv);
@@ -1419,6 +1452,25 @@ extern "C" int sem_pmg_restrict(sem_pmg *P, int level, const double *rf_g, doubl
   return SEM_OK;
 }
 
+extern "C" int sem_pmg_level_apply(sem_pmg *P, int level, const double *u_g, double *w_g, void *stream) {
+  if (!P || !u_g || !w_g || u_g == w_g || level < 0 || level + 1 >= (int)P->L.size())
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_pmg_level_apply: bad argument (smoothing levels only)");
+  cudaStream_t st = as_stream(stream);
+  PmgLevel &lv = P->L[level];
+  const int64_t n = lv.m->n_unique;
+  if (P->o.smoother_precision == SEM_PREC_DF64) {
+    SEM_CUDA(cudaMemsetAsync(w_g, 0, sizeof(double) * n, st));
+    return ax64(P, level, 1.0, u_g, w_g, st);
+  }
+  // the level's scratch vectors d (input) and t (output) are free between V-cycles
+  k_d2f<<<grid_for(n, 256), 256, 0, st>>>(n, u_g, lv.d);
+  SEM_CUDA(cudaMemsetAsync(lv.t, 0, sizeof(float) * n, st));
+  if (int rc = ax32(P, level, 1.0f, lv.d, lv.t, st)) return rc;
+  k_f2d<<<grid_for(n, 256), 256, 0, st>>>(n, lv.t, w_g);
+  SEM_LAUNCH_CHECK("sem_pmg_level_apply");
+  return check_err(P, st);
+}
+
 extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, const sem_solver_opts *opts,
                                  sem_solve_stats *stats, void *stream) {
   SemRange nvtx_range("sem_pmg_pcg_solve");
@@ -1476,7 +1528,12 @@ extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, con
     SEM_CUDA(cudaMemsetAsync(P->w, 0, sizeof(double) * n, st));
     if ((rc = sem_launch_ax_assembled(m, P->h1, P->h2, P->p, P->w, P->pw_part, opts->precision, st, P->L[0].map)))
       return rc;
-    k_sum_fixed<<<1, kSumThreads, 0, st>>>(P->pw_part, npw, P->pw_part + npw);
+    {  // two-level fixed-order sum; P->part (2 kPart doubles) is free until k_dots below
+      const int chunk = std::max(1024, (npw + 2 * kPart - 1) / (2 * kPart));
+      const int nch = std::max(1, (npw + chunk - 1) / chunk);
+      k_sum_chunks<<<nch, 256, 0, st>>>(P->pw_part, npw, chunk, P->part);
+      k_sum_fixed<<<1, kSumThreads, 0, st>>>(P->part, nch, P->pw_part + npw);
+    }
     SEM_LAUNCH_CHECK("k_sum_fixed");
     double pw = 0.0;
     SEM_CUDA(cudaMemcpyAsync(&pw, P->pw_part + npw, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -119,6 +119,56 @@ def test_fcg_from_initial_guess(hier, prec):
     np.testing.assert_array_equal(host(x), tight.x)
 
 
+def bf16_round(x):
+    """binary64 values rounded to the nearest bfloat16 (8 significant bits,
+    ties to even), computed exactly on the bits: the rounding of the
+    operator's inputs, applied before the oracle sees them"""
+    b = np.ascontiguousarray(x, dtype=np.float64).view(np.uint64)
+    lsb = (b >> np.uint64(45)) & np.uint64(1)
+    return ((b + np.uint64((1 << 44) - 1) + lsb) & ~np.uint64((1 << 45) - 1)).view(np.float64)
+
+
+def test_bf16_round_helper():
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -9, -(1.0 + 2.0 ** -9), 3.0 + 2.0 ** -7 + 2.0 ** -30])
+    np.testing.assert_array_equal(bf16_round(x), [1.0, 1.0, 1.0 + 2.0 ** -7, -1.0, 3.0 + 2.0 ** -6])
+
+
+@pytest.mark.parametrize("h2", [0.0, 3.0], ids=["poisson", "helmholtz"])
+@pytest.mark.parametrize("nel", [(3, 3, 2), (4, 3, 3)], ids=["18el", "36el"])
+def test_bf16_tensor_core_level_operator(nel, h2):
+    """The N = 7 bfloat16 smoothing operator (tensor cores, two-part bfloat16
+    operands, binary32 accumulation) element by element against the
+    oracle's operator on the same inputs: G rounded to bfloat16 before the
+    oracle sees it (the level's stored geometry), u binary32 values,
+    binary64 arithmetic.
+
+    Bound, from the kernel's arithmetic: u, D and the metric's outputs
+    (wr, ws) are carried as hi + lo bfloat16 parts, each exact to 2^-17
+    relative, and the lo x lo products are dropped, so the operator is off
+    by at most about 4 x 2^-17 = 2^-15 of |D|^T |G| |D| |u| at each node,
+    plus binary32 accumulation (2^-21 for 16-term sums). The test allows
+    2^-14 |A||u|, |A| the operator with |D|, |G|, |B| entry by entry. 18 and
+    36 elements: a partial last CTA (four elements per CTA) and full ones."""
+    kw = dict(deform_amp=0.05, kappa=KAPPA, phi=PHI)
+    om = oracle.box_mesh(nel, 7, **kw)
+    gm = sem.sem_mesh_create_box(nel, 7, **kw)
+    gp = sem.sem_pmg_create(gm, 1.0, h2, orders=(7, 3, 1), smoother_precision=sem.SEM_PREC_BF16)
+    u = np.random.default_rng(9).uniform(-1, 1, om.n_unique).astype(np.float32).astype(np.float64)
+    w = torch.empty(om.n_unique, dtype=torch.float64, device="cuda")
+    sem.sem_pmg_level_apply(gp, 0, dev(u), w)
+    got = host(w)
+    Gb = bf16_round(om.G)
+    uL = oracle.scatter(om, u * om.mask)
+    ref = oracle.gather_sum(om, oracle.ax_local_raw(7, om.D, Gb, om.B, uL, 1.0, h2)) * om.mask
+    absA = oracle.gather_sum(om, oracle.ax_local_raw(7, np.abs(om.D), np.abs(Gb), np.abs(om.B), np.abs(uL), 1.0,
+                                                     h2)) * om.mask
+    err = np.abs(got - ref)
+    assert (err <= 2.0 ** -14 * absA).all(), float((err / np.maximum(absA, 1e-300)).max())
+    assert (got[om.mask == 0] == 0.0).all()
+    gp.destroy()
+    gm.destroy()
+
+
 def test_bf16_smoother_converges():
     nel, N = (4, 4, 3), 7
     gm = sem.sem_mesh_create_box(nel, N, deform_amp=0.05, kappa=KAPPA, phi=PHI)
