@@ -12,7 +12,8 @@
 // from 12 to 21 on the 64^3 Poisson problem and from 5 to 13-15 in the
 // Rayleigh-Benard pressure solve.
 //
-// One warp per element, everything in registers. Lane (g, q) = (lane / 4,
+// One warp per element at a time; the element's fields stay in registers
+// (inputs arrive through shared memory, see below). Lane (g, q) = (lane / 4,
 // lane % 4) owns the 16 points (i, j, k) = (g, 2q + jj, k), jj = 0, 1,
 // k = 0..7: for every k-plane the pair (j = 2q, 2q + 1) at row i = g, which
 // is both the A-fragment and the accumulator layout of mma m16n8k16, and
@@ -32,7 +33,11 @@
 // Memory per local point: G 12 B and the map 4 B, read as 16-byte vectors
 // from lane-major copies made at set-up, u gathered and w scattered once
 // per unique node (binary32): about 21 B, the same as the bfloat16-geometry
-// binary32 kernel it replaces at this order.
+// binary32 kernel it replaces at this order. The warps are persistent and
+// pipeline two elements each: cp.async brings the next element's u values
+// (through the map) and geometry into one shared-memory slot while the
+// current element is computed from the other. Each lane copies, and later
+// reads, only its own words, so the slots need no barrier.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -141,6 +146,27 @@ __device__ __forceinline__ void split_bf16(float d, float &hi, float &lo) {
   lo = __bfloat162float(__float2bfloat16_rn(d - hi));
 }
 
+// asynchronous global -> shared copies (each lane copies, and later reads, its own words)
+__device__ __forceinline__ void cp16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp4(void *dst, const float *src, bool valid) {  // zero-filled when !valid
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Shared memory per warp: two slots, each one element's lane-major geometry
+// (12 x 32 uint4) and gathered u values (4 x 32 float4, the map's order).
+constexpr int kSlotG = 12 * 32;                       // uint4 per slot
+constexpr int kSlotU = 4 * 32;                        // float4 per slot
+constexpr int kWarpSmem = 2 * (kSlotG + kSlotU) * 16;  // bytes
+constexpr int kSmem = kWarps * kWarpSmem;              // 64 KB per CTA
+
 template <bool HELM>
 __global__ void __launch_bounds__(kWarps * 32, 3)
     k_ax_bf16(int64_t E, const uint4 *__restrict__ Gl, const int4 *__restrict__ Ml, const float4 *__restrict__ Bl,
@@ -161,16 +187,43 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
     Th = pack_bf16(h0, h1v);
     Tl = pack_bf16(l0, l1v);
   }
-  const int64_t estride = (int64_t)gridDim.x * kWarps;
-  for (int64_t e = (int64_t)blockIdx.x * kWarps + warp; e < E; e += estride) {  // warp-uniform
-    // gather u at the lane's 16 points as two-part bfloat16 pairs:
+  // Persistent warps, each over elements e = w0, w0 + nw, ...: while one
+  // element is computed from its slot, the next element's u values (through
+  // the map) and geometry are in flight into the other slot.
+  extern __shared__ __align__(16) uint4 sm4[];
+  uint4 *const wbase = sm4 + warp * (kWarpSmem / 16);  // slot sl: geometry at sl (G + U), then u
+  auto slot_g = [&](int sl) { return wbase + sl * (kSlotG + kSlotU); };
+  auto prefetch = [&](int64_t en, int sl) {
+    float *du = reinterpret_cast<float *>(slot_g(sl) + kSlotG);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int4 mc = __ldg(&Ml[(en * 4 + c) * 32 + lane]);
+      float *d = du + 4 * (c * 32 + lane);
+      cp4(d, u + (mc.x >= 0 ? mc.x : 0), mc.x >= 0);
+      cp4(d + 1, u + (mc.y >= 0 ? mc.y : 0), mc.y >= 0);
+      cp4(d + 2, u + (mc.z >= 0 ? mc.z : 0), mc.z >= 0);
+      cp4(d + 3, u + (mc.w >= 0 ? mc.w : 0), mc.w >= 0);
+    }
+#pragma unroll
+    for (int c = 0; c < 12; ++c) cp16(slot_g(sl) + c * 32 + lane, Gl + (en * 12 + c) * 32 + lane);
+  };
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  int64_t e = (int64_t)blockIdx.x * kWarps + warp;  // warp-uniform
+  if (e < E) prefetch(e, 0);
+  cp_commit();
+  for (int sl = 0; e < E; e += nw, sl ^= 1) {
+    if (e + nw < E) prefetch(e + nw, sl ^ 1);
+    cp_commit();
+    cp_wait_prev();  // this lane's copies of element e have landed
+    const uint4 *sg = slot_g(sl);
+    const float4 *su = reinterpret_cast<const float4 *>(sg + kSlotG);
+    // u at the lane's 16 points as two-part bfloat16 pairs:
     // U[k] + V[k] = (u(g, 2q, k), u(g, 2q+1, k)) to 2^-17
     uint32_t U[NP], V[NP];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int4 mc = Ml[(e * 4 + c) * 32 + lane];
-      const float v00 = mc.x >= 0 ? u[mc.x] : 0.0f, v01 = mc.y >= 0 ? u[mc.y] : 0.0f;
-      const float v10 = mc.z >= 0 ? u[mc.z] : 0.0f, v11 = mc.w >= 0 ? u[mc.w] : 0.0f;
+      const float4 uv = su[c * 32 + lane];
+      const float v00 = uv.x, v01 = uv.y, v10 = uv.z, v11 = uv.w;
       U[2 * c] = pack_bf16(v00, v01);
       U[2 * c + 1] = pack_bf16(v10, v11);
       V[2 * c] = pack_bf16(v00 - bf_lo(U[2 * c]), v01 - bf_hi(U[2 * c]));
@@ -207,9 +260,9 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
       mma_bf16(cs, U[k1], 0u, 0u, U[k2], Fl, Fl);
       mma_bf16(cs, V[k1], 0u, 0u, V[k2], Fh, Fh);
       // metric: factor f of point (kl, jj) is half jj of word 2 (f % 2) + kl of G[f / 2]
-      const uint4 G0 = Gl[(e * 12 + 3 * a) * 32 + lane];
-      const uint4 G1 = Gl[(e * 12 + 3 * a + 1) * 32 + lane];
-      const uint4 G2 = Gl[(e * 12 + 3 * a + 2) * 32 + lane];
+      const uint4 G0 = sg[(3 * a) * 32 + lane];
+      const uint4 G1 = sg[(3 * a + 1) * 32 + lane];
+      const uint4 G2 = sg[(3 * a + 2) * 32 + lane];
       float wr[4], ws[4], wt[4];
 #pragma unroll
       for (int idx = 0; idx < 4; ++idx) {
@@ -251,7 +304,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
     // h1 A u (+ h2 B u) to the lane's points
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int4 mc = Ml[(e * 4 + c) * 32 + lane];  // again (cached): not held across the element
+      const int4 mc = __ldg(&Ml[(e * 4 + c) * 32 + lane]);  // again (cached): not held across the element
       const int gi[4] = {mc.x, mc.y, mc.z, mc.w};
       float bv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       if (HELM) {
@@ -271,6 +324,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
       }
     }
   }
+  cp_wait_all();  // no copy is left in flight when the warp exits
 }
 
 }  // namespace
@@ -301,13 +355,16 @@ int sem_launch_ax_bf16(const sem_mesh *m, const void *Gl, const void *Ml, const 
   if (m->n != NP) return sem_fail(SEM_ERR_INVALID_ARG, "bfloat16 tensor-core operator: N = 7 only");
   if (h2 != 0.0f && !Bl) return sem_fail(SEM_ERR_INVALID_ARG, "bfloat16 tensor-core operator: no mass copy");
   if (int rc = ensure_d8(m->device)) return rc;
-  const unsigned grid = (unsigned)std::max<int64_t>((m->E + kWarps - 1) / kWarps, 1);
-  if (h2 != 0.0f)
-    k_ax_bf16<true><<<grid, kWarps * 32, 0, st>>>(m->E, (const uint4 *)Gl, (const int4 *)Ml, (const float4 *)Bl, h1,
-                                                 h2, u, w, wloc);
-  else
-    k_ax_bf16<false><<<grid, kWarps * 32, 0, st>>>(m->E, (const uint4 *)Gl, (const int4 *)Ml, nullptr, h1, 0.0f, u,
-                                                  w, wloc);
+  auto kern = h2 != 0.0f ? k_ax_bf16<true> : k_ax_bf16<false>;
+  SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  // persistent: the CTAs that fit on the GPU at once, at most one warp per element
+  int per_sm = 0, nsm = 0;
+  SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, kSmem));
+  SEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+  const int64_t need = (m->E + kWarps - 1) / kWarps;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * nsm));
+  kern<<<grid, kWarps * 32, kSmem, st>>>(m->E, (const uint4 *)Gl, (const int4 *)Ml,
+                                         h2 != 0.0f ? (const float4 *)Bl : nullptr, h1, h2, u, w, wloc);
   SEM_LAUNCH_CHECK("k_ax_bf16");
   return SEM_OK;
 }

@@ -169,6 +169,35 @@ def test_bf16_tensor_core_level_operator(nel, h2):
     gm.destroy()
 
 
+@pytest.mark.parametrize("h2", [0.0, 3.0], ids=["poisson", "helmholtz"])
+def test_bf16_vcycle_matches_oracle_on_bf16_geometry(h2):
+    """A bfloat16 V-cycle (tensor-core operator at N = 7, binary32 with
+    bfloat16 geometry at N = 3) element by element against the oracle's
+    V-cycle run on the same bfloat16-rounded geometry of the smoothing
+    levels (lambda_max recomputed from that operator), binary64 arithmetic.
+    Bound: a degree-2 V-cycle applies the level-0 operator four times, each
+    within 2^-15 of |A||v| (see the operator test), and the Chebyshev-Jacobi
+    polynomial is bounded by 1 on the smoother's spectrum: 4 x 2^-15 of
+    max|z|."""
+    nel = (3, 3, 2)
+    box = dict(nel=nel, deform_amp=0.05, kappa=KAPPA, phi=PHI)
+    pm = pmg.PMG(box, orders=(7, 3, 1), h2=h2)
+    for lev in pm.levels[:-1]:  # the smoothing levels' geometry as the library stores it
+        lev.m.G = bf16_round(lev.m.G)
+        lev.lam = 1.1 * pm.lambda_max(lev, 20)
+    gm = sem.sem_mesh_create_box(nel, 7, deform_amp=0.05, kappa=KAPPA, phi=PHI)
+    gp = sem.sem_pmg_create(gm, 1.0, h2, orders=(7, 3, 1), smoother_precision=sem.SEM_PREC_BF16)
+    m = pm.levels[0].m
+    r = np.random.default_rng(6).standard_normal(m.n_unique) * m.mask
+    z = torch.empty(m.n_unique, dtype=torch.float64, device="cuda")
+    sem.sem_pmg_vcycle(gp, dev(r), z)
+    assert rel_err(host(z), pm.vcycle(r)) < 4 * 2.0 ** -15
+    for l in range(2):
+        assert abs(gp.lam(l) - pm.levels[l].lam) <= 1e-3 * pm.levels[l].lam
+    gp.destroy()
+    gm.destroy()
+
+
 def test_bf16_smoother_converges():
     nel, N = (4, 4, 3), 7
     gm = sem.sem_mesh_create_box(nel, N, deform_amp=0.05, kappa=KAPPA, phi=PHI)
