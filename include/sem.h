@@ -69,8 +69,10 @@ enum {
                         coefficients h1, h2 must lie within |x| in
                         [2^-80, 2^100] (binary32 exponent range). */
   SEM_PREC_FP32 = 2, /* binary32 (multigrid smoothing levels) */
-  SEM_PREC_BF16 = 3  /* geometric factors stored as bfloat16, binary32 arithmetic
-                        (multigrid smoothing levels) */
+  SEM_PREC_BF16 = 3  /* multigrid smoothing levels: geometric factors stored as
+                        bfloat16; at N = 7 the operator runs on the bfloat16
+                        tensor cores (two-part bfloat16 operands, binary32
+                        accumulation), at other orders in binary32 */
 };
 
 typedef struct sem_mesh sem_mesh; /* opaque */

@@ -75,7 +75,10 @@ def test_vcycle(hier):
     r = np.random.default_rng(6).standard_normal(m.n_unique) * m.mask
     z = torch.empty(m.n_unique, dtype=torch.float64, device="cuda")
     sem.sem_pmg_vcycle(gp, dev(r), z)
-    assert rel_err(host(z), pm.vcycle(r)) < 1e-4
+    # binary32 smoothing against the binary64 oracle: each operator output
+    # is a sum of about 100 binary32 terms (worst case 100 x 2^-24 = 6e-6 of
+    # |A||v|); measured about 1e-7 of max|z| on these meshes
+    assert rel_err(host(z), pm.vcycle(r)) < 1e-5
 
 
 @pytest.mark.parametrize("prec", [sem.SEM_PREC_DF64, sem.SEM_PREC_FP64], ids=["df64", "fp64"])
