@@ -206,10 +206,15 @@ int sem_mesh_set_deterministic(sem_mesh *m, int on);
  * on = 1 evaluates the 1-D tensor contractions of Sec. 2.2 exactly on the
  * fp16 tensor cores (operands cut into five 10-bit digits on a fixed-point
  * grid per element, digit products summed exactly in binary32 by level,
- * levels recombined to double-float); on = 0 (the default, faster on this
- * GPU) uses the compensated double-float dot products on the binary32 pipe.
- * Both meet the same binary64-level accuracy; the setting exists to compare
- * them. Other orders always use the binary32 route. */
+ * levels recombined to double-float), four warps per element through
+ * shared memory; on = 2 does the r- and s-contractions the same way with one
+ * warp per element entirely in registers (t-lines on the binary32 pipe) for
+ * the Poisson operator (h1 = 1, h2 = 0, the masked map), allocating
+ * lane-major copies of the geometry and map (about 50 B per local point)
+ * and using on = 0 for other calls; on = 0 (the default) uses the
+ * compensated double-float dot products on the binary32 pipe. All meet the
+ * same binary64-level accuracy. Other orders always use the binary32 route.
+ * Synchronises the device when on = 2 first builds its copies. */
 int sem_mesh_set_tensor_cores(sem_mesh *m, int on);
 
 /* Copy l2g (n_local int32) and mask (n_unique uint8) to host arrays; either

@@ -387,10 +387,11 @@ def sem_mesh_set_deterministic(mesh: Mesh, on: bool = True):
     _check(lib().sem_mesh_set_deterministic(mesh.handle, int(bool(on))))
 
 
-def sem_mesh_set_tensor_cores(mesh: Mesh, on: bool = True):
-    """N = 7 double-float operator on the tensor pipe (default) or on the
-    binary32 pipe."""
-    _check(lib().sem_mesh_set_tensor_cores(mesh.handle, int(bool(on))))
+def sem_mesh_set_tensor_cores(mesh: Mesh, on=True):
+    """Route of the N = 7 double-float operator: 0 / False the binary32 pipe,
+    1 / True the tensor cores (four warps per element), 2 the tensor cores
+    with one warp per element in registers (Poisson operator)."""
+    _check(lib().sem_mesh_set_tensor_cores(mesh.handle, int(on)))
 
 
 class Partition:

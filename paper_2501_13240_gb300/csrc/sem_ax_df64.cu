@@ -703,7 +703,9 @@ int sem_df64_pw_count(const sem_mesh *m) {
 
 int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
                        bool assembled, cudaStream_t st, const int32_t *map, const int *skip) {
-  if (m->n == 8 && m->use_tc) return sem_launch_ax_tc(m, h1, h2, u, w, pw_partial, assembled, st, map, skip);
+  if (m->n == 8 && m->use_tc == 1) return sem_launch_ax_tc(m, h1, h2, u, w, pw_partial, assembled, st, map, skip);
+  if (m->n == 8 && m->use_tc == 2 && m->Gt && h1 == 1.0 && h2 == 0.0 && (!assembled || map == m->l2gm))
+    return sem_launch_ax_tcr(m, u, w, pw_partial, assembled, st, skip);
   if (int rc = ensure_tables(m->device)) return rc;
   switch (m->n) {
 #define CASE(NPV) \
@@ -718,7 +720,7 @@ int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u,
 
 int sem_launch_ax_df64_list(const sem_mesh *m, double h1, double h2, const double *u, double *w, cudaStream_t st,
                             const int32_t *elist, int64_t nlist) {
-  if (m->n == 8 && m->use_tc)
+  if (m->n == 8 && m->use_tc == 1)
     return sem_launch_ax_tc(m, h1, h2, u, w, nullptr, true, st, m->l2gm, nullptr, elist, nlist);
   if (int rc = ensure_tables(m->device)) return rc;
   switch (m->n) {

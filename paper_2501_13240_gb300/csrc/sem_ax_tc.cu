@@ -73,6 +73,13 @@ constexpr int kMinBlocks = 5;      // resident 128-thread CTAs per SM the regist
 // [1][j][lane] = (D_j[2q][g], D_j[2q+1][g]) (the transposed contractions)
 __device__ uint32_t g_dig[2][NSL][32];
 
+// The even-odd split of D for the register-resident kernel's t-lines, whose
+// two columns are the lanes of packed instructions: entry [tr][0][i 4 + m] =
+// A (i, m) = (M(i, m) + M(i, 7 - m)) / 2 and [tr][1][...] = Bq = (M(i, m) -
+// M(i, 7 - m)) / 2, M = D (tr 0) or D^T (tr 1), each as (hi, hi, lo, lo) so
+// that one 16-byte load gives both lanes' operands.
+__constant__ float4 c_tq[2][2][16];
+
 std::mutex g_dig_mu;
 unsigned g_dig_ready = 0;  // bit per device
 
@@ -115,6 +122,18 @@ int ensure_digits(int device) {
                                        ((uint32_t)f16_bits_of_int(dig[j][2 * q + 1][g]) << 16);
     }
   SEM_CUDA(cudaMemcpyToSymbol(g_dig, tab.data(), sizeof(uint32_t) * tab.size()));
+  std::vector<float4> tq(2 * 2 * 16);
+  for (int tr = 0; tr < 2; ++tr) {
+    auto M = [&](int i, int m) { return tr ? D[m * NP + i] : D[i * NP + m]; };
+    for (int i = 0; i < 4; ++i)
+      for (int m = 0; m < 4; ++m)
+        for (int ab = 0; ab < 2; ++ab) {
+          const double v = 0.5 * (M(i, m) + (ab ? -1.0 : 1.0) * M(i, NP - 1 - m));
+          const float hi = (float)v, lo = (float)(v - (double)hi);
+          tq[(tr * 2 + ab) * 16 + i * 4 + m] = make_float4(hi, hi, lo, lo);
+        }
+  }
+  SEM_CUDA(cudaMemcpyToSymbol(c_tq, tq.data(), sizeof(float4) * tq.size()));
   if (device < 32) g_dig_ready |= 1u << device;
   return SEM_OK;
 }
@@ -575,6 +594,348 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   }
 }
 
+// ---------------------------------------------------------------- register-resident form
+// One warp per element, the element's fields in registers, no shared-memory
+// tiles and no barriers. Lane (g, q) owns the 16 points (i, j, k) =
+// (g, 2q + jj, k), jj = 0, 1, k = 0..7: in every k-plane the pair
+// (j = 2q, 2q + 1) at row i = g, which is the A-fragment and the
+// accumulator layout of the mma, and the whole k-line of both its (i, j)
+// columns. Two k-planes k1, k2 share one mma against a block-diagonal
+// operand, so each digit product of a plane pair is one mma:
+//   r: A = diag(D_a, D_a), B = the digit planes of x transposed (movmatrix);
+//   s: A = diag(X_b(k1), X_b(k2)), B = [D_a^T; D_a^T];
+// and the accumulator lands on the lane's own points (rows 0-7 plane k1,
+// rows 8-15 plane k2). The t-lines are thread-local: double-float on the
+// binary32 pipe, the two columns as the lanes of packed instructions, with
+// the even-odd split of D. The transposed r and s contractions of a plane
+// pair use one digit scale for wr and ws (their own maximum) and sum into
+// one level set; the transposed t-line is added in double-float.
+__device__ __forceinline__ int rr_point(int lane, int k, int jj) {
+  return (lane >> 2) + 8 * (2 * (lane & 3) + jj) + 64 * k;
+}
+
+// Lane-major geometry: per element, plane pair a = (a, 7 - a), c = 2 f + kl
+// and lane, one uint4 (hi(jj 0), hi(jj 1), lo(jj 0), lo(jj 1)) of factor f
+// at the lane's points of plane a (kl 0) or 7 - a (kl 1); the map as int4 c = (P(2c, 0), P(2c, 1),
+// P(2c + 1, 0), P(2c + 1, 1)). Each uint4 load of a warp reads 512
+// contiguous bytes.
+__global__ void k_tcr_pack(int64_t E, const float2 *__restrict__ Gdf, const int32_t *__restrict__ map,
+                           uint4 *__restrict__ Gt, int4 *__restrict__ Mt) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < E * 32; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t >> 5;
+    const int lane = (int)(t & 31);
+    for (int a = 0; a < 4; ++a)
+      for (int f = 0; f < 6; ++f)
+        for (int kl = 0; kl < 2; ++kl) {
+          const int k = kl ? NP - 1 - a : a;  // the plane pairs are (a, 7 - a)
+          const float2 g0 = Gdf[(e * 6 + f) * N3 + rr_point(lane, k, 0)];
+          const float2 g1 = Gdf[(e * 6 + f) * N3 + rr_point(lane, k, 1)];
+          Gt[((e * 4 + a) * 12 + 2 * f + kl) * 32 + lane] =
+              make_uint4(__float_as_uint(g0.x), __float_as_uint(g1.x), __float_as_uint(g0.y), __float_as_uint(g1.y));
+        }
+    if (map)
+      for (int c = 0; c < 4; ++c)
+        Mt[(e * 4 + c) * 32 + lane] =
+            make_int4(map[e * N3 + rr_point(lane, 2 * c, 0)], map[e * N3 + rr_point(lane, 2 * c, 1)],
+                      map[e * N3 + rr_point(lane, 2 * c + 1, 0)], map[e * N3 + rr_point(lane, 2 * c + 1, 1)]);
+  }
+}
+
+// The t-lines of the lane's two columns (the lanes of packed pairs) with the
+// even-odd split of the double-float kernel's line_apply, each lane doing
+// its scalar operation sequence: the even and odd forms of a line,
+// e_m = x_m + x_{7-m}, o_m = x_m - x_{7-m} (m < 4), then outputs i and
+// 7 - i from the 4-term dot products P = A(i, .) e, Q = Bq(i, .) o:
+// y_i = P + Q, y_{7-i} = Q - P. The coefficients (hi, hi, lo, lo) come from
+// the shared table tq.
+__device__ __forceinline__ void eo_form(float2 xmh, float2 xml, float2 xnh, float2 xnl, float2 &eh, float2 &el,
+                                        float2 &oh, float2 &ol) {
+  float2 s, e;
+  dfx::two_sum(xmh, xnh, s, e);
+  eh = s;
+  el = add2(e, add2(xml, xnl));
+  dfx::two_sum(xmh, neg2(xnh), s, e);
+  oh = s;
+  ol = add2(e, sub2(xml, xnl));
+}
+
+template <bool TR>
+__device__ __forceinline__ void t_outputs(int i, const float2 (&eh)[4], const float2 (&el)[4], const float2 (&oh)[4],
+                                          const float2 (&ol)[4], const float4 (&tq)[2][2][16], float2 &yih,
+                                          float2 &yil, float2 &ymh, float2 &yml) {
+  const float4 *A = tq[TR ? 1 : 0][0], *Bq = tq[TR ? 1 : 0][1];
+  float4 c = A[i * 4];
+  dfx::Acc P = dfx::mul_first(make_float2(c.x, c.y), make_float2(c.z, c.w), eh[0], el[0]);
+  c = Bq[i * 4];
+  dfx::Acc Q = dfx::mul_first(make_float2(c.x, c.y), make_float2(c.z, c.w), oh[0], ol[0]);
+#pragma unroll
+  for (int m = 1; m < 4; ++m) {
+    c = A[i * 4 + m];
+    dfx::mac(P, make_float2(c.x, c.y), make_float2(c.z, c.w), eh[m], el[m]);
+    c = Bq[i * 4 + m];
+    dfx::mac(Q, make_float2(c.x, c.y), make_float2(c.z, c.w), oh[m], ol[m]);
+  }
+  float2 s, e;
+  dfx::two_sum(P.s, Q.s, s, e);
+  const float2 t1 = add2(add2(P.c, Q.c), e);
+  yih = add2(s, t1);  // Fast2Sum
+  yil = sub2(t1, sub2(yih, s));
+  dfx::two_sum(Q.s, neg2(P.s), s, e);
+  const float2 t2 = add2(sub2(Q.c, P.c), e);
+  ymh = add2(s, t2);
+  yml = sub2(t2, sub2(ymh, s));
+}
+
+// a 16-byte global load that stays where it is in the program (the compiler
+// would otherwise hoist all of an element's geometry loads and spill)
+__device__ __forceinline__ uint4 ld_keep(const uint4 *p) {
+  uint4 v;
+  asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+
+// L += A B (m16n8k16, fp16 digits, exact binary32 level sums)
+__device__ __forceinline__ void mma_acc(float4 &L, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                        uint32_t b1) {
+  mma16(L.x, L.y, L.z, L.w, a0, a1, a2, a3, b0, b1, L.x, L.y, L.z, L.w);
+}
+
+// transpose of the 8x8 fp16 matrix whose row g, cols 2q, 2q+1 this lane holds
+__device__ __forceinline__ uint32_t trans8(uint32_t a) {
+  uint32_t d;
+  asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(d) : "r"(a));
+  return d;
+}
+
+// The Poisson operator (h1 = 1, h2 = 0) in the register-resident form,
+// local (E-vectors) or assembled (map through the lane-major copy Mt), with
+// the p.w partial of each element from the energy form u^T A_e u =
+// sum (ur wr + us ws + ut wt) over the element's points. One warp per
+// element (grid = E / 4 CTAs): the partials are [2e] = the element's, [2e + 1] = 0.
+constexpr int kTcrWarpF4 = 2 * 4 * 32 * 2;           // float4 of staging per warp (8 KB: x then r + s, wt)
+constexpr int kTcrSmem = 4 * kTcrWarpF4 * 16;          // bytes per CTA (4 warps)
+
+template <bool ASSEMBLED>
+__global__ void __launch_bounds__(128, 4)
+    k_ax_tcr(int64_t E, const uint4 *__restrict__ Gt, const int4 *__restrict__ Mt, const double *__restrict__ u,
+             double *__restrict__ w, double *__restrict__ pw_partial, double *__restrict__ wloc,
+             const int *__restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
+  __shared__ float4 s_tq[2][2][16];
+  for (int t = threadIdx.x; t < 64; t += blockDim.x) (&s_tq[0][0][0])[t] = (&c_tq[0][0][0])[t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  // per-warp staging, each lane only its own words: x at the plane pairs
+  // (then, in the same slot, the transposed r + s results) and the even-odd
+  // forms of wt, [pair][lane][2] float4 (hi pair, lo pair)
+  extern __shared__ __align__(16) float4 s_stage[];
+  float4 *sx = s_stage + wp * kTcrWarpF4, *so = sx, *sw = sx + 4 * 32 * 2;
+  uint32_t Fd[NSL], Td[NSL];  // D's digits: (D_j[g][2q], D_j[g][2q+1]) and (D_j[2q][g], D_j[2q+1][g])
+#pragma unroll
+  for (int j = 0; j < NSL; ++j) {
+    Fd[j] = g_dig[0][j][lane];
+    Td[j] = g_dig[1][j][lane];
+  }
+  constexpr float scD = (float)kDScale * 0x1p-20f;  // weight of level 0
+  const int64_t e = (int64_t)blockIdx.x * 4 + wp;  // one element per warp
+  if (e >= E) return;                              // no barrier follows
+  if (lane == 0) prefetch_l2(Gt + e * 4 * 12 * 32, 4 * 12 * 32 * 16);  // the element's 24 KB of geometry
+  // P0: gather; the element's scale su (|u| 2^-su < 1)
+  double uv[NP][2];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (ASSEMBLED) {
+      const int4 mc = Mt[(e * 4 + c) * 32 + lane];
+      uv[2 * c][0] = mc.x >= 0 ? u[mc.x] : 0.0;
+      uv[2 * c][1] = mc.y >= 0 ? u[mc.y] : 0.0;
+      uv[2 * c + 1][0] = mc.z >= 0 ? u[mc.z] : 0.0;
+      uv[2 * c + 1][1] = mc.w >= 0 ? u[mc.w] : 0.0;
+    } else {
+#pragma unroll
+      for (int kl = 0; kl < 2; ++kl)
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) uv[2 * c + kl][jj] = u[e * N3 + rr_point(lane, 2 * c + kl, jj)];
+    }
+  }
+  int em = 0;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) em = max(em, max(df::exp_field(uv[k][0]), df::exp_field(uv[k][1])));
+  const int su = __reduce_max_sync(0xffffffffu, em) - 1022;
+  float2 xh[NP], xl[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const float2 x0 = df::from_f64_scaled(uv[k][0], su), x1 = df::from_f64_scaled(uv[k][1], su);
+    xh[k] = make_float2(x0.x, x1.x);
+    xl[k] = make_float2(x0.y, x1.y);
+  }
+  float2 xeh[4], xel[4], xoh[4], xol[4];  // even and odd forms of the x k-lines
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    eo_form(xh[m], xl[m], xh[NP - 1 - m], xl[NP - 1 - m], xeh[m], xel[m], xoh[m], xol[m]);
+    sx[(m * 32 + lane) * 2] = make_float4(xh[m].x, xh[m].y, xl[m].x, xl[m].y);
+    sx[(m * 32 + lane) * 2 + 1] = make_float4(xh[NP - 1 - m].x, xh[NP - 1 - m].y, xl[NP - 1 - m].x, xl[NP - 1 - m].y);
+  }
+  dfx::Acc pwe = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+  // plane pairs (a, 7 - a): stacked in the mma, and the even-odd output pair of the t-lines
+#pragma unroll 1
+  for (int a = 0; a < NP / 2; ++a) {
+    // forward t at the two planes
+    float2 th[2], tl[2];
+    t_outputs<false>(a, xeh, xel, xoh, xol, s_tq, th[0], tl[0], th[1], tl[1]);
+    // digit planes of x at the two planes: (digit at (g, 2q, k), digit at (g, 2q+1, k))
+    uint32_t dx1[NSL], dx2[NSL];
+    {
+      const float4 p1 = sx[(a * 32 + lane) * 2], p2 = sx[(a * 32 + lane) * 2 + 1];
+      digits5(make_float2(p1.x, p1.y), make_float2(p1.z, p1.w), 1024.0f, 1048576.0f, dx1);
+      digits5(make_float2(p2.x, p2.y), make_float2(p2.z, p2.w), 1024.0f, 1048576.0f, dx2);
+    }
+    // forward r: level i + j from D's digit i and x's digit j
+    float2 urh[2], url[2], ush[2], usl[2];
+    {
+      uint32_t b1[NSL], b2[NSL];
+#pragma unroll
+      for (int j = 0; j < NSL; ++j) {
+        b1[j] = trans8(dx1[j]);
+        b2[j] = trans8(dx2[j]);
+      }
+      float4 L[NSL];
+#pragma unroll
+      for (int l = 0; l < NSL; ++l) L[l] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+      for (int i = 0; i < NSL; ++i)
+#pragma unroll
+        for (int j = 0; i + j < NSL; ++j) mma_acc(L[i + j], Fd[i], 0u, 0u, Fd[i], b1[j], b2[j]);
+      recombine(make_float2(L[0].x, L[0].y), make_float2(L[1].x, L[1].y), make_float2(L[2].x, L[2].y),
+                make_float2(L[3].x, L[3].y), make_float2(L[4].x, L[4].y), scD, urh[0], url[0]);
+      recombine(make_float2(L[0].z, L[0].w), make_float2(L[1].z, L[1].w), make_float2(L[2].z, L[2].w),
+                make_float2(L[3].z, L[3].w), make_float2(L[4].z, L[4].w), scD, urh[1], url[1]);
+    }
+    // forward s
+    {
+      float4 L[NSL];
+#pragma unroll
+      for (int l = 0; l < NSL; ++l) L[l] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+      for (int i = 0; i < NSL; ++i)
+#pragma unroll
+        for (int j = 0; i + j < NSL; ++j) mma_acc(L[i + j], dx1[j], 0u, 0u, dx2[j], Fd[i], Fd[i]);
+      recombine(make_float2(L[0].x, L[0].y), make_float2(L[1].x, L[1].y), make_float2(L[2].x, L[2].y),
+                make_float2(L[3].x, L[3].y), make_float2(L[4].x, L[4].y), scD, ush[0], usl[0]);
+      recombine(make_float2(L[0].z, L[0].w), make_float2(L[1].z, L[1].w), make_float2(L[2].z, L[2].w),
+                make_float2(L[3].z, L[3].w), make_float2(L[4].z, L[4].w), scD, ush[1], usl[1]);
+    }
+    // metric at the pair's four points; kl 0 is plane a, kl 1 plane 7 - a
+    float2 wrh[2], wrl[2], wsh[2], wsl[2], wth[2], wtl[2];
+    int ev = 0;
+#pragma unroll
+    for (int kl = 0; kl < 2; ++kl) {
+      float2 gh[6], gl[6];
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        const uint4 G4 = Gt[((e * 4 + a) * 12 + 2 * f + kl) * 32 + lane];
+        gh[f] = make_float2(__uint_as_float(G4.x), __uint_as_float(G4.y));
+        gl[f] = make_float2(__uint_as_float(G4.z), __uint_as_float(G4.w));
+      }
+      const float2 uh[3] = {urh[kl], ush[kl], th[kl]}, ul[3] = {url[kl], usl[kl], tl[kl]};
+      metric_row2(gh, gl, 0, 1, 2, uh, ul, wrh[kl], wrl[kl]);
+      metric_row2(gh, gl, 1, 3, 4, uh, ul, wsh[kl], wsl[kl]);
+      metric_row2(gh, gl, 2, 4, 5, uh, ul, wth[kl], wtl[kl]);
+      ev = max(ev, max(fexp2(wrh[kl]), fexp2(wsh[kl])));
+      if (ASSEMBLED && pw_partial != nullptr) {  // energy form of p.w
+        dfx::mac(pwe, uh[0], ul[0], wrh[kl], wrl[kl]);
+        dfx::mac(pwe, uh[1], ul[1], wsh[kl], wsl[kl]);
+        dfx::mac(pwe, uh[2], ul[2], wth[kl], wtl[kl]);
+      }
+    }
+    {
+      float2 eh, el, oh_, ol_;
+      eo_form(wth[0], wtl[0], wth[1], wtl[1], eh, el, oh_, ol_);
+      sw[(a * 32 + lane) * 2] = make_float4(eh.x, eh.y, el.x, el.y);
+      sw[(a * 32 + lane) * 2 + 1] = make_float4(oh_.x, oh_.y, ol_.x, ol_.y);
+    }
+    // digits of (wr, ws) 2^-sv, |.| <= 1, sv from the plane pair's largest exponent
+    const int sv = max(__reduce_max_sync(0xffffffffu, ev) - 126, -100);
+    const float s1 = pow2f(10 - sv), c2 = pow2f(20 - sv), scV = pow2f(sv - 15);
+    uint32_t dr[2][NSL], ds[2][NSL];
+#pragma unroll
+    for (int kl = 0; kl < 2; ++kl) {
+      digits5(wrh[kl], wrl[kl], s1, c2, dr[kl]);
+      digits5(wsh[kl], wsl[kl], s1, c2, ds[kl]);
+    }
+    // transposed r and s into one level set
+    {
+      float4 L[NSL];
+#pragma unroll
+      for (int l = 0; l < NSL; ++l) L[l] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+      for (int j = 0; j < NSL; ++j) {
+        const uint32_t t1 = trans8(dr[0][j]), t2 = trans8(dr[1][j]);
+#pragma unroll
+        for (int i = 0; i + j < NSL; ++i) mma_acc(L[i + j], Td[i], 0u, 0u, Td[i], t1, t2);
+      }
+#pragma unroll
+      for (int i = 0; i < NSL; ++i)
+#pragma unroll
+        for (int j = 0; i + j < NSL; ++j) mma_acc(L[i + j], ds[0][j], 0u, 0u, ds[1][j], Td[i], Td[i]);
+      float2 o1h, o1l, o2h, o2l;
+      recombine(make_float2(L[0].x, L[0].y), make_float2(L[1].x, L[1].y), make_float2(L[2].x, L[2].y),
+                make_float2(L[3].x, L[3].y), make_float2(L[4].x, L[4].y), scV, o1h, o1l);
+      recombine(make_float2(L[0].z, L[0].w), make_float2(L[1].z, L[1].w), make_float2(L[2].z, L[2].w),
+                make_float2(L[3].z, L[3].w), make_float2(L[4].z, L[4].w), scV, o2h, o2l);
+      so[(a * 32 + lane) * 2] = make_float4(o1h.x, o1h.y, o1l.x, o1l.y);
+      so[(a * 32 + lane) * 2 + 1] = make_float4(o2h.x, o2h.y, o2l.x, o2l.y);
+    }
+  }
+  // transposed t-lines pair by pair, the sum, back to binary64, scatter
+  float2 weh[4], wel[4], woh[4], wol[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const float4 pe = sw[(m * 32 + lane) * 2], po = sw[(m * 32 + lane) * 2 + 1];
+    weh[m] = make_float2(pe.x, pe.y);
+    wel[m] = make_float2(pe.z, pe.w);
+    woh[m] = make_float2(po.x, po.y);
+    wol[m] = make_float2(po.z, po.w);
+  }
+#pragma unroll 1
+  for (int a = 0; a < NP / 2; ++a) {
+    float2 yh[2], yl[2];
+    t_outputs<true>(a, weh, wel, woh, wol, s_tq, yh[0], yl[0], yh[1], yl[1]);
+#pragma unroll
+    for (int kl = 0; kl < 2; ++kl) {
+      const int k = kl ? NP - 1 - a : a;
+      const float4 o4 = so[(a * 32 + lane) * 2 + kl];
+      float2 s_, e_, vh, vl;
+      dfx::two_sum(make_float2(o4.x, o4.y), yh[kl], s_, e_);
+      dfx::two_sum(s_, add2(add2(make_float2(o4.z, o4.w), yl[kl]), e_), vh, vl);
+      const double v0 = df::to_f64_scaled(vh.x, vl.x, su), v1 = df::to_f64_scaled(vh.y, vl.y, su);
+      const int p0 = rr_point(lane, k, 0), p1 = rr_point(lane, k, 1);
+      if (ASSEMBLED) {
+        const int4 mc = Mt[(e * 4 + k / 2) * 32 + lane];  // again (cached)
+        const int g0 = (k & 1) ? mc.z : mc.x, g1 = (k & 1) ? mc.w : mc.y;
+        if (wloc) {
+          wloc[e * N3 + p0] = g0 >= 0 ? v0 : 0.0;
+          wloc[e * N3 + p1] = g1 >= 0 ? v1 : 0.0;
+        } else {
+          if (g0 >= 0) atomicAdd(&w[g0], v0);
+          if (g1 >= 0) atomicAdd(&w[g1], v1);
+        }
+      } else {
+        w[e * N3 + p0] = v0;
+        w[e * N3 + p1] = v1;
+      }
+    }
+  }
+  if (ASSEMBLED && pw_partial != nullptr) {
+    const float2 pa = df::norm(df::Acc{pwe.s.x, pwe.c.x}), pb = df::norm(df::Acc{pwe.s.y, pwe.c.y});
+    double v = df::to_f64_scaled(pa.x, pa.y, 2 * su) + df::to_f64_scaled(pb.x, pb.y, 2 * su);
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) {
+      pw_partial[2 * e] = v;
+      pw_partial[2 * e + 1] = 0.0;
+    }
+  }
+}
+
 }  // namespace
 
 // Launch the tensor-core operator (N = 7 only): same arguments and results as
@@ -604,6 +965,48 @@ int sem_launch_ax_tc(const sem_mesh *m, double h1, double h2, const double *u, d
   }
 #undef LAUNCH
   SEM_LAUNCH_CHECK("k_ax_tc");
+  if (wloc) return sem_launch_gather_add(m, wloc, w, st);
+  return SEM_OK;
+}
+
+// Lane-major copies of the register-resident route (made once per mesh).
+int sem_tcr_prepare(sem_mesh *m, cudaStream_t st) {
+  if (m->n != NP) return sem_fail(SEM_ERR_INVALID_ARG, "tensor-core operator: N = 7 only");
+  if (int rc = ensure_digits(m->device)) return rc;
+  const size_t gbytes = (size_t)m->E * 4 * 12 * 32 * sizeof(uint4), mbytes = (size_t)m->E * 4 * 32 * sizeof(int4);
+  void *Gt = nullptr, *Mt = nullptr;
+  cudaError_t e = cudaMalloc(&Gt, std::max<size_t>(gbytes, 16));
+  if (e == cudaSuccess) e = cudaMalloc(&Mt, std::max<size_t>(mbytes, 16));
+  if (e != cudaSuccess) {
+    if (Gt) cudaFree(Gt);
+    return sem_cuda_fail(e, "sem_mesh_set_tensor_cores: cudaMalloc (lane-major copies)");
+  }
+  k_tcr_pack<<<grid_for(m->E * 32, 256), 256, 0, st>>>(m->E, m->Gdf, m->l2gm, (uint4 *)Gt, (int4 *)Mt);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(Gt);
+    cudaFree(Mt);
+    return sem_cuda_fail(e, "sem_mesh_set_tensor_cores: k_tcr_pack");
+  }
+  m->Gt = Gt;
+  m->Mt = Mt;
+  return SEM_OK;
+}
+
+int sem_launch_ax_tcr(const sem_mesh *m, const double *u, double *w, double *pw_partial, bool assembled,
+                      cudaStream_t st, const int *skip) {
+  if (m->n != NP || !m->Gt) return sem_fail(SEM_ERR_INVALID_ARG, "tensor-core operator: no lane-major copies");
+  if (int rc = ensure_digits(m->device)) return rc;
+  double *wloc = assembled ? (double *)m->det_w : nullptr;
+  auto kern = assembled ? k_ax_tcr<true> : k_ax_tcr<false>;
+  SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcrSmem));
+  // one warp per element (a persistent grid with the next element's u
+  // prefetched by cp.async measured slower: 2.97 vs 2.54 ms on 64^3)
+  const unsigned grid = (unsigned)std::max<int64_t>((m->E + 3) / 4, 1);
+  kern<<<grid, 128, kTcrSmem, st>>>(m->E, (const uint4 *)m->Gt, assembled ? (const int4 *)m->Mt : nullptr, u, w,
+                                    assembled ? pw_partial : nullptr, wloc, skip);
+  SEM_LAUNCH_CHECK("k_ax_tcr");
   if (wloc) return sem_launch_gather_add(m, wloc, w, st);
   return SEM_OK;
 }

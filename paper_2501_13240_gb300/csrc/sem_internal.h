@@ -56,7 +56,8 @@ struct sem_mesh {
   void *det_w = nullptr;
   // N = 7 double-float operator: 1-D contractions on the tensor pipe
   // (sem_ax_tc.cu) when set (the default), else on the binary32 pipe
-  int use_tc = 0;
+  int use_tc = 0;  // N = 7 double-float route: 0 binary32 pipe, 1 tensor cores, 2 tensor cores register-resident
+  void *Gt = nullptr, *Mt = nullptr;  // lane-major geometry and masked map of the register-resident route
   // a slab of element planes of a box (a partition's share, sem_part): its
   // own unique numbering, no periodic wrap in z; first plane slab_p0
   int slab = 0;
@@ -117,6 +118,11 @@ int sem_launch_ax_bf16(const sem_mesh *m, const void *Gl, const void *Ml, const 
 int sem_df64_pw_count(const sem_mesh *m);
 int sem_launch_ax_df64(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
                        bool assembled, cudaStream_t st, const int32_t *map, const int *skip = nullptr);
+// fill the register-resident route's lane-major copies (N = 7)
+int sem_tcr_prepare(sem_mesh *m, cudaStream_t st);
+// the register-resident route: Poisson operator (h1 = 1, h2 = 0), masked map
+int sem_launch_ax_tcr(const sem_mesh *m, const double *u, double *w, double *pw_partial, bool assembled,
+                      cudaStream_t st, const int *skip);
 int sem_launch_ax_tc(const sem_mesh *m, double h1, double h2, const double *u, double *w, double *pw_partial,
                      bool assembled, cudaStream_t st, const int32_t *map, const int *skip,
                      const int32_t *elist = nullptr, int64_t nlist = 0);

@@ -360,7 +360,8 @@ __global__ void k_sort_segments(int64_t nU, const int32_t *off, int32_t *perm, d
 static void free_mesh(sem_mesh *m) {
   if (!m) return;
   void *ptrs[] = {m->X,    m->Y,    m->Z,      m->G,      m->Gdf,  m->B,     m->Bdf, m->l2g,
-                  m->l2gm, m->mask, m->mult,   m->gs_off, m->gs_perm, m->dD, m->det_w, m->K1, m->K1df};
+                  m->l2gm, m->mask, m->mult,   m->gs_off, m->gs_perm, m->dD, m->det_w, m->K1, m->K1df,
+                  m->Gt,   m->Mt};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete m;
@@ -620,7 +621,11 @@ extern "C" int sem_mesh_set_deterministic(sem_mesh *m, int on) {
 
 extern "C" int sem_mesh_set_tensor_cores(sem_mesh *m, int on) {
   if (!m) return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_set_tensor_cores: NULL mesh");
-  m->use_tc = on ? 1 : 0;
+  if (on < 0 || on > 2) return sem_fail(SEM_ERR_INVALID_ARG, "sem_mesh_set_tensor_cores: on must be 0, 1 or 2");
+  if (on == 2 && m->n == 8 && !m->Gt) {  // the register-resident route's lane-major copies
+    if (int rc = sem_tcr_prepare(m, 0)) return rc;
+  }
+  m->use_tc = on;
   return SEM_OK;
 }
 
