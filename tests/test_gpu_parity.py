@@ -200,6 +200,27 @@ def test_pcg_from_initial_guess(pair, prec):
     assert st["iterations"] == 0 and st["status"] == 0 and float(x.abs().max()) == 0.0
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_pcg_guess_edge_cases(prec):
+    """A non-finite guess ends in SEM_ERR_BREAKDOWN with 0 iterations (not a
+    silent result); the flag must be 0 or 1; a zero guess is the cold start
+    (same iterations and solution as initial_guess = False)."""
+    gm = sem.sem_mesh_create_box((2, 2, 2), 5, deform_amp=0.05)
+    om = oracle.box_mesh((2, 2, 2), 5, deform_amp=0.05)
+    b = np.random.default_rng(19).standard_normal(om.n_unique) * om.mask
+    x = torch.zeros(om.n_unique, dtype=torch.float64, device="cuda")
+    x[om.n_unique // 2] = float("nan")
+    st = sem.sem_pcg_solve(gm, 1.0, 0.0, dev(b), x, precision=prec, initial_guess=True, raise_on_error=False)
+    assert st["status"] == sem.SEM_ERR_BREAKDOWN and st["iterations"] == 0
+    cold = torch.zeros_like(x)
+    st0 = sem.sem_pcg_solve(gm, 1.0, 0.0, dev(b), cold, tol=1e-10, precision=prec)
+    warm = torch.zeros_like(x)
+    st1 = sem.sem_pcg_solve(gm, 1.0, 0.0, dev(b), warm, tol=1e-10, precision=prec, initial_guess=True)
+    assert st1["iterations"] == st0["iterations"]
+    assert rel_err(host(warm), host(cold)) < 1e-12
+    gm.destroy()
+
+
 def test_pcg_initial_guess_pure_neumann():
     """The singular operator (mask_mode 1, right-hand side of zero mean) from
     a guess, as the pressure solve runs it, against the oracle's iteration."""

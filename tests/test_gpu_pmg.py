@@ -201,6 +201,28 @@ def test_bf16_vcycle_matches_oracle_on_bf16_geometry(h2):
     gm.destroy()
 
 
+def test_level_apply_arguments():
+    """sem_pmg_level_apply: smoothing levels only, no overlapping vectors;
+    at a binary32 level it equals the oracle's operator to binary32 accuracy."""
+    nel = (2, 2, 2)
+    gm = sem.sem_mesh_create_box(nel, 7, deform_amp=0.05, kappa=KAPPA, phi=PHI)
+    om = oracle.box_mesh(nel, 7, deform_amp=0.05, kappa=KAPPA, phi=PHI)
+    gp = sem.sem_pmg_create(gm, orders=(7, 3, 1))
+    u = torch.from_numpy(np.random.default_rng(12).uniform(-1, 1, om.n_unique)).cuda()
+    w = torch.empty_like(u)
+    for bad in (-1, 2, 3):  # level 2 is the coarsest: no smoother there
+        with pytest.raises(sem.SemError) as ei:
+            sem.sem_pmg_level_apply(gp, bad, u, w)
+        assert ei.value.code == sem.SEM_ERR_INVALID_ARG
+    with pytest.raises(sem.SemError):
+        sem.sem_pmg_level_apply(gp, 0, u, u)
+    sem.sem_pmg_level_apply(gp, 0, u, w)
+    ref = oracle.apply_assembled(om, u.cpu().numpy(), 1.0, 0.0)
+    assert rel_err(host(w), ref) < 1e-5
+    gp.destroy()
+    gm.destroy()
+
+
 def test_bf16_smoother_converges():
     nel, N = (4, 4, 3), 7
     gm = sem.sem_mesh_create_box(nel, N, deform_amp=0.05, kappa=KAPPA, phi=PHI)
