@@ -595,13 +595,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
 }
 
 // ---------------------------------------------------------------- register-resident form
-// One warp per element, the element's fields in registers, no shared-memory
-// tiles and no barriers. Lane (g, q) owns the 16 points (i, j, k) =
+// One warp per element, no tiles shared between threads and no barriers.
+// Each lane stages only its own words in shared memory (x, then the
+// transposed r + s results, and the even-odd forms of wt, per plane pair)
+// so that the plane-pair loops can stay rolled: fully unrolled, the code
+// outgrew the instruction cache. Lane (g, q) owns the 16 points (i, j, k) =
 // (g, 2q + jj, k), jj = 0, 1, k = 0..7: in every k-plane the pair
 // (j = 2q, 2q + 1) at row i = g, which is the A-fragment and the
 // accumulator layout of the mma, and the whole k-line of both its (i, j)
-// columns. Two k-planes k1, k2 share one mma against a block-diagonal
-// operand, so each digit product of a plane pair is one mma:
+// columns. Two k-planes k1, k2 = (a, 7 - a) share one mma against a
+// block-diagonal operand, so each digit product of a plane pair is one mma
+// (and the pair is also the t-line's even-odd output pair):
 //   r: A = diag(D_a, D_a), B = the digit planes of x transposed (movmatrix);
 //   s: A = diag(X_b(k1), X_b(k2)), B = [D_a^T; D_a^T];
 // and the accumulator lands on the lane's own points (rows 0-7 plane k1,
@@ -684,14 +688,6 @@ __device__ __forceinline__ void t_outputs(int i, const float2 (&eh)[4], const fl
   const float2 t2 = add2(sub2(Q.c, P.c), e);
   ymh = add2(s, t2);
   yml = sub2(t2, sub2(ymh, s));
-}
-
-// a 16-byte global load that stays where it is in the program (the compiler
-// would otherwise hoist all of an element's geometry loads and spill)
-__device__ __forceinline__ uint4 ld_keep(const uint4 *p) {
-  uint4 v;
-  asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
-  return v;
 }
 
 // L += A B (m16n8k16, fp16 digits, exact binary32 level sums)
