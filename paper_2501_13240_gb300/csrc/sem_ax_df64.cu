@@ -157,10 +157,12 @@ __device__ __forceinline__ void line_apply(const float2 (&x)[NP], float2 (&y)[NP
 
 // The same contraction for even NP, writing its outputs straight to the
 // shared tile O at base + str m. The even and the odd dot product of each
-// output pair run as the two lanes of packed f32x2 instructions (each lane
-// does exactly the operation sequence of line_apply, so the results are
-// bit-identical to it) with coefficients (A.hi, Bq.hi, A.lo, Bq.lo) from kq;
-// the output loop is rolled pairwise to bound the live registers.
+// output pair run as the two lanes of packed f32x2 instructions with
+// coefficients (A.hi, Bq.hi, A.lo, Bq.lo) from kq, and so do the folding of
+// the inputs (sum and difference of x_m and x_{N-m}) and the final sums of
+// each output pair (P + Q and Q - P). Each lane does exactly the operation
+// sequence of line_apply, so the results are bit-identical to it. The output
+// loop is rolled pairwise to bound the live registers.
 template <int NP, bool TR>
 __device__ __forceinline__ void line_apply_store(const float2 (&x)[NP], float2 *O, int base, int str,
                                                  const float4 *__restrict__ kq) {
@@ -169,14 +171,10 @@ __device__ __forceinline__ void line_apply_store(const float2 (&x)[NP], float2 *
   const float4 *K = kq + (TR ? H * H : 0);
   float2 eh[H], el[H];
 #pragma unroll
-  for (int m = 0; m < H; ++m) {
-    float s, e;
-    df::two_sum(x[m].x, x[N - m].x, s, e);
-    eh[m].x = s;
-    el[m].x = df::add(e, df::add(x[m].y, x[N - m].y));
-    df::two_sum(x[m].x, -x[N - m].x, s, e);
-    eh[m].y = s;
-    el[m].y = df::add(e, df::sub(x[m].y, x[N - m].y));
+  for (int m = 0; m < H; ++m) {  // lane x: x_m + x_{N-m}, lane y: x_m - x_{N-m}
+    const float2 xn = make_float2(x[N - m].x, -x[N - m].x);
+    dfx::two_sum(make_float2(x[m].x, x[m].x), xn, eh[m], el[m]);
+    el[m] = dfx::add(el[m], dfx::add(make_float2(x[m].y, x[m].y), make_float2(x[N - m].y, -x[N - m].y)));
   }
 #pragma unroll 2
   for (int i = 0; i < H; ++i) {
@@ -187,13 +185,14 @@ __device__ __forceinline__ void line_apply_store(const float2 (&x)[NP], float2 *
       k = K[i * H + m];
       dfx::mac(PQ, make_float2(k.x, k.y), make_float2(k.z, k.w), eh[m], el[m]);
     }
-    float s, e, h, l;
-    df::two_sum(PQ.s.x, PQ.s.y, s, e);
-    df::fast_two_sum(s, df::add(df::add(PQ.c.x, PQ.c.y), e), h, l);
-    O[base + str * i] = make_float2(h, l);
-    df::two_sum(PQ.s.y, -PQ.s.x, s, e);
-    df::fast_two_sum(s, df::add(df::sub(PQ.c.y, PQ.c.x), e), h, l);
-    O[base + str * (N - i)] = make_float2(h, l);
+    // lane x: output i = P + Q, lane y: output N - i = Q - P
+    float2 s, e;
+    dfx::two_sum(PQ.s, make_float2(PQ.s.y, -PQ.s.x), s, e);
+    const float2 c = dfx::add(dfx::add(PQ.c, make_float2(PQ.c.y, -PQ.c.x)), e);
+    const float2 h = dfx::add(s, c);
+    const float2 l = dfx::sub(c, dfx::sub(h, s));  // Fast2Sum
+    O[base + str * i] = make_float2(h.x, l.x);
+    O[base + str * (N - i)] = make_float2(h.y, l.y);
   }
 }
 
