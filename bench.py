@@ -50,7 +50,7 @@ TRAFFIC = {"df64": 9.08e9}
 # (smsp__inst_executed.sum x 32 / local points, same ncu capture), and the SM
 # issue limit: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (one warp
 # instruction per scheduler per clock)
-INST_PER_POINT = {"df64": 512.0}
+INST_PER_POINT = {"df64": 491.7}
 ISSUE_PEAK_TINST = 152 * 4 * 32 * 2.07e9 / 1e12
 # binary32 lane operations per local point of the double-float Poisson operator
 # (each packed f32x2 instruction counts two): 6 one-dimensional contractions x
