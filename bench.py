@@ -73,13 +73,13 @@ RBC_UNIT_BYTES = {
     # binary64 operand gather and result scatter of an operator, per unique node
     "op_vec64_unique": 16.0,
     "op_vec32_unique": 8.0,
-    # Jacobi-PCG iteration vectors: update1 reads x r p w dinv, writes x r;
-    # update2 reads r p dinv, writes p w (12 binary64 words)
-    "pcg_vec_unique": 96.0,
-    # flexible-CG iteration vectors: memset w, update (p w x r read, x r
-    # written), r.r, binary64<->binary32 at the V-cycle ends (r read, b
-    # written; x read, z written), r.zn and r.z, p = zn + beta p
-    "fcg_vec_unique": 8 + 48 + 8 + 12 + 12 + 24 + 24,
+    # Jacobi-PCG iteration vectors: update1 reads r w dinv, writes r;
+    # update2 reads x r p dinv, writes x p w (11 binary64 words)
+    "pcg_vec_unique": 88.0,
+    # flexible-CG iteration vectors: update with r.r (p w x r read, x r
+    # written), binary64<->binary32 at the V-cycle ends (r read, b written;
+    # x read, z written), r.zn and r.z, p = zn + beta p with w = 0
+    "fcg_vec_unique": 48 + 12 + 12 + 24 + 32,
     # one V-cycle's smoothing vectors on a level at Chebyshev degree 16, in
     # binary32 words: start 5, 15 x (x, d, r, dinv -> x, d) 6, final x += d 3,
     # two residual copies 2 + 2, scaled start 3, 15 x 6, x += d 3, prolongation
@@ -142,7 +142,7 @@ def parse():
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"])
     ap.add_argument("--once", default="",
                     help="profiling mode: comma list of kernels to launch once each on the workload "
-                         "(local_df64, asm_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16, rbc, rbcx, pcg_df64), then exit")
+                         "(local_df64, asm_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16, pmgsolve_fp32, pmgsolve_bf16, rbc, rbcx, pcg_df64), then exit")
     return ap.parse_args()
 
 
@@ -308,6 +308,14 @@ def run_once(sem, mesh, u, names):
             st = sem.sem_pcg_solve(mesh, 1.0, 0.0, b, x, tol=0.0, maxit=16, precision=P[prec],
                                    raise_on_error=False)
             print(json.dumps(st))
+        elif kind == "pmgsolve":  # 4 p-multigrid flexible-CG iterations (no stopping), for launch lists
+            sp = {"fp32": sem.SEM_PREC_FP32, "bf16": sem.SEM_PREC_BF16}[prec]
+            H = sem.sem_pmg_create(mesh, orders=(mesh.N, 3, 1), smoother_precision=sp, coarse_tol=1e-2)
+            b = torch.ones_like(u)
+            x = torch.zeros_like(u)
+            st = sem.sem_pmg_pcg_solve(H, b, x, tol=0.0, maxit=4, raise_on_error=False)
+            print(json.dumps(st))
+            H.destroy()
         elif kind == "vcycle":
             sp = {"fp32": sem.SEM_PREC_FP32, "bf16": sem.SEM_PREC_BF16}[prec]
             H = sem.sem_pmg_create(mesh, orders=(mesh.N, 3, 1), smoother_precision=sp, coarse_tol=1e-2)
