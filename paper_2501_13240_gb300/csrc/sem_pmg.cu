@@ -577,6 +577,199 @@ __global__ void k_restrict(int nf, int nc, int64_t E, const T *__restrict__ J, c
   }
 }
 
+// The same two transfers with the orders fixed at compile time (the (7, 3)
+// and (3, 1) level pairs): loops unrolled, J in registers, ELB elements per
+// CTA so that a CTA is at least two warps, and the work of the restriction's
+// second and third stages spread over all threads. Every output is the same
+// sequence of multiply-adds as in k_prolong / k_restrict, so the results are
+// bit-identical to theirs.
+template <int NF, int NC>
+struct XferCfg {
+  static constexpr int NT = NF * NF;                    // threads per element
+  static constexpr int ELB = NT >= 64 ? 1 : 64 / NT;    // elements per CTA
+  static constexpr int THREADS = NT * ELB;
+  static constexpr int NC3 = NC * NC * NC, NF3 = NF * NF * NF;
+};
+
+template <typename T, int NF, int NC>
+__global__ void __launch_bounds__(XferCfg<NF, NC>::THREADS)
+    k_prolong_t(int64_t E, const T *__restrict__ Jg, const int32_t *__restrict__ mapc, const T *__restrict__ uc,
+                const int32_t *__restrict__ mapf, T *__restrict__ uf, int accumulate, Owner ow,
+                const T *__restrict__ bf, T *__restrict__ rf) {
+  using C = XferCfg<NF, NC>;
+  __shared__ T tile[C::ELB][C::NC3];
+  T J[NF][NC];
+#pragma unroll
+  for (int a = 0; a < NF; ++a)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) J[a][c] = Jg[a * NC + c];
+  const int le = threadIdx.x / C::NT, tid = threadIdx.x - le * C::NT, i = tid % NF, j = tid / NF;
+  T Ji[NC], Jj[NC];  // this thread's rows (runtime indices: loaded, not indexed from J)
+#pragma unroll
+  for (int a = 0; a < NC; ++a) {
+    Ji[a] = Jg[i * NC + a];
+    Jj[a] = Jg[j * NC + a];
+  }
+  for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += (int64_t)gridDim.x * C::ELB) {
+    const int64_t e = e0 + le;
+    const bool act = e < E;
+    int32_t gk[NF];  // the column's fine map entries, loaded before the coarse tile is awaited
+#pragma unroll
+    for (int k = 0; k < NF; ++k) gk[k] = act ? mapf[e * C::NF3 + i + NF * (j + NF * k)] : -1;
+    __syncthreads();
+    for (int t = tid; t < C::NC3; t += C::NT) {
+      const int32_t g = act ? mapc[e * C::NC3 + t] : -1;
+      tile[le][t] = g >= 0 ? uc[g] : T(0);
+    }
+    __syncthreads();
+    if (!act) continue;
+    T t2[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T sb = T(0);
+#pragma unroll
+      for (int b = 0; b < NC; ++b) {
+        T sa = T(0);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) sa = fma(Ji[a], tile[le][a + NC * (b + NC * c)], sa);
+        sb = fma(Jj[b], sa, sb);
+      }
+      t2[c] = sb;
+    }
+    T sk[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      T s = T(0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) s = fma(J[k][c], t2[c], s);
+      sk[k] = s;
+    }
+    if (!accumulate) {
+#pragma unroll
+      for (int k = 0; k < NF; ++k)
+        if (gk[k] >= 0) uf[gk[k]] = sk[k];
+      continue;
+    }
+    const int64_t ex = e % ow.nel[0], ey = (e / ow.nel[0]) % ow.nel[1], ez = e / ((int64_t)ow.nel[0] * ow.nel[1]);
+    const bool own_ij = (i < NF - 1 || (!ow.per[0] && ex == ow.nel[0] - 1)) &&
+                        (j < NF - 1 || (!ow.per[1] && ey == ow.nel[1] - 1));
+    // the owned points' old values and right-hand sides, all loads first
+    T uo[NF], bo[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const bool own = gk[k] >= 0 && own_ij && (k < NF - 1 || (!ow.per[2] && ez == ow.nel[2] - 1));
+      if (!own) gk[k] = -1;
+      uo[k] = own ? uf[gk[k]] : T(0);
+      bo[k] = own ? bf[gk[k]] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+      if (gk[k] >= 0) {
+        uf[gk[k]] = uo[k] + sk[k];
+        rf[gk[k]] = bo[k];
+      }
+  }
+}
+
+template <typename T, int NF, int NC>
+__global__ void __launch_bounds__(XferCfg<NF, NC>::THREADS)
+    k_restrict_t(int64_t E, const T *__restrict__ Jg, const int32_t *__restrict__ mapf,
+                 const T *__restrict__ minvf, const T *__restrict__ rf, const int32_t *__restrict__ mapc,
+                 T *__restrict__ rc, T *__restrict__ wloc) {
+  using C = XferCfg<NF, NC>;
+  __shared__ T u1[C::ELB][NF * NF * NC];  // [i][j][c]
+  __shared__ T u2[C::ELB][NF * NC * NC];  // [i][b][c]
+  __shared__ T Js[NF * NC];
+  for (int t = threadIdx.x; t < NF * NC; t += C::THREADS) Js[t] = Jg[t];
+  T J[NF][NC];
+#pragma unroll
+  for (int a = 0; a < NF; ++a)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) J[a][c] = Jg[a * NC + c];
+  const int le = threadIdx.x / C::NT, tid = threadIdx.x - le * C::NT, i = tid % NF, j = tid / NF;
+  for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += (int64_t)gridDim.x * C::ELB) {
+    const int64_t e = e0 + le;
+    const bool act = e < E;
+    __syncthreads();
+    if (act) {
+      T v[NF];
+#pragma unroll
+      for (int k = 0; k < NF; ++k) {
+        const int32_t g = mapf[e * C::NF3 + i + NF * (j + NF * k)];
+        v[k] = g >= 0 ? rf[g] * minvf[g] : T(0);
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) s = fma(J[k][c], v[k], s);
+        u1[le][(i * NF + j) * NC + c] = s;
+      }
+    }
+    __syncthreads();
+    if (act) {  // outputs (ii, b, c), spread over the element's threads
+#pragma unroll
+      for (int o = tid; o < NF * NC * NC; o += C::NT) {
+        const int c = o % NC, b = (o / NC) % NC, ii = o / (NC * NC);
+        T s = T(0);
+#pragma unroll
+        for (int jj = 0; jj < NF; ++jj) s = fma(Js[jj * NC + b], u1[le][(ii * NF + jj) * NC + c], s);
+        u2[le][(ii * NC + b) * NC + c] = s;
+      }
+    }
+    __syncthreads();
+    if (act) {  // outputs (a, b, c)
+#pragma unroll
+      for (int o = tid; o < C::NC3; o += C::NT) {
+        const int a = o % NC, b = (o / NC) % NC, c = o / (NC * NC);
+        T s = T(0);
+#pragma unroll
+        for (int ii = 0; ii < NF; ++ii) s = fma(Js[ii * NC + a], u2[le][(ii * NC + b) * NC + c], s);
+        const int64_t lc = e * C::NC3 + a + NC * (b + NC * c);
+        const int32_t g = mapc[lc];
+        if (wloc) wloc[lc] = (g >= 0) ? s : T(0);
+        else if (g >= 0) atomicAdd(&rc[g], s);
+      }
+    }
+  }
+}
+
+// Launch the transfer for the level pair (nf, nc): the compile-time kernels
+// for the pairs they cover, else the general ones.
+template <typename T>
+void launch_prolong(int nf, int nc, int64_t E, const T *J, const int32_t *mapc, const T *uc, const int32_t *mapf,
+                    T *uf, int accumulate, Owner ow, const T *bf, T *rf, cudaStream_t st) {
+  if (nf == 8 && nc == 4) {
+    using C = XferCfg<8, 4>;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((E + C::ELB - 1) / C::ELB, 152 * 256));
+    k_prolong_t<T, 8, 4><<<grid, C::THREADS, 0, st>>>(E, J, mapc, uc, mapf, uf, accumulate, ow, bf, rf);
+  } else if (nf == 4 && nc == 2) {
+    using C = XferCfg<4, 2>;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((E + C::ELB - 1) / C::ELB, 152 * 256));
+    k_prolong_t<T, 4, 2><<<grid, C::THREADS, 0, st>>>(E, J, mapc, uc, mapf, uf, accumulate, ow, bf, rf);
+  } else {
+    const unsigned grid = (unsigned)std::min<int64_t>(E, 152 * 256);
+    k_prolong<T><<<grid, nf * nf, 0, st>>>(nf, nc, E, J, mapc, uc, mapf, uf, accumulate, ow, bf, rf);
+  }
+}
+
+template <typename T>
+void launch_restrict(int nf, int nc, int64_t E, const T *J, const int32_t *mapf, const T *minvf, const T *rf,
+                     const int32_t *mapc, T *rc, T *wloc, cudaStream_t st) {
+  if (nf == 8 && nc == 4) {
+    using C = XferCfg<8, 4>;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((E + C::ELB - 1) / C::ELB, 152 * 256));
+    k_restrict_t<T, 8, 4><<<grid, C::THREADS, 0, st>>>(E, J, mapf, minvf, rf, mapc, rc, wloc);
+  } else if (nf == 4 && nc == 2) {
+    using C = XferCfg<4, 2>;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((E + C::ELB - 1) / C::ELB, 152 * 256));
+    k_restrict_t<T, 4, 2><<<grid, C::THREADS, 0, st>>>(E, J, mapf, minvf, rf, mapc, rc, wloc);
+  } else {
+    const unsigned grid = (unsigned)std::min<int64_t>(E, 152 * 256);
+    k_restrict<T><<<grid, nf * nf, 0, st>>>(nf, nc, E, J, mapf, minvf, rf, mapc, rc, wloc);
+  }
+}
+
 // ---------------------------------------------------------------- vector kernels
 template <typename T>
 __global__ void k_cheb_start(int64_t n, const T *__restrict__ b, const T *__restrict__ dinv, T c0,
@@ -755,7 +948,28 @@ __global__ void k_dots(int64_t n, const double *__restrict__ a, const double *__
                        const double *__restrict__ c, const double *__restrict__ d, double *__restrict__ part) {
   __shared__ double red[2][32];
   double s0 = 0.0, s1 = 0.0;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+  // four nodes per pass with their loads issued first (kPart CTAs leave too
+  // few loads in flight otherwise); each thread keeps the plain loop's order
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; g + 3 * S < n; g += 4 * S) {
+    double av[4], bv[4], cv[4], dv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      av[u] = a[g + u * S];
+      bv[u] = b[g + u * S];
+      if (c) {
+        cv[u] = c[g + u * S];
+        dv[u] = d[g + u * S];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      s0 = fma(av[u], bv[u], s0);
+      if (c) s1 = fma(cv[u], dv[u], s1);
+    }
+  }
+  for (; g < n; g += S) {
     s0 = fma(a[g], b[g], s0);
     if (c) s1 = fma(c[g], d[g], s1);
   }
@@ -779,19 +993,58 @@ __global__ void k_dots(int64_t n, const double *__restrict__ a, const double *__
   }
 }
 
-// x += alpha p; r -= alpha w
+// x += alpha p; r -= alpha w; and the partial sums of r.r of the new r.
+// Launched on kPart blocks of 256 threads, it visits the nodes in the order of
+// k_dots and sums the same way, so the partials are the bits k_dots(r, r)
+// would give (one pass over r less per iteration).
 __global__ void k_fcg_update(int64_t n, double alpha, const double *__restrict__ p, const double *__restrict__ w,
-                             double *__restrict__ x, double *__restrict__ r) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+                             double *__restrict__ x, double *__restrict__ r, double *__restrict__ part) {
+  __shared__ double red[32];
+  double s0 = 0.0;
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; g + 3 * S < n; g += 4 * S) {  // four nodes per pass, loads first (as in k_dots)
+    double pv[4], wv[4], xv[4], rv0[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pv[u] = p[g + u * S];
+      wv[u] = w[g + u * S];
+      xv[u] = x[g + u * S];
+      rv0[u] = r[g + u * S];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[g + u * S] = fma(alpha, pv[u], xv[u]);
+      const double rv = fma(-alpha, wv[u], rv0[u]);
+      r[g + u * S] = rv;
+      s0 = fma(rv, rv, s0);
+    }
+  }
+  for (; g < n; g += S) {
     x[g] = fma(alpha, p[g], x[g]);
-    r[g] = fma(-alpha, w[g], r[g]);
+    const double rv = fma(-alpha, w[g], r[g]);
+    r[g] = rv;
+    s0 = fma(rv, rv, s0);
+  }
+  for (int off = 16; off > 0; off >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0;
+    for (int t = 0; t < (int)(blockDim.x >> 5); ++t) v += red[t];
+    part[2 * blockIdx.x] = v;
+    part[2 * blockIdx.x + 1] = 0.0;
   }
 }
 
-// p = z + beta p
-__global__ void k_xpby(int64_t n, const double *__restrict__ z, double beta, double *__restrict__ p) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+// p = z + beta p; w = 0 for the next operator application (no separate
+// clearing pass)
+__global__ void k_xpby(int64_t n, const double *__restrict__ z, double beta, double *__restrict__ p,
+                       double *__restrict__ w) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     p[g] = fma(beta, p[g], z[g]);
+    w[g] = 0.0;
+  }
 }
 
 // r = M b; x = 0 unless the solve starts from the guess held in x
@@ -912,10 +1165,8 @@ int smooth(sem_pmg *P, int l, bool zero, cudaStream_t st) {
 int restrict_to(sem_pmg *P, int l, const float *rf, float *rc, cudaStream_t st) {
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   SEM_CUDA(cudaMemsetAsync(rc, 0, sizeof(float) * c.m->n_unique, st));
-  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
   float *wloc = (float *)c.m->det_w;
-  k_restrict<float><<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], f.map, f.minv, rf, c.map, rc,
-                                                wloc);
+  launch_restrict<float>(f.m->n, c.m->n, f.m->E, P->J[l], f.map, f.minv, rf, c.map, rc, wloc, st);
   SEM_LAUNCH_CHECK("k_restrict");
   if (wloc) return sem_launch_gather_add_f(c.m, wloc, rc, st);
   return SEM_OK;
@@ -933,9 +1184,7 @@ Owner owner_of(const sem_mesh *m) {
 int prolong_to(sem_pmg *P, int l, const float *uc, float *uf, cudaStream_t st) {
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   SEM_CUDA(cudaMemsetAsync(uf, 0, sizeof(float) * f.m->n_unique, st));
-  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
-  k_prolong<float><<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, uf, 0,
-                                              owner_of(f.m), nullptr, nullptr);
+  launch_prolong<float>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, uf, 0, owner_of(f.m), nullptr, nullptr, st);
   SEM_LAUNCH_CHECK("k_prolong");
   return SEM_OK;
 }
@@ -943,9 +1192,7 @@ int prolong_to(sem_pmg *P, int l, const float *uc, float *uf, cudaStream_t st) {
 // x += P uc and r = b on level l (each unique node once, by its owner copy)
 int prolong_add(sem_pmg *P, int l, const float *uc, float *x, const float *b, float *r, cudaStream_t st) {
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
-  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
-  k_prolong<float><<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, x, 1,
-                                              owner_of(f.m), b, r);
+  launch_prolong<float>(f.m->n, c.m->n, f.m->E, P->J[l], c.map, uc, f.map, x, 1, owner_of(f.m), b, r, st);
   SEM_LAUNCH_CHECK("k_prolong (accumulate)");
   return SEM_OK;
 }
@@ -1101,10 +1348,8 @@ int smooth64(sem_pmg *P, int l, bool zero, cudaStream_t st) {
 int restrict64(sem_pmg *P, int l, const double *rf, double *rc, cudaStream_t st) {
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   SEM_CUDA(cudaMemsetAsync(rc, 0, sizeof(double) * c.m->n_unique, st));
-  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
   double *wloc = (double *)c.m->det_w;
-  k_restrict<double><<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J64[l], f.map, f.minv64, rf,
-                                                        c.map, rc, wloc);
+  launch_restrict<double>(f.m->n, c.m->n, f.m->E, P->J64[l], f.map, f.minv64, rf, c.map, rc, wloc, st);
   SEM_LAUNCH_CHECK("k_restrict (binary64)");
   if (wloc) return sem_launch_gather_add(c.m, wloc, rc, st);
   return SEM_OK;
@@ -1113,9 +1358,8 @@ int restrict64(sem_pmg *P, int l, const double *rf, double *rc, cudaStream_t st)
 int prolong64(sem_pmg *P, int l, const double *uc, double *uf, cudaStream_t st) {
   PmgLevel &f = P->L[l], &c = P->L[l + 1];
   SEM_CUDA(cudaMemsetAsync(uf, 0, sizeof(double) * f.m->n_unique, st));
-  const unsigned grid = (unsigned)std::min<int64_t>(f.m->E, 152 * 256);
-  k_prolong<double><<<grid, f.m->n * f.m->n, 0, st>>>(f.m->n, c.m->n, f.m->E, P->J64[l], c.map, uc, f.map, uf, 0,
-                                                       owner_of(f.m), nullptr, nullptr);
+  launch_prolong<double>(f.m->n, c.m->n, f.m->E, P->J64[l], c.map, uc, f.map, uf, 0, owner_of(f.m), nullptr, nullptr,
+                         st);
   SEM_LAUNCH_CHECK("k_prolong (binary64)");
   return SEM_OK;
 }
@@ -1524,8 +1768,8 @@ extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, con
   double rz;
   if ((rc = sum_pairs(P->part, &rz, &unused, st))) return rc;
   const int npw = sem_ax_assembled_blocks(m, opts->precision);
+  SEM_CUDA(cudaMemsetAsync(P->w, 0, sizeof(double) * n, st));  // later iterations: cleared by k_xpby
   for (int it = 1; it <= opts->maxit; ++it) {
-    SEM_CUDA(cudaMemsetAsync(P->w, 0, sizeof(double) * n, st));
     if ((rc = sem_launch_ax_assembled(m, P->h1, P->h2, P->p, P->w, P->pw_part, opts->precision, st, P->L[0].map)))
       return rc;
     {  // two-level fixed-order sum; P->part (2 kPart doubles) is free until k_dots below
@@ -1540,8 +1784,7 @@ extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, con
     SEM_CUDA(cudaStreamSynchronize(st));
     if (!(pw > 0.0) || !std::isfinite(pw)) return finish(SEM_ERR_BREAKDOWN, it, rr);
     const double alpha = rz / pw;
-    k_fcg_update<<<g, 256, 0, st>>>(n, alpha, P->p, P->w, x_g, P->r);
-    k_dots<<<kPart, 256, 0, st>>>(n, P->r, P->r, nullptr, nullptr, P->part);
+    k_fcg_update<<<kPart, 256, 0, st>>>(n, alpha, P->p, P->w, x_g, P->r, P->part);
     SEM_LAUNCH_CHECK("fcg update");
     if ((rc = sum_pairs(P->part, &rr, &unused, st))) return rc;
     if (!std::isfinite(rr)) return finish(SEM_ERR_BREAKDOWN, it, rr);
@@ -1555,7 +1798,7 @@ extern "C" int sem_pmg_pcg_solve(sem_pmg *P, const double *b_g, double *x_g, con
     if ((rc = sum_pairs(P->part, &rzn, &rzo, st))) return rc;
     const double beta = (rzn - rzo) / rz;
     rz = rzn;
-    k_xpby<<<g, 256, 0, st>>>(n, P->zn, beta, P->p);
+    k_xpby<<<g, 256, 0, st>>>(n, P->zn, beta, P->p, P->w);
     SEM_LAUNCH_CHECK("fcg direction");
     std::swap(P->z, P->zn);
   }
