@@ -73,9 +73,9 @@ RBC_UNIT_BYTES = {
     # binary64 operand gather and result scatter of an operator, per unique node
     "op_vec64_unique": 16.0,
     "op_vec32_unique": 8.0,
-    # Jacobi-PCG iteration vectors: update1 reads r w dinv, writes r;
-    # update2 reads x r p dinv, writes x p w (11 binary64 words)
-    "pcg_vec_unique": 88.0,
+    # Jacobi-PCG iteration vectors: update1 reads x r p w dinv, writes x r;
+    # update2 reads r p dinv, writes p w (12 binary64 words)
+    "pcg_vec_unique": 96.0,
     # flexible-CG iteration vectors: update with r.r (p w x r read, x r
     # written), binary64<->binary32 at the V-cycle ends (r read, b written;
     # x read, z written), r.zn and r.z, p = zn + beta p with w = 0

@@ -4,12 +4,15 @@
 //
 // Vectors are U-vectors (one value per unique node). Each iteration runs
 //   w = M Q^T A_L Q p  (fused operator into w = 0, also the p.w partial sums)
-//   update1: alpha = rho / p.w;  r -= alpha w;  partial r.z, r.r
-//   update2: beta = r.z / rho;   x += alpha p;  p = z + beta p   (z = dinv * r,
-//            not stored); w = 0 for the next operator; the stopping test on
-//            the device
-// (x is updated in update2, which reads p anyway: 11 vector words per unique
-// node and iteration outside the operator instead of 12.)
+//   update1: alpha = rho / p.w;  x += alpha p;  r -= alpha w;  partial r.z, r.r
+//   update2: beta = r.z / rho;   p = z + beta p   (z = dinv * r, not stored);
+//            w = 0 for the next operator; the stopping test on the device
+// (On GB300 binary64 arithmetic runs at 1/64 of the binary32 rate, so these
+// streaming kernels are bound by memory or by the FP64 pipe: update1 does
+// five binary64 operations per node against seven vector words, update2 two
+// against five. With x += alpha p in update2 instead, update1's four
+// operations against four words made it FP64-bound, 0.44 of DRAM
+// throughput, and the pair was slower although it moved one word less.)
 // All reductions are two-level and in a fixed order, so for a given mesh and
 // input every scalar is reproducible except through the operator's atomics.
 // The stopping test (||r|| <= tol ||b||, or a breakdown) is taken by update2
@@ -161,9 +164,9 @@ __global__ void __launch_bounds__(kUpdThreads)
 }
 
 __global__ void __launch_bounds__(kUpdThreads)
-    k_pcg_update1(int64_t nU, double *__restrict__ r, const double *__restrict__ w, const double *__restrict__ dinv,
-                  const double *__restrict__ pw_part, int n_pw, PcgScalars *s, int par, double *__restrict__ rz_part,
-                  double *__restrict__ rr_part) {
+    k_pcg_update1(int64_t nU, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                  const double *__restrict__ w, const double *__restrict__ dinv, const double *__restrict__ pw_part,
+                  int n_pw, PcgScalars *s, int par, double *__restrict__ rz_part, double *__restrict__ rr_part) {
   __shared__ double red[32];
   if (*(volatile const int *)&s->stop_it != 0) return;  // stopped at an earlier iteration
   const double pw = sum_partials(pw_part, n_pw, red);
@@ -175,23 +178,25 @@ __global__ void __launch_bounds__(kUpdThreads)
     s->alpha = alpha;
   }
   double rz = 0.0, rr = 0.0;
-  // x += alpha p is left to k_pcg_update2, which reads p anyway (one vector
-  // pass less per iteration). The grid-stride loop takes four nodes per
-  // pass with all their loads issued first (enough loads in flight to cover
-  // the memory latency with 608 CTAs); each thread still visits its nodes in
-  // the plain loop's order, so the partial sums are the same bits.
+  // The grid-stride loop takes four nodes per pass with all their loads
+  // issued first (enough loads in flight to cover the memory latency with
+  // 608 CTAs); each thread still visits its nodes in the plain loop's order,
+  // so the partial sums are the same bits.
   const int64_t S = (int64_t)gridDim.x * blockDim.x;
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (; g + 3 * S < nU; g += 4 * S) {
-    double wv[4], rv0[4], dv[4];
+    double pv[4], xv[4], wv[4], rv0[4], dv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
+      pv[u] = p[g + u * S];
+      xv[u] = x[g + u * S];
       wv[u] = w[g + u * S];
       rv0[u] = r[g + u * S];
       dv[u] = dinv[g + u * S];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
+      x[g + u * S] = fma(alpha, pv[u], xv[u]);
       const double rv = fma(-alpha, wv[u], rv0[u]);
       r[g + u * S] = rv;
       const double z = dv[u] * rv;
@@ -200,6 +205,7 @@ __global__ void __launch_bounds__(kUpdThreads)
     }
   }
   for (; g < nU; g += S) {
+    x[g] = fma(alpha, p[g], x[g]);
     const double rv = fma(-alpha, w[g], r[g]);
     r[g] = rv;
     const double z = dinv[g] * rv;
@@ -215,8 +221,8 @@ __global__ void __launch_bounds__(kUpdThreads)
 }
 
 __global__ void __launch_bounds__(kUpdThreads)
-    k_pcg_update2(int64_t nU, double *__restrict__ x, const double *__restrict__ r, double *__restrict__ p,
-                  double *__restrict__ w, const double *__restrict__ dinv, const double *__restrict__ rz_part,
+    k_pcg_update2(int64_t nU, const double *__restrict__ r, double *__restrict__ p, double *__restrict__ w,
+                  const double *__restrict__ dinv, const double *__restrict__ rz_part,
                   const double *__restrict__ rr_part, int n_part, PcgScalars *s, int par, int it, double thresh) {
   __shared__ double red[32];
   // block 0 of this launch may record a stop at this iteration while the other
@@ -224,7 +230,6 @@ __global__ void __launch_bounds__(kUpdThreads)
   const int sit = *(volatile const int *)&s->stop_it;
   if (sit != 0 && sit < it) return;
   const double rz = sum_partials(rz_part, n_part, red);
-  const double alpha = s->alpha;  // this iteration's step length, from k_pcg_update1
   const double rho_old = s->rho[par];
   const double beta = (rho_old != 0.0) ? rz / rho_old : 0.0;
   if (blockIdx.x == 0) {  // only block 0 needs r.r (block-uniform branch)
@@ -248,25 +253,21 @@ __global__ void __launch_bounds__(kUpdThreads)
   const int64_t S = (int64_t)gridDim.x * blockDim.x;
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (; g + 3 * S < nU; g += 4 * S) {
-    double pv[4], xv[4], rv[4], dv[4];
+    double pv[4], rv[4], dv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       pv[u] = p[g + u * S];
-      xv[u] = x[g + u * S];
       rv[u] = r[g + u * S];
       dv[u] = dinv[g + u * S];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      x[g + u * S] = fma(alpha, pv[u], xv[u]);
       p[g + u * S] = fma(beta, pv[u], dv[u] * rv[u]);
       w[g + u * S] = 0.0;
     }
   }
   for (; g < nU; g += S) {
-    const double pv = p[g];
-    x[g] = fma(alpha, pv, x[g]);
-    p[g] = fma(beta, pv, dinv[g] * r[g]);
+    p[g] = fma(beta, p[g], dinv[g] * r[g]);
     w[g] = 0.0;
   }
 }
@@ -557,10 +558,10 @@ int sem_pcg_solve_ex(const sem_mesh *m, double h1, double h2, const double *b_g,
     if ((rc = sem_launch_ax_assembled(m, h1, h2, wk.p, wk.w, wk.pw_part, opts->precision, st, map, stop)) != SEM_OK)
       return rc;
     k_pw_reduce<<<n_chunks, kUpdThreads, 0, st>>>(wk.pw_part, n_pw, chunk, wk.part_c, wk.s);
-    k_pcg_update1<<<nblk, kUpdThreads, 0, st>>>(nU, wk.r, wk.w, dinv, wk.part_c, n_chunks, wk.s, par, wk.part_a,
-                                                wk.part_b);
-    k_pcg_update2<<<nblk, kUpdThreads, 0, st>>>(nU, x_g, wk.r, wk.p, wk.w, dinv, wk.part_a, wk.part_b, nblk, wk.s, par,
-                                                it, thresh);
+    k_pcg_update1<<<nblk, kUpdThreads, 0, st>>>(nU, x_g, wk.r, wk.p, wk.w, dinv, wk.part_c, n_chunks, wk.s, par,
+                                                wk.part_a, wk.part_b);
+    k_pcg_update2<<<nblk, kUpdThreads, 0, st>>>(nU, wk.r, wk.p, wk.w, dinv, wk.part_a, wk.part_b, nblk, wk.s, par, it,
+                                                thresh);
     SEM_LAUNCH_CHECK("pcg iteration");
     if (it % check_every != 0 && it != opts->maxit) continue;
     SEM_CUDA(cudaMemcpyAsync(&hs, wk.s, sizeof(hs), cudaMemcpyDeviceToHost, st));
