@@ -13,8 +13,8 @@
 //       values), split to df64 into the shared tile U; thread 0 starts the
 //       L2 prefetch of the element's geometric factors
 //   P1  each thread contracts three lines with D, one loop body: the r-line
-//       u(:,a,b) -> R, the s-line u(a,:,b) -> S, its t-line -> T (without the
-//       Helmholtz term T is the U tile, written after a barrier)
+//       u(:,a,b) -> R, the s-line u(a,:,b) -> S, its t-line -> T (T is the
+//       U tile, written after a barrier; u stays in the thread's registers)
 //   P2  pointwise metric on its t-column: (wr, ws, wt) = G (ur, us, ut), the
 //       factors of level k + 1 loaded while level k is computed
 //   P3  transposed contractions of the same lines, in place
@@ -224,9 +224,10 @@ struct DfCfg {
   // NP = 8: one element (64 threads) per CTA, so barriers wait on two warps only
   static constexpr int ELB = (NP == 8) ? 1 : (ELB_T < ELB_S ? ELB_T : (ELB_S > 0 ? ELB_S : 1));
   static constexpr int THREADS = N2 * ELB;
-  // the operator: tiles U, R, S, and T (the t-derivative) in a fourth tile
-  // only when the Helmholtz term needs u at the end; otherwise T replaces U
-  static constexpr int smem_ax(bool helm) { return (helm ? 4 : 3) * TILE * ELB * (int)sizeof(float2); }
+  // the operator: tiles U, R, S; the t-derivative T replaces U once every
+  // thread has read its r/s lines (the Helmholtz term takes u from the
+  // thread's own registers). The same for both forms.
+  static constexpr int smem_ax(bool) { return 3 * TILE * ELB * (int)sizeof(float2); }
   // NP = 8: twelve 64-thread CTAs per SM (at most 85 registers per thread)
   static constexpr int MINB = (NP == 8) ? 12 : 1;
   // p.w partial sums per CTA: one per warp when the CTA is whole warps (a
@@ -249,11 +250,11 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
   const int le = tid / C::N2;
   const int t = tid - le * C::N2;
   const int a = t % NP, b = t / NP;
-  constexpr int NT = HELM ? 4 : 3;  // tiles per element
+  constexpr int NT = 3;  // tiles per element
   float2 *U = sm2 + le * NT * C::TILE;
   float2 *R = U + C::TILE;
   float2 *S = R + C::TILE;
-  float2 *T = HELM ? S + C::TILE : U;  // without the Helmholtz term T replaces U after the r/s passes
+  float2 *T = U;  // T replaces U after the r/s passes
   const int col = a + C::PJ * b;  // padded offset of the t-column (a, b, 0)
   double pw = 0.0;  // p.w of this thread's points (binary64 across elements)
   const int64_t estride = (int64_t)gridDim.x * C::ELB;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
   __syncthreads();
 
   int32_t go[NP];  // gather indices of this thread's column, kept for the scatter
-  float2 uk[NP];   // its (scaled) u values, kept for p.w when T replaces the U tile
+  float2 uk[NP];   // its (scaled) u values, kept for p.w and the Helmholtz term (T replaces the U tile)
   int sh = 0;      // the element's scale: values are carried as x 2^-sh
   for (int64_t e0 = (int64_t)blockIdx.x * C::ELB; e0 < E; e0 += estride) {
     const int64_t ei = e0 + le;  // position in the element list (or the element itself)
@@ -281,6 +282,10 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
     // P0: gather and split the t-column; one thread per element starts the
     // L2 prefetch of the element's geometric factors (read in P2)
     if (act && t == 0) prefetch_l2(Gdf + e * 6 * C::N3, 48u * C::N3);
+    // the mass term's B (read in P4) likewise; its block is 16-byte aligned
+    // and a multiple of 16 bytes when NP^3 is even
+    if constexpr (HELM && C::N3 % 2 == 0)
+      if (act && t == 1) prefetch_l2(Bdf + e * C::N3, 8u * C::N3);
     {
       double v[NP];
       if (ASSEMBLED) {  // all indices, then all values: one round trip each
@@ -322,11 +327,11 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
       }
       __syncthreads();
     }
-    // P1: forward contractions, r-, s- and t-lines, one loop body (when T
-    // replaces U, the t-lines wait until every thread has read its r/s lines)
+    // P1: forward contractions, r-, s- and t-lines, one loop body (T
+    // replaces U: the t-lines wait until every thread has read its r/s lines)
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
-      if (!HELM && d == 2) __syncthreads();
+      if (d == 2) __syncthreads();
       const int base = d == 0 ? C::PJ * a + C::PK * b : (d == 1 ? a + C::PK * b : col);
       const int str = d == 0 ? 1 : (d == 1 ? C::PJ : C::PK);
       float2 *O = d == 0 ? R : (d == 1 ? S : T);
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(DfCfg<NP>::THREADS, DfCfg<NP>::MINB)
       float2 v;
       df::fast_two_sum(acc.s, acc.c, v.x, v.y);
       if (HELM) {
-        const float2 xk = U[q];
+        const float2 xk = uk[k];  // u at the point, from P0 (the U tile now holds T)
         const float2 Bv = act ? Bdf[e * C::N3 + p] : make_float2(0.0f, 0.0f);
         const float2 buv = df::norm(df::mul_first(Bv.x, Bv.y, xk.x, xk.y));
         df::Acc o = df::mul_first(h1.x, h1.y, v.x, v.y);
