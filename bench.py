@@ -142,7 +142,7 @@ def parse():
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"])
     ap.add_argument("--once", default="",
                     help="profiling mode: comma list of kernels to launch once each on the workload "
-                         "(local_df64, asm_df64, asmtc1_df64, asmtc2_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16, pmgsolve_fp32, pmgsolve_bf16, rbc, rbcx, pcg_df64), then exit")
+                         "(local_df64, asm_df64, asmh_df64, asmtc1_df64, asmtc2_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16, pmgsolve_fp32, pmgsolve_bf16, rbc, rbcx, pcg_df64), then exit")
     return ap.parse_args()
 
 
@@ -289,6 +289,8 @@ def run_once(sem, mesh, u, names):
             sem.sem_ax_apply(mesh, 1.0, 0.0, uL, wL, precision=P[prec])
         elif kind == "asm":
             sem.sem_ax_assembled_add(mesh, 1.0, 0.0, u, wg, precision=P[prec])
+        elif kind == "asmh":  # the Helmholtz form (h1 = 1, h2 = 0.37)
+            sem.sem_ax_assembled_add(mesh, 1.0, 0.37, u, wg, precision=P[prec])
         elif kind in ("asmtc1", "asmtc2"):  # the N = 7 double-float operator on a tensor-core route
             sem.sem_mesh_set_tensor_cores(mesh, 1 if kind == "asmtc1" else 2)
             sem.sem_ax_assembled_add(mesh, 1.0, 0.0, u, wg, precision=P[prec])
