@@ -159,6 +159,8 @@ class RBCState:
     p_prev: Optional[np.ndarray] = None
     step: int = 0
     iters: dict = field(default_factory=dict)
+    u_prev2: Optional[List[np.ndarray]] = None  # two steps earlier (third-order guesses only)
+    T_prev2: Optional[np.ndarray] = None
 
 
 class RBC:
@@ -166,7 +168,12 @@ class RBC:
     second-order extrapolation 2 x^n - x^{n-1} of the two previous solutions
     (the stopping test stays ||r|| <= tol ||b||). The paper does not describe
     its solvers' initial guesses; this is the extrapolation of the scheme's
-    own order (EXT2), a simple form of starting from earlier solutions."""
+    own order (EXT2), a simple form of starting from earlier solutions.
+    extrapolate = 2: the temperature and velocity solves start from the
+    third-order extrapolation 3 x^n - 3 x^{n-1} + x^{n-2} once three levels
+    exist (from the third step; the second step uses 2 x^n - x^{n-1}); the
+    pressure keeps the second-order guess (its history is not smooth enough
+    for a higher order, measured on this oracle)."""
 
     def __init__(self, m: Mesh, Ra: float, Pr: float, dt: float, tol=1e-12, maxit=5000, extrapolate=False):
         self.extrapolate = extrapolate
@@ -222,8 +229,12 @@ class RBC:
         TbL = scatter(m, self.Tb)
         rhsT = gather_sum(m, m.B * ((b1 * TL + b2 * TpL) / dt + NTs))
         rhsT = rhsT - gather_sum(m, (b0 / dt) * m.B * TbL) - self.kappa * gather_sum(m, ax_local(m, TbL, 1.0, 0.0))
-        ex = self.extrapolate and s.step >= 1  # two earlier levels exist
-        x0 = mk * (2.0 * (s.T - self.Tb) - (s.T_prev - self.Tb)) if ex else None
+        ex = bool(self.extrapolate) and s.step >= 1  # two earlier levels exist
+        ex3 = self.extrapolate == 2 and s.step >= 2  # three earlier levels exist
+        if ex3:
+            x0 = mk * (3.0 * (s.T - self.Tb) - 3.0 * (s.T_prev - self.Tb) + (s.T_prev2 - self.Tb))
+        else:
+            x0 = mk * (2.0 * (s.T - self.Tb) - (s.T_prev - self.Tb)) if ex else None
         rT = _pcg_helm(m, mk * rhsT, self.kappa, b0 / dt, self.tol, self.maxit, x0=x0)
         T_new = self.Tb + rT.x
         # pressure
@@ -237,12 +248,16 @@ class RBC:
         u_new, its = [], []
         for c in range(3):
             rhs = mk * gather_sum(m, m.B * (fs[c] - gp[c]))
-            x0 = mk * (2.0 * s.u[c] - s.u_prev[c]) if ex else None
+            if ex3:
+                x0 = mk * (3.0 * s.u[c] - 3.0 * s.u_prev[c] + s.u_prev2[c])
+            else:
+                x0 = mk * (2.0 * s.u[c] - s.u_prev[c]) if ex else None
             r = _pcg_helm(m, rhs, self.nu, b0 / dt, self.tol, self.maxit, x0=x0)
             u_new.append(r.x)
             its.append(r.iterations)
         out = RBCState(u_new, T_new, p, [c.copy() for c in s.u], s.T.copy(), NT, Nu, W, s.p.copy(), s.step + 1,
-                       {"T": rT.iterations, "p": rp.iterations, "u": its})
+                       {"T": rT.iterations, "p": rp.iterations, "u": its},
+                       [c.copy() for c in s.u_prev], s.T_prev.copy())
         return out
 
     def divergence(self, s: RBCState) -> float:

@@ -248,3 +248,36 @@ def test_extrapolated_initial_guesses_change_only_the_iterations():
     for _ in range(3):
         s = R.step(s)
         assert np.abs(s.T - (1.0 - z)).max() < 1e-13
+
+
+def test_third_order_guesses_change_only_the_iterations():
+    """extrapolate = 2 (temperature and velocity from 3x^n - 3x^{n-1} +
+    x^{n-2} once three levels exist, pressure from 2p^n - p^{n-1}) leaves the
+    fields the same up to the solver tolerance, gives the first two steps the
+    iterations of the second-order option, and needs no more Helmholtz
+    iterations than it afterwards; conduction stays a fixed point."""
+    m = rbc_mesh((2, 2, 3), 4, 1.5)
+    pert = 0.2 * np.random.default_rng(5).standard_normal(m.n_unique)
+    runs = {}
+    for ex in (1, 2):
+        R = rbc.RBC(m, 2e4, 1.0, 5e-3, tol=1e-11, extrapolate=ex)
+        s = R.initial_state(pert)
+        hist = []
+        for _ in range(8):
+            s = R.step(s)
+            hist.append(s.iters)
+        runs[ex] = (s, hist)
+    (s1, h1), (s2, h2) = runs[1], runs[2]
+    assert np.abs(s2.T - s1.T).max() < 1e-9
+    assert max(np.abs(a - b).max() for a, b in zip(s2.u, s1.u)) < 1e-9
+    assert np.abs(s2.p - s1.p).max() < 1e-7 * max(1.0, np.abs(s1.p).max())
+    assert h2[:2] == h1[:2]  # third order needs three earlier levels
+    later1 = sum(h["T"] + sum(h["u"]) for h in h1[2:])
+    later2 = sum(h["T"] + sum(h["u"]) for h in h2[2:])
+    assert later2 < later1, (h1, h2)
+    R = rbc.RBC(m, 1e8, 0.7, 1e-3, tol=1e-13, extrapolate=2)
+    s = R.initial_state()
+    z = zg(m)
+    for _ in range(4):
+        s = R.step(s)
+        assert np.abs(s.T - (1.0 - z)).max() < 1e-13
