@@ -142,7 +142,7 @@ def parse():
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"])
     ap.add_argument("--once", default="",
                     help="profiling mode: comma list of kernels to launch once each on the workload "
-                         "(local_df64, asm_df64, asmh_df64, asmtc1_df64, asmtc2_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16, pmgsolve_fp32, pmgsolve_bf16, rbc, rbcx, pcg_df64), then exit")
+                         "(local_df64, asm_df64, asmh_df64, asmtc1_df64, asmtc2_df64, local_fp64, asm_fp64, gs, vcycle_fp32, vcycle_bf16, pmgsolve_fp32, pmgsolve_bf16, rbc, rbcx, rbcx3, pcg_df64), then exit")
     return ap.parse_args()
 
 
@@ -297,13 +297,14 @@ def run_once(sem, mesh, u, names):
             sem.sem_mesh_set_tensor_cores(mesh, 0)
         elif kind == "gs":
             sem.sem_gs_op(mesh, wL, True)
-        elif kind in ("rbc", "rbcx"):  # Rayleigh-Benard steps on the 32^3-element workload
+        elif kind in ("rbc", "rbcx", "rbcx3"):  # Rayleigh-Benard steps on the 32^3-element workload
             rw = workloads.RBC_32
             rm = sem.mesh_from_workload(rw)
             pert = torch.from_numpy(workloads.perturbation(rm.n_unique, 1e-3)).cuda()
-            # rbcx: solves from the extrapolated guess, four steps (the fourth steady)
+            # rbcx: solves from the extrapolated guess, four steps (the fourth steady);
+            # rbcx3: the same with third-order guesses for the temperature and velocity
             rs = sem.sem_rbc_create(rm, 1e8, 0.7, 1e-3, tol=1e-8, precision=sem.SEM_PREC_DF64, T_pert=pert,
-                                    extrapolate=kind == "rbcx")
+                                    extrapolate={"rbc": 0, "rbcx": 1, "rbcx3": 2}[kind])
             for _ in range(3 if kind == "rbc" else 4):
                 print(json.dumps(sem.sem_bdf_ext_step(rs)))
             rs.destroy()
@@ -593,7 +594,8 @@ def main():
         m48.destroy()
 
     # --- Rayleigh-Benard BDF2/EXT2 steps (32^3 elements, Ra = 1e8, Pr = 0.7),
-    # solves from zero and from the extrapolated guess 2 x^n - x^{n-1}
+    # solves from zero, from the extrapolated guess 2 x^n - x^{n-1}, and with
+    # the temperature and velocity from 3 x^n - 3 x^{n-1} + x^{n-2}
     rbc = None
     if not args.no_rbc:
         rw = workloads.RBC_32
@@ -602,19 +604,21 @@ def main():
         hbm_gbs, _ = peaks()
         rbc = {"workload": rw.name, "tol": 1e-8, "unit_bytes": RBC_UNIT_BYTES,
                "roofline_peak_gbs": hbm_gbs}
-        for mode, ex in (("cold", False), ("extrapolated", True)):
+        keep = None
+        for mode, ex in (("cold", 0), ("extrapolated", 1), ("extrapolated3", 2)):
             rs = sem.sem_rbc_create(rm, 1e8, 0.7, 1e-3, tol=1e-8, precision=sem.SEM_PREC_DF64, T_pert=pert,
                                     extrapolate=ex)
             steps = [sem.sem_bdf_ext_step(rs, raise_on_error=False) for _ in range(5)]
             for s_ in steps:
-                s_["phase_roofline"] = rbc_phase_roofline(rw, s_, ex and s_["step"] > 1, hbm_gbs)
+                s_["phase_roofline"] = rbc_phase_roofline(rw, s_, bool(ex) and s_["step"] > 1, hbm_gbs)
             rbc[mode] = {"steps": steps,
                          "ms_per_step_after_first": float(np.mean([s_["step_ms"] for s_ in steps[1:]])),
                          # the first two steps differ (BDF1, then new Jacobi inverses for b0 = 3/2);
                          # step times are host wall clock, so the median is also given
                          "ms_per_steady_step": float(np.mean([s_["step_ms"] for s_ in steps[2:]])),
                          "ms_per_steady_step_median": float(np.median([s_["step_ms"] for s_ in steps[2:]]))}
-            if mode == "extrapolated":
+            if mode == "extrapolated":  # its temperature is rendered below
+                keep = rs
                 T = sem.sem_rbc_fields(rs)["T"]
             else:
                 rs.destroy()
@@ -649,7 +653,7 @@ def main():
         render["iso_scene_4096x2048_grid256"] = {"ms": rms, "hit_fraction": float((sd >= 0).float().mean())}
         del sv, sd, sr
         rbc["render_4096x4096"] = render
-        rs.destroy()
+        keep.destroy()
         rm.destroy()
 
     # --- adjoint: gradient of the bottom-plate Nusselt number after K = 20

@@ -409,7 +409,9 @@ int sem_pmg_destroy(sem_pmg *p);
  *       nu = sqrt(Pr/Ra).
  * The first step uses history levels equal to the initial state. Explicit
  * terms are binary64 kernels; the five solves are sem_pcg_solve, from x0 = 0
- * or (extrapolate = 1, every step after the first) from 2 x^n - x^{n-1}.
+ * or (extrapolate = 1, every step after the first) from 2 x^n - x^{n-1}
+ * (extrapolate = 2: temperature and velocity from 3 x^n - 3 x^{n-1} + x^{n-2}
+ * from the third step on).
  * ------------------------------------------------------------------------ */
 typedef struct sem_rbc sem_rbc; /* opaque; owns its fields and scratch */
 
@@ -427,7 +429,13 @@ typedef struct {
                        solutions (T - Tb, p, u, v, w); the stopping test is
                        unchanged. The paper does not describe initial guesses;
                        this is the scheme's own second-order extrapolation.
-                       0: every solve starts from 0 */
+                       2: the same, except that from the third step on the
+                       temperature and velocity solves start from the
+                       third-order extrapolation 3 x^n - 3 x^{n-1} + x^{n-2}
+                       (the state then holds u^{n-2} and T^{n-2} too, in its
+                       snapshots as well); the pressure keeps 2 p^n - p^{n-1}.
+                       0: every solve starts from 0. Other values are rejected
+                       with SEM_ERR_INVALID_ARG. */
 } sem_rbc_params;
 
 typedef struct {
@@ -463,14 +471,15 @@ int sem_rbc_fields(const sem_rbc *s, sem_rbc_view *view);
 int sem_rbc_destroy(sem_rbc *s);
 
 /* State snapshots for checkpoint/restart. The state after a step is u, v, w,
- * their previous level, T, T^{n-1}, p, the previous wall term, p^{n-1} (U-vectors),
+ * their previous level, T, T^{n-1}, p, the previous wall term, p^{n-1}, with
+ * extrapolate = 2 also u, v, w and T two steps earlier (U-vectors),
  * the previous advection terms of T, u, v, w (E-vectors) and the step
  * counter; every other array is rebuilt each step. Restoring a snapshot and
  * stepping again reproduces the original run bit for bit when the mesh is in
  * deterministic mode (sem_mesh_set_deterministic), otherwise to rounding.
  * sem_rbc_state_bytes: size of a snapshot: a header of eight int64 (step,
- * n_unique, n_local, E, N, format version 2, the bits of dt, 0) then the
- * arrays.
+ * n_unique, n_local, E, N, format version 2, the bits of dt, 1 when the
+ * levels two steps earlier are held else 0) then the arrays.
  * sem_rbc_save_state / sem_rbc_load_state: copy to / from a caller-owned
  * device buffer of that size; both synchronise the stream. Loading a
  * snapshot whose header differs in anything but the step (another mesh, dt

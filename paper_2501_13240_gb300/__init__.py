@@ -716,10 +716,12 @@ class RBC:
 
 def sem_rbc_create(mesh: Mesh, Ra: float, Pr: float, dt: float, tol: float = 1e-10, maxit: int = 5000,
                    precision: int = SEM_PREC_DF64, T_pert=None, pressure_pmg: bool = True, stream=None,
-                   extrapolate: bool = False) -> RBC:
+                   extrapolate: int = 0) -> RBC:
+    """extrapolate: 0 (solves from zero), 1 or True (2 x^n - x^{n-1}), 2
+    (temperature and velocity from 3 x^n - 3 x^{n-1} + x^{n-2})"""
     import torch
     prm = sem_rbc_params(float(Ra), float(Pr), float(dt), float(tol), int(maxit), int(precision),
-                         int(bool(pressure_pmg)), int(bool(extrapolate)))
+                         int(bool(pressure_pmg)), int(extrapolate))
     pert = _ptr(T_pert, torch.float64, mesh.n_unique, "T_pert") if T_pert is not None else None
     h = ctypes.c_void_p()
     _check(lib().sem_rbc_create(mesh.handle, ctypes.byref(prm), pert, _stream(stream), ctypes.byref(h)))

@@ -36,6 +36,8 @@ struct sem_rbc {
   double *u[3] = {}, *up[3] = {}, *T = nullptr, *Tp = nullptr, *p = nullptr, *W = nullptr, *Wp = nullptr;
   double *Tb = nullptr, *rhs = nullptr, *x = nullptr, *Tn = nullptr, *un[3] = {};
   double *pp = nullptr;  // p^{n-1}: the second level of the pressure extrapolation
+  // u^{n-2}, T^{n-2}: the third level of the third-order guesses (extrapolate = 2 only)
+  double *upp[3] = {}, *Tpp = nullptr;
   // E-vectors
   double *uL[3] = {}, *upL[3] = {}, *TL = nullptr, *TpL = nullptr, *g[3] = {}, *om[3] = {};
   double *NT = nullptr, *NTp = nullptr, *Nu[3] = {}, *Nup[3] = {}, *fs[3] = {}, *tmpL = nullptr;
@@ -81,6 +83,25 @@ __global__ void k_extrap(int64_t n, const uint8_t *__restrict__ mask, const doub
     double v;
     if (c) v = 2.0 * (a[g] - c[g]) - (b[g] - c[g]);
     else v = 2.0 * a[g] - b[g];
+    out[g] = (!mask || mask[g]) ? v : 0.0;
+  }
+}
+
+// third-order guess 3 a - 3 b + d of the levels a = x^n, b = x^{n-1},
+// d = x^{n-2} (each less the lifting c when given), zero on masked nodes;
+// the operations unfused and in the order the oracle takes them
+__global__ void k_extrap3(int64_t n, const uint8_t *__restrict__ mask, const double *__restrict__ a,
+                          const double *__restrict__ b, const double *__restrict__ d, const double *__restrict__ c,
+                          double *__restrict__ out) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    double v;
+    if (c) {
+      const double cg = c[g];
+      v = __dadd_rn(__dsub_rn(__dmul_rn(3.0, __dsub_rn(a[g], cg)), __dmul_rn(3.0, __dsub_rn(b[g], cg))),
+                    __dsub_rn(d[g], cg));
+    } else {
+      v = __dadd_rn(__dsub_rn(__dmul_rn(3.0, a[g]), __dmul_rn(3.0, b[g])), d[g]);
+    }
     out[g] = (!mask || mask[g]) ? v : 0.0;
   }
 }
@@ -259,8 +280,8 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: Ra, Pr, dt, tol must be > 0 and maxit >= 1");
   if (prm->precision != SEM_PREC_FP64 && prm->precision != SEM_PREC_DF64)
     return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: unknown precision");
-  if (prm->extrapolate != 0 && prm->extrapolate != 1)
-    return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: extrapolate must be 0 or 1");
+  if (prm->extrapolate < 0 || prm->extrapolate > 2)
+    return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: extrapolate must be 0, 1 or 2");
   int dev = -1;
   SEM_CUDA(cudaGetDevice(&dev));
   if (dev != m->device) return sem_fail(SEM_ERR_INVALID_ARG, "sem_rbc_create: the mesh's device must be current");
@@ -290,6 +311,11 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
                       &s->dinvT, &s->dinvU, &s->pp};
   for (double **p : uvecs)
     if (!rc) rc = alloc(p, s->nU);
+  if (prm->extrapolate == 2) {
+    double **lv3[] = {&s->upp[0], &s->upp[1], &s->upp[2], &s->Tpp};
+    for (double **p : lv3)
+      if (!rc) rc = alloc(p, s->nU);
+  }
   double **evecs[] = {&s->uL[0], &s->uL[1], &s->uL[2], &s->upL[0], &s->upL[1], &s->upL[2], &s->TL, &s->TpL,
                       &s->g[0],  &s->g[1],  &s->g[2],  &s->om[0],  &s->om[1],  &s->om[2],  &s->NT, &s->NTp,
                       &s->Nu[0], &s->Nu[1], &s->Nu[2], &s->Nup[0], &s->Nup[1], &s->Nup[2], &s->fs[0], &s->fs[1],
@@ -341,6 +367,10 @@ extern "C" int sem_rbc_create(const sem_mesh *m, const sem_rbc_params *prm, cons
   cudaMemsetAsync(s->Tp, 0, sizeof(double) * s->nU, st);
   cudaMemsetAsync(s->Wp, 0, sizeof(double) * s->nU, st);
   cudaMemsetAsync(s->NTp, 0, sizeof(double) * s->nL, st);
+  if (s->Tpp) {
+    for (int c = 0; c < 3; ++c) cudaMemsetAsync(s->upp[c], 0, sizeof(double) * s->nU, st);
+    cudaMemsetAsync(s->Tpp, 0, sizeof(double) * s->nU, st);
+  }
   if (prm->pressure_pmg && m->N > 1) {
     sem_pmg_opts po;
     memset(&po, 0, sizeof(po));
@@ -472,9 +502,14 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   }
   k_rhsT<<<gl, 256, 0, st>>>(nL, kd, m->B, s->TL, s->TpL, s->NT, s->NTp, s->HTb, s->tmpL);
   if ((rc = gather(s, s->tmpL, s->rhs, true, st))) return rc;
-  // initial guesses: the extrapolation 2 x^n - x^{n-1} once two levels exist
+  // initial guesses: the extrapolation 2 x^n - x^{n-1} once two levels exist;
+  // with extrapolate = 2, 3 x^n - 3 x^{n-1} + x^{n-2} for T and u once three do
   const bool ex = s->prm.extrapolate && s->step >= 1;
-  if (ex) {
+  const bool ex3 = s->prm.extrapolate == 2 && s->step >= 2;
+  if (ex3) {
+    k_extrap3<<<gu, 256, 0, st>>>(nU, m->mask, s->T, s->Tp, s->Tpp, s->Tb, s->x);
+    SEM_LAUNCH_CHECK("k_extrap3");
+  } else if (ex) {
     k_extrap<<<gu, 256, 0, st>>>(nU, m->mask, s->T, s->Tp, s->Tb, s->x);
     SEM_LAUNCH_CHECK("k_extrap");
   }
@@ -528,7 +563,10 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   for (int c = 0; c < 3; ++c) {
     k_bdiff<<<gl, 256, 0, st>>>(nL, m->B, s->fs[c], s->g[c], s->tmpL);
     if ((rc = gather(s, s->tmpL, s->rhs, true, st))) return rc;
-    if (ex) {
+    if (ex3) {
+      k_extrap3<<<gu, 256, 0, st>>>(nU, m->mask, s->u[c], s->up[c], s->upp[c], nullptr, s->un[c]);
+      SEM_LAUNCH_CHECK("k_extrap3");
+    } else if (ex) {
       k_extrap<<<gu, 256, 0, st>>>(nU, m->mask, s->u[c], s->up[c], nullptr, s->un[c]);
       SEM_LAUNCH_CHECK("k_extrap");
     }
@@ -538,12 +576,14 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
   }
   SEM_CUDA(cudaStreamSynchronize(st));
   stt->ms_u = lap();
-  // rotate histories
+  // rotate histories (u^{n-2} <- u^{n-1} <- u^n <- u^{n+1}, the same for T)
   for (int c = 0; c < 3; ++c) {
+    if (s->Tpp) std::swap(s->upp[c], s->up[c]);
     std::swap(s->up[c], s->u[c]);
     std::swap(s->u[c], s->un[c]);
     std::swap(s->Nup[c], s->Nu[c]);
   }
+  if (s->Tpp) std::swap(s->Tpp, s->Tp);
   std::swap(s->Tp, s->T);
   std::swap(s->T, s->Tn);
   std::swap(s->NTp, s->NT);
@@ -557,9 +597,11 @@ extern "C" int sem_bdf_ext_step(sem_rbc *s, sem_step_stats *stt, void *stream) {
 
 // ---------------------------------------------------------------- checkpoints
 // The state after a step: u, u^{n-1}, T, T^{n-1}, p, W^{n-1}, p^{n-1} (U-vectors),
-// N_T^{n-1}, N_u^{n-1} (E-vectors) and the step counter; the rest is rebuilt
-// every step. Layout: 64-byte header of eight int64 (step, n_unique, n_local,
-// E, N, format version, the bits of dt, 0) then the arrays in that order.
+// with extrapolate = 2 also u^{n-2} and T^{n-2}, then N_T^{n-1}, N_u^{n-1}
+// (E-vectors) and the step counter; the rest is rebuilt every step. Layout:
+// 64-byte header of eight int64 (step, n_unique, n_local, E, N, format
+// version, the bits of dt, 1 when the n-2 levels are held else 0) then the
+// arrays in that order.
 namespace {
 
 struct StateLayout {
@@ -571,6 +613,10 @@ StateLayout layout(const sem_rbc *s) {
   StateLayout L;
   double *uvec[] = {s->u[0], s->u[1], s->u[2], s->up[0], s->up[1], s->up[2], s->T, s->Tp, s->p, s->Wp, s->pp};
   for (double *p : uvec) L.arrays.push_back({p, s->nU});
+  if (s->Tpp) {  // the third levels of the third-order guesses
+    double *lv3[] = {s->upp[0], s->upp[1], s->upp[2], s->Tpp};
+    for (double *p : lv3) L.arrays.push_back({p, s->nU});
+  }
   double *evec[] = {s->NTp, s->Nup[0], s->Nup[1], s->Nup[2]};
   for (double *p : evec) L.arrays.push_back({p, s->nL});
   L.bytes = 64;
@@ -583,7 +629,7 @@ constexpr int64_t kStateVersion = 2;  // 2: p^{n-1} added
 void make_header(const sem_rbc *s, int64_t hdr[8]) {
   int64_t dtbits;
   memcpy(&dtbits, &s->prm.dt, sizeof(dtbits));
-  const int64_t h[8] = {s->step, s->nU, s->nL, s->m->E, s->m->N, kStateVersion, dtbits, 0};
+  const int64_t h[8] = {s->step, s->nU, s->nL, s->m->E, s->m->N, kStateVersion, dtbits, s->Tpp ? 1 : 0};
   memcpy(hdr, h, sizeof(h));
 }
 

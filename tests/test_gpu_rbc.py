@@ -78,20 +78,22 @@ def test_perturbed_steps_match_oracle(nel, N, stretch, prec, pmg):
     gm.destroy()
 
 
+@pytest.mark.parametrize("order", [1, 2], ids=["ext2", "ext3"])
 @pytest.mark.parametrize("pmg", [False, True], ids=["jacobi_p", "pmg_p"])
 @pytest.mark.parametrize("prec", [sem.SEM_PREC_FP64, sem.SEM_PREC_DF64], ids=["fp64", "df64"])
-def test_extrapolated_initial_guess_matches_oracle(prec, pmg):
+def test_extrapolated_initial_guess_matches_oracle(prec, pmg, order):
     """Every step after the first starts its five solves from 2 x^n - x^{n-1}
-    (T - Tb, p, u, v, w), as the oracle's option: four steps, same fields
-    (T 1e-10, p and u 1e-8) and iteration counts; from the second step on the
-    solves need fewer iterations than from zero."""
+    (T - Tb, p, u, v, w), and with order 2 the temperature and velocity from
+    3 x^n - 3 x^{n-1} + x^{n-2} from the third step, as the oracle's option:
+    four steps, same fields (T 1e-10, p and u 1e-8) and iteration counts;
+    from the second step on the solves need fewer iterations than from zero."""
     om, gm = meshes((2, 3, 4), 7, 1.3)
     Ra, Pr, dt, tol = 1e5, 0.7, 2e-3, 1e-12
     pert = workloads.perturbation(om.n_unique, 1e-2, seed=2)
-    R = rbc.RBC(om, Ra, Pr, dt, tol=tol, extrapolate=True)
+    R = rbc.RBC(om, Ra, Pr, dt, tol=tol, extrapolate=order)
     s = R.initial_state(pert)
     mk = dict(tol=tol, precision=prec, T_pert=torch.from_numpy(pert).cuda(), pressure_pmg=pmg)
-    st = sem.sem_rbc_create(gm, Ra, Pr, dt, extrapolate=True, **mk)
+    st = sem.sem_rbc_create(gm, Ra, Pr, dt, extrapolate=order, **mk)
     cold = sem.sem_rbc_create(gm, Ra, Pr, dt, **mk)
     for k in range(4):
         s = R.step(s)
@@ -116,20 +118,28 @@ def test_extrapolated_initial_guess_matches_oracle(prec, pmg):
     gm.destroy()
 
 
-def test_extrapolated_restart_is_bit_identical():
-    """A snapshot holds p^{n-1} too: restoring it and stepping again repeats
-    the extrapolated run bit for bit (deterministic assembly)."""
+@pytest.mark.parametrize("order", [1, 2], ids=["ext2", "ext3"])
+def test_extrapolated_restart_is_bit_identical(order, tmp_path):
+    """A snapshot holds p^{n-1} (and with order 2 u^{n-2}, T^{n-2}) too:
+    restoring it and stepping again repeats the extrapolated run bit for bit
+    (deterministic assembly); a snapshot of the other order is refused."""
     kw = dict(periodic=(1, 1, 0), dirichlet=(0, 0, 0, 0, 1, 1), z_stretch=1.5)
     gm = sem.sem_mesh_create_box((3, 3, 3), 5, deterministic=True, **kw)
     pert = workloads.perturbation(gm.n_unique, 1e-2, seed=2)
-    st = sem.sem_rbc_create(gm, 1e7, 1.0, 2e-3, tol=1e-10, T_pert=torch.from_numpy(pert).cuda(), extrapolate=True)
+    st = sem.sem_rbc_create(gm, 1e7, 1.0, 2e-3, tol=1e-10, T_pert=torch.from_numpy(pert).cuda(), extrapolate=order)
     for _ in range(3):
         sem.sem_bdf_ext_step(st)
     buf = sem.sem_rbc_save_state(st)
     for _ in range(2):
         sem.sem_bdf_ext_step(st)
     ref = fields(st)
-    st2 = sem.sem_rbc_create(gm, 1e7, 1.0, 2e-3, tol=1e-10, extrapolate=True)
+    path = str(tmp_path / "rbc.chk")
+    sem.sem_rbc_save(st, path)
+    other = sem.sem_rbc_create(gm, 1e7, 1.0, 2e-3, tol=1e-10, extrapolate=3 - order)
+    with pytest.raises(sem.SemError):
+        sem.sem_rbc_load(other, path)
+    other.destroy()
+    st2 = sem.sem_rbc_create(gm, 1e7, 1.0, 2e-3, tol=1e-10, extrapolate=order)
     sem.sem_rbc_load_state(st2, buf)
     for _ in range(2):
         g = sem.sem_bdf_ext_step(st2)
@@ -146,6 +156,10 @@ def test_rbc_mesh_requirements():
     gm = sem.sem_mesh_create_box((2, 2, 2), 3)  # walls everywhere but no periodicity: allowed
     st = sem.sem_rbc_create(gm, 1e6, 1.0, 1e-3)
     st.destroy()
+    for bad in (-1, 3):  # extrapolation orders other than 0, 1, 2
+        with pytest.raises(sem.SemError) as ei:
+            sem.sem_rbc_create(gm, 1e6, 1.0, 1e-3, extrapolate=bad)
+        assert ei.value.code == sem.SEM_ERR_INVALID_ARG
     gm.destroy()
     gm = sem.sem_mesh_create_box((2, 2, 2), 3, periodic=(1, 1, 1), dirichlet=(0,) * 6)
     with pytest.raises(sem.SemError) as ei:
